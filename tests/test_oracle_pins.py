@@ -1,0 +1,484 @@
+"""Pins for the FP64 oracle: checks against what the paper and the mathematics fix,
+not against the oracle itself.
+
+Field: exact discrete harmonics (polynomials and the separable discrete
+sine-sinh), the annulus log-radial solution at second order, brute-force dense
+solves on small grids, the maximum principle, the random-walk reading by Monte
+Carlo, symmetry, goal-free components, and the a-posteriori bound through the
+exit time.  Raster: hand cases with counts of lattice points, the closed ring
+boundary, the ring count of the 512x512 benchmark scene, and the closed forms
+of the elliptic law (Eqs. 14-15).  Kalman filter: ordinary least squares under
+a diffuse prior with Q = 0 (Eqs. 9-13) and the steady state of the discrete
+algebraic Riccati equation.  Path: Eq. 3 descent invariants and rubber-band
+energy monotonicity.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# field: exact discrete harmonic functions
+# ---------------------------------------------------------------------------
+
+def _rect_problem(nx, ny, f):
+    """Dirichlet problem on a rectangle: border fixed at f, interior free."""
+    jj, ii = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    exact = f(ii, jj)
+    fixed = np.zeros((ny, nx), np.uint8)
+    fixed[0, :] = fixed[-1, :] = fixed[:, 0] = fixed[:, -1] = 1
+    u0 = np.where(fixed == 1, exact, 0.0)
+    return u0, fixed, exact
+
+
+POLYS = {
+    "linear": lambda x, y: 0.3 + 0.02 * x - 0.05 * y,
+    "xy": lambda x, y: (x - 9.0) * (y - 7.0) / 100.0,
+    "x2-y2": lambda x, y: ((x - 9.0) ** 2 - (y - 7.0) ** 2) / 100.0,
+    "x3-3xy2": lambda x, y: ((x - 9.0) ** 3 - 3.0 * (x - 9.0) * (y - 7.0) ** 2) / 1000.0,
+}
+
+
+@pytest.mark.parametrize("name", sorted(POLYS))
+def test_polynomials_are_fixed_points_of_all_solvers(name):
+    u0, fixed, exact = _rect_problem(21, 17, POLYS[name])
+    scale = np.abs(exact).max()
+    u, _, r, st = oracle.cg(u0, fixed, tol=1e-15 * scale)
+    assert st == oracle.OK
+    assert np.abs(u - exact).max() <= 1e-12 * scale
+    uj, _, _, st = oracle.jacobi(u0, fixed, tol=1e-13 * scale)
+    assert st == oracle.OK and np.abs(uj - exact).max() <= 1e-10 * scale
+    ug, _, _, st = oracle.gauss_seidel(u0, fixed, tol=1e-13 * scale)
+    assert st == oracle.OK and np.abs(ug - exact).max() <= 1e-10 * scale
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_discrete_sine_sinh(k):
+    N, M = 24, 30   # i = 0..N, j = 0..M
+    mu = math.acosh(2.0 - math.cos(k * math.pi / N))
+
+    def f(i, j):
+        return np.sin(k * np.pi * i / N) * np.sinh(mu * j) / math.sinh(mu * M)
+
+    u0, fixed, exact = _rect_problem(N + 1, M + 1, f)
+    u, _, _, st = oracle.cg(u0, fixed, tol=1e-15)
+    assert st == oracle.OK
+    assert np.abs(u - exact).max() <= 1e-13
+
+
+def test_continuous_sine_matches_to_second_order():
+    errs = []
+    for n in (17, 33, 65):
+        h = 1.0 / (n - 1)
+
+        def f(i, j):
+            x, y = i * h, j * h
+            return np.sin(np.pi * x) * np.sinh(np.pi * y) / math.sinh(math.pi)
+
+        u0, fixed, exact = _rect_problem(n, n, f)
+        u, _, _, _ = oracle.cg(u0, fixed, tol=1e-14)
+        errs.append(np.abs(u - exact).max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 < o < 2.2 for o in orders), (errs, orders)
+
+
+def _annulus(n, a=0.25, b=0.9):
+    h = 2.0 / (n - 1)
+    jj, ii = np.mgrid[0:n, 0:n].astype(np.float64)
+    x, y = -1.0 + ii * h, -1.0 + jj * h
+    r = np.hypot(x, y)
+    exact = np.log(np.maximum(r, 1e-300) / a) / math.log(b / a)
+    fixed = ((r <= a) | (r >= b)).astype(np.uint8)
+    fixed[0, :] = fixed[-1, :] = fixed[:, 0] = fixed[:, -1] = 1
+    u0 = np.where(fixed == 1, exact, 0.5)
+    return u0, fixed, exact
+
+
+def test_annulus_log_radial_second_order():
+    errs = []
+    for n in (32, 64, 128, 256):
+        u0, fixed, exact = _annulus(n)
+        u, _, _, st = oracle.cg(u0, fixed, tol=1e-13)
+        assert st == oracle.OK
+        free = fixed == 0
+        errs.append(np.abs(u - exact)[free].max())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    # staircase boundary: the order fluctuates around 2 but the error must fall ~4x
+    assert np.mean(orders) > 1.6, (errs, orders)
+    assert errs[-1] < 2e-3
+
+
+# ---------------------------------------------------------------------------
+# field: brute-force dense solve and invariants
+# ---------------------------------------------------------------------------
+
+def _random_small(seed, nx=16, ny=16, p=0.2):
+    rng = np.random.default_rng(seed)
+    occ = (rng.random((ny, nx)) < p).astype(np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+    free = np.argwhere(occ == 0)
+    gy, gx = free[rng.integers(len(free))]
+    return occ, (int(gx), int(gy))
+
+
+def _dense_solve(occ, goal):
+    """Assemble (I - J) on free cells with numpy and solve it directly."""
+    u0, fixed = oracle.dirichlet_from_occ(occ, goal)
+    ny, nx = occ.shape
+    idx = -np.ones((ny, nx), np.int64)
+    free = np.argwhere(fixed == 0)
+    for n, (j, i) in enumerate(free):
+        idx[j, i] = n
+    A = np.eye(len(free))
+    b = np.zeros(len(free))
+    for n, (j, i) in enumerate(free):
+        for dj, di in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+            jj, ii = j + dj, i + di
+            if fixed[jj, ii]:
+                b[n] += 0.25 * u0[jj, ii]
+            else:
+                A[n, idx[jj, ii]] -= 0.25
+    x = np.linalg.solve(A, b)
+    u = u0.copy()
+    u[fixed == 0] = x
+    return u, fixed
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_brute_force_dense_solve(seed):
+    occ, goal = _random_small(seed, 16, 13 + seed % 3)
+    ref, fixed = _dense_solve(occ, goal)
+    u0, _ = oracle.dirichlet_from_occ(occ, goal)
+    u, _, _, st = oracle.cg(u0, fixed, tol=1e-15)
+    assert st == oracle.OK and np.abs(u - ref).max() <= 1e-14
+    uj, _, _, st = oracle.jacobi(u0, fixed, tol=1e-15)
+    assert st == oracle.OK and np.abs(uj - ref).max() <= 1e-12
+    ug, _, _, st = oracle.gauss_seidel(u0, fixed, tol=1e-15)
+    assert st == oracle.OK and np.abs(ug - ref).max() <= 1e-12
+
+
+def test_maximum_principle_and_no_interior_extrema():
+    sc = scenes.static_occupancy(77, 48, 6, 0.15, start=(3, 3), goal=(44, 44))
+    occ, _, _ = oracle.build_grid(sc)
+    u, fixed = oracle.solve_field(occ, sc.goal, tol=1e-15)
+    assert u.min() >= 0.0 and u.max() <= 1.0
+    from scipy import ndimage
+    lab, _ = ndimage.label(fixed == 0)
+    gx, gy = sc.goal
+    # the goal's component: free cells adjacent to the goal
+    comp = {lab[gy + dy, gx + dx] for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1))} - {0}
+    ny, nx = u.shape
+    checked = 0
+    for j in range(1, ny - 1):
+        for i in range(1, nx - 1):
+            if fixed[j, i] or lab[j, i] not in comp or u[j, i] < 1e-9:
+                continue
+            nb = max(u[j, i + 1], u[j, i - 1], u[j + 1, i], u[j - 1, i])
+            assert nb > u[j, i]
+            checked += 1
+    assert checked > 500
+
+
+def test_component_without_goal_is_zero():
+    n = 32
+    occ = np.zeros((n, n), np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+    occ[8:20, 8] = occ[8:20, 19] = occ[8, 8:20] = occ[19, 8:20] = 1   # closed box
+    u, fixed = oracle.solve_field(occ, (26, 26), tol=1e-15)
+    assert np.abs(u[9:19, 9:19]).max() <= 1e-14
+    assert u[25, 25] > 0.1
+
+
+def test_transpose_and_mirror_symmetry():
+    occ, goal = _random_small(11, 24, 24, 0.15)
+    u, _ = oracle.solve_field(occ, goal, tol=1e-15)
+    ut, _ = oracle.solve_field(np.ascontiguousarray(occ.T), (goal[1], goal[0]), tol=1e-15)
+    assert np.abs(u.T - ut).max() <= 1e-13
+    um, _ = oracle.solve_field(np.ascontiguousarray(occ[:, ::-1]), (23 - goal[0], goal[1]), tol=1e-15)
+    assert np.abs(u[:, ::-1] - um).max() <= 1e-13
+
+
+def test_random_walk_monte_carlo():
+    """u(c) = P(a simple random walk from c reaches the goal before any obstacle)."""
+    occ, goal = _random_small(3, 8, 8, 0.1)
+    u, fixed = oracle.solve_field(occ, goal, tol=1e-15)
+    rng = np.random.default_rng(12345)
+    free = np.argwhere(fixed == 0)
+    steps = np.array([(1, 0), (-1, 0), (0, 1), (0, -1)])
+    W = 40000
+    for (j, i) in free[:: max(1, len(free) // 6)]:
+        pos = np.tile([i, j], (W, 1))
+        alive = np.ones(W, bool)
+        hit = np.zeros(W, bool)
+        for _ in range(4000):
+            if not alive.any():
+                break
+            pos[alive] += steps[rng.integers(0, 4, alive.sum())]
+            at_fixed = fixed[pos[:, 1], pos[:, 0]] == 1
+            newly = alive & at_fixed
+            hit |= newly & (pos[:, 0] == goal[0]) & (pos[:, 1] == goal[1])
+            alive &= ~at_fixed
+        p = hit.mean()
+        sd = math.sqrt(max(u[j, i] * (1 - u[j, i]), 1e-12) / W)
+        assert abs(p - u[j, i]) <= 3.5 * sd + 1e-4, (i, j, p, u[j, i])
+
+
+def test_a_posteriori_bound_through_exit_time():
+    sc = scenes.static128()
+    occ, _, _ = oracle.build_grid(sc)
+    ustar, fixed = oracle.solve_field(occ, sc.goal, tol=1e-14)
+    tau = oracle.exit_time(fixed)
+    assert tau.min() >= 0.0
+    u0, _ = oracle.dirichlet_from_occ(occ, sc.goal)
+    for sweeps in (50, 400, 2000):
+        uj, _, r, _ = oracle.jacobi(u0, fixed, tol=0.0, max_sweeps=sweeps)
+        err = np.abs(uj - ustar).max()
+        assert err <= tau.max() * r * (1 + 1e-9) + 1e-13
+        assert err >= r          # an error of at least one update size remains
+
+
+def test_jacobi_gs_cg_share_the_fixed_point():
+    sc = scenes.static128()
+    occ, _, _ = oracle.build_grid(sc)
+    ustar, fixed = oracle.solve_field(occ, sc.goal, tol=1e-14)
+    u0, _ = oracle.dirichlet_from_occ(occ, sc.goal)
+    tau_max = oracle.exit_time(fixed).max()
+    uj, _, rj, _ = oracle.jacobi(u0, fixed, tol=1e-8)
+    ug, _, rg, _ = oracle.gauss_seidel(u0, fixed, tol=1e-11)
+    assert np.abs(uj - ustar).max() <= tau_max * rj
+    assert np.abs(ug - ustar).max() <= tau_max * rg
+
+
+# ---------------------------------------------------------------------------
+# raster: hand cases
+# ---------------------------------------------------------------------------
+
+def _lattice_count(r2):
+    """Number of integer points (a, b) with a^2 + b^2 <= r2."""
+    r = int(math.isqrt(int(r2)))
+    return sum(1 for a in range(-r, r + 1) for b in range(-r, r + 1) if a * a + b * b <= r2)
+
+
+def _one_track(x, y, vx, vy, radius, P=None):
+    T = np.zeros((1, 21))
+    T[0, :4] = (x, y, vx, vy)
+    if P is not None:
+        T[0, 4:20] = np.asarray(P, float).reshape(16)
+    T[0, 20] = radius
+    return T
+
+
+def test_raster_stationary_disk_is_gauss_circle():
+    # 0.1 m cells; obstacle centred on cell (30, 30) with rho = 0.2 m = 2 cells
+    sc = scenes.Scene("hand", 0, 64, 64, 0.1, static_occ=np.zeros((64, 64), np.uint8))
+    sc.robot = np.array([0.55, 0.55, 1.0, 0.0, 1.0])
+    law = scenes.RingLaw(r0=0.5, growth=1.5, q_accel=0.0, kappa=2.0, d_safe=0.05)
+    T = _one_track(3.05, 3.05, 0.0, 0.0, 0.15)
+    occ, ring, J = oracle.build_grid(sc, law=law, tracks=T)
+    dyn = np.argwhere(occ == 2)
+    assert len(dyn) == _lattice_count(4) == 13
+    assert set(map(tuple, dyn - [30, 30])) == {(a, b) for a in range(-2, 3) for b in range(-2, 3)
+                                                if a * a + b * b <= 4}
+
+
+def test_raster_border_and_static_priority():
+    sc = scenes.Scene("hand", 0, 20, 10, 0.1, static_occ=np.zeros((10, 20), np.uint8))
+    sc.static_occ[4, 5] = 1
+    sc.static_occ[0, 3] = 1          # static on the border stays border
+    sc.robot = np.array([0.55, 0.55, 1.0, 0.0, 1.0])
+    T = _one_track(0.55, 0.45, 0.0, 0.0, 0.3)   # disk over the border corner and cell (5, 4)?
+    occ, _, _ = oracle.build_grid(sc, law=scenes.RingLaw(kappa=0.0, d_safe=0.0, q_accel=0.0), tracks=T)
+    assert (occ[0, :] == 3).all() and (occ[-1, :] == 3).all()
+    assert (occ[:, 0] == 3).all() and (occ[:, -1] == 3).all()
+    assert occ[4, 5] == 1
+    assert set(np.unique(occ)) <= {0, 1, 2, 3}
+
+
+def test_ring_boundary_is_closed_and_rings_nest():
+    # robot at the centre of cell (50, 50); 0.1 m cells; R = 1, 2, 4, 8 m (10, 20, 40, 80 cells)
+    sc = scenes.Scene("hand", 0, 101, 101, 0.1, static_occ=np.zeros((101, 101), np.uint8))
+    sc.robot = np.array([5.05, 5.05, 1.0, 0.0, 1.0])
+    law = scenes.RingLaw(r0=1.0, growth=2.0, n_rings=4)
+    _, ring, J = oracle.build_grid(sc, law=law, tracks=np.zeros((0, 21)))
+    assert J == 4
+    assert ring[50, 60] == 0 and ring[50, 61] == 1      # exactly 10 cells: inner ring
+    assert ring[50, 70] == 1 and ring[50, 71] == 2
+    assert ring[56, 58] == 0                            # 6^2 + 8^2 = 10^2, on the boundary
+    assert ring[50, 100] == 3 and ring[0, 0] == 3       # beyond the last ring: last ring
+
+
+def test_ring_count_of_512_scene():
+    R, t = oracle.ring_table(scenes.RingLaw(), 512, 512, 0.05, 0.75)
+    with open(os.path.join(GOLDEN, "ring_table_512.json")) as f:
+        g = json.load(f)
+    assert len(R) == g["J"]
+    assert R[-1] >= g["diagonal_m"] > R[-2]
+    assert abs(R[-1] - g["R_last_m"]) < 0.05
+    assert t[0] == 0.0 and abs(t[1] - 0.5 / 0.75) < 1e-15
+
+
+def test_arrival_time_moves_the_disk_into_the_right_ring():
+    # robot at cell (50,50) centre, v = 1 m/s, rings 1, 2, 4, 8 m -> t = 0, 1, 2, 4 s.
+    # An obstacle 6 m ahead closing at 1 m/s is predicted 4 m ahead at t_2 = 2 s: the
+    # disk (rho = 0.25 m = 2.5 cells) is marked only where it overlaps ring 2.
+    sc = scenes.Scene("hand", 0, 161, 101, 0.1, static_occ=np.zeros((101, 161), np.uint8))
+    sc.robot = np.array([5.05, 5.05, 1.0, 0.0, 1.0])
+    law = scenes.RingLaw(r0=1.0, growth=2.0, n_rings=4, q_accel=0.0, kappa=0.0, d_safe=0.05)
+    T = _one_track(5.05 + 6.0, 5.05, -1.0, 0.0, 0.2)
+    occ, ring, _ = oracle.build_grid(sc, law=law, tracks=T)
+    got = {(int(i) - 50, int(j) - 50) for j, i in np.argwhere(occ == 2)}
+    want = {(40 + a, b) for a in range(-3, 4) for b in range(-3, 4)
+            if a * a + b * b <= 6.25 and (40 + a) ** 2 + b * b <= 1600}
+    assert got == want and len(want) == 9
+
+
+def _elliptic_ring_radius(d_ahead, d_side):
+    """Closed form of Eqs. 14-15 with r_x = 4 r_y and centre 0.9 r_x ahead."""
+    u, v = d_ahead, d_side
+    return (-1.8 * u + math.sqrt(4 * u * u + 12.16 * v * v)) / 0.38
+
+
+def test_elliptic_closed_forms():
+    with open(os.path.join(GOLDEN, "elliptic_ring.json")) as f:
+        g = json.load(f)
+    assert abs(_elliptic_ring_radius(1.0, 0.0) - g["ahead_factor"]) < 1e-12
+    assert abs(_elliptic_ring_radius(-1.0, 0.0) - g["behind_factor"]) < 1e-12
+    assert abs(_elliptic_ring_radius(0.0, 1.0) - g["abeam_factor"]) < 1e-9
+    # oracle's elliptic rings against the closed form, for cells straight ahead,
+    # behind and abeam of a robot heading +x (rings 1, 2, 4, ... cells x 0.1 m)
+    sc = scenes.Scene("hand", 0, 301, 301, 0.1, static_occ=np.zeros((301, 301), np.uint8))
+    sc.robot = np.array([15.05, 15.05, 1.0, 0.0, 1.0])
+    law = scenes.RingLaw(kind=scenes.RING_ELLIPTIC, r0=0.1, growth=2.0, n_rings=12)
+    R, _ = oracle.ring_table(law, 301, 301, 0.1, 1.0)
+    _, ring, _ = oracle.build_grid(sc, law=law, tracks=np.zeros((0, 21)))
+    for dx, dy in ((37, 0), (-3, 0), (-11, 0), (0, 2), (0, 5), (123, 0), (0, 13)):
+        r_needed = _elliptic_ring_radius(dx * 0.1, dy * 0.1)
+        want = next((j for j in range(len(R)) if R[j] >= r_needed * (1 + 1e-12)), len(R) - 1)
+        assert ring[150 + dy, 150 + dx] == want, (dx, dy, r_needed)
+
+
+def test_per_obstacle_marking_uses_own_ring():
+    sc = scenes.Scene("hand", 0, 161, 101, 0.1, static_occ=np.zeros((101, 161), np.uint8))
+    sc.robot = np.array([5.05, 5.05, 1.0, 0.0, 1.0])
+    law = scenes.RingLaw(r0=1.0, growth=2.0, n_rings=4, q_accel=0.0, kappa=0.0, d_safe=0.05,
+                         mark=scenes.MARK_PER_OBSTACLE)
+    # 6 m ahead: own ring 3 (4, 8] -> t_3 = 4 s -> predicted 2 m ahead, marked in full
+    T = _one_track(5.05 + 6.0, 5.05, -1.0, 0.0, 0.2)
+    occ, _, _ = oracle.build_grid(sc, law=law, tracks=T)
+    got = {(int(i) - 50, int(j) - 50) for j, i in np.argwhere(occ == 2)}
+    want = {(20 + a, b) for a in range(-3, 4) for b in range(-3, 4) if a * a + b * b <= 6.25}
+    assert got == want and len(want) == 21
+
+
+def test_inflation_grows_with_covariance_and_time():
+    sc = scenes.Scene("hand", 0, 161, 161, 0.1, static_occ=np.zeros((161, 161), np.uint8))
+    law = scenes.RingLaw(q_accel=0.0, kappa=2.0, d_safe=0.0)
+    P = np.diag([0.01, 0.01, 0.04, 0.04])
+    _, _, r0q = oracle.predict_disk(_one_track(0, 0, 0, 0, 0.2, P)[0], 0.0, law, 0.1)
+    _, _, r1q = oracle.predict_disk(_one_track(0, 0, 0, 0, 0.2, P)[0], 1.0, law, 0.1)
+    # sigma(0) = 0.1 -> rho = 0.4 m = 4 cells; sigma(1) = sqrt(0.01 + 0.04) -> rho = 0.2 + 2 sqrt(0.05)
+    assert r0q == 4 * 256
+    assert r1q == round((0.2 + 2 * math.sqrt(0.05)) / 0.1 * 256)
+
+
+# ---------------------------------------------------------------------------
+# Kalman filter
+# ---------------------------------------------------------------------------
+
+def test_kf_matches_least_squares_under_diffuse_prior():
+    rng = np.random.default_rng(5)
+    n, dt = 12, 0.1
+    times = dt * np.arange(n)
+    truth = np.stack([1.0 + 0.7 * times, -2.0 + 0.3 * times], 1)
+    z = truth + 0.05 * rng.standard_normal((n, 2))
+    # diffuse prior P0 = 1e6 I: its pull on the posterior is O(r^2 / 1e6) ~ 1e-9,
+    # while the (I - KH) P form of Eq. 12 loses ~6 digits of P to cancellation
+    T = oracle.kf_init(z[0:1], np.array([0.2]), r_meas=0.05, p_vel=1e6)
+    T[0, 4:20] = np.diag([1e6, 1e6, 1e6, 1e6]).reshape(16)
+    T[0, 0:2] = 0.0
+    T = oracle.kf_step(T, z[0:1], dt=0.0, q=0.0, r=0.05)
+    for k in range(1, n):
+        T = oracle.kf_step(T, z[k:k + 1], dt=dt, q=0.0, r=0.05)
+    for ax in range(2):
+        X = np.stack([np.ones(n), times - times[-1]], 1)
+        coef, *_ = np.linalg.lstsq(X, z[:, ax], rcond=None)
+        assert abs(T[0, ax] - coef[0]) < 1e-6
+        assert abs(T[0, 2 + ax] - coef[1]) < 1e-5
+
+
+def test_kf_covariance_reaches_riccati_steady_state():
+    from scipy.linalg import solve_discrete_are
+    dt, q, r = 0.1, 0.01, 0.05
+    T = oracle.kf_init(np.zeros((1, 2)), np.array([0.2]), r_meas=r, p_vel=1.0)
+    for _ in range(2000):
+        T = oracle.kf_step(T, np.zeros((1, 2)), dt=dt, q=q, r=r)
+    P_post = T[0, 4:20].reshape(4, 4)
+    assert np.allclose(P_post, P_post.T, atol=1e-15)
+    assert np.linalg.eigvalsh(P_post).min() > 0
+    A = np.array([[1, 0, dt, 0], [0, 1, 0, dt], [0, 0, 1, 0], [0, 0, 0, 1.0]])
+    H = np.hstack([np.eye(2), np.zeros((2, 2))])
+    d3, d2 = dt ** 3 / 3, dt ** 2 / 2
+    Q = q * np.array([[d3, 0, d2, 0], [0, d3, 0, d2], [d2, 0, dt, 0], [0, d2, 0, dt]])
+    P_prior = solve_discrete_are(A.T, H.T, Q, r * r * np.eye(2))
+    # the filter's prior for the next step is A P_post A^T + Q
+    assert np.allclose(A @ P_post @ A.T + Q, P_prior, rtol=1e-8, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# path
+# ---------------------------------------------------------------------------
+
+def test_descent_invariants_on_static_scene():
+    sc = scenes.static128()
+    occ, _, _ = oracle.build_grid(sc)
+    u, fixed = oracle.solve_field(occ, sc.goal, tol=1e-14)
+    st, path = oracle.descent(u, fixed, sc.start, sc.goal)
+    assert st == oracle.OK
+    assert tuple(path[0]) == sc.start and tuple(path[-1]) == sc.goal
+    steps = np.abs(np.diff(path, axis=0)).sum(1)
+    assert (steps == 1).all()
+    vals = u[path[:, 1], path[:, 0]]
+    assert (np.diff(vals) > 0).all()
+    assert (occ[path[:-1, 1], path[:-1, 0]] == 0).all()
+
+
+def test_rubber_band_energy_non_increasing_and_valid():
+    sc = scenes.static128()
+    occ, _, _ = oracle.build_grid(sc)
+    u, fixed = oracle.solve_field(occ, sc.goal, tol=1e-14)
+    st, path = oracle.descent(u, fixed, sc.start, sc.goal)
+    # total energy E = sum_i w/u(p_i) + (k/2) sum_i |p_{i+1} - p_i|^2 over the chain
+    def E(p):
+        pot = (1e-3 / u[p[1:-1, 1], p[1:-1, 0]]).sum()
+        d = np.diff(p.astype(np.float64), axis=0)
+        return pot + 0.5 * (d * d).sum()
+    e_prev = E(path)
+    for _ in range(30):
+        path, _ = oracle.rubber_band(u, fixed, sc.goal, path, iters=1)
+        e = E(path)
+        assert e <= e_prev * (1 + 1e-12)
+        e_prev = e
+        assert (np.abs(np.diff(path, axis=0)).max(1) == 1).all()    # 8-connected, no repeats
+        inner = path[:-1]
+        assert (fixed[inner[:, 1], inner[:, 0]] == 0).all()
+    assert tuple(path[0]) == sc.start and tuple(path[-1]) == sc.goal
+
+
+def test_enclosed_goal_has_no_path_and_blocked_start():
+    n = 40
+    occ = np.zeros((n, n), np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+    occ[10:20, 10] = occ[10:20, 19] = occ[10, 10:20] = occ[19, 10:20] = 1
+    u, fixed = oracle.solve_field(occ, (15, 15), tol=1e-15)
+    st, _ = oracle.descent(u, fixed, (30, 30), (15, 15))
+    assert st == oracle.NO_PATH
+    st, _ = oracle.descent(u, fixed, (10, 12), (15, 15))
+    assert st == oracle.ESTART
