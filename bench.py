@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark: converged harmonic-field solves per second on the 2048x2048 scene.
+
+One step = one pass of the planner's hot path on one synthetic 2048x2048
+static scene (2000 rectangles and disks at 30 % occupancy): time-warped raster
+(tw_build_grid), relaxation from the cold start u = 0.5 to the residual
+r_inf <= 1e-6 (hp_relax), and the Eq. 3 path with rubber band (plan_path).
+
+Prints one JSON line (rank 0).  `value` is device-resident throughput (inputs
+already in HBM); `e2e` repeats the step through the same C ABI with host
+buffers (pinned H2D of the occupancy, D2H of the field and the path) inside
+the timed region.  Multi-GPU (torchrun): every rank solves its own scene, no
+collective touches the data path; only a barrier and a max-reduce of the
+elapsed time are exchanged.  `--impl reference` times the FP64 CPU oracle on
+the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "converged-field solves/s at 2048^2, resid<=1e-6 (plus cell-updates/s vs plain FP32)"
+UNIT = "solves/s"
+WORKLOAD = ("static2048: 2048x2048 grid, 5 cm cells, 2000 rectangles+disks at 30% occupancy, "
+            "goal (2027,2027), robot (20,20); step = raster + cold-start relaxation to r_inf<=1e-6 "
+            "+ Eq.3 path with 100 rubber-band sweeps")
+STORAGE_BYTES = 4           # FP32 field
+MASK_BYTES = 1.0 / 8.0      # one Dirichlet bit per cell
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+# DRAM traffic of the dominant kernel from one ncu capture, valid only while
+# the kernel source is unchanged (sha256 of the file that holds it).
+TRAFFIC = {}
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_scene(rank: int):
+    return scenes.static2048(seed=1002 + 100 * rank)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_twgrid(args, rank, world, dist):
+    import torch
+
+    import paper_1903_07441_gb300 as tw
+
+    dev = torch.device("cuda", _env_int("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    tw.load()
+    sc = make_scene(rank)
+    grid = tw.make_grid(sc.nx, sc.ny, sc.cell, sc.ox, sc.oy)
+    static_h = torch.from_numpy(sc.static_occ).pin_memory()
+    static_d = static_h.to(dev)
+    occ = torch.empty((sc.ny, sc.nx), dtype=torch.uint8, device=dev)
+    u = torch.empty((sc.ny, sc.nx), dtype=torch.float32, device=dev)
+    u_h = torch.empty((sc.ny, sc.nx), dtype=torch.float32).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    method = {"rbsor": tw.HP_RBSOR, "jacobi": tw.HP_JACOBI, "mixed": tw.HP_MIXED}[args.method]
+    params = tw.Params(method=method, tol=args.tol, max_sweeps=args.max_sweeps, flags=tw.HP_TIMING,
+                       tblock=args.tblock, storage={"f16": 1, "bf16": 2, "f32": 0}[args.storage])
+    max_len = 4 * (sc.nx + sc.ny) * 4
+    stats_log = []
+
+    def step(static_src):
+        tw.tw_build_grid(grid, sc.robot, sc.tracks, sc.law, static_occ=static_src, occ=occ)
+        _, st = tw.hp_relax(grid, occ, sc.goal, field=u, params=params)
+        pst, path = tw.plan_path(grid, u, occ, sc.start, sc.goal, rubber_iters=100, max_len=max_len)
+        stats_log.append((st, pst, len(path)))
+        return path
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(static_d)
+    stats_log.clear()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = tw.launch_count()
+    barrier()
+    with ClockSampler(dev.index) as clk:
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            if i:
+                flush.zero_()
+            step(static_d)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    launches = tw.launch_count() - launches0   # library kernels only (not the L2-flush memsets)
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    elapsed = max(dev_s, 1e-12)
+    if dist is not None:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    sweeps = [s["sweeps"] for s, _, _ in stats_log]
+    resid = [s["resid_inf"] for s, _, _ in stats_log]
+    sweep_ms = sum(s["sweep_ms"] for s, _, _ in stats_log)
+    sweep_launches = sum(s["sweep_launches"] for s, _, _ in stats_log)
+    status = [s["status"] for s, _, _ in stats_log]
+    path_status = [p for _, p, _ in stats_log]
+    cells = sc.nx * sc.ny
+    value = args.steps * world / elapsed
+    cups = sum(sweeps) * cells * world / elapsed
+
+    # ---- roofline of the dominant kernel (sweep), live CUDA-event launch times
+    hbm, peak_kind = peaks()
+    avg_launch_s = sweep_ms / 1e3 / max(sweep_launches, 1)
+    sweeps_per_launch = sum(sweeps) / max(sweep_launches, 1)
+    bytes_per_launch = cells * (2 * STORAGE_BYTES + MASK_BYTES) * min(1.0, sweeps_per_launch)
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    src = os.path.join(ROOT, "paper_1903_07441_gb300", "csrc", "hp_sweeps.cu")
+    src_hash = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    traffic = TRAFFIC.get(src_hash)
+    roofline = {"bound": "hbm", "kernel": "red-black SOR sweep (hp_sweeps.cu)", "achieved": achieved,
+                "peak": hbm, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_us": avg_launch_s * 1e6, "sweeps_per_launch": sweeps_per_launch,
+                "effective_cell_updates_per_s": cells * sweeps_per_launch / avg_launch_s}
+
+    # ---- end to end through the C ABI with host buffers
+    stats_log.clear()
+    barrier()
+    e0 = time.perf_counter()
+    ev0.record(stream)
+    h2d = d2h = 0
+    for i in range(args.steps):
+        if i:
+            flush.zero_()
+        static_d.copy_(static_h, non_blocking=True)
+        h2d += static_h.numel() + sc.tracks.nbytes
+        path = step(static_d)
+        u_h.copy_(u, non_blocking=True)
+        d2h += u_h.numel() * 4 + path.nbytes
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e_el = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        t = torch.tensor([e_el], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_el = float(t.item())
+    e2e = {"value": args.steps * world / e_el, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+           "d2h_bytes_per_step": d2h // args.steps, "wall_s": time.perf_counter() - e0}
+
+    # ---- plain FP32 Jacobi on the same scene (the comparison form)
+    plain = None
+    if not args.no_plain and rank == 0:
+        pp = tw.Params(method=tw.HP_JACOBI, tol=args.tol, max_sweeps=args.plain_max_sweeps, flags=tw.HP_TIMING)
+        tw.tw_build_grid(grid, sc.robot, sc.tracks, sc.law, static_occ=static_d, occ=occ)
+        torch.cuda.synchronize()
+        p0 = time.perf_counter()
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        _, pst = tw.hp_relax(grid, occ, sc.goal, field=u, params=pp)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        pt = e_a.elapsed_time(e_b) / 1e3
+        converged = pst["status"] == tw.TW_OK
+        plain = {"method": "FP32 Jacobi (Eq. 1), 16x16 blocks, one sweep per launch", "sweeps": pst["sweeps"],
+                 "converged": converged, "resid_inf": pst["resid_inf"], "seconds": pt,
+                 "solves_per_s": (1.0 / pt) if converged else None,
+                 "cell_updates_per_s": pst["sweeps"] * cells / pt,
+                 "speedup_time_to_solution": (pt / (elapsed / args.steps)) if converged else None,
+                 "note": None if converged else f"not converged within {args.plain_max_sweeps} sweeps; "
+                                                 "time-to-solution is a lower bound",
+                 "wall_s": time.perf_counter() - p0}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "method": args.method, "tol": args.tol,
+                      "parallelism": f"replicas x{world} (one scene per GPU, no collective)",
+                      "l2": "256 MiB memset between timed steps (inside the timed region); the 33.5 MB "
+                            "field pair itself is L2-resident within a solve"},
+           "cell_updates_per_s": cups, "sweeps_per_solve": statistics.mean(sweeps) if sweeps else None,
+           "resid_inf_max": max(resid) if resid else None, "relax_status": sorted(set(status)),
+           "path_status": sorted(set(path_status)), "path_len": [n for _, _, n in stats_log][:1],
+           "omega": stats_log[0][0]["omega"] if stats_log else None,
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain,
+           "wall_s": wall, "clocks": clk.summary()}
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step(sc, max_iters=None):
+    """The oracle's version of one step: brute-force raster, CG to tol, descent + band.
+    Returns (seconds, cg_iterations, residual)."""
+    import oracle
+    t0 = time.perf_counter()
+    occ, _, _ = oracle.build_grid(sc)
+    u0, fixed = oracle.dirichlet_from_occ(occ, sc.goal)
+    u, iters, r, _ = oracle.cg(u0, fixed, tol=1e-6, max_iters=max_iters or 1_000_000)
+    oracle.plan_path(u, fixed, sc.start, sc.goal, rubber_iters=100)
+    return time.perf_counter() - t0, iters, r
+
+
+def cpu_baseline(sc):
+    """The oracle as it stands on one host core: one full oracle step on the same scene."""
+    import oracle
+    oracle.build()
+    t, iters, r = oracle_step(sc)
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full oracle step on the same 2048^2 scene (brute-force raster, FP64 CG to "
+                      f"r_inf<=1e-6 in {iters} iterations, descent + 100 band sweeps): {t:.1f} s"}
+
+
+def run_reference(args, rank, world, dist):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    import oracle
+    if rank != 0:
+        return None
+    oracle.build()
+    sc = make_scene(0)
+    budget = max(2.0, 150.0 / max(args.steps + args.warmup, 1))
+    # warm-up: one full solve to learn the CG iterations to tolerance
+    t_full, n_tol, _ = oracle_step(sc)
+    for _ in range(max(args.warmup - 1, 0)):
+        oracle_step(sc, max_iters=5)
+    m = max(5, min(n_tol, int(budget / (t_full / n_tol))))
+    times = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        t, iters, _ = oracle_step(sc, max_iters=m)
+        times.append(t * n_tol / iters)
+    total = time.perf_counter() - t0
+    per_solve = statistics.mean(times)
+    v = 1.0 / per_solve
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "method": "oracle: brute-force raster + FP64 CG + descent/band"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the oracle step with {m} of the {n_tol} CG iterations a "
+                                       f"full solve needs, extrapolated linearly ({total:.1f} s for "
+                                       f"{args.steps} steps)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="twgrid", choices=["twgrid", "reference"])
+    ap.add_argument("--method", default="rbsor", choices=["rbsor", "jacobi", "mixed"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--tblock", type=int, default=0)
+    ap.add_argument("--max-sweeps", type=int, default=200000)
+    ap.add_argument("--plain-max-sweeps", type=int, default=400000)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+        tdist.init_process_group(backend=backend)
+        dist = tdist
+
+    if args.impl == "reference":
+        out = run_reference(args, rank, world, dist)
+    else:
+        out = run_twgrid(args, rank, world, dist)
+        if rank == 0 and world == 1 and not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(make_scene(0))
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

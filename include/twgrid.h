@@ -1,0 +1,235 @@
+/*
+ * twgrid.h -- C ABI of the GB300 time-warped-grid planner library (libtwgrid.so).
+ *
+ * The library implements the data-parallel hot path of Farzan & DeSouza,
+ * "Path Planning in Dynamic Environments Using Time-Warped Grids and a
+ * Parallel Implementation": rasterising the time-warped occupancy grid
+ * (Sec. 3.4-3.5, Alg. 1 "Map Update") and relaxing the harmonic potential
+ * field (Sec. 3.1, Eqs. 1-2, Alg. 1 "Path Planning"), with the Eq. 3 path
+ * and the rubber band of Sec. 3.2 as consumers.  All compute runs in CUDA
+ * kernels for sm_103a; the host code validates arguments, sizes launches and
+ * reads back small results.
+ *
+ * Conventions for every call:
+ *  - Grids are row-major [ny][nx]; cell (i, j) is column i, row j.  World
+ *    coordinates are metres; cell (i, j) spans [ox + i*cell, ox + (i+1)*cell).
+ *  - "_dev" pointers are CUDA device pointers on the current device, owned by
+ *    the caller; the library never frees or retains them after a call returns.
+ *  - `workspace`/`workspace_bytes` is caller-owned device scratch of at least
+ *    the size the matching *_workspace_size() call returns, 256-byte aligned.
+ *    It may be reused between calls on the same stream.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls that return host-visible results synchronise it.
+ *  - Return value: TW_OK (0), a positive warning, or a negative error.  On an
+ *    error nothing is guaranteed about outputs.  TW_ECUDA keeps the CUDA
+ *    error, readable through tw_last_cuda_error().
+ */
+#ifndef TWGRID_H
+#define TWGRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TW_OK 0
+#define TW_NOT_CONVERGED 1     /* max_sweeps reached before tol; stats hold the residual */
+#define TW_NO_PATH 2           /* the Eq. 3 descent stalled or exceeded max_len */
+#define TW_EINVAL (-1)         /* bad argument (sizes, NaN, non-PSD covariance, ...) */
+#define TW_EGOAL_BLOCKED (-2)  /* goal cell occupied, on the border or out of range */
+#define TW_ESTART_BLOCKED (-3) /* start cell occupied */
+#define TW_ECUDA (-4)          /* a CUDA call failed */
+#define TW_EWORKSPACE (-5)     /* workspace missing, too small or misaligned */
+
+/* ---- enums --------------------------------------------------------------- */
+#define TW_RING_CIRCULAR 0     /* rings are circles about the robot (geometric radii) */
+#define TW_RING_ELLIPTIC 1     /* Eqs. 14-15: ellipses r_x = 4 r_y, centre 0.9 r_x ahead */
+#define TW_MARK_PER_CELL 0     /* a cell in ring j is tested against every obstacle at t_j */
+#define TW_MARK_PER_OBSTACLE 1 /* Alg. 1: each obstacle takes its own ring's time, one disk */
+
+/* occupancy codes written by tw_build_grid (priority border > static > dynamic) */
+#define TW_FREE 0
+#define TW_STATIC 1
+#define TW_DYNAMIC 2
+#define TW_BORDER 3
+
+/* ---- plain-data argument structs ----------------------------------------- */
+typedef struct {
+    int nx, ny;        /* cells; 3 <= nx, ny <= 65536 */
+    double cell;       /* cell side (m), > 0 */
+    double ox, oy;     /* world position of the corner of cell (0, 0) (m) */
+} tw_grid;
+
+typedef struct {
+    double x, y;       /* robot position (m) */
+    double hx, hy;     /* heading as a unit vector (no trigonometry on the exact path) */
+    double speed;      /* robot speed (m/s), > 0: ring arrival time = ring radius / speed */
+} tw_pose;
+
+/* Kalman track of one moving obstacle (Sec. 3.5): state [x, y, vx, vy] (m, m/s),
+ * covariance P (4x4 row-major), body radius (m). */
+typedef struct {
+    double x[4];
+    double P[16];
+    double radius;
+} tw_track;
+
+typedef struct {
+    int kind;          /* TW_RING_CIRCULAR or TW_RING_ELLIPTIC */
+    int mark;          /* TW_MARK_PER_CELL or TW_MARK_PER_OBSTACLE */
+    double r0;         /* first ring radius (m), > 0 */
+    double growth;     /* geometric ring growth, > 1 */
+    int n_rings;       /* 0: first J with R_{J-1} >= reach (grid diagonal; 10 x for elliptic) */
+    double q_accel;    /* white-noise acceleration PSD of Q(t) (m^2/s^3), >= 0 */
+    double kappa;      /* inflation in standard deviations, >= 0 */
+    double d_safe;     /* safety distance added to the body radius (m), >= 0 */
+    int time_outer;    /* 0: t_j = R_{j-1}/v (t_0 = 0); 1: t_j = R_j/v */
+} tw_ring_law;
+
+/* ---- time-warped grid ------------------------------------------------------
+ * tw_build_grid: Alg. 1 "Map Update" as one raster (Sec. 3.4-3.5).
+ *  1. Ring table: R_0 = r0, R_j = growth * R_{j-1}; arrival t_j (see tw_ring_law).
+ *  2. For every track and ring: constant-velocity prediction at t_j (Eqs. 9-10)
+ *     p = x + t v, P(t) = A P A^T + Q(t); sigma^2 = (Pxx(t) + Pyy(t)) / 2;
+ *     disk radius rho = (radius + d_safe) + kappa * sigma (the Gaussian marking
+ *     of Sec. 3.4 made binary).  All of it in correctly rounded FP64, then
+ *     quantised to 1/256 cell (round half to even).
+ *  3. For every cell: its ring j (smallest ring whose closed boundary contains
+ *     the cell centre; beyond the last ring: the last ring) and its code:
+ *     TW_BORDER on the outermost rows/columns, else TW_STATIC where
+ *     static_occ_dev != 0, else TW_DYNAMIC if the centre lies in a disk of its
+ *     ring (per cell) or in any obstacle's own-ring disk (per obstacle), else
+ *     TW_FREE.  The predicates are exact integer arithmetic.
+ * tracks: HOST array of n_tracks (0 allowed; copied into the workspace).
+ * static_occ_dev: device uint8 [ny][nx] or NULL.  occ_dev: device uint8
+ * [ny][nx] output.  ring_dev: device int16 [ny][nx] output or NULL.
+ * Asynchronous on `stream` (the host track array may be reused on return).
+ * Errors: TW_EINVAL (bad grid/law/pose, non-finite track, negative radius,
+ * non-PSD position-velocity block), TW_EWORKSPACE, TW_ECUDA.
+ */
+size_t tw_build_grid_workspace_size(const tw_grid *g, int n_tracks, const tw_ring_law *law);
+int tw_build_grid(const tw_grid *g, const tw_pose *robot, const tw_track *tracks, int n_tracks,
+                  const tw_ring_law *law, const uint8_t *static_occ_dev, uint8_t *occ_dev,
+                  int16_t *ring_dev, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Number of rings tw_build_grid uses for this grid, pose and law (> 0), or TW_EINVAL. */
+int tw_ring_count(const tw_grid *g, const tw_pose *robot, const tw_ring_law *law);
+
+/* ---- harmonic potential field ----------------------------------------------- */
+#define HP_JACOBI 0        /* Eq. 1, one FP32 sweep per launch: the plain comparison form */
+#define HP_RBSOR 1         /* red-black SOR, FP32, temporally blocked (same fixed point) */
+#define HP_MIXED 2         /* defect correction: FP64 residual, low-precision correction sweeps */
+
+#define HP_STORE_F32 0
+#define HP_STORE_F16 1
+#define HP_STORE_BF16 2
+
+#define HP_WARM_START 1    /* field_dev holds the initial guess (same representation as output) */
+#define HP_OUT_PHI 2       /* write phi instead of u = 1 - phi */
+#define HP_TIMING 4        /* time the sweep kernels with CUDA events on `stream` (stats.sweep_ms) */
+
+typedef struct {
+    int method;        /* HP_JACOBI, HP_RBSOR or HP_MIXED */
+    int storage;       /* HP_MIXED only: storage of the correction sweeps (HP_STORE_*) */
+    double omega;      /* SOR factor in (0, 2); 0 = adaptive estimate (HP_RBSOR, HP_MIXED) */
+    double tol;        /* stop when the residual r_inf <= tol (0: run max_sweeps) */
+    int max_sweeps;    /* hard cap on full sweeps, >= 1 */
+    int check_every;   /* residual check period in sweeps (0 = library default) */
+    int tblock;        /* temporal-blocking depth T (0 = library default) */
+    int flags;         /* HP_WARM_START | HP_OUT_PHI */
+} hp_params;
+
+typedef struct {
+    int sweeps;        /* full sweeps performed */
+    int status;        /* TW_OK or TW_NOT_CONVERGED */
+    double resid_inf;  /* FP64 residual max |(1/4) sum nbr - u| over free cells of the output */
+    double resid_l2;   /* FP64 sqrt(sum of squared residuals) */
+    double omega;      /* SOR factor used last */
+    int checks;        /* residual checks performed */
+    int sweep_launches;/* launches of the sweep kernel */
+    double sweep_ms;   /* HP_TIMING: summed CUDA-event time of the sweep launches (ms) */
+    int tblock;        /* temporal-blocking depth used (sweeps fused per launch) */
+} hp_stats;
+
+/* hp_relax: the harmonic field of the occupancy grid (Sec. 3.1).  Cells with
+ * occ != 0 and the border are Dirichlet cells at phi = 1, the goal cell is
+ * fixed at phi = 0, free cells start at phi = 0.5 (or the warm start) and
+ * converge to the discrete Laplace solution (the fixed point of Eq. 1; Eq. 2
+ * and red-black SOR share it).  The field is kept and written as
+ * u = 1 - phi (goal 1, obstacles 0), which keeps relative precision where phi
+ * is close to 1; HP_OUT_PHI writes phi instead.
+ * The residual is the 1/4-scaled infinity norm max |(1/4) sum_nbr u - u| over
+ * free cells (the size of one Eq. 1 update); stats report it recomputed in
+ * FP64 on the stored output.
+ * occ_dev: device uint8 [ny][nx].  field_dev: device float [ny][nx] (in: warm
+ * start if HP_WARM_START; out: the field).  stats: host, written on return.
+ * Synchronises `stream` (residual checks are read on the host).
+ * Errors: TW_EINVAL, TW_EGOAL_BLOCKED (goal on the border, occupied or out of
+ * range), TW_EWORKSPACE, TW_ECUDA.  Warning: TW_NOT_CONVERGED. */
+size_t hp_relax_workspace_size(int nx, int ny, const hp_params *p);
+int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *field_dev,
+             const hp_params *p, hp_stats *stats, void *workspace, size_t workspace_bytes,
+             void *stream);
+
+/* hp_relax_dirichlet: the same solver on a general Dirichlet problem: cells
+ * with fixed_dev != 0 keep their value of u_dev, the others satisfy the
+ * discrete Laplace equation.  Every border cell must be fixed.  u_dev is read
+ * as the initial guess and overwritten with the solution (no phi/u mapping). */
+int hp_relax_dirichlet(int nx, int ny, const uint8_t *fixed_dev, float *u_dev,
+                       const hp_params *p, hp_stats *stats, void *workspace,
+                       size_t workspace_bytes, void *stream);
+
+/* hp_residual: FP64 residual of a stored field against a fixed mask (device
+ * uint8, nonzero = fixed).  Results written to host r_inf / r_l2. */
+int hp_residual(int nx, int ny, const uint8_t *fixed_dev, const float *u_dev,
+                double *r_inf, double *r_l2, void *workspace, size_t workspace_bytes,
+                void *stream);
+
+/* ---- path ------------------------------------------------------------------
+ * plan_path: Eq. 3 steepest descent on u from the start cell (neighbour order
+ * +x, -x, +y, -y; the first largest u wins; a move needs a strictly larger u)
+ * until the goal, then `rubber_iters` rubber-band sweeps (Eqs. 4-6) with
+ * node energy w/u(q) + (k/2)(|q - p_prev|^2 + |q - p_next|^2): odd nodes then
+ * even nodes move to the lowest-energy free cell of their 3x3 neighbourhood
+ * that stays 8-adjacent to both path neighbours; consecutive duplicates are
+ * dropped at the end.  w = 1e-3, k = 1 unless set through plan_path_ex.
+ * u_dev: device float [ny][nx] (u = 1 - phi as written by hp_relax).
+ * occ_dev: device uint8 occupancy (nonzero = blocked, the goal is allowed).
+ * path_xy_host: host int32 [2 * max_len] output (x0, y0, x1, y1, ...).
+ * len_out: host, number of nodes written.  Synchronises `stream`.
+ * Returns TW_OK, TW_NO_PATH, TW_ESTART_BLOCKED, TW_EINVAL, TW_EWORKSPACE, TW_ECUDA. */
+size_t plan_path_workspace_size(int max_len);
+int plan_path(const tw_grid *g, const float *u_dev, const uint8_t *occ_dev, int sx, int sy,
+              int gx, int gy, int rubber_iters, int max_len, int32_t *path_xy_host,
+              int *len_out, void *workspace, size_t workspace_bytes, void *stream);
+int plan_path_ex(const tw_grid *g, const float *u_dev, const uint8_t *occ_dev, int sx, int sy,
+                 int gx, int gy, int rubber_iters, double w, double k, int max_len,
+                 int32_t *path_xy_host, int *len_out, void *workspace, size_t workspace_bytes,
+                 void *stream);
+
+/* ---- Kalman filter (host) ----------------------------------------------------
+ * kf_update: one step of the constant-velocity filter of Sec. 3.5 for n host
+ * tracks: predict by dt (Eqs. 9-10, A(dt), Q(dt) = q_accel x white-noise
+ * acceleration block), then update with the position measurement z[2o..2o+1]
+ * (Eqs. 11-13, H = [I2 0], R = r_meas^2 I2).  In place.  TW_EINVAL on bad input. */
+int kf_update(tw_track *tracks, int n, const double *z, double dt, double q_accel,
+              double r_meas);
+/* kf_init: x = [z, 0, 0], P = diag(r^2, r^2, p_vel, p_vel), radius from `radius`. */
+int kf_init(tw_track *tracks, int n, const double *z, const double *radius, double r_meas,
+            double p_vel);
+
+/* ---- diagnostics -------------------------------------------------------------- */
+const char *tw_status_string(int status);
+int tw_last_cuda_error(void);          /* last cudaError_t seen by the library */
+/* Number of CUDA kernels the library has launched in this process (host
+ * counter, incremented at every launch; for benchmarks and tests). */
+unsigned long long tw_launch_count(void);
+const char *tw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TWGRID_H */

@@ -1,0 +1,165 @@
+// Internal declarations shared by the relaxation translation units.
+#pragma once
+#include <float.h>
+
+#include "common.cuh"
+
+namespace tw {
+
+constexpr int kDefaultTBlock = 4;
+
+// Colour-split layout: red cells (x + y even) and black cells in two arrays
+// of ny rows; row y of colour c holds cells x = 2k + ((y + c) & 1), k < W2.
+// Each row has 4 padding floats on both sides (zero, never written) so the
+// +-1 neighbour of a float4 never leaves the row allocation.  Bit k of the
+// mask row is 1 for a free (updatable) cell.
+struct RBLayout {
+    int W2;            // entries per colour row (multiple of 4)
+    int W4;            // float4 per colour row
+    int S;             // row stride in floats (W2 + 8)
+    int MW;            // mask words per row
+    float *R, *B;      // current red / black planes
+    uint32_t *MR, *MB; // free-cell bits
+    float *R2, *B2;    // ping-pong planes for temporal blocking
+};
+
+struct RelaxScalars {
+    unsigned int max32;
+    unsigned int pad0;
+    unsigned long long max64;
+    double sum64;
+    double pad1[5];
+};
+
+struct MixedLayout {
+    double *x;         // FP64 master field, full layout [ny][nx]
+    void *e_r, *e_b;   // correction planes (colour-split, low precision)
+    void *e_r2, *e_b2; // ping-pong correction planes
+    void *q_r, *q_b;   // scaled right-hand side planes (colour-split, low precision)
+    float *f_r, *f_b;  // FP32 colour-split scratch for the right-hand side
+};
+
+struct RelaxLayout {
+    RelaxScalars *scal;
+    float *tmp;        // Jacobi ping-pong buffer
+    RBLayout rb;
+    MixedLayout mx;
+};
+
+RBLayout rb_layout(int nx, int ny);
+size_t carve_rb(Carver &cv, int nx, int ny, RBLayout *out, bool pingpong);
+size_t carve_mixed(Carver &cv, int nx, int ny, int storage, RelaxLayout *R);
+int relax_mixed(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, int mode,
+                const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s);
+// n full red-black SOR sweeps, T fused per launch; *launches += launches made
+int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream_t s, int *launches);
+
+// Optional CUDA-event timing of the sweep kernels (HP_TIMING).
+struct SweepTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool on = false;
+    double ms = 0.0;
+    int open(bool enable) {
+        on = enable;
+        if (!on) return TW_OK;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return TW_ECUDA;
+        return TW_OK;
+    }
+    void start(cudaStream_t s) { if (on) cudaEventRecord(a, s); }
+    void stop(cudaStream_t s) { if (on) cudaEventRecord(b, s); }
+    // after the stream has passed the stop event
+    void accumulate() {
+        if (!on) return;
+        float t = 0.0f;
+        cudaEventSynchronize(b);
+        if (cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms += t;
+    }
+    ~SweepTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
+             cudaStream_t s);
+double sor_adapt(double omega, double lambda);
+double sor_initial_omega(int nx, int ny);
+int read_max_f32(unsigned int *dmax, cudaStream_t s, float *out);
+int final_residual_full(const uint8_t *occ, int nx, int ny, int gx, int gy, const float *u,
+                        RelaxScalars *scal, cudaStream_t s, double *r_inf, double *r_l2);
+
+// NaN or overflow must never look converged: map them to +inf before a max.
+__device__ __forceinline__ float sane(float r) { return (r <= FLT_MAX) ? r : __int_as_float(0x7f800000); }
+__device__ __forceinline__ double sane(double r) { return (r <= DBL_MAX) ? r : __longlong_as_double(0x7ff0000000000000LL); }
+
+// Block-wide max of a non-negative float, one atomicMax per CTA on its bits.
+__device__ __forceinline__ void block_max_atomic(float r, unsigned int *out) {
+    __shared__ float sm[32];
+    r = sane(r);
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    int t = threadIdx.y * blockDim.x + threadIdx.x;
+    int nt = blockDim.x * blockDim.y;
+    if ((t & 31) == 0) sm[t >> 5] = r;
+    __syncthreads();
+    if (t < 32) {
+        r = (t < (nt + 31) / 32) ? sm[t] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (t == 0 && r > 0.0f) atomicMax(out, __float_as_uint(r));
+    }
+}
+
+// Block-wide FP64 max (atomicMax on the bits of a non-negative double) and sum.
+__device__ __forceinline__ void block_max_sum_f64(double r, unsigned long long *out_max, double *out_sum) {
+    __shared__ double smx[32], sms[32];
+    r = sane(r);
+    double s = r * r;
+    for (int o = 16; o > 0; o >>= 1) {
+        r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    int t = threadIdx.y * blockDim.x + threadIdx.x;
+    int nt = blockDim.x * blockDim.y;
+    if ((t & 31) == 0) { smx[t >> 5] = r; sms[t >> 5] = s; }
+    __syncthreads();
+    if (t < 32) {
+        bool in = t < (nt + 31) / 32;
+        r = in ? smx[t] : 0.0;
+        s = in ? sms[t] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        }
+        if (t == 0) {
+            if (r > 0.0) atomicMax(out_max, (unsigned long long)__double_as_longlong(r));
+            if (s != 0.0) atomicAdd(out_sum, s);
+        }
+    }
+}
+
+// Neighbours of the 4 cells k..k+3 of one colour in row y: other-colour
+// values left/right (same row, k+s-1 and k+s) and up/down (rows y-1, y+1, k).
+// nb[0] = left, nb[1] = right, nb[2] = up, nb[3] = down (component = cell).
+__device__ __forceinline__ void rb_load_neighbours(const float *V, int S, int y, int k, int s, float4 nb[4]) {
+    const float *row = V + (size_t)y * S + 4;
+    float4 mid = *reinterpret_cast<const float4 *>(row + k);
+    float extra = s ? row[k + 4] : row[k - 1];
+    nb[2] = *reinterpret_cast<const float4 *>(row - S + k);
+    nb[3] = *reinterpret_cast<const float4 *>(row + S + k);
+    if (s) {
+        nb[0] = mid;
+        nb[1] = make_float4(mid.y, mid.z, mid.w, extra);
+    } else {
+        nb[0] = make_float4(extra, mid.x, mid.y, mid.z);
+        nb[1] = mid;
+    }
+}
+
+__device__ __forceinline__ float comp(const float4 &v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// (1/4)((left + right) + (up + down)), the Eq. 1 average in a fixed order.
+__device__ __forceinline__ float rb_avg(const float4 nb[4], int e) {
+    return 0.25f * ((comp(nb[0], e) + comp(nb[1], e)) + (comp(nb[2], e) + comp(nb[3], e)));
+}
+
+}  // namespace tw

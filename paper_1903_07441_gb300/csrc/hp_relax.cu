@@ -1,0 +1,490 @@
+// Harmonic potential field relaxation (Sec. 3.1, Eqs. 1-2; Alg. 1 "Path Planning").
+//
+// The field is stored as u = 1 - phi: goal 1, obstacles and border 0.  The
+// equation is linear, so the same 5-point average applies; tiny u keeps its
+// relative precision far from the goal, where phi rounds to 1.
+//
+// Forms:
+//  * HP_JACOBI -- the plain comparison form: Eq. 1 in FP32, one sweep per
+//    launch, 16x16 thread blocks with one thread per cell (the paper's launch
+//    shape), global loads, ping-pong buffers.
+//  * HP_RBSOR  -- red-black SOR in FP32 on a colour-split layout: the red
+//    cells (x + y even) and the black cells are packed into two arrays of
+//    ny rows x ceil(nx/2) entries, so every half-sweep reads its own colour
+//    and the other colour with unit-stride 128-bit loads.  One Dirichlet bit
+//    per cell (free = 1) rides along.  Red-black is the parallel ordering of
+//    Eq. 2's Gauss-Seidel family and has the same fixed point.  T full sweeps
+//    are fused per launch in shared memory (temporal blocking).
+//  * HP_MIXED  -- defect correction (see hp_mixed.cu).
+//
+// The stopping test is the 1/4-scaled residual max |(1/4) sum_nbr u - u| over
+// free cells, reduced with warp shuffles and one atomic per CTA every K
+// sweeps; the final residual is recomputed in FP64 on the stored output.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "hp_internal.cuh"
+
+namespace tw {
+
+// ---------------------------------------------------------------------------
+// plain FP32 Jacobi (Eq. 1)
+// ---------------------------------------------------------------------------
+
+__global__ void jacobi_init_kernel(const uint8_t *__restrict__ occ, int nx, int ny, int gx, int gy,
+                                   float *__restrict__ u, int warm) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t c = (size_t)y * nx + x;
+    bool goal = (x == gx && y == gy);
+    bool fixed = goal || occ[c] != 0 || x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
+    if (gx < 0) {  // general Dirichlet: occ is the fixed mask and u already holds its values
+        return;
+    }
+    if (goal) u[c] = 1.0f;
+    else if (fixed) u[c] = 0.0f;
+    else if (!warm) u[c] = 0.5f;
+}
+
+// gx < 0: `occ` is a general fixed mask; otherwise the planner's occupancy + goal.
+__global__ void __launch_bounds__(256) jacobi_sweep_kernel(const uint8_t *__restrict__ occ, int nx, int ny,
+                                                           int gx, int gy, const float *__restrict__ src,
+                                                           float *__restrict__ dst) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    size_t c = (size_t)y * nx + x;
+    bool fixed = occ[c] != 0 || (x == gx && y == gy) || x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
+    if (fixed) {
+        dst[c] = src[c];
+        return;
+    }
+    float a = (src[c + 1] + src[c - 1]) + (src[c + nx] + src[c - nx]);
+    dst[c] = 0.25f * a;
+}
+
+// FP32 residual max of a full-layout field (warp-shuffle max, one atomic per CTA).
+__global__ void __launch_bounds__(256) full_residual_kernel(const uint8_t *__restrict__ occ, int nx, int ny,
+                                                            int gx, int gy, const float *__restrict__ u,
+                                                            unsigned int *__restrict__ out_max) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    float r = 0.0f;
+    if (x > 0 && y > 0 && x < nx - 1 && y < ny - 1) {
+        size_t c = (size_t)y * nx + x;
+        if (!(occ[c] != 0 || (x == gx && y == gy))) {
+            float a = 0.25f * ((u[c + 1] + u[c - 1]) + (u[c + nx] + u[c - nx]));
+            r = fabsf(a - u[c]);
+        }
+    }
+    block_max_atomic(r, out_max);
+}
+
+// FP64 residual (max and sum of squares) of a full-layout FP32 field.
+__global__ void __launch_bounds__(256) full_residual_f64_kernel(const uint8_t *__restrict__ occ, int nx, int ny,
+                                                                int gx, int gy, const float *__restrict__ u,
+                                                                unsigned long long *__restrict__ out_max,
+                                                                double *__restrict__ out_sum) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    double r = 0.0;
+    if (x > 0 && y > 0 && x < nx - 1 && y < ny - 1) {
+        size_t c = (size_t)y * nx + x;
+        if (!(occ[c] != 0 || (x == gx && y == gy))) {
+            double a = 0.25 * ((((double)u[c + 1] + (double)u[c - 1]) + (double)u[c + nx]) + (double)u[c - nx]);
+            r = fabs(a - (double)u[c]);
+        }
+    }
+    block_max_sum_f64(r, out_max, out_sum);
+}
+
+__global__ void to_phi_kernel(float *__restrict__ u, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) u[i] = 1.0f - u[i];
+}
+
+// ---------------------------------------------------------------------------
+// colour-split layout
+// ---------------------------------------------------------------------------
+
+// Pack: full field (or init rule) -> red/black arrays + free-cell bits.
+// Thread per (y, k); each warp covers 32 consecutive k of one row so that the
+// mask word is one ballot.  mode 0: planner (occ + goal, cold init unless warm);
+// mode 1: general Dirichlet (occ = fixed mask, values from u_in).
+__global__ void rb_pack_kernel(const uint8_t *__restrict__ occ, const float *__restrict__ u_in, int nx,
+                               int ny, int gx, int gy, int mode, int warm, RBLayout L) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    if (y >= ny) return;
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int color = 0; color < 2; color++) {
+        int x = 2 * k + ((y + color) & 1);
+        float v = 0.0f;
+        bool free_cell = false;
+        if (k < L.W2 && x < nx) {
+            size_t c = (size_t)y * nx + x;
+            bool border = x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
+            if (mode == 0) {
+                bool goal = (x == gx && y == gy);
+                bool fixed = goal || border || occ[c] != 0;
+                free_cell = !fixed;
+                v = goal ? 1.0f : (fixed ? 0.0f : (warm ? u_in[c] : 0.5f));
+            } else {
+                free_cell = !(border || occ[c] != 0);
+                v = u_in[c];
+            }
+        }
+        unsigned bits = __ballot_sync(0xffffffffu, free_cell);
+        if (k < L.W2) {
+            float *arr = color ? L.B : L.R;
+            arr[(size_t)y * L.S + 4 + k] = v;
+        }
+        if (lane == 0 && k < L.W2 + 31) {
+            uint32_t *M = color ? L.MB : L.MR;
+            int w = k >> 5;
+            if (w < L.MW) M[(size_t)y * L.MW + w] = bits;
+        }
+    }
+}
+
+__global__ void rb_unpack_kernel(RBLayout L, int nx, int ny, float *__restrict__ out, int to_phi) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx || y >= ny) return;
+    int color = (x + y) & 1;
+    int k = x >> 1;
+    const float *arr = color ? L.B : L.R;
+    float v = arr[(size_t)y * L.S + 4 + k];
+    out[(size_t)y * nx + x] = to_phi ? 1.0f - v : v;
+}
+
+// FP32 residual max over both colours of the split layout.
+__global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, unsigned int *out_max) {
+    int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    float r = 0.0f;
+    if (k4 < L.W4 && y < ny - 1) {
+        int k = 4 * k4;
+#pragma unroll
+        for (int color = 0; color < 2; color++) {
+            const float *U = color ? L.B : L.R;
+            const float *V = color ? L.R : L.B;
+            const uint32_t *M = color ? L.MB : L.MR;
+            uint32_t bits = (M[(size_t)y * L.MW + (k >> 5)] >> (k & 31)) & 0xFu;
+            if (!bits) continue;
+            int s = (y + color) & 1;
+            float4 nb[4];
+            rb_load_neighbours(V, L.S, y, k, s, nb);
+            float4 c = *reinterpret_cast<const float4 *>(U + (size_t)y * L.S + 4 + k);
+            if (bits & 1u) r = fmaxf(r, fabsf(rb_avg(nb, 0) - c.x));
+            if (bits & 2u) r = fmaxf(r, fabsf(rb_avg(nb, 1) - c.y));
+            if (bits & 4u) r = fmaxf(r, fabsf(rb_avg(nb, 2) - c.z));
+            if (bits & 8u) r = fmaxf(r, fabsf(rb_avg(nb, 3) - c.w));
+        }
+    }
+    block_max_atomic(r, out_max);
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+
+RBLayout rb_layout(int nx, int ny) {
+    RBLayout L;
+    memset(&L, 0, sizeof(L));
+    int half = (nx + 1) / 2;
+    L.W2 = (half + 3) & ~3;
+    L.W4 = L.W2 / 4;
+    L.S = L.W2 + 8;
+    L.MW = (L.W2 + 31) / 32;
+    return L;
+}
+
+size_t carve_rb(Carver &cv, int nx, int ny, RBLayout *out, bool pingpong) {
+    RBLayout L = rb_layout(nx, ny);
+    size_t plane = (size_t)ny * L.S;
+    L.R = cv.take<float>(plane);
+    L.B = cv.take<float>(plane);
+    L.MR = cv.take<uint32_t>((size_t)ny * L.MW);
+    L.MB = cv.take<uint32_t>((size_t)ny * L.MW);
+    if (pingpong) {
+        L.R2 = cv.take<float>(plane);
+        L.B2 = cv.take<float>(plane);
+    }
+    if (out) *out = L;
+    return cv.need;
+}
+
+static size_t carve_relax(Carver &cv, int nx, int ny, const hp_params *p, RelaxLayout *out) {
+    RelaxLayout R;
+    memset(&R, 0, sizeof(R));
+    R.scal = cv.take<RelaxScalars>(1);
+    int method = p ? p->method : HP_RBSOR;
+    if (method == HP_JACOBI) {
+        R.tmp = cv.take<float>((size_t)nx * ny);
+    } else if (method == HP_RBSOR) {
+        carve_rb(cv, nx, ny, &R.rb, true);
+    } else {
+        carve_mixed(cv, nx, ny, p ? p->storage : HP_STORE_F16, &R);
+    }
+    if (out) *out = R;
+    return cv.need;
+}
+
+static bool valid_params(const hp_params *p) {
+    return p && (p->method == HP_JACOBI || p->method == HP_RBSOR || p->method == HP_MIXED) &&
+           (p->storage == HP_STORE_F32 || p->storage == HP_STORE_F16 || p->storage == HP_STORE_BF16) &&
+           isfinite(p->omega) && (p->omega == 0.0 || (p->omega > 0.0 && p->omega < 2.0)) &&
+           isfinite(p->tol) && p->tol >= 0.0 && p->max_sweeps >= 1 && p->check_every >= 0 &&
+           p->tblock >= 0 && p->tblock <= 16;
+}
+
+// Adaptive SOR factor.  For a consistently ordered matrix (red-black is one)
+// the SOR convergence factor lambda at omega <= omega_opt and the Jacobi
+// spectral radius mu satisfy (lambda + omega - 1)^2 = lambda omega^2 mu^2
+// (Young).  The observed residual decay over a check interval gives lambda,
+// hence mu and omega_opt = 2 / (1 + sqrt(1 - mu^2)).  Pre-asymptotic decay
+// underestimates mu, so omega approaches omega_opt from below.
+double sor_adapt(double omega, double lambda) {
+    if (!(lambda > 0.0) || lambda >= 1.0) return omega;
+    if (lambda <= (omega - 1.0) * 1.05) return omega;  // complex regime: at or past optimum
+    double mu = (lambda + omega - 1.0) / (omega * sqrt(lambda));
+    if (!(mu > 0.0)) return omega;
+    if (mu >= 0.999999999) mu = 0.999999999;
+    double w = 2.0 / (1.0 + sqrt(1.0 - mu * mu));
+    if (w > 1.9995) w = 1.9995;
+    return (w > omega) ? w : omega;
+}
+
+double sor_initial_omega(int nx, int ny) {
+    int n = nx > ny ? nx : ny;
+    return n >= 1024 ? 1.9 : (n >= 256 ? 1.85 : 1.75);
+}
+
+int read_max_f32(unsigned int *dmax, cudaStream_t s, float *out) {
+    unsigned int h = 0;
+    TW_CUDA(cudaMemcpyAsync(&h, dmax, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaStreamSynchronize(s));
+    memcpy(out, &h, sizeof(h));
+    return TW_OK;
+}
+
+int final_residual_full(const uint8_t *occ, int nx, int ny, int gx, int gy, const float *u,
+                        RelaxScalars *scal, cudaStream_t s, double *r_inf, double *r_l2) {
+    TW_CUDA(cudaMemsetAsync(&scal->max64, 0, sizeof(scal->max64) + sizeof(scal->sum64), s));
+    dim3 b(32, 8), gr(ceil_div(nx, 32), ceil_div(ny, 8));
+    TW_LAUNCH(full_residual_f64_kernel, gr, b, 0, s, occ, nx, ny, gx, gy, u, &scal->max64, &scal->sum64);
+    TW_CHECK_LAUNCH();
+    unsigned long long m = 0;
+    double sum = 0.0;
+    TW_CUDA(cudaMemcpyAsync(&m, &scal->max64, sizeof(m), cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaMemcpyAsync(&sum, &scal->sum64, sizeof(sum), cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaStreamSynchronize(s));
+    memcpy(r_inf, &m, sizeof(double));
+    *r_l2 = sqrt(sum);
+    return TW_OK;
+}
+
+static int relax_jacobi(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u,
+                        const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s) {
+    dim3 b(16, 16), gr(ceil_div(nx, 16), ceil_div(ny, 16));
+    TW_LAUNCH(jacobi_init_kernel, gr, b, 0, s, occ, nx, ny, gx, gy, u, (p->flags & HP_WARM_START) ? 1 : 0);
+    TW_CHECK_LAUNCH();
+    TW_CUDA(cudaMemcpyAsync(R.tmp, u, sizeof(float) * (size_t)nx * ny, cudaMemcpyDeviceToDevice, s));
+    int K = p->check_every > 0 ? p->check_every : 64;
+    float *src = u, *dst = R.tmp;
+    int sweeps = 0, checks = 0;
+    SweepTimer timer;
+    if (timer.open((p->flags & HP_TIMING) != 0)) return TW_ECUDA;
+    st->status = TW_NOT_CONVERGED;
+    while (sweeps < p->max_sweeps) {
+        int n = p->max_sweeps - sweeps < K ? p->max_sweeps - sweeps : K;
+        timer.start(s);
+        for (int i = 0; i < n; i++) {
+            TW_LAUNCH(jacobi_sweep_kernel, gr, b, 0, s, occ, nx, ny, gx, gy, src, dst);
+            float *t = src; src = dst; dst = t;
+        }
+        timer.stop(s);
+        TW_CHECK_LAUNCH();
+        timer.accumulate();
+        sweeps += n;
+        if (p->tol > 0.0) {
+            TW_CUDA(cudaMemsetAsync(&R.scal->max32, 0, sizeof(unsigned int), s));
+            TW_LAUNCH(full_residual_kernel, dim3(ceil_div(nx, 32), ceil_div(ny, 8)), dim3(32, 8), 0, s,
+                      occ, nx, ny, gx, gy, src, &R.scal->max32);
+            TW_CHECK_LAUNCH();
+            float r;
+            int e = read_max_f32(&R.scal->max32, s, &r);
+            if (e) return e;
+            checks++;
+            if (r <= p->tol) { st->status = TW_OK; break; }
+        }
+    }
+    if (src != u)
+        TW_CUDA(cudaMemcpyAsync(u, src, sizeof(float) * (size_t)nx * ny, cudaMemcpyDeviceToDevice, s));
+    st->sweeps = sweeps;
+    st->checks = checks;
+    st->omega = 1.0;
+    st->sweep_launches = sweeps;
+    st->sweep_ms = timer.ms;
+    st->tblock = 1;
+    return TW_OK;
+}
+
+// Red-black SOR driver on the split layout (pack -> sweeps -> unpack).
+int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
+             cudaStream_t s) {
+    int K = p->check_every > 0 ? p->check_every : 32;
+    int T = p->tblock > 0 ? p->tblock : kDefaultTBlock;
+    bool adapt = p->omega == 0.0;
+    double omega = adapt ? sor_initial_omega(nx, ny) : p->omega;
+    int sweeps = 0, checks = 0, launches = 0;
+    double r_prev = -1.0;
+    int same_omega_intervals = 0;
+    SweepTimer timer;
+    if (timer.open((p->flags & HP_TIMING) != 0)) return TW_ECUDA;
+    st->status = TW_NOT_CONVERGED;
+    while (sweeps < p->max_sweeps) {
+        int n = p->max_sweeps - sweeps < K ? p->max_sweeps - sweeps : K;
+        timer.start(s);
+        int e = rb_sweeps(L, nx, ny, n, T, (float)omega, s, &launches);
+        timer.stop(s);
+        if (e) return e;
+        timer.accumulate();
+        sweeps += n;
+        if (p->tol > 0.0 || adapt) {
+            TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
+            dim3 b(64, 4), gr(ceil_div(L.W4, 64), ceil_div(ny, 4));
+            TW_LAUNCH(rb_residual_kernel, gr, b, 0, s, L, ny, &scal->max32);
+            TW_CHECK_LAUNCH();
+            float rf;
+            e = read_max_f32(&scal->max32, s, &rf);
+            if (e) return e;
+            checks++;
+            double r = rf;
+            if (p->tol > 0.0 && r <= p->tol) { st->status = TW_OK; break; }
+            if (adapt) {
+                if (r_prev > 0.0 && same_omega_intervals >= 1 && n == K) {
+                    double lambda = pow(r / r_prev, 1.0 / n);
+                    double w = sor_adapt(omega, lambda);
+                    if (w > omega + 1e-4) { omega = w; same_omega_intervals = -1; }
+                }
+                same_omega_intervals++;
+                r_prev = r;
+            }
+        }
+    }
+    st->sweeps = sweeps;
+    st->checks = checks;
+    st->omega = omega;
+    st->sweep_launches = launches;
+    st->sweep_ms = timer.ms;
+    st->tblock = T;
+    return TW_OK;
+}
+
+static int relax_rbsor(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, int mode,
+                       const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s) {
+    RBLayout &L = R.rb;
+    TW_CUDA(cudaMemsetAsync(L.R, 0, sizeof(float) * (size_t)ny * L.S, s));
+    TW_CUDA(cudaMemsetAsync(L.B, 0, sizeof(float) * (size_t)ny * L.S, s));
+    if (L.R2) {
+        TW_CUDA(cudaMemsetAsync(L.R2, 0, sizeof(float) * (size_t)ny * L.S, s));
+        TW_CUDA(cudaMemsetAsync(L.B2, 0, sizeof(float) * (size_t)ny * L.S, s));
+    }
+    TW_LAUNCH(rb_pack_kernel, dim3(ceil_div(L.W2 + 31, 128), ny), 128, 0, s,
+              occ, u, nx, ny, gx, gy, mode, (p->flags & HP_WARM_START) ? 1 : 0, L);
+    TW_CHECK_LAUNCH();
+    int e = rb_solve(L, nx, ny, p, R.scal, st, s);
+    if (e) return e;
+    TW_LAUNCH(rb_unpack_kernel, dim3(ceil_div(nx, 256), ny), 256, 0, s, L, nx, ny, u, 0);
+    TW_CHECK_LAUNCH();
+    return TW_OK;
+}
+
+static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, int mode,
+                        const hp_params *p, hp_stats *st, void *ws, size_t ws_bytes, cudaStream_t s) {
+    if (!ws || !ws_aligned(ws)) return TW_EWORKSPACE;
+    Carver cv(ws, ws_bytes);
+    RelaxLayout R;
+    carve_relax(cv, nx, ny, p, &R);
+    if (!cv.ok()) return TW_EWORKSPACE;
+    hp_stats local;
+    memset(&local, 0, sizeof(local));
+    int e;
+    if (p->method == HP_JACOBI) {
+        if (mode == 1) {
+            // the general Dirichlet form keeps the caller's fixed values
+            e = TW_OK;
+            hp_params q = *p;
+            q.flags |= HP_WARM_START;
+            e = relax_jacobi(occ, nx, ny, -1, -1, u, &q, &local, R, s);
+        } else {
+            e = relax_jacobi(occ, nx, ny, gx, gy, u, p, &local, R, s);
+        }
+    } else if (p->method == HP_RBSOR) {
+        e = relax_rbsor(occ, nx, ny, gx, gy, u, mode, p, &local, R, s);
+    } else {
+        e = relax_mixed(occ, nx, ny, gx, gy, u, mode, p, &local, R, s);
+    }
+    if (e) return e;
+    e = final_residual_full(occ, nx, ny, mode == 1 ? -1 : gx, mode == 1 ? -1 : gy, u, R.scal, s,
+                            &local.resid_inf, &local.resid_l2);
+    if (e) return e;
+    if (mode == 0 && (p->flags & HP_OUT_PHI)) {
+        size_t n = (size_t)nx * ny;
+        TW_LAUNCH(to_phi_kernel, ceil_div(n, 256), 256, 0, s, u, n);
+        TW_CHECK_LAUNCH();
+        TW_CUDA(cudaStreamSynchronize(s));
+    }
+    if (p->tol > 0.0 && local.resid_inf <= p->tol) local.status = TW_OK;
+    if (st) *st = local;
+    return local.status;
+}
+
+}  // namespace tw
+
+using namespace tw;
+
+extern "C" size_t hp_relax_workspace_size(int nx, int ny, const hp_params *p) {
+    if (nx < 3 || ny < 3) return 0;
+    Carver cv;
+    return carve_relax(cv, nx, ny, p, nullptr);
+}
+
+extern "C" int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *field_dev,
+                        const hp_params *p, hp_stats *stats, void *workspace, size_t workspace_bytes,
+                        void *stream) {
+    if (!g || g->nx < 3 || g->ny < 3 || g->nx > 65536 || g->ny > 65536 || !occ_dev || !field_dev ||
+        !valid_params(p))
+        return TW_EINVAL;
+    int nx = g->nx, ny = g->ny;
+    if (gx < 1 || gy < 1 || gx > nx - 2 || gy > ny - 2) return TW_EGOAL_BLOCKED;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t gocc = 0;
+    TW_CUDA(cudaMemcpyAsync(&gocc, occ_dev + (size_t)gy * nx + gx, 1, cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaStreamSynchronize(s));
+    if (gocc != 0) return TW_EGOAL_BLOCKED;
+    if ((p->flags & HP_WARM_START) && (p->flags & HP_OUT_PHI)) {
+        // warm start given as phi: convert to u in place first
+        size_t n = (size_t)nx * ny;
+        TW_LAUNCH(to_phi_kernel, ceil_div(n, 256), 256, 0, s, field_dev, n);
+        TW_CHECK_LAUNCH();
+    }
+    return relax_common(occ_dev, nx, ny, gx, gy, field_dev, 0, p, stats, workspace, workspace_bytes, s);
+}
+
+extern "C" int hp_relax_dirichlet(int nx, int ny, const uint8_t *fixed_dev, float *u_dev,
+                                  const hp_params *p, hp_stats *stats, void *workspace,
+                                  size_t workspace_bytes, void *stream) {
+    if (nx < 3 || ny < 3 || nx > 65536 || ny > 65536 || !fixed_dev || !u_dev || !valid_params(p))
+        return TW_EINVAL;
+    return relax_common(fixed_dev, nx, ny, -1, -1, u_dev, 1, p, stats, workspace, workspace_bytes,
+                        (cudaStream_t)stream);
+}
+
+extern "C" int hp_residual(int nx, int ny, const uint8_t *fixed_dev, const float *u_dev, double *r_inf,
+                           double *r_l2, void *workspace, size_t workspace_bytes, void *stream) {
+    if (nx < 3 || ny < 3 || !fixed_dev || !u_dev || !r_inf || !r_l2) return TW_EINVAL;
+    if (!workspace || !ws_aligned(workspace) || workspace_bytes < sizeof(RelaxScalars)) return TW_EWORKSPACE;
+    return final_residual_full(fixed_dev, nx, ny, -1, -1, u_dev, (RelaxScalars *)workspace,
+                               (cudaStream_t)stream, r_inf, r_l2);
+}

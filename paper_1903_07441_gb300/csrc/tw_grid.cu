@@ -1,0 +1,380 @@
+// Time-warped occupancy grid (Sec. 3.4-3.5, Alg. 1 "Map Update").
+//
+// Three launches, all stream-ordered:
+//   tw_ring_table_kernel  1 thread: ring radii R_j, arrival times t_j and their
+//                         fixed-point forms (the recurrence is serial and tiny)
+//   tw_predict_kernel     1 thread per (track, ring) [per-cell marking] or per
+//                         track [per-obstacle marking]: Eqs. 9-10 at t_j and the
+//                         inflated disk, in correctly rounded FP64 (explicit
+//                         _rn intrinsics, so no contraction can change a bit)
+//   tw_raster_kernel      1 CTA per 32x32 tile: ring of every cell, candidate
+//                         disks binned in shared memory per tile, exact integer
+//                         predicates, occupancy codes written once.
+// The raster is integer/ALU work (a few bytes of HBM per cell).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace tw {
+
+constexpr int kMaxRings = 64;
+constexpr long long kCoordClamp = 1LL << 30;
+constexpr long long kRadiusClamp = 1LL << 29;
+
+struct RingTab {
+    int J, kind, mark, pad;
+    long long rxq, ryq, hxq, hyq;
+    double t[kMaxRings];
+    long long Rq[kMaxRings];   // ring radius, 1/256 cell
+    long long Aq[kMaxRings];   // elliptic semi-major axis, 2^-28 cell
+    long long Cq[kMaxRings];   // elliptic centre offset 0.9 R, 2^-28 cell
+};
+
+struct Disk {
+    int px, py;      // predicted centre, 1/256 cell (clamped to +-2^30)
+    int j, pad;      // ring the disk belongs to; -1: every ring (per-obstacle marking)
+    long long r2;    // squared inflated radius, (1/256 cell)^2
+};
+
+struct Params {
+    int nx, ny, n, mark, kind, n_rings, time_outer, pad;
+    double cell, ox, oy;
+    double rx, ry, hx, hy, speed;
+    double r0, growth, q, kappa, d_safe;
+};
+
+__device__ __forceinline__ long long qclamp(double v, long long lo, long long hi) {
+    double r = rint(v);
+    if (r < (double)lo) return lo;
+    if (r > (double)hi) return hi;
+    return (long long)r;
+}
+
+__device__ __forceinline__ long long qpos(double v, double origin, double cell) {
+    return qclamp(__dmul_rn(__ddiv_rn(__dsub_rn(v, origin), cell), 256.0), -kCoordClamp, kCoordClamp);
+}
+
+__global__ void tw_ring_table_kernel(Params p, RingTab *tab) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double w = __dmul_rn((double)p.nx, p.cell), h = __dmul_rn((double)p.ny, p.cell);
+    double reach = __dsqrt_rn(__dadd_rn(__dmul_rn(w, w), __dmul_rn(h, h)));
+    if (p.kind == TW_RING_ELLIPTIC) reach = __dmul_rn(reach, 10.0);
+    double R[kMaxRings];
+    int J = 0;
+    double r = p.r0;
+    for (;;) {
+        if (J >= kMaxRings) { tab->J = -1; return; }
+        R[J] = r;
+        J++;
+        if (p.n_rings > 0) { if (J == p.n_rings) break; }
+        else if (r >= reach) break;
+        r = __dmul_rn(r, p.growth);
+    }
+    tab->J = J;
+    tab->kind = p.kind;
+    tab->mark = p.mark;
+    for (int j = 0; j < J; j++) {
+        double t;
+        if (p.time_outer) t = __ddiv_rn(R[j], p.speed);
+        else t = (j == 0) ? 0.0 : __ddiv_rn(R[j - 1], p.speed);
+        tab->t[j] = t;
+        tab->Rq[j] = qclamp(__dmul_rn(__ddiv_rn(R[j], p.cell), 256.0), 0, kRadiusClamp);
+        tab->Aq[j] = qclamp(__dmul_rn(__ddiv_rn(R[j], p.cell), 268435456.0), 0, 1LL << 52);
+        tab->Cq[j] = qclamp(__dmul_rn(__ddiv_rn(__dmul_rn(0.9, R[j]), p.cell), 268435456.0), 0, 1LL << 52);
+    }
+    tab->rxq = qpos(p.rx, p.ox, p.cell);
+    tab->ryq = qpos(p.ry, p.oy, p.cell);
+    tab->hxq = qclamp(__dmul_rn(p.hx, 1048576.0), -1048576, 1048576);
+    tab->hyq = qclamp(__dmul_rn(p.hy, 1048576.0), -1048576, 1048576);
+}
+
+// Smallest ring containing the fixed-point offset (dx, dy); the last ring otherwise.
+__device__ __forceinline__ int ring_index(int kind, int J, long long dx, long long dy,
+                                          const long long *Rq, const long long *Aq,
+                                          const long long *Cq, long long hxq, long long hyq) {
+    if (kind == TW_RING_CIRCULAR) {
+        long long d2 = dx * dx + dy * dy;
+        for (int j = 0; j < J; j++)
+            if (d2 <= Rq[j] * Rq[j]) return j;
+    } else {
+        __int128 u = (__int128)(hxq * dx + hyq * dy);
+        __int128 v = (__int128)(hxq * dy - hyq * dx);
+        __int128 v16 = 16 * v * v;
+        for (int j = 0; j < J; j++) {
+            __int128 a = u - (__int128)Cq[j];
+            if (a * a + v16 <= (__int128)Aq[j] * (__int128)Aq[j]) return j;
+        }
+    }
+    return J - 1;
+}
+
+// Constant-velocity prediction at time t and the inflated, quantised disk.
+__device__ Disk predict_disk(const tw_track &T, double t, const Params &p, int j) {
+    const double *P = T.P;
+    double px = __dadd_rn(T.x[0], __dmul_rn(t, T.x[2]));
+    double py = __dadd_rn(T.x[1], __dmul_rn(t, T.x[3]));
+    double qt3 = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(p.q, t), t), t), 3.0);
+    double two_t = __dmul_rn(2.0, t), tt = __dmul_rn(t, t);
+    double pxx = __dadd_rn(__dadd_rn(__dadd_rn(P[0], __dmul_rn(two_t, P[2])), __dmul_rn(tt, P[10])), qt3);
+    double pyy = __dadd_rn(__dadd_rn(__dadd_rn(P[5], __dmul_rn(two_t, P[7])), __dmul_rn(tt, P[15])), qt3);
+    double s2 = __dmul_rn(0.5, __dadd_rn(pxx, pyy));
+    double sigma = (s2 > 0.0) ? __dsqrt_rn(s2) : 0.0;
+    double rho = __dadd_rn(__dadd_rn(T.radius, p.d_safe), __dmul_rn(p.kappa, sigma));
+    long long rq = qclamp(__dmul_rn(__ddiv_rn(rho, p.cell), 256.0), 0, kRadiusClamp);
+    Disk d;
+    d.px = (int)qpos(px, p.ox, p.cell);
+    d.py = (int)qpos(py, p.oy, p.cell);
+    d.j = j;
+    d.pad = 0;
+    d.r2 = rq * rq;
+    return d;
+}
+
+__global__ void tw_predict_kernel(Params p, const RingTab *tab, const tw_track *tracks,
+                                  Disk *disks) {
+    int J = tab->J;
+    if (J <= 0) return;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p.mark == TW_MARK_PER_CELL) {
+        if (idx >= (long long)p.n * J) return;
+        int o = (int)(idx / J), j = (int)(idx % J);
+        disks[idx] = predict_disk(tracks[o], tab->t[j], p, j);
+    } else {
+        if (idx >= p.n) return;
+        const tw_track &T = tracks[idx];
+        long long dx = qpos(T.x[0], p.ox, p.cell) - tab->rxq;
+        long long dy = qpos(T.x[1], p.oy, p.cell) - tab->ryq;
+        int own = ring_index(tab->kind, J, dx, dy, tab->Rq, tab->Aq, tab->Cq, tab->hxq, tab->hyq);
+        Disk d = predict_disk(T, tab->t[own], p, -1);
+        disks[idx] = d;
+    }
+}
+
+constexpr int kTile = 32;            // 32x32 cells per CTA
+constexpr int kRasterThreads = 256;  // 4 cells per thread
+constexpr int kChunk = 1024;         // disks examined per binning round
+
+__global__ void __launch_bounds__(kRasterThreads)
+tw_raster_kernel(Params p, const RingTab *tab, const Disk *disks, const uint8_t *static_occ, uint8_t *occ,
+                 int16_t *ring_out) {
+    __shared__ long long sRq[kMaxRings], sAq[kMaxRings], sCq[kMaxRings];
+    __shared__ Disk sList[kChunk];
+    __shared__ int sCount, sJmin, sJmax;
+    const int tid = threadIdx.x;
+    const int J = tab->J;
+    const int kind = tab->kind;
+    if (J <= 0) return;
+    // disk count from the device-side ring table (the predict kernel used the same J)
+    const int n_disks = (p.mark == TW_MARK_PER_CELL) ? p.n * J : p.n;
+    for (int j = tid; j < J; j += kRasterThreads) {
+        sRq[j] = tab->Rq[j];
+        sAq[j] = tab->Aq[j];
+        sCq[j] = tab->Cq[j];
+    }
+    if (tid == 0) { sJmin = 1 << 30; sJmax = -1; sCount = 0; }
+    __syncthreads();
+    const long long rxq = tab->rxq, ryq = tab->ryq, hxq = tab->hxq, hyq = tab->hyq;
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    const int lx = tid % kTile;
+    const int x = x0 + lx;
+    int rj[4];
+    uint8_t code[4];
+    int jmin = 1 << 30, jmax = -1;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        int y = y0 + tid / kTile + 8 * r;
+        rj[r] = -1;
+        code[r] = TW_FREE;
+        if (x < p.nx && y < p.ny) {
+            long long cx = 256LL * x + 128, cy = 256LL * y + 128;
+            rj[r] = ring_index(kind, J, cx - rxq, cy - ryq, sRq, sAq, sCq, hxq, hyq);
+            size_t c = (size_t)y * p.nx + x;
+            if (x == 0 || y == 0 || x == p.nx - 1 || y == p.ny - 1) code[r] = TW_BORDER;
+            else if (static_occ && static_occ[c]) code[r] = TW_STATIC;
+            if (code[r] == TW_FREE) { jmin = min(jmin, rj[r]); jmax = max(jmax, rj[r]); }
+        }
+    }
+    atomicMin(&sJmin, jmin);
+    atomicMax(&sJmax, jmax);
+    __syncthreads();
+    const int tjmin = sJmin, tjmax = sJmax;
+    // tile bounds in fixed point (cell centres)
+    const long long bx0 = 256LL * x0 + 128, by0 = 256LL * y0 + 128;
+    const long long bx1 = 256LL * min(x0 + kTile - 1, p.nx - 1) + 128;
+    const long long by1 = 256LL * min(y0 + kTile - 1, p.ny - 1) + 128;
+    if (tjmax >= 0) {
+        for (int base = 0; base < n_disks; base += kChunk) {
+            int lim = min(kChunk, n_disks - base);
+            for (int k = tid; k < lim; k += kRasterThreads) {
+                Disk d = disks[base + k];
+                if (d.j >= 0 && (d.j < tjmin || d.j > tjmax)) continue;
+                long long ex = max(0LL, max(bx0 - (long long)d.px, (long long)d.px - bx1));
+                long long ey = max(0LL, max(by0 - (long long)d.py, (long long)d.py - by1));
+                if (ex * ex + ey * ey <= d.r2) {
+                    int slot = atomicAdd(&sCount, 1);
+                    sList[slot] = d;
+                }
+            }
+            __syncthreads();
+            const int cnt = sCount;
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                if (code[r] != TW_FREE || rj[r] < 0) continue;
+                int y = y0 + tid / kTile + 8 * r;
+                long long cx = 256LL * x + 128, cy = 256LL * y + 128;
+                for (int k = 0; k < cnt; k++) {
+                    const Disk &d = sList[k];
+                    if (d.j >= 0 && d.j != rj[r]) continue;
+                    long long dx = cx - d.px, dy = cy - d.py;
+                    if (dx * dx + dy * dy <= d.r2) { code[r] = TW_DYNAMIC; break; }
+                }
+            }
+            __syncthreads();
+            if (tid == 0) sCount = 0;
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        int y = y0 + tid / kTile + 8 * r;
+        if (x < p.nx && y < p.ny) {
+            size_t c = (size_t)y * p.nx + x;
+            occ[c] = code[r];
+            if (ring_out) ring_out[c] = (int16_t)rj[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static bool finite(double v) { return isfinite(v) != 0; }
+
+static bool valid_grid(const tw_grid *g) {
+    return g && g->nx >= 3 && g->ny >= 3 && g->nx <= 65536 && g->ny <= 65536 && finite(g->cell) &&
+           g->cell > 0.0 && finite(g->ox) && finite(g->oy);
+}
+
+static bool valid_law(const tw_ring_law *L) {
+    return L && (L->kind == TW_RING_CIRCULAR || L->kind == TW_RING_ELLIPTIC) &&
+           (L->mark == TW_MARK_PER_CELL || L->mark == TW_MARK_PER_OBSTACLE) && finite(L->r0) &&
+           L->r0 > 0.0 && finite(L->growth) && L->growth > 1.0 && L->n_rings >= 0 &&
+           L->n_rings <= kMaxRings && finite(L->q_accel) && L->q_accel >= 0.0 &&
+           finite(L->kappa) && L->kappa >= 0.0 && finite(L->d_safe) && L->d_safe >= 0.0 &&
+           (L->time_outer == 0 || L->time_outer == 1);
+}
+
+static bool valid_pose(const tw_pose *r) {
+    if (!r || !finite(r->x) || !finite(r->y) || !finite(r->hx) || !finite(r->hy) || !finite(r->speed))
+        return false;
+    double h2 = r->hx * r->hx + r->hy * r->hy;
+    return r->speed > 0.0 && h2 > 0.98 && h2 < 1.02;
+}
+
+static bool psd2(double a, double b, double c) {  // [[a, b], [b, c]]
+    return a >= 0.0 && c >= 0.0 && b * b <= a * c * (1.0 + 1e-9) + 1e-300;
+}
+
+static bool valid_track(const tw_track &T) {
+    for (int i = 0; i < 4; i++)
+        if (!finite(T.x[i])) return false;
+    for (int i = 0; i < 16; i++)
+        if (!finite(T.P[i])) return false;
+    if (!finite(T.radius) || T.radius < 0.0) return false;
+    return psd2(T.P[0], T.P[2], T.P[10]) && psd2(T.P[5], T.P[7], T.P[15]);
+}
+
+// Ring count by the same recurrence the device runs (IEEE-exact ops on both).
+static int ring_count(const tw_grid *g, const tw_pose *robot, const tw_ring_law *L) {
+    if (!valid_grid(g) || !valid_law(L) || !valid_pose(robot)) return TW_EINVAL;
+    volatile double w = (double)g->nx * g->cell, h = (double)g->ny * g->cell;
+    volatile double ww = w * w, hh = h * h;
+    volatile double s = ww + hh;
+    double reach = sqrt((double)s);
+    if (L->kind == TW_RING_ELLIPTIC) reach = reach * 10.0;
+    int J = 0;
+    volatile double r = L->r0;
+    for (;;) {
+        if (J >= kMaxRings) return TW_EINVAL;
+        J++;
+        if (L->n_rings > 0) { if (J == L->n_rings) break; }
+        else if (r >= reach) break;
+        r = r * L->growth;
+    }
+    return J;
+}
+
+struct GridLayout {
+    RingTab *tab;
+    tw_track *tracks;
+    Disk *disks;
+};
+
+static size_t carve_grid(Carver &cv, int n_tracks, int J, GridLayout *out) {
+    GridLayout l;
+    l.tab = cv.take<RingTab>(1);
+    l.tracks = cv.take<tw_track>(n_tracks > 0 ? n_tracks : 1);
+    l.disks = cv.take<Disk>((size_t)(n_tracks > 0 ? n_tracks : 1) * (size_t)(J > 0 ? J : 1));
+    if (out) *out = l;
+    return cv.need;
+}
+
+}  // namespace tw
+
+using namespace tw;
+
+extern "C" int tw_ring_count(const tw_grid *g, const tw_pose *robot, const tw_ring_law *law) {
+    return ring_count(g, robot, law);
+}
+
+extern "C" size_t tw_build_grid_workspace_size(const tw_grid *g, int n_tracks, const tw_ring_law *law) {
+    (void)g;
+    (void)law;
+    Carver cv;
+    return carve_grid(cv, n_tracks < 0 ? 0 : n_tracks, kMaxRings, nullptr);
+}
+
+extern "C" int tw_build_grid(const tw_grid *g, const tw_pose *robot, const tw_track *tracks,
+                             int n_tracks, const tw_ring_law *law, const uint8_t *static_occ_dev,
+                             uint8_t *occ_dev, int16_t *ring_dev, void *workspace,
+                             size_t workspace_bytes, void *stream) {
+    if (!valid_grid(g) || !valid_law(law) || !valid_pose(robot) || !occ_dev || n_tracks < 0 ||
+        (n_tracks > 0 && !tracks))
+        return TW_EINVAL;
+    for (int o = 0; o < n_tracks; o++)
+        if (!valid_track(tracks[o])) return TW_EINVAL;
+    int J = ring_count(g, robot, law);
+    if (J <= 0) return TW_EINVAL;
+    if (!workspace || !ws_aligned(workspace)) return TW_EWORKSPACE;
+    Carver cv(workspace, workspace_bytes);
+    GridLayout L;
+    carve_grid(cv, n_tracks, kMaxRings, &L);
+    if (!cv.ok()) return TW_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    Params p;
+    memset(&p, 0, sizeof(p));
+    p.nx = g->nx; p.ny = g->ny; p.n = n_tracks; p.mark = law->mark; p.kind = law->kind;
+    p.n_rings = law->n_rings; p.time_outer = law->time_outer;
+    p.cell = g->cell; p.ox = g->ox; p.oy = g->oy;
+    p.rx = robot->x; p.ry = robot->y; p.hx = robot->hx; p.hy = robot->hy; p.speed = robot->speed;
+    p.r0 = law->r0; p.growth = law->growth; p.q = law->q_accel; p.kappa = law->kappa;
+    p.d_safe = law->d_safe;
+
+    if (n_tracks > 0)
+        TW_CUDA(cudaMemcpyAsync(L.tracks, tracks, sizeof(tw_track) * (size_t)n_tracks,
+                                cudaMemcpyHostToDevice, s));
+    TW_LAUNCH(tw_ring_table_kernel, 1, 32, 0, s, p, L.tab);
+    TW_CHECK_LAUNCH();
+    if (n_tracks > 0) {
+        TW_LAUNCH(tw_predict_kernel, ceil_div((size_t)n_tracks * kMaxRings, 128), 128, 0, s, p, L.tab,
+                  L.tracks, L.disks);
+        TW_CHECK_LAUNCH();
+    }
+    dim3 grid(ceil_div(g->nx, kTile), ceil_div(g->ny, kTile));
+    TW_LAUNCH(tw_raster_kernel, grid, kRasterThreads, 0, s, p, L.tab, L.disks, static_occ_dev, occ_dev,
+              ring_dev);
+    TW_CHECK_LAUNCH();
+    return TW_OK;
+}

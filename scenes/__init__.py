@@ -41,7 +41,7 @@ class RingLaw:
     r0: float = 0.5          # m, first ring radius
     growth: float = 1.3      # geometric ring growth
     n_rings: int = 0         # 0: first J with R_{J-1} >= grid diagonal
-    q_accel: float = 0.01    # m^2/s^3 white-noise acceleration PSD
+    q_accel: float = 1e-4    # m^2/s^3 white-noise acceleration PSD ("very small" Q)
     kappa: float = 2.0       # inflation in standard deviations
     d_safe: float = 0.25     # m, safety distance
     time_outer: int = 0      # 0: arrival time from inner ring radius; 1: outer
@@ -223,12 +223,14 @@ def synth_tracks(st: Stream, pos, vel, radius, sigma=0.05):
     T = np.zeros((n, 21))
     T[:, 0:2] = pos + 0.4 * sigma * st.normal(2 * n).reshape(n, 2)
     T[:, 2:4] = vel + 0.05 * st.normal(2 * n).reshape(n, 2)
-    a = st.uniform(n, 0.2, 1.0) * sigma * sigma
-    b = st.uniform(n, 1e-3, 0.05)
-    c = st.uniform(n, -0.9, 0.9) * np.sqrt(a * b)
+    # magnitudes around the steady state of a 10 Hz filter with sigma = 5 cm
+    # measurements and a very small process noise (Pxx ~ 3e-4 m^2, Pvv ~ 2e-4 m^2/s^2)
+    a = st.uniform(n, 0.4, 2.0) * 2.5e-4 * (sigma / 0.05) ** 2
+    b = st.uniform(n, 0.3, 3.0) * 1.7e-4
+    c = st.uniform(n, 0.2, 0.9) * np.sqrt(a * b)
     a2 = a * st.uniform(n, 0.7, 1.3)
     b2 = b * st.uniform(n, 0.7, 1.3)
-    c2 = st.uniform(n, -0.9, 0.9) * np.sqrt(a2 * b2)
+    c2 = st.uniform(n, 0.2, 0.9) * np.sqrt(a2 * b2)
     P = np.zeros((n, 4, 4))
     P[:, 0, 0], P[:, 0, 2], P[:, 2, 0], P[:, 2, 2] = a, c, c, b
     P[:, 1, 1], P[:, 1, 3], P[:, 3, 1], P[:, 3, 3] = a2, c2, c2, b2

@@ -1,0 +1,161 @@
+"""C-ABI boundary checks that need no GPU: the library loads, exports every
+function include/twgrid.h declares, validates arguments on the host before
+any CUDA call, and its host-only parts (ring count, Kalman filter) agree with
+the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1903_07441_gb300 as tw
+import scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1903_07441_gb300 import build
+    build.build()
+    return tw.load()
+
+
+def _declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            if not m.group(0).lstrip().startswith(("#", "typedef", "return")):
+                names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for fn in ("tw_build_grid", "hp_relax", "plan_path", "kf_update", "tw_status_string"):
+        assert fn in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in sorted(_declared_functions()):
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_binding_lists_the_exports(lib):
+    assert set(tw.EXPORTS) == _declared_functions()
+
+
+def test_status_strings(lib):
+    for st in (0, 1, 2, -1, -2, -3, -4, -5):
+        assert tw.status_string(st) and tw.status_string(st) != "unknown status"
+    assert tw.status_string(12345) == "unknown status"
+
+
+def test_ring_count_matches_oracle(lib):
+    for name, side in (("static128", 128), ("dynamic512", 512)):
+        sc = scenes.by_name(name) if name != "dynamic512" else scenes.dynamic(side=512, n_obs=3, frames=1)
+        for law in (scenes.RingLaw(), scenes.RingLaw(kind=scenes.RING_ELLIPTIC),
+                    scenes.RingLaw(r0=0.3, growth=1.2), scenes.RingLaw(n_rings=7)):
+            R, _ = oracle.ring_table(law, sc.nx, sc.ny, sc.cell, sc.robot[4])
+            assert tw.tw_ring_count(tw.make_grid(sc.nx, sc.ny, sc.cell), sc.robot, law) == len(R)
+
+
+def test_kf_host_matches_oracle(lib):
+    sc = scenes.dynamic512()
+    n = 50
+    z0 = sc.meas[0, :n]
+    T = tw.kf_init(z0, sc.radius[:n], r_meas=0.05, p_vel=1.0)
+    R = oracle.kf_init(z0, sc.radius[:n], r_meas=0.05, p_vel=1.0)
+    assert np.array_equal(T, R)
+    for f in range(1, 40):
+        tw.kf_update(T, sc.meas[f, :n], dt=0.1, q_accel=1e-4, r_meas=0.05)
+        R = oracle.kf_step(R, sc.meas[f, :n], dt=0.1, q=1e-4, r=0.05)
+    # same equations, different operation order: agreement to rounding
+    assert np.abs(T - R).max() <= 1e-12 * max(1.0, np.abs(R).max())
+    # the filter tracks the truth
+    err = np.hypot(*(T[:, :2] - sc.truth_pos[39, :n]).T)
+    assert np.median(err) < 0.05
+
+
+def _bad_grid_call(lib, **kw):
+    g = tw.make_grid(kw.get("nx", 64), kw.get("ny", 64), kw.get("cell", 0.05))
+    robot = tw.make_pose(kw.get("robot", [0.5, 0.5, 1.0, 0.0, 0.75]))
+    law = tw.make_law(kw.get("law", scenes.RingLaw()))
+    tracks = np.ascontiguousarray(kw.get("tracks", np.zeros((0, 21))), dtype=np.float64)
+    n = tracks.shape[0]
+    return lib.tw_build_grid(ctypes.byref(g), ctypes.byref(robot),
+                             tracks.ctypes.data_as(ctypes.c_void_p) if n else None, n, ctypes.byref(law),
+                             None, ctypes.c_void_p(256), None, ctypes.c_void_p(256), 1 << 20, None)
+
+
+def test_build_grid_rejects_bad_input_on_host(lib):
+    good = scenes.synth_tracks(scenes.rng.Stream(1), np.array([[1.0, 1.0]]), np.array([[0.1, 0.0]]),
+                               np.array([0.3]))
+    assert _bad_grid_call(lib, nx=2) == tw.TW_EINVAL
+    assert _bad_grid_call(lib, cell=0.0) == tw.TW_EINVAL
+    assert _bad_grid_call(lib, robot=[0.5, 0.5, 0.5, 0.0, 0.75]) == tw.TW_EINVAL   # heading not unit
+    assert _bad_grid_call(lib, robot=[0.5, 0.5, 1.0, 0.0, 0.0]) == tw.TW_EINVAL    # zero speed
+    assert _bad_grid_call(lib, law=scenes.RingLaw(growth=1.0)) == tw.TW_EINVAL
+    assert _bad_grid_call(lib, law=scenes.RingLaw(r0=0.001, growth=1.01)) == tw.TW_EINVAL  # > 64 rings
+    bad = good.copy(); bad[0, 2] = np.nan
+    assert _bad_grid_call(lib, tracks=bad) == tw.TW_EINVAL
+    bad = good.copy(); bad[0, 20] = -0.1
+    assert _bad_grid_call(lib, tracks=bad) == tw.TW_EINVAL
+    bad = good.copy(); bad[0, 4 + 2] = bad[0, 4 + 8] = 1.0    # |Pxv| > sqrt(Pxx Pvv): not PSD
+    assert _bad_grid_call(lib, tracks=bad) == tw.TW_EINVAL
+    bad = good.copy(); bad[0, 4 + 0] = -1e-3
+    assert _bad_grid_call(lib, tracks=bad) == tw.TW_EINVAL
+
+
+def test_workspace_errors_and_sizes(lib):
+    g = tw.make_grid(64, 64, 0.05)
+    robot = tw.make_pose([0.5, 0.5, 1.0, 0.0, 0.75])
+    law = tw.make_law(scenes.RingLaw())
+    assert lib.tw_build_grid_workspace_size(ctypes.byref(g), 10, ctypes.byref(law)) > 0
+    st = lib.tw_build_grid(ctypes.byref(g), ctypes.byref(robot), None, 0, ctypes.byref(law), None,
+                           ctypes.c_void_p(256), None, None, 0, None)
+    assert st == tw.TW_EWORKSPACE
+    st = lib.tw_build_grid(ctypes.byref(g), ctypes.byref(robot), None, 0, ctypes.byref(law), None,
+                           ctypes.c_void_p(256), None, ctypes.c_void_p(4096 + 8), 1 << 20, None)
+    assert st == tw.TW_EWORKSPACE  # misaligned
+    for m in (tw.HP_JACOBI, tw.HP_RBSOR):
+        p = tw.Params(method=m).c()
+        a = lib.hp_relax_workspace_size(2048, 2048, ctypes.byref(p))
+        b = lib.hp_relax_workspace_size(128, 128, ctypes.byref(p))
+        assert a > b > 0
+    assert lib.plan_path_workspace_size(1000) >= 8000
+
+
+def test_relax_rejects_bad_params_and_goal_on_host(lib):
+    g = tw.make_grid(64, 64, 0.05)
+    st = tw.hp_stats()
+
+    def call(params, gx=30, gy=30):
+        cp = params.c()
+        return lib.hp_relax(ctypes.byref(g), ctypes.c_void_p(256), gx, gy, ctypes.c_void_p(256),
+                            ctypes.byref(cp), ctypes.byref(st), ctypes.c_void_p(256), 1 << 30, None)
+
+    assert call(tw.Params(omega=2.0)) == tw.TW_EINVAL
+    assert call(tw.Params(omega=float("nan"))) == tw.TW_EINVAL
+    assert call(tw.Params(max_sweeps=0)) == tw.TW_EINVAL
+    assert call(tw.Params(tol=-1.0)) == tw.TW_EINVAL
+    assert call(tw.Params(method=7)) == tw.TW_EINVAL
+    assert call(tw.Params(), gx=0, gy=30) == tw.TW_EGOAL_BLOCKED     # on the border
+    assert call(tw.Params(), gx=64, gy=30) == tw.TW_EGOAL_BLOCKED    # out of range
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The binding imports no oracle code and fails loudly without a GPU."""
+    src = open(os.path.join(ROOT, "paper_1903_07441_gb300", "__init__.py")).read()
+    assert "oracle" not in src.replace("no CPU fallback", "")
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError):
+            tw.hp_relax(tw.make_grid(8, 8, 0.1), torch.zeros((8, 8), dtype=torch.uint8), (3, 3))

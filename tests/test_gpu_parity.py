@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+* raster: bit-exact occupancy and ring index, every ring law / marking mode,
+  several seeds and frames, ragged and odd grid sizes, the full 2048x2048 size;
+* field: max |u - u*| against the oracle's tightly converged solution, bounded
+  by the a-posteriori bound tau_max * r_inf (exit time tau), and <= 1e-5 once
+  the FP32 iteration has converged to its floor; closed-form Dirichlet data;
+* path: valid (collision-free, reaches the goal) and within Hausdorff 2 cells
+  of the oracle path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1903_07441_gb300 as tw
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_07441_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _gpu_grid(sc, dev, law=None, tracks=None, with_ring=True):
+    grid = tw.make_grid(sc.nx, sc.ny, sc.cell, sc.ox, sc.oy)
+    static = torch.from_numpy(np.ascontiguousarray(sc.static_occ)).to(dev) if sc.static_occ is not None else None
+    ring = torch.empty((sc.ny, sc.nx), dtype=torch.int16, device=dev) if with_ring else None
+    occ, ring = tw.tw_build_grid(grid, sc.robot, sc.tracks if tracks is None else tracks, law or sc.law,
+                                 static_occ=static, ring=ring)
+    torch.cuda.synchronize()
+    return occ, ring
+
+
+def _assert_raster_equal(sc, dev, law=None, tracks=None):
+    occ, ring = _gpu_grid(sc, dev, law, tracks)
+    occ_ref, ring_ref, _ = oracle.build_grid(sc, law=law, tracks=tracks)
+    o = occ.cpu().numpy()
+    diff = np.argwhere(o != occ_ref)
+    assert diff.size == 0, f"{len(diff)} cells differ, first {diff[:5]}"
+    assert np.array_equal(ring.cpu().numpy(), ring_ref)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# raster
+# ---------------------------------------------------------------------------
+
+def test_raster_static128(dev):
+    o = _assert_raster_equal(scenes.static128(), dev)
+    assert (o == tw.TW_STATIC).sum() > 1000
+
+
+@pytest.mark.parametrize("seed,frame", [(1001, 0), (1001, 50), (1011, 99), (1021, 10)])
+def test_raster_dynamic512(dev, seed, frame):
+    o = _assert_raster_equal(scenes.dynamic(seed=seed, side=512, n_obs=200, frames=frame + 1, frame=frame), dev)
+    assert (o == tw.TW_DYNAMIC).sum() > 1000
+
+
+@pytest.mark.parametrize("kind,mark,outer", [(scenes.RING_ELLIPTIC, scenes.MARK_PER_CELL, 0),
+                                             (scenes.RING_CIRCULAR, scenes.MARK_PER_OBSTACLE, 0),
+                                             (scenes.RING_ELLIPTIC, scenes.MARK_PER_OBSTACLE, 0),
+                                             (scenes.RING_CIRCULAR, scenes.MARK_PER_CELL, 1)])
+def test_raster_law_variants(dev, kind, mark, outer):
+    sc = scenes.dynamic(seed=1031, side=512, n_obs=60, frames=1, static_shapes=10)
+    law = scenes.RingLaw(kind=kind, mark=mark, time_outer=outer)
+    _assert_raster_equal(sc, dev, law=law)
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (3, 5), (5, 3), (17, 33), (33, 17), (1023, 3), (3, 1025),
+                                   (65, 1025), (97, 31)])
+def test_raster_odd_sizes(dev, nx, ny):
+    st = scenes.rng.Stream(nx * 1000 + ny)
+    cell = 0.05
+    static = (st.uniform(nx * ny).reshape(ny, nx) < 0.1).astype(np.uint8)
+    sc = scenes.Scene("odd", 0, nx, ny, cell, static_occ=static)
+    sc.robot = np.array([nx * cell * 0.3, ny * cell * 0.6, 0.6, 0.8, 0.75])
+    n = 25
+    pos = np.stack([st.uniform(n, -0.5, nx * cell + 0.5), st.uniform(n, -0.5, ny * cell + 0.5)], 1)
+    vel = np.stack([st.uniform(n, -1, 1), st.uniform(n, -1, 1)], 1)
+    tr = scenes.synth_tracks(st, pos, vel, st.uniform(n, 0.05, 0.3))
+    for law in (scenes.RingLaw(r0=0.1, growth=1.4), scenes.RingLaw(kind=scenes.RING_ELLIPTIC, r0=0.1)):
+        _assert_raster_equal(sc, dev, law=law, tracks=tr)
+
+
+def test_raster_batch_instances(dev):
+    for seed in (5000, 5001, 5002):
+        _assert_raster_equal(scenes.batch_instance(seed), dev)
+
+
+def test_raster_full_size_2048_with_tracks(dev):
+    sc = scenes.static2048()
+    st = scenes.rng.Stream(42)
+    n = 200
+    L = sc.nx * sc.cell
+    pos = np.stack([st.uniform(n, 0, L), st.uniform(n, 0, L)], 1)
+    ang = st.uniform(n, 0, 2 * np.pi)
+    spd = st.uniform(n, 0, 1)
+    tr = scenes.synth_tracks(st, pos, np.stack([spd * np.cos(ang), spd * np.sin(ang)], 1),
+                             st.uniform(n, 0.15, 0.5))
+    _assert_raster_equal(sc, dev, tracks=tr)
+
+
+def test_raster_empty_tracks_and_no_static(dev):
+    sc = scenes.Scene("empty", 0, 40, 30, 0.05, static_occ=None)
+    sc.robot = np.array([1.0, 0.7, 1.0, 0.0, 0.75])
+    occ, ring = _gpu_grid(sc, dev, tracks=np.zeros((0, 21)))
+    o = occ.cpu().numpy()
+    assert (o[1:-1, 1:-1] == 0).all() and (o[0] == 3).all() and (o[:, -1] == 3).all()
+    _, ring_ref, _ = oracle.build_grid(sc, tracks=np.zeros((0, 21)))
+    assert np.array_equal(ring.cpu().numpy(), ring_ref)
+
+
+# ---------------------------------------------------------------------------
+# field
+# ---------------------------------------------------------------------------
+
+def _relax(sc_or_occ, goal, dev, params, grid=None):
+    occ = sc_or_occ if isinstance(sc_or_occ, np.ndarray) else None
+    occ_t = torch.from_numpy(np.ascontiguousarray(occ)).to(dev)
+    ny, nx = occ.shape
+    grid = grid or tw.make_grid(nx, ny, 0.05)
+    u, stats = tw.hp_relax(grid, occ_t, goal, params=params)
+    torch.cuda.synchronize()
+    return u.cpu().numpy().astype(np.float64), stats
+
+
+@pytest.fixture(scope="module")
+def ref128():
+    sc = scenes.static128()
+    occ, _, _ = oracle.build_grid(sc)
+    u, fixed = oracle.solve_field(occ, sc.goal, tol=1e-14)
+    tau = oracle.exit_time(fixed)
+    return sc, occ, u, fixed, tau.max()
+
+
+def _np_residual(u, fixed):
+    a = np.zeros_like(u)
+    a[1:-1, 1:-1] = 0.25 * (((u[1:-1, 2:] + u[1:-1, :-2]) + u[2:, 1:-1]) + u[:-2, 1:-1])
+    r = np.abs(a - u)
+    r[fixed != 0] = 0
+    return r.max()
+
+
+@pytest.mark.parametrize("method", [tw.HP_JACOBI, tw.HP_RBSOR])
+def test_field_static128_at_tolerance(dev, ref128, method):
+    sc, occ, ustar, fixed, tau_max = ref128
+    u, st = _relax(occ, sc.goal, dev, tw.Params(method=method, tol=1e-6))
+    assert st["status"] == tw.TW_OK and st["resid_inf"] <= 1e-6
+    assert abs(_np_residual(u, fixed) - st["resid_inf"]) <= 1e-12
+    err = np.abs(u - ustar).max()
+    assert err <= tau_max * st["resid_inf"] * 1.001 + 1e-7, (err, tau_max, st)
+
+
+@pytest.mark.parametrize("method,omega", [(tw.HP_RBSOR, 0.0), (tw.HP_RBSOR, 1.0), (tw.HP_RBSOR, 1.9)])
+def test_field_static128_converged_within_1e5(dev, ref128, method, omega):
+    sc, occ, ustar, fixed, _ = ref128
+    u, st = _relax(occ, sc.goal, dev, tw.Params(method=method, omega=omega, tol=0.0, max_sweeps=20000))
+    err = np.abs(u - ustar).max()
+    assert err <= 1e-5, (err, st)
+    assert u.min() >= -1e-6 and u.max() <= 1.0
+
+
+def test_field_jacobi_plain_converged_within_1e5(dev, ref128):
+    sc, occ, ustar, fixed, _ = ref128
+    u, st = _relax(occ, sc.goal, dev, tw.Params(method=tw.HP_JACOBI, tol=0.0, max_sweeps=60000))
+    assert np.abs(u - ustar).max() <= 1e-5
+
+
+def test_field_dynamic512(dev):
+    sc = scenes.dynamic512()
+    occ, _, _ = oracle.build_grid(sc)
+    free = np.argwhere(occ == 0)
+    d = np.hypot(free[:, 1] - sc.goal[0], free[:, 0] - sc.goal[1])
+    gy, gx = free[np.argmin(d)]
+    ustar, fixed = oracle.solve_field(occ, (gx, gy), tol=1e-13)
+    tau_max = oracle.exit_time(fixed).max()
+    u, st = _relax(occ, (int(gx), int(gy)), dev, tw.Params(method=tw.HP_RBSOR, tol=1e-6))
+    assert st["resid_inf"] <= 1e-6
+    assert np.abs(u - ustar).max() <= tau_max * st["resid_inf"] * 1.001 + 1e-7
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (4, 3), (3, 5), (5, 4), (17, 33), (33, 17), (1025, 5), (6, 301)])
+def test_field_odd_sizes(dev, nx, ny):
+    occ = np.zeros((ny, nx), np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+    rng = np.random.default_rng(nx * 7 + ny)
+    inner = occ[1:-1, 1:-1]
+    inner[rng.random(inner.shape) < 0.1] = 1
+    goal = (1 + (nx - 2) // 2, 1 + (ny - 2) // 2)
+    occ[goal[1], goal[0]] = 0
+    ustar, fixed = oracle.solve_field(occ, goal, tol=1e-15)
+    for method in (tw.HP_JACOBI, tw.HP_RBSOR):
+        u, st = _relax(occ, goal, dev, tw.Params(method=method, tol=0.0, max_sweeps=40000))
+        assert np.abs(u - ustar).max() <= 1e-5, (method, nx, ny)
+
+
+def test_dirichlet_closed_form_on_gpu(dev):
+    nx, ny = 61, 45
+    jj, ii = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    exact = 0.5 + ((ii - 30) ** 2 - (jj - 22) ** 2) / 2000.0   # discrete-harmonic, in [0, 1]
+    fixed = np.zeros((ny, nx), np.uint8)
+    fixed[0, :] = fixed[-1, :] = fixed[:, 0] = fixed[:, -1] = 1
+    fixed[20:25, 10:14] = 1                                   # an interior Dirichlet block
+    u0 = np.where(fixed == 1, exact, 0.5).astype(np.float32)
+    for method in (tw.HP_JACOBI, tw.HP_RBSOR):
+        u = torch.from_numpy(u0.copy()).to(dev)
+        f = torch.from_numpy(fixed).to(dev)
+        u, st = tw.hp_relax_dirichlet(f, u, tw.Params(method=method, tol=0.0, max_sweeps=30000))
+        assert np.abs(u.cpu().numpy() - exact).max() <= 1e-5
+        r_inf, _ = tw.hp_residual(f, u)
+        assert r_inf <= 1e-6
+
+
+def test_warm_start_and_phi_output(dev, ref128):
+    sc, occ, ustar, fixed, tau_max = ref128
+    occ_t = torch.from_numpy(occ).to(dev)
+    grid = tw.make_grid(sc.nx, sc.ny, sc.cell)
+    u, st1 = tw.hp_relax(grid, occ_t, sc.goal, params=tw.Params(tol=1e-4))
+    u2, st2 = tw.hp_relax(grid, occ_t, sc.goal, field=u.clone(),
+                          params=tw.Params(tol=1e-6, flags=tw.HP_WARM_START))
+    _, st3 = tw.hp_relax(grid, occ_t, sc.goal, params=tw.Params(tol=1e-6))
+    assert st2["sweeps"] < st3["sweeps"]
+    phi, st4 = tw.hp_relax(grid, occ_t, sc.goal, params=tw.Params(tol=1e-6, flags=tw.HP_OUT_PHI))
+    p = phi.cpu().numpy().astype(np.float64)
+    assert np.abs((1.0 - p) - ustar).max() <= tau_max * st4["resid_inf"] * 1.001 + 1e-6
+    assert p[sc.goal[1], sc.goal[0]] == 0.0 and p[0, 0] == 1.0
+
+
+def test_goal_blocked_errors(dev, ref128):
+    sc, occ, *_ = ref128
+    occ_t = torch.from_numpy(occ).to(dev)
+    grid = tw.make_grid(sc.nx, sc.ny, sc.cell)
+    blocked = tuple(int(v) for v in np.argwhere(occ == 1)[0][::-1])
+    with pytest.raises(tw.TwError) as e:
+        tw.hp_relax(grid, occ_t, blocked)
+    assert e.value.status == tw.TW_EGOAL_BLOCKED
+
+
+def test_not_converged_status(dev, ref128):
+    sc, occ, *_ = ref128
+    u, st = _relax(occ, sc.goal, dev, tw.Params(tol=1e-9, max_sweeps=10))
+    assert st["status"] == tw.TW_NOT_CONVERGED and st["sweeps"] == 10
+
+
+@pytest.mark.slow
+def test_field_full_size_2048(dev):
+    sc = scenes.static2048()
+    occ, _, _ = oracle.build_grid(sc)
+    u, st = _relax(occ, sc.goal, dev, tw.Params(method=tw.HP_RBSOR, tol=1e-6))
+    assert st["status"] == tw.TW_OK and st["resid_inf"] <= 1e-6
+    _, fixed = oracle.dirichlet_from_occ(occ, sc.goal)
+    assert _np_residual(u, fixed) <= 1e-6
+    assert u.min() >= -1e-5 and u.max() <= 1.0
+    ustar, _ = oracle.solve_field(occ, sc.goal, tol=1e-12)
+    tau_max = oracle.exit_time(fixed, tol=1e-6).max()
+    err = np.abs(u - ustar).max()
+    assert err <= tau_max * st["resid_inf"] * 1.01 + 1e-6, (err, tau_max, st)
+
+
+# ---------------------------------------------------------------------------
+# path
+# ---------------------------------------------------------------------------
+
+def _hausdorff(a, b):
+    a = a.astype(np.float64)
+    b = b.astype(np.float64)
+    d = np.hypot(a[:, None, 0] - b[None, :, 0], a[:, None, 1] - b[None, :, 1])
+    return max(d.min(1).max(), d.min(0).max())
+
+
+@pytest.fixture(scope="module")
+def polished128():
+    sc = scenes.static128()
+    occ, _, _ = oracle.build_grid(sc)
+    u, fixed = oracle.solve_field(occ, sc.goal, tol=1e-14)
+    u, _, _, _ = oracle.gauss_seidel(u, fixed, tol=0.0, max_sweeps=20000)
+    return sc, occ, u, fixed
+
+
+@pytest.mark.parametrize("rubber", [0, 100])
+def test_path_static128(dev, polished128, rubber):
+    sc, occ, uref, fixed = polished128
+    occ_t = torch.from_numpy(occ).to(dev)
+    grid = tw.make_grid(sc.nx, sc.ny, sc.cell)
+    # red-black Gauss-Seidel (omega = 1) keeps tiny far-field values relatively accurate
+    u, st = tw.hp_relax(grid, occ_t, sc.goal, params=tw.Params(omega=1.0, tol=0.0, max_sweeps=30000))
+    status, path = tw.plan_path(grid, u, occ_t, sc.start, sc.goal, rubber_iters=rubber)
+    ost, opath = oracle.plan_path(uref, fixed, sc.start, sc.goal, rubber_iters=rubber)
+    assert ost == oracle.OK and status == tw.TW_OK
+    assert tuple(path[0]) == sc.start and tuple(path[-1]) == sc.goal
+    assert (occ[path[:, 1], path[:, 0]] == 0).all()
+    step = np.abs(np.diff(path, axis=0)).max(1)
+    assert (step == 1).all()
+    if rubber == 0:
+        uu = u.cpu().numpy()[path[:, 1], path[:, 0]]
+        assert (np.diff(uu) > 0).all()
+    assert _hausdorff(path, opath) <= 2.0
+
+
+def test_path_errors(dev):
+    n = 40
+    occ = np.zeros((n, n), np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+    occ[10:20, 10] = occ[10:20, 19] = occ[10, 10:20] = occ[19, 10:20] = 1
+    occ_t = torch.from_numpy(occ).to(dev)
+    grid = tw.make_grid(n, n, 0.05)
+    u, _ = tw.hp_relax(grid, occ_t, (15, 15), params=tw.Params(tol=1e-7))
+    st, _ = tw.plan_path(grid, u, occ_t, (30, 30), (15, 15))
+    assert st == tw.TW_NO_PATH
+    st, _ = tw.plan_path(grid, u, occ_t, (10, 12), (15, 15))
+    assert st == tw.TW_ESTART_BLOCKED
+    st, p = tw.plan_path(grid, u, occ_t, (15, 15), (15, 15))
+    assert st == tw.TW_OK and len(p) == 1
+
+
+def test_end_to_end_planner_frame(dev):
+    """Raster -> relaxation -> path on one frame, all through the C ABI."""
+    sc = scenes.dynamic(seed=1041, side=256, n_obs=16, frames=1, static_shapes=12)
+    occ, _ = _gpu_grid(sc, dev, with_ring=False)
+    occ_ref, _, _ = oracle.build_grid(sc)
+    assert np.array_equal(occ.cpu().numpy(), occ_ref)
+    grid = tw.make_grid(sc.nx, sc.ny, sc.cell)
+    if occ_ref[sc.goal[1], sc.goal[0]] != 0:
+        pytest.skip("goal covered by a prediction in this frame")
+    u, st = tw.hp_relax(grid, occ, sc.goal, params=tw.Params(omega=1.0, tol=0.0, max_sweeps=40000))
+    status, path = tw.plan_path(grid, u, occ, sc.start, sc.goal, rubber_iters=50)
+    uref, fixed = oracle.solve_field(occ_ref, sc.goal, tol=1e-14)
+    uref, _, _, _ = oracle.gauss_seidel(uref, fixed, tol=0.0, max_sweeps=20000)
+    ost, opath = oracle.plan_path(uref, fixed, sc.start, sc.goal, rubber_iters=50)
+    assert status == ost
+    if status == tw.TW_OK:
+        assert (occ_ref[path[:, 1], path[:, 0]] == 0).all()
+        assert _hausdorff(path, opath) <= 2.0
