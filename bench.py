@@ -82,6 +82,12 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi's start-up (NVML init) stalls the GPU context: let it
+            # finish and deliver a first sample before the timed region opens
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.05)
+            time.sleep(0.3)
         except OSError:
             self.proc = None
         return self

@@ -332,8 +332,10 @@ static int relax_jacobi(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
 // Red-black SOR driver on the split layout (pack -> sweeps -> unpack).
 int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
              cudaStream_t s) {
-    int K = p->check_every > 0 ? p->check_every : 32;
     int T = p->tblock > 0 ? p->tblock : kDefaultTBlock;
+    if (T > 4) T = 4;
+    int K = p->check_every > 0 ? p->check_every : 32;
+    if (T > 1 && K % T) K += T - K % T;   // whole launches per check interval
     bool adapt = p->omega == 0.0;
     double omega = adapt ? sor_initial_omega(nx, ny) : p->omega;
     int sweeps = 0, checks = 0, launches = 0;
@@ -350,7 +352,7 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
         if (e) return e;
         timer.accumulate();
         sweeps += n;
-        if (p->tol > 0.0 || adapt) {
+        if (p->tol > 0.0 || adapt || p->omega == 0.0) {
             TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
             dim3 b(64, 4), gr(ceil_div(L.W4, 64), ceil_div(ny, 4));
             TW_LAUNCH(rb_residual_kernel, gr, b, 0, s, L, ny, &scal->max32);
@@ -361,15 +363,23 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
             checks++;
             double r = rf;
             if (p->tol > 0.0 && r <= p->tol) { st->status = TW_OK; break; }
-            if (adapt) {
+            // Stagnation over a whole interval means the FP32 rounding floor,
+            // which over-relaxation amplifies by ~omega / (2 - omega): halve the
+            // over-relaxation and stop adapting upwards.
+            if (r_prev > 0.0 && n == K && r > 0.8 * r_prev && omega > 1.0) {
+                omega = 1.0 + 0.5 * (omega - 1.0);
+                if (omega < 1.05) omega = 1.0;
+                adapt = false;
+                same_omega_intervals = 0;
+            } else if (adapt) {
                 if (r_prev > 0.0 && same_omega_intervals >= 1 && n == K) {
                     double lambda = pow(r / r_prev, 1.0 / n);
                     double w = sor_adapt(omega, lambda);
                     if (w > omega + 1e-4) { omega = w; same_omega_intervals = -1; }
                 }
                 same_omega_intervals++;
-                r_prev = r;
             }
+            r_prev = r;
         }
     }
     st->sweeps = sweeps;

@@ -219,6 +219,26 @@ def test_dirichlet_closed_form_on_gpu(dev):
         assert r_inf <= 1e-6
 
 
+@pytest.mark.parametrize("tblock", [1, 2, 3, 4])
+def test_temporal_blocking_matches_unfused_sweeps(dev, tblock):
+    """T fused sweeps per launch equal T separate red-black sweeps (same omega)."""
+    for nx, ny in ((128, 128), (301, 97), (1030, 67), (67, 1030)):
+        occ = np.zeros((ny, nx), np.uint8)
+        occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+        rng = np.random.default_rng(nx + 3 * ny)
+        inner = occ[1:-1, 1:-1]
+        inner[rng.random(inner.shape) < 0.2] = 1
+        goal = (nx // 2, ny // 2)
+        occ[goal[1], goal[0]] = 0
+        outs = []
+        for tb in (1, tblock):
+            u, st = _relax(occ, goal, dev, tw.Params(method=tw.HP_RBSOR, omega=1.7, tol=0.0, max_sweeps=37,
+                                                     tblock=tb, check_every=12))
+            assert st["sweeps"] == 37
+            outs.append(u)
+        assert np.abs(outs[0] - outs[1]).max() <= 2e-7, (nx, ny, tblock)
+
+
 def test_warm_start_and_phi_output(dev, ref128):
     sc, occ, ustar, fixed, tau_max = ref128
     occ_t = torch.from_numpy(occ).to(dev)
