@@ -363,10 +363,12 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
             checks++;
             double r = rf;
             if (p->tol > 0.0 && r <= p->tol) { st->status = TW_OK; break; }
-            // Stagnation over a whole interval means the FP32 rounding floor,
-            // which over-relaxation amplifies by ~omega / (2 - omega): halve the
-            // over-relaxation and stop adapting upwards.
-            if (r_prev > 0.0 && n == K && r > 0.8 * r_prev && omega > 1.0) {
+            // Stagnation over a whole interval close to the tolerance means the
+            // FP32 rounding floor, which over-relaxation amplifies by about
+            // omega / (2 - omega): halve the over-relaxation and stop adapting
+            // upwards.  (Far from the tolerance the max-norm can plateau while
+            // the iteration still converges, so it is left alone there.)
+            if (r_prev > 0.0 && n == K && r > 0.8 * r_prev && r < 16.0 * p->tol && omega > 1.0) {
                 omega = 1.0 + 0.5 * (omega - 1.0);
                 if (omega < 1.05) omega = 1.0;
                 adapt = false;
