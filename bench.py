@@ -177,16 +177,24 @@ def run_twgrid(args, rank, world, dist):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = tw.launch_count()
     barrier()
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    host_ms = []
     with ClockSampler(dev.index) as clk:
         ev0.record(stream)
         t0 = time.perf_counter()
         for i in range(args.steps):
             if i:
                 flush.zero_()
+            h0 = time.perf_counter()
+            step_ev[i][0].record(stream)
             step(static_d)
+            step_ev[i][1].record(stream)
+            host_ms.append((time.perf_counter() - h0) * 1e3)
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
     launches = tw.launch_count() - launches0   # library kernels only (not the L2-flush memsets)
     dev_s = ev0.elapsed_time(ev1) / 1e3
     elapsed = max(dev_s, 1e-12)
@@ -278,6 +286,8 @@ def run_twgrid(args, rank, world, dist):
            "path_status": sorted(set(path_status)), "path_len": [n for _, _, n in stats_log][:1],
            "omega": stats_log[0][0]["omega"] if stats_log else None,
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain,
+           "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "min": min(step_ms), "max": max(step_ms), "host_p50": float(np.percentile(host_ms, 50))},
            "wall_s": wall, "clocks": clk.summary()}
     return out
 
