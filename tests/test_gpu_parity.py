@@ -210,13 +210,20 @@ def test_dirichlet_closed_form_on_gpu(dev):
     fixed[0, :] = fixed[-1, :] = fixed[:, 0] = fixed[:, -1] = 1
     fixed[20:25, 10:14] = 1                                   # an interior Dirichlet block
     u0 = np.where(fixed == 1, exact, 0.5).astype(np.float32)
-    for method in (tw.HP_JACOBI, tw.HP_RBSOR):
+    f = torch.from_numpy(fixed).to(dev)
+    # converged to the FP32 floor: Jacobi and red-black Gauss-Seidel round each
+    # update once (floor ~ 1 ulp); over-relaxation amplifies the rounding noise
+    # by ~omega / (2 - omega), so at omega = 1.9 only the field error is checked
+    for method, omega, r_max in ((tw.HP_JACOBI, 0.0, 1e-6), (tw.HP_RBSOR, 1.0, 1e-6), (tw.HP_RBSOR, 1.9, None)):
         u = torch.from_numpy(u0.copy()).to(dev)
-        f = torch.from_numpy(fixed).to(dev)
-        u, st = tw.hp_relax_dirichlet(f, u, tw.Params(method=method, tol=0.0, max_sweeps=30000))
-        assert np.abs(u.cpu().numpy() - exact).max() <= 1e-5
+        u, st = tw.hp_relax_dirichlet(f, u, tw.Params(method=method, omega=omega, tol=0.0, max_sweeps=30000))
+        assert np.abs(u.cpu().numpy() - exact).max() <= 1e-5, (method, omega)
         r_inf, _ = tw.hp_residual(f, u)
-        assert r_inf <= 1e-6
+        assert r_max is None or r_inf <= r_max, (method, omega, r_inf)
+    # adaptive SOR with a tolerance below its over-relaxed floor backs off and reaches it
+    u = torch.from_numpy(u0.copy()).to(dev)
+    u, st = tw.hp_relax_dirichlet(f, u, tw.Params(method=tw.HP_RBSOR, tol=3e-7, max_sweeps=30000))
+    assert st["status"] == tw.TW_OK and st["resid_inf"] <= 3e-7, st
 
 
 @pytest.mark.parametrize("tblock", [1, 2, 3, 4])
