@@ -174,6 +174,29 @@ int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *fi
              const hp_params *p, hp_stats *stats, void *workspace, size_t workspace_bytes,
              void *stream);
 
+/* hp_relax_noalloc: hp_relax without a caller workspace, for callers that
+ * cannot allocate device memory -- e.g. a real-time control loop that may not
+ * allocate after start-up (cudaMalloc can synchronise the device and take
+ * unbounded time) or a plug-in inside a host application that owns every
+ * device allocation.  The paper has no counterpart; this is a library
+ * convenience.  Its scratch is one file-scope device array of
+ * HP_RELAX_NOALLOC_SCRATCH_BYTES (9 MiB), held by every GPU that loads the
+ * library until the process exits; the call itself allocates nothing.
+ * Same arguments and results as hp_relax (occ_dev and field_dev are still the
+ * caller's), for method HP_RBSOR or HP_JACOBI without HP_TIMING.
+ * Limits: grids whose hp_relax_workspace_size() exceeds the array (for
+ * HP_RBSOR anything above about 1024 x 1024 cells) return TW_EWORKSPACE
+ * before any GPU work; other methods or HP_TIMING return TW_EINVAL.
+ * Set-up: the first call on a device, with that device current, looks up the
+ * array's device address once and caches it; make that first call before any
+ * stream capture.  All calls on a device share the array and it keeps the
+ * previous call's contents (each call clears what must start at zero), so
+ * calls whose GPU work overlaps -- on different streams or host threads --
+ * race and must be serialised by the caller. */
+#define HP_RELAX_NOALLOC_SCRATCH_BYTES ((size_t)9 << 20)
+int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *field_dev,
+                     const hp_params *p, hp_stats *stats, void *stream);
+
 /* hp_relax_dirichlet: the same solver on a general Dirichlet problem: cells
  * with fixed_dev != 0 keep their value of u_dev, the others satisfy the
  * discrete Laplace equation.  Every border cell must be fixed.  u_dev is read

@@ -31,7 +31,7 @@ HP_WARM_START, HP_OUT_PHI, HP_TIMING = 1, 2, 4
 
 EXPORTS = (
     "tw_build_grid_workspace_size", "tw_build_grid", "tw_ring_count",
-    "hp_relax_workspace_size", "hp_relax", "hp_relax_dirichlet", "hp_residual",
+    "hp_relax_workspace_size", "hp_relax", "hp_relax_noalloc", "hp_relax_dirichlet", "hp_residual",
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
     "kf_update", "kf_init", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
 )
@@ -124,6 +124,8 @@ def load() -> ctypes.CDLL:
     lib.hp_relax_workspace_size.restype = Z
     lib.hp_relax.argtypes = [P, P, I, I, P, P, P, P, Z, P]
     lib.hp_relax.restype = I
+    lib.hp_relax_noalloc.argtypes = [P, P, I, I, P, P, P, P]
+    lib.hp_relax_noalloc.restype = I
     lib.hp_relax_dirichlet.argtypes = [I, I, P, P, P, P, P, Z, P]
     lib.hp_relax_dirichlet.restype = I
     lib.hp_residual.argtypes = [I, I, P, P, P, P, P, Z, P]
@@ -254,6 +256,20 @@ def hp_relax(grid: tw_grid, occ, goal, field=None, params: Optional[Params] = No
     st = lib.hp_relax(ctypes.byref(grid), _ptr(occ), int(goal[0]), int(goal[1]), _ptr(field),
                       ctypes.byref(cp), ctypes.byref(stats), _ptr(ws), ws.numel(), _stream(occ.device))
     _check("hp_relax", st, ok=(TW_OK, TW_NOT_CONVERGED))
+    return field, stats.as_dict()
+
+
+def hp_relax_noalloc(grid: tw_grid, occ, goal, field=None, params: Optional[Params] = None):
+    """hp_relax on the library's static scratch array (no workspace; see the C header)."""
+    torch = _torch()
+    params = params or Params()
+    if field is None:
+        field = torch.empty((grid.ny, grid.nx), dtype=torch.float32, device=occ.device)
+    cp = params.c()
+    stats = hp_stats()
+    st = load().hp_relax_noalloc(ctypes.byref(grid), _ptr(occ), int(goal[0]), int(goal[1]), _ptr(field),
+                                 ctypes.byref(cp), ctypes.byref(stats), _stream(occ.device))
+    _check("hp_relax_noalloc", st, ok=(TW_OK, TW_NOT_CONVERGED))
     return field, stats.as_dict()
 
 
