@@ -126,7 +126,27 @@ class ClockSampler:
 
 
 def make_scene(rank: int):
-    return scenes.static2048(seed=1002 + 100 * rank)
+    """Each rank solves its own scene (weak scaling, no data exchanged)."""
+    return scenes.static2048(seed=scene_seed(rank))
+
+
+def scene_seed(rank: int) -> int:
+    return 1002 + 100 * rank
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """Max of a per-rank scalar (the elapsed time) over all ranks; identity without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(steps: int, world: int, elapsed_max: float) -> float:
+    """Whole-job solves/s: the units all ranks processed over the slowest rank's time."""
+    return steps * world / elapsed_max
 
 
 # ---------------------------------------------------------------------------
@@ -197,11 +217,7 @@ def run_twgrid(args, rank, world, dist):
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     launches = tw.launch_count() - launches0   # library kernels only (not the L2-flush memsets)
     dev_s = ev0.elapsed_time(ev1) / 1e3
-    elapsed = max(dev_s, 1e-12)
-    if dist is not None:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(max(dev_s, 1e-12), dist, dev)
     sweeps = [s["sweeps"] for s, _, _ in stats_log]
     resid = [s["resid_inf"] for s, _, _ in stats_log]
     sweep_ms = sum(s["sweep_ms"] for s, _, _ in stats_log)
@@ -209,7 +225,7 @@ def run_twgrid(args, rank, world, dist):
     status = [s["status"] for s, _, _ in stats_log]
     path_status = [p for _, p, _ in stats_log]
     cells = sc.nx * sc.ny
-    value = args.steps * world / elapsed
+    value = throughput(args.steps, world, elapsed)
     cups = sum(sweeps) * cells * world / elapsed
 
     # ---- roofline of the dominant kernel (sweep), live CUDA-event launch times
@@ -243,12 +259,8 @@ def run_twgrid(args, rank, world, dist):
         d2h += u_h.numel() * 4 + path.nbytes
     ev1.record(stream)
     torch.cuda.synchronize()
-    e_el = ev0.elapsed_time(ev1) / 1e3
-    if dist is not None:
-        t = torch.tensor([e_el], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_el = float(t.item())
-    e2e = {"value": args.steps * world / e_el, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+    e_el = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
+    e2e = {"value": throughput(args.steps, world, e_el), "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
            "d2h_bytes_per_step": d2h // args.steps, "wall_s": time.perf_counter() - e0}
 
     # ---- plain FP32 Jacobi on the same scene (the comparison form)
