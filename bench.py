@@ -64,7 +64,13 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms.
+
+    Start it before the warm-up: nvidia-smi's start-up (NVML initialisation)
+    can stall the GPU context for a long time, so it must be over before the
+    timed region opens.  mark_start()/mark_end() bracket the timed region and
+    summary() keeps only the samples that arrived inside it (plus one period).
+    """
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -73,30 +79,36 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (arrival time, text)
+        self.t0 = self.t1 = None
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                           "-lms", "200", "-i", str(self.idx)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
-            # nvidia-smi's start-up (NVML init) stalls the GPU context: let it
-            # finish and deliver a first sample before the timed region opens
-            t0 = time.time()
-            while not self.lines and time.time() - t0 < 5.0:
-                time.sleep(0.05)
-            time.sleep(0.3)
         except OSError:
             self.proc = None
         return self
 
+    def wait_ready(self, timeout=10.0):
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.05)
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def __exit__(self, *a):
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -107,7 +119,11 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo = self.t0 if self.t0 is not None else 0.0
+        hi = (self.t1 if self.t1 is not None else time.time()) + 0.25
+        for ts, ln in list(self.lines):
+            if ts < lo or ts > hi:
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -187,6 +203,8 @@ def run_twgrid(args, rank, world, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
+    clk = ClockSampler(dev.index).start()
+    clk.wait_ready()
     for _ in range(args.warmup):
         step(static_d)
     stats_log.clear()
@@ -200,20 +218,23 @@ def run_twgrid(args, rank, world, dist):
     step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
     host_ms = []
-    with ClockSampler(dev.index) as clk:
-        ev0.record(stream)
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            if i:
-                flush.zero_()
-            h0 = time.perf_counter()
-            step_ev[i][0].record(stream)
-            step(static_d)
-            step_ev[i][1].record(stream)
-            host_ms.append((time.perf_counter() - h0) * 1e3)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+    clk.mark_start()
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        if i:
+            flush.zero_()
+        h0 = time.perf_counter()
+        step_ev[i][0].record(stream)
+        step(static_d)
+        step_ev[i][1].record(stream)
+        host_ms.append((time.perf_counter() - h0) * 1e3)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk.mark_end()
+    clocks = clk.summary()
+    clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     launches = tw.launch_count() - launches0   # library kernels only (not the L2-flush memsets)
     dev_s = ev0.elapsed_time(ev1) / 1e3
@@ -300,7 +321,7 @@ def run_twgrid(args, rank, world, dist):
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain,
            "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": min(step_ms), "max": max(step_ms), "host_p50": float(np.percentile(host_ms, 50))},
-           "wall_s": wall, "clocks": clk.summary()}
+           "wall_s": wall, "clocks": clocks}
     return out
 
 
