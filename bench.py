@@ -64,43 +64,88 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms.
+    """SM clocks and throttle reasons sampled during the timed region.
 
-    Start it before the warm-up: nvidia-smi's start-up (NVML initialisation)
-    can stall the GPU context for a long time, so it must be over before the
-    timed region opens.  mark_start()/mark_end() bracket the timed region and
-    summary() keeps only the samples that arrived inside it (plus one period).
+    Reads NVML in-process (libnvidia-ml through ctypes, on a helper thread)
+    so no extra process competes for the driver; falls back to nvidia-smi
+    when NVML cannot be loaded.  Start it before the warm-up (initialisation
+    can stall the GPU context); mark_start()/mark_end() bracket the timed
+    region and summary() keeps the samples taken inside it, widened by one
+    sampling period on each side.
     """
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clocks-event-reason bits
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+               "hw_thermal_slowdown": 0x40}
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period=0.1, mode=None):
         self.idx = gpu_index
+        self.period = period
+        self.mode = mode or os.environ.get("TWGRID_CLOCK_SAMPLER", "nvml")
         self.proc = None
-        self.lines = []          # (arrival time, text)
+        self.samples = []        # (time, sm_mhz, sm_max_mhz, set of reasons)
         self.t0 = self.t1 = None
+        self._stop = False
 
     def start(self):
+        if self.mode == "nvml" and self._start_nvml():
+            return self
+        self.mode = "nvidia-smi"
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.idx)],
+                                          "-lms", str(int(self.period * 1000)), "-i", str(self.idx)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read_smi, daemon=True).start()
         except OSError:
             self.proc = None
         return self
 
+    def _start_nvml(self):
+        import ctypes
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.idx), ctypes.byref(h)) != 0:
+                return False
+        except OSError:
+            return False
+        self.nv, self.h = nv, h
+        threading.Thread(target=self._read_nvml, daemon=True).start()
+        return True
+
+    def _read_nvml(self):
+        import ctypes
+        cur, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop:
+            ok = (self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(cur)) == 0 and
+                  self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 and
+                  self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(rs)) == 0)
+            if ok:
+                act = {n for n, b in self.REASONS.items() if rs.value & b}
+                self.samples.append((time.time(), float(cur.value), float(mx.value), act))
+            time.sleep(self.period)
+
+    def _read_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                act = {n for n, v in zip(names, parts[5:9]) if v.lower().startswith("active")}
+                self.samples.append((time.time(), float(parts[1]), float(parts[2]), act))
+            except ValueError:
+                continue
+
     def wait_ready(self, timeout=10.0):
         t0 = time.time()
-        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
-            time.sleep(0.05)
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append((time.time(), line.strip()))
+        while not self.samples and time.time() - t0 < timeout and (self.mode == "nvml" or self.proc):
+            time.sleep(0.02)
 
     def mark_start(self):
         self.t0 = time.time()
@@ -109,6 +154,7 @@ class ClockSampler:
         self.t1 = time.time()
 
     def stop(self):
+        self._stop = True
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -117,28 +163,14 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        lo = self.t0 if self.t0 is not None else 0.0
-        hi = (self.t1 if self.t1 is not None else time.time()) + 0.25
-        for ts, ln in list(self.lines):
-            if ts < lo or ts > hi:
-                continue
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        lo = (self.t0 if self.t0 is not None else 0.0) - self.period
+        hi = (self.t1 if self.t1 is not None else time.time()) + self.period
+        sel = [s for s in list(self.samples) if lo <= s[0] <= hi]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": self.mode}
+        reasons = set().union(*[s[3] for s in sel])
+        return {"sm_mhz": statistics.median(s[1] for s in sel), "sm_max_mhz": max(s[2] for s in sel),
+                "reasons": sorted(reasons), "samples": len(sel), "source": self.mode}
 
 
 def make_scene(rank: int):
@@ -186,14 +218,17 @@ def run_twgrid(args, rank, world, dist):
     u_h = torch.empty((sc.ny, sc.nx), dtype=torch.float32).pin_memory()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     method = {"rbsor": tw.HP_RBSOR, "jacobi": tw.HP_JACOBI, "mixed": tw.HP_MIXED}[args.method]
-    params = tw.Params(method=method, tol=args.tol, max_sweeps=args.max_sweeps, flags=tw.HP_TIMING,
+    params = tw.Params(method=method, tol=args.tol, max_sweeps=args.max_sweeps,
                        tblock=args.tblock, storage={"f16": 1, "bf16": 2, "f32": 0}[args.storage])
+    # the same solve with the host-driven loop and CUDA events around every batch of sweep launches
+    params_timed = tw.Params(method=method, tol=args.tol, max_sweeps=args.max_sweeps, flags=tw.HP_TIMING,
+                             tblock=args.tblock, storage=params.storage)
     max_len = 4 * (sc.nx + sc.ny) * 4
     stats_log = []
 
-    def step(static_src):
+    def step(static_src, prm=None):
         tw.tw_build_grid(grid, sc.robot, sc.tracks, sc.law, static_occ=static_src, occ=occ)
-        _, st = tw.hp_relax(grid, occ, sc.goal, field=u, params=params)
+        _, st = tw.hp_relax(grid, occ, sc.goal, field=u, params=prm or params)
         pst, path = tw.plan_path(grid, u, occ, sc.start, sc.goal, rubber_iters=100, max_len=max_len)
         stats_log.append((st, pst, len(path)))
         return path
@@ -205,8 +240,14 @@ def run_twgrid(args, rank, world, dist):
 
     clk = ClockSampler(dev.index).start()
     clk.wait_ready()
-    for _ in range(args.warmup):
+    # at least W warm-up steps and at least one second of them: a GPU coming out
+    # of idle needs that long to reach its steady clocks
+    tw0 = time.perf_counter()
+    n_warm = 0
+    while n_warm < args.warmup or time.perf_counter() - tw0 < args.warmup_seconds:
         step(static_d)
+        torch.cuda.synchronize()
+        n_warm += 1
     stats_log.clear()
     torch.cuda.synchronize()
 
@@ -241,10 +282,22 @@ def run_twgrid(args, rank, world, dist):
     elapsed = max_over_ranks(max(dev_s, 1e-12), dist, dev)
     sweeps = [s["sweeps"] for s, _, _ in stats_log]
     resid = [s["resid_inf"] for s, _, _ in stats_log]
-    sweep_ms = sum(s["sweep_ms"] for s, _, _ in stats_log)
-    sweep_launches = sum(s["sweep_launches"] for s, _, _ in stats_log)
     status = [s["status"] for s, _, _ in stats_log]
     path_status = [p for _, p, _ in stats_log]
+    timed_log = list(stats_log)
+    # sweep-kernel launch durations: the same steps again with HP_TIMING (CUDA events
+    # on the launching stream around each batch of sweep launches, host-driven loop)
+    stats_log.clear()
+    n_roof = max(3, min(args.steps, 10))
+    for i in range(n_roof):
+        if i:
+            flush.zero_()
+        step(static_d, params_timed)
+    torch.cuda.synchronize()
+    sweep_ms = sum(s["sweep_ms"] for s, _, _ in stats_log)
+    sweep_launches = sum(s["sweep_launches"] for s, _, _ in stats_log)
+    roof_sweeps = sum(s["sweeps"] for s, _, _ in stats_log)
+    stats_log[:] = timed_log
     cells = sc.nx * sc.ny
     value = throughput(args.steps, world, elapsed)
     cups = sum(sweeps) * cells * world / elapsed
@@ -252,7 +305,7 @@ def run_twgrid(args, rank, world, dist):
     # ---- roofline of the dominant kernel (sweep), live CUDA-event launch times
     hbm, peak_kind = peaks()
     avg_launch_s = sweep_ms / 1e3 / max(sweep_launches, 1)
-    sweeps_per_launch = sum(sweeps) / max(sweep_launches, 1)
+    sweeps_per_launch = roof_sweeps / max(sweep_launches, 1)
     bytes_per_launch = cells * (2 * STORAGE_BYTES + MASK_BYTES) * min(1.0, sweeps_per_launch)
     achieved = bytes_per_launch / avg_launch_s / 1e9
     src = os.path.join(ROOT, "paper_1903_07441_gb300", "csrc", "hp_sweeps.cu")
@@ -262,7 +315,10 @@ def run_twgrid(args, rank, world, dist):
                 "peak": hbm, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": avg_launch_s * 1e6, "sweeps_per_launch": sweeps_per_launch,
-                "effective_cell_updates_per_s": cells * sweeps_per_launch / avg_launch_s}
+                "effective_cell_updates_per_s": cells * sweeps_per_launch / avg_launch_s,
+                "timing": f"CUDA events on the launching stream around the sweep launches of {n_roof} "
+                          "further steps of the same workload run with the host-driven loop (HP_TIMING); "
+                          "the timed steps above use the graph-driven loop"}
 
     # ---- end to end through the C ABI with host buffers
     stats_log.clear()
@@ -386,8 +442,9 @@ def run_reference(args, rank, world, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup-seconds", type=float, default=1.0)
     ap.add_argument("--impl", default="twgrid", choices=["twgrid", "reference"])
     ap.add_argument("--method", default="rbsor", choices=["rbsor", "jacobi", "mixed"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])

@@ -129,7 +129,11 @@ int tw_ring_count(const tw_grid *g, const tw_pose *robot, const tw_ring_law *law
 
 #define HP_WARM_START 1    /* field_dev holds the initial guess (same representation as output) */
 #define HP_OUT_PHI 2       /* write phi instead of u = 1 - phi */
-#define HP_TIMING 4        /* time the sweep kernels with CUDA events on `stream` (stats.sweep_ms) */
+#define HP_TIMING 4        /* time the sweep kernels with CUDA events on `stream` (stats.sweep_ms);
+                              implies HP_HOST_LOOP */
+#define HP_HOST_LOOP 8     /* drive the convergence loop from the host (one stream synchronisation per
+                              residual check) instead of the default CUDA graph whose conditional
+                              while-node runs the check intervals on the device */
 
 typedef struct {
     int method;        /* HP_JACOBI, HP_RBSOR or HP_MIXED */
@@ -183,7 +187,8 @@ int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *fi
  * HP_RELAX_NOALLOC_SCRATCH_BYTES (9 MiB), held by every GPU that loads the
  * library until the process exits; the call itself allocates nothing.
  * Same arguments and results as hp_relax (occ_dev and field_dev are still the
- * caller's), for method HP_RBSOR or HP_JACOBI without HP_TIMING.
+ * caller's), for method HP_RBSOR or HP_JACOBI without HP_TIMING; the
+ * convergence loop is always host-driven (HP_HOST_LOOP).
  * Limits: grids whose hp_relax_workspace_size() exceeds the array (for
  * HP_RBSOR anything above about 1024 x 1024 cells) return TW_EWORKSPACE
  * before any GPU work; other methods or HP_TIMING return TW_EINVAL.

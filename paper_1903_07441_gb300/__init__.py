@@ -27,7 +27,7 @@ TW_MARK_PER_CELL, TW_MARK_PER_OBSTACLE = 0, 1
 TW_FREE, TW_STATIC, TW_DYNAMIC, TW_BORDER = 0, 1, 2, 3
 HP_JACOBI, HP_RBSOR, HP_MIXED = 0, 1, 2
 HP_STORE_F32, HP_STORE_F16, HP_STORE_BF16 = 0, 1, 2
-HP_WARM_START, HP_OUT_PHI, HP_TIMING = 1, 2, 4
+HP_WARM_START, HP_OUT_PHI, HP_TIMING, HP_HOST_LOOP = 1, 2, 4, 8
 
 EXPORTS = (
     "tw_build_grid_workspace_size", "tw_build_grid", "tw_ring_count",

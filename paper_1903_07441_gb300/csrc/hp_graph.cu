@@ -1,0 +1,173 @@
+// Graph-driven convergence loop for the red-black SOR solve.
+//
+// One CUDA graph holds a conditional WHILE node whose body is one check
+// interval: K/T launches of the T-fused sweep kernel, the FP32 residual
+// reduction and a one-thread control kernel.  The control kernel applies the
+// same decision as the host loop (relax_control: stop at the tolerance, back
+// off over-relaxation at the rounding floor, adapt omega), writes the new omega
+// where the sweep kernels read it, and sets the loop condition.  The host
+// launches the graph once per solve and reads the state back once, instead
+// of synchronising at every check.  The loop is bounded: the control kernel
+// stops after max_intervals intervals.
+//
+// Instantiated graphs are cached per (device, workspace, grid, T, K): the
+// kernel arguments are workspace pointers and shapes, so a cached graph is
+// valid for every solve that reuses the same workspace.
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "hp_internal.cuh"
+
+namespace tw {
+
+void tb_kernel_node(int T, RBLayout &L, int ny, void **func, dim3 *grid, dim3 *block);
+void *rb_residual_kernel_ptr();
+
+__global__ void relax_control_kernel(RelaxCtl *ctl, unsigned int *rmax, int max_intervals,
+                                     cudaGraphConditionalHandle handle) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    RelaxCtl c = *ctl;
+    const float rf = __uint_as_float(*rmax);
+    *rmax = 0u;
+    c.sweeps += c.K;
+    int go = relax_control(c, (double)rf, c.K);
+    if (c.checks >= max_intervals || c.sweeps + c.K > c.max_sweeps) go = 0;
+    *ctl = c;
+    cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
+struct GraphEntry {
+    int dev, nx, ny, T, K, max_intervals;
+    const void *key;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+static std::mutex g_graph_mutex;
+static std::vector<GraphEntry> g_graphs;
+constexpr size_t kMaxCachedGraphs = 16;
+
+static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_intervals, RelaxScalars *scal,
+                       GraphEntry *out) {
+    (void)nx;
+    cudaGraph_t g = nullptr;
+    TW_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return 1; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    e = cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return 1; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    // K/T sweep launches alternating the ping-pong planes (an even count, so the
+    // planes are back in place when the residual reads them)
+    void *func;
+    dim3 grid, block;
+    tb_kernel_node(T, L, ny, &func, &grid, &block);
+    const int n_launch = K / T;
+    const float *omega_dev = &scal->ctl.omega_f;
+    float omega_unused = 0.0f;
+    cudaGraphNode_t prev = nullptr;
+    float *R = L.R, *B = L.B, *R2 = L.R2, *B2 = L.B2;
+    for (int i = 0; i < n_launch; i++) {
+        const float *rin = R, *bin = B;
+        float *rout = R2, *bout = B2;
+        const uint32_t *mr = L.MR, *mb = L.MB;
+        int ny_ = ny, w4 = L.W4, S = L.S, mw = L.MW;
+        void *args[] = {(void *)&rin, (void *)&bin, (void *)&rout, (void *)&bout, (void *)&mr, (void *)&mb,
+                        (void *)&ny_, (void *)&w4, (void *)&S, (void *)&mw, (void *)&omega_unused,
+                        (void *)&omega_dev};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.func = func;
+        kp.gridDim = grid;
+        kp.blockDim = block;
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
+        prev = node;
+        float *t = R; R = R2; R2 = t;
+        t = B; B = B2; B2 = t;
+    }
+    {   // residual of the current planes
+        RBLayout Lc = L;
+        Lc.R = R; Lc.B = B;
+        int ny_ = ny;
+        unsigned int *rmax = &scal->max32;
+        void *args[] = {(void *)&Lc, (void *)&ny_, (void *)&rmax};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.func = rb_residual_kernel_ptr();
+        kp.gridDim = dim3(ceil_div(L.W4, 64), ceil_div(ny, 4));
+        kp.blockDim = dim3(64, 4);
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, body, &prev, 1, &kp);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
+        prev = node;
+    }
+    {   // control
+        RelaxCtl *ctl = &scal->ctl;
+        unsigned int *rmax = &scal->max32;
+        int mi = max_intervals;
+        void *args[] = {(void *)&ctl, (void *)&rmax, (void *)&mi, (void *)&h};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.func = (void *)relax_control_kernel;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, body, &prev, 1, &kp);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
+    }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return 1; }
+    out->graph = g;
+    out->exec = exec;
+    return TW_OK;
+}
+
+int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, RelaxScalars *scal,
+                   cudaStream_t s, int *launches) {
+    if (max_intervals < 1) return 1;
+    int dev = 0;
+    TW_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_graph_mutex);
+    GraphEntry *ent = nullptr;
+    for (auto &g : g_graphs)
+        if (g.dev == dev && g.key == (const void *)scal && g.nx == nx && g.ny == ny && g.T == T && g.K == K &&
+            g.max_intervals == max_intervals)
+            ent = &g;
+    if (!ent) {
+        if (g_graphs.size() >= kMaxCachedGraphs) {
+            cudaGraphExecDestroy(g_graphs.front().exec);
+            cudaGraphDestroy(g_graphs.front().graph);
+            g_graphs.erase(g_graphs.begin());
+        }
+        GraphEntry ne;
+        ne.dev = dev; ne.nx = nx; ne.ny = ny; ne.T = T; ne.K = K; ne.max_intervals = max_intervals;
+        ne.key = (const void *)scal;
+        int e = build_graph(L, nx, ny, T, K, max_intervals, scal, &ne);
+        if (e) return e;
+        g_graphs.push_back(ne);
+        ent = &g_graphs.back();
+    }
+    TW_CUDA(cudaGraphLaunch(ent->exec, s));
+    (void)launches;   // counted by the caller once the number of intervals is known
+    return TW_OK;
+}
+
+}  // namespace tw

@@ -23,12 +23,23 @@ struct RBLayout {
     float *R2, *B2;    // ping-pong planes for temporal blocking
 };
 
+// Convergence-loop state, shared by the host-driven loop and the device
+// control kernel of the graph-driven loop (lives in the workspace).
+struct RelaxCtl {
+    float omega_f;         // omega as read by the sweep kernels
+    unsigned int rmax;     // FP32 residual max accumulator (bits); reset after each check
+    int sweeps, checks, status, adapt, same_iv, K, max_sweeps, pad;
+    double omega, r_prev, tol, r_last;
+};
+
+
 struct RelaxScalars {
     unsigned int max32;
     unsigned int pad0;
     unsigned long long max64;
     double sum64;
     double pad1[5];
+    RelaxCtl ctl;
 };
 
 struct MixedLayout {
@@ -53,6 +64,12 @@ int relax_mixed(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, in
                 const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s);
 // n full red-black SOR sweeps, T fused per launch; *launches += launches made
 int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream_t s, int *launches);
+// Graph-driven loop: up to max_intervals check intervals of K sweeps (K/T even)
+// run on the device; ctl_dev must hold the initial state.  Returns TW_OK, or
+// a positive value when graphs are unavailable (the caller uses the host loop).
+int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, RelaxScalars *scal,
+                   cudaStream_t s, int *launches);
+void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, cudaStream_t s);
 
 // Optional CUDA-event timing of the sweep kernels (HP_TIMING).
 struct SweepTimer {
@@ -81,11 +98,62 @@ struct SweepTimer {
 };
 int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
              cudaStream_t s);
-double sor_adapt(double omega, double lambda);
 double sor_initial_omega(int nx, int ny);
 int read_max_f32(unsigned int *dmax, cudaStream_t s, float *out);
 int final_residual_full(const uint8_t *occ, int nx, int ny, int gx, int gy, const float *u,
                         RelaxScalars *scal, cudaStream_t s, double *r_inf, double *r_l2);
+
+// Adaptive SOR factor.  For a consistently ordered matrix (red-black is one)
+// the SOR convergence factor lambda at omega <= omega_opt and the Jacobi
+// spectral radius mu satisfy (lambda + omega - 1)^2 = lambda omega^2 mu^2
+// (Young).  The observed residual decay over a check interval gives lambda,
+// hence mu and omega_opt = 2 / (1 + sqrt(1 - mu^2)).  Pre-asymptotic decay
+// underestimates mu, so omega approaches omega_opt from below.
+__host__ __device__ inline double sor_adapt(double omega, double lambda) {
+    if (!(lambda > 0.0) || lambda >= 1.0) return omega;
+    if (lambda <= (omega - 1.0) * 1.05) return omega;  // complex regime: at or past optimum
+    double mu = (lambda + omega - 1.0) / (omega * sqrt(lambda));
+    if (!(mu > 0.0)) return omega;
+    if (mu >= 0.999999999) mu = 0.999999999;
+    double w = 2.0 / (1.0 + sqrt(1.0 - mu * mu));
+    // Pre-asymptotic decay underestimates mu, and the SOR rate degrades much
+    // faster below omega_opt than above it: move 15 % of the way towards 2.
+    w = 2.0 - (2.0 - w) * 0.85;
+    if (w > 1.9995) w = 1.9995;
+    return (w > omega) ? w : omega;
+}
+
+// One residual check: stop test, over-relaxation back-off at the rounding
+// floor, adaptive omega.  Returns 1 to continue, 0 when converged.
+__host__ __device__ inline int relax_control(RelaxCtl &c, double r, int n) {
+    c.checks++;
+    c.r_last = r;
+    if (c.tol > 0.0 && r <= c.tol) {
+        c.status = TW_OK;
+        return 0;
+    }
+    // Stagnation over a whole interval close to the tolerance means the FP32
+    // rounding floor, which over-relaxation amplifies by about
+    // omega / (2 - omega): halve the over-relaxation and stop adapting
+    // upwards.  (Far from the tolerance the max-norm can plateau while the
+    // iteration still converges, so it is left alone there.)
+    if (c.r_prev > 0.0 && n == c.K && r > 0.8 * c.r_prev && r < 16.0 * c.tol && c.omega > 1.0) {
+        c.omega = 1.0 + 0.5 * (c.omega - 1.0);
+        if (c.omega < 1.05) c.omega = 1.0;
+        c.adapt = 0;
+        c.same_iv = 0;
+    } else if (c.adapt) {
+        if (c.r_prev > 0.0 && c.same_iv >= 1 && n == c.K) {
+            double lambda = pow(r / c.r_prev, 1.0 / n);
+            double w = sor_adapt(c.omega, lambda);
+            if (w > c.omega + 1e-4) { c.omega = w; c.same_iv = -1; }
+        }
+        c.same_iv++;
+    }
+    c.r_prev = r;
+    c.omega_f = (float)c.omega;
+    return 1;
+}
 
 // NaN or overflow must never look converged: map them to +inf before a max.
 __device__ __forceinline__ float sane(float r) { return (r <= FLT_MAX) ? r : __int_as_float(0x7f800000); }

@@ -237,26 +237,6 @@ static bool valid_params(const hp_params *p) {
            p->tblock >= 0 && p->tblock <= 16;
 }
 
-// Adaptive SOR factor.  For a consistently ordered matrix (red-black is one)
-// the SOR convergence factor lambda at omega <= omega_opt and the Jacobi
-// spectral radius mu satisfy (lambda + omega - 1)^2 = lambda omega^2 mu^2
-// (Young).  The observed residual decay over a check interval gives lambda,
-// hence mu and omega_opt = 2 / (1 + sqrt(1 - mu^2)).  Pre-asymptotic decay
-// underestimates mu, so omega approaches omega_opt from below.
-double sor_adapt(double omega, double lambda) {
-    if (!(lambda > 0.0) || lambda >= 1.0) return omega;
-    if (lambda <= (omega - 1.0) * 1.05) return omega;  // complex regime: at or past optimum
-    double mu = (lambda + omega - 1.0) / (omega * sqrt(lambda));
-    if (!(mu > 0.0)) return omega;
-    if (mu >= 0.999999999) mu = 0.999999999;
-    double w = 2.0 / (1.0 + sqrt(1.0 - mu * mu));
-    // Pre-asymptotic decay underestimates mu, and the SOR rate degrades much
-    // faster below omega_opt than above it: move 15 % of the way towards 2.
-    w = 2.0 - (2.0 - w) * 0.85;
-    if (w > 1.9995) w = 1.9995;
-    return (w > omega) ? w : omega;
-}
-
 double sor_initial_omega(int nx, int ny) {
     int n = nx > ny ? nx : ny;
     return n >= 1024 ? 1.9 : (n >= 256 ? 1.85 : 1.75);
@@ -333,63 +313,75 @@ static int relax_jacobi(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
 }
 
 // Red-black SOR driver on the split layout (pack -> sweeps -> unpack).
+void *rb_residual_kernel_ptr() { return (void *)rb_residual_kernel; }
+
+void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, cudaStream_t s) {
+    dim3 b(64, 4), gr(ceil_div(L.W4, 64), ceil_div(ny, 4));
+    TW_LAUNCH(rb_residual_kernel, gr, b, 0, s, L, ny, out);
+}
+
+// Red-black SOR driver on the split layout.  By default the check intervals
+// run inside one CUDA graph (a conditional while-node re-runs "K sweeps,
+// residual, control" on the device); the host loop below finishes any
+// remainder and serves HP_TIMING / HP_HOST_LOOP.
 int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
              cudaStream_t s) {
     int T = p->tblock > 0 ? p->tblock : kDefaultTBlock;
     if (T > 4) T = 4;
     int K = p->check_every > 0 ? p->check_every : 32;
     if (T > 1 && K % T) K += T - K % T;   // whole launches per check interval
-    bool adapt = p->omega == 0.0;
-    double omega = adapt ? sor_initial_omega(nx, ny) : p->omega;
-    int sweeps = 0, checks = 0, launches = 0;
-    double r_prev = -1.0;
-    int same_omega_intervals = 0;
+    const bool checks = p->tol > 0.0 || p->omega == 0.0;
+    RelaxCtl c;
+    memset(&c, 0, sizeof(c));
+    c.adapt = p->omega == 0.0;
+    c.omega = c.adapt ? sor_initial_omega(nx, ny) : p->omega;
+    c.omega_f = (float)c.omega;
+    c.r_prev = -1.0;
+    c.tol = p->tol;
+    c.K = K;
+    c.max_sweeps = p->max_sweeps;
+    c.status = TW_NOT_CONVERGED;
+    int launches = 0;
+    bool done = false;
+    const bool host_loop = (p->flags & (HP_TIMING | HP_HOST_LOOP)) != 0;
+    if (checks && !host_loop && T > 1 && (K / T) % 2 == 0 && p->max_sweeps >= K) {
+        TW_CUDA(cudaMemcpyAsync(&scal->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+        TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
+        int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, scal, s, &launches);
+        if (e < 0) return e;
+        if (e == TW_OK) {
+            TW_CUDA(cudaMemcpyAsync(&c, &scal->ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
+            TW_CUDA(cudaStreamSynchronize(s));
+            done = c.status == TW_OK;
+            // every interval ran K/T sweep launches, the residual and the control kernel
+            launches += c.checks * (K / T);
+            count_launches((unsigned long long)c.checks * (K / T + 2));
+        }
+    }
     SweepTimer timer;
     if (timer.open((p->flags & HP_TIMING) != 0)) return TW_ECUDA;
-    st->status = TW_NOT_CONVERGED;
-    while (sweeps < p->max_sweeps) {
-        int n = p->max_sweeps - sweeps < K ? p->max_sweeps - sweeps : K;
+    while (!done && c.sweeps < p->max_sweeps) {
+        int n = p->max_sweeps - c.sweeps < K ? p->max_sweeps - c.sweeps : K;
         timer.start(s);
-        int e = rb_sweeps(L, nx, ny, n, T, (float)omega, s, &launches);
+        int e = rb_sweeps(L, nx, ny, n, T, (float)c.omega, s, &launches);
         timer.stop(s);
         if (e) return e;
         timer.accumulate();
-        sweeps += n;
-        if (p->tol > 0.0 || adapt || p->omega == 0.0) {
+        c.sweeps += n;
+        if (checks) {
             TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
-            dim3 b(64, 4), gr(ceil_div(L.W4, 64), ceil_div(ny, 4));
-            TW_LAUNCH(rb_residual_kernel, gr, b, 0, s, L, ny, &scal->max32);
+            rb_residual_launch(L, ny, &scal->max32, s);
             TW_CHECK_LAUNCH();
             float rf;
             e = read_max_f32(&scal->max32, s, &rf);
             if (e) return e;
-            checks++;
-            double r = rf;
-            if (p->tol > 0.0 && r <= p->tol) { st->status = TW_OK; break; }
-            // Stagnation over a whole interval close to the tolerance means the
-            // FP32 rounding floor, which over-relaxation amplifies by about
-            // omega / (2 - omega): halve the over-relaxation and stop adapting
-            // upwards.  (Far from the tolerance the max-norm can plateau while
-            // the iteration still converges, so it is left alone there.)
-            if (r_prev > 0.0 && n == K && r > 0.8 * r_prev && r < 16.0 * p->tol && omega > 1.0) {
-                omega = 1.0 + 0.5 * (omega - 1.0);
-                if (omega < 1.05) omega = 1.0;
-                adapt = false;
-                same_omega_intervals = 0;
-            } else if (adapt) {
-                if (r_prev > 0.0 && same_omega_intervals >= 1 && n == K) {
-                    double lambda = pow(r / r_prev, 1.0 / n);
-                    double w = sor_adapt(omega, lambda);
-                    if (w > omega + 1e-4) { omega = w; same_omega_intervals = -1; }
-                }
-                same_omega_intervals++;
-            }
-            r_prev = r;
+            if (!relax_control(c, (double)rf, n)) done = true;
         }
     }
-    st->sweeps = sweeps;
-    st->checks = checks;
-    st->omega = omega;
+    st->status = c.status;
+    st->sweeps = c.sweeps;
+    st->checks = c.checks;
+    st->omega = c.omega;
     st->sweep_launches = launches;
     st->sweep_ms = timer.ms;
     st->tblock = T;

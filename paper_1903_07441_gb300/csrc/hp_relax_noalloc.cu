@@ -63,5 +63,8 @@ extern "C" int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx
     void *ws = nullptr;
     int e = noalloc_scratch(&ws);
     if (e) return e;
-    return hp_relax(g, occ_dev, gx, gy, field_dev, p, stats, ws, kNoAllocScratchBytes, stream);
+    // the host-driven convergence loop: instantiating the default CUDA graph could allocate
+    hp_params q = *p;
+    q.flags |= HP_HOST_LOOP;
+    return hp_relax(g, occ_dev, gx, gy, field_dev, &q, stats, ws, kNoAllocScratchBytes, stream);
 }

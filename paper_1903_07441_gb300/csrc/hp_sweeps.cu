@@ -127,8 +127,10 @@ template <int T, int RB, int WARPS, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
 rb_tb_kernel(const float *__restrict__ Rin, const float *__restrict__ Bin, float *__restrict__ Rout,
              float *__restrict__ Bout, const uint32_t *__restrict__ MR, const uint32_t *__restrict__ MB,
-             int ny, int W4, int S, int MW, float omega) {
+             int ny, int W4, int S, int MW, float omega_arg, const float *__restrict__ omega_dev) {
     using Sh = TBShape<T, RB, WARPS>;
+    // the graph-driven loop keeps omega in device memory (it adapts on the device)
+    const float omega = omega_dev ? *omega_dev : omega_arg;
     __shared__ float4 s_top[2][WARPS][32];
     __shared__ float4 s_bot[2][WARPS][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -195,7 +197,7 @@ static void launch_tb(RBLayout &L, int ny, float omega, cudaStream_t s) {
     using Sh = TBShape<T, kTBRows, kTBWarps>;
     dim3 grid(ceil_div(L.W4, Sh::KI4), ceil_div(ny, Sh::YI));
     TW_LAUNCH((rb_tb_kernel<T, kTBRows, kTBWarps, kTBMinBlocks>), grid, kTBWarps * 32, 0, s, L.R, L.B, L.R2,
-              L.B2, L.MR, L.MB, ny, L.W4, L.S, L.MW, omega);
+              L.B2, L.MR, L.MB, ny, L.W4, L.S, L.MW, omega, (const float *)nullptr);
     float *t = L.R; L.R = L.R2; L.R2 = t;
     t = L.B; L.B = L.B2; L.B2 = t;
 }
@@ -216,6 +218,22 @@ int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream
     }
     TW_CHECK_LAUNCH();
     return TW_OK;
+}
+
+// Kernel entry and launch shape of the T-fused sweep, for graph construction.
+void tb_kernel_node(int T, RBLayout &L, int ny, void **func, dim3 *grid, dim3 *block) {
+    switch (T) {
+        case 4: { using Sh = TBShape<4, kTBRows, kTBWarps>;
+                  *func = (void *)rb_tb_kernel<4, kTBRows, kTBWarps, kTBMinBlocks>;
+                  *grid = dim3(ceil_div(L.W4, Sh::KI4), ceil_div(ny, Sh::YI)); break; }
+        case 3: { using Sh = TBShape<3, kTBRows, kTBWarps>;
+                  *func = (void *)rb_tb_kernel<3, kTBRows, kTBWarps, kTBMinBlocks>;
+                  *grid = dim3(ceil_div(L.W4, Sh::KI4), ceil_div(ny, Sh::YI)); break; }
+        default: { using Sh = TBShape<2, kTBRows, kTBWarps>;
+                   *func = (void *)rb_tb_kernel<2, kTBRows, kTBWarps, kTBMinBlocks>;
+                   *grid = dim3(ceil_div(L.W4, Sh::KI4), ceil_div(ny, Sh::YI)); break; }
+    }
+    *block = dim3(kTBWarps * 32);
 }
 
 }  // namespace tw

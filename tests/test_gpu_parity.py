@@ -246,6 +246,23 @@ def test_temporal_blocking_matches_unfused_sweeps(dev, tblock):
         assert np.abs(outs[0] - outs[1]).max() <= 2e-7, (nx, ny, tblock)
 
 
+def test_graph_loop_matches_host_loop(dev):
+    """The CUDA-graph convergence loop takes the same decisions as the host loop."""
+    for sc in (scenes.static128(), scenes.static_occupancy(5, 700, 260, 0.25)):
+        occ, _, _ = oracle.build_grid(sc)
+        a, sa = _relax(occ, sc.goal, dev, tw.Params(tol=1e-6))
+        b, sb = _relax(occ, sc.goal, dev, tw.Params(tol=1e-6, flags=tw.HP_HOST_LOOP))
+        assert sa["status"] == sb["status"] == tw.TW_OK
+        assert sa["sweeps"] == sb["sweeps"] and sa["checks"] == sb["checks"]
+        assert abs(sa["omega"] - sb["omega"]) < 1e-9
+        assert np.abs(a - b).max() <= 1e-6
+        # a cap that is not a multiple of the check interval: graph intervals + host remainder
+        c, sc_ = _relax(occ, sc.goal, dev, tw.Params(tol=1e-12, max_sweeps=100))
+        d, sd = _relax(occ, sc.goal, dev, tw.Params(tol=1e-12, max_sweeps=100, flags=tw.HP_HOST_LOOP))
+        assert sc_["sweeps"] == sd["sweeps"] == 100 and sc_["status"] == tw.TW_NOT_CONVERGED
+        assert np.abs(c - d).max() <= 1e-6
+
+
 def test_warm_start_and_phi_output(dev, ref128):
     sc, occ, ustar, fixed, tau_max = ref128
     occ_t = torch.from_numpy(occ).to(dev)
