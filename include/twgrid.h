@@ -149,7 +149,8 @@ typedef struct {
 typedef struct {
     int sweeps;        /* full sweeps performed */
     int status;        /* TW_OK or TW_NOT_CONVERGED */
-    double resid_inf;  /* FP64 residual max |(1/4) sum nbr - u| over free cells of the output */
+    double resid_inf;  /* FP64 residual max |(1/4) sum nbr - u| over free cells of the output
+                          (HP_MIXED: of its FP64 master field, which the FP32 output rounds) */
     double resid_l2;   /* FP64 sqrt(sum of squared residuals) */
     double omega;      /* SOR factor used last */
     int checks;        /* residual checks performed */

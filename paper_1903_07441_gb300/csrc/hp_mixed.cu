@@ -1,18 +1,442 @@
-// Mixed-precision defect correction (placeholder until the correction sweeps land).
+// Mixed-precision defect correction (HP_MIXED).
+//
+// The field is kept as an FP64 master x (full layout).  Each outer step
+//   1. r = (1/4) sum_nbr x - x on free cells, in FP64 (the Eq. 1 residual);
+//      s = max |r|; stop when s <= tol;
+//   2. q = r / s stored in low precision (FP16 or BF16, colour-split planes);
+//   3. the correction equation e = (1/4) sum_nbr e + q (e = 0 on Dirichlet
+//      cells) is relaxed by red-black SOR with e stored in FP16/BF16 and every
+//      update computed in FP32, T sweeps fused per launch, until its own
+//      residual drops by a fixed factor (the storage precision bounds what one
+//      inner solve can reach);
+//   4. x += s * e in FP64.
+// Since A x_true = b, A e_exact = r, so x + s e converges to the solution
+// while every low-precision rounding only enters through the correction;
+// the final residual is that of the FP64 master, far below the FP32 floor.
+// The inner sweeps move 2 + 2 + 2 bytes per cell (e read, e write, q read)
+// plus the mask bit instead of 4 + 4 for FP32 storage.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+#include <string.h>
+
+#include <type_traits>
+
 #include "common.cuh"
 #include "hp_internal.cuh"
 
 namespace tw {
 
+// ---- storage conversions ---------------------------------------------------
+template <class S> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float4 load4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+    static __device__ __forceinline__ void store4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+    static __device__ __forceinline__ float from(float v) { return v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float4 load4(const __half *p) {
+        uint2 u = *reinterpret_cast<const uint2 *>(p);
+        float2 a = __half22float2(*reinterpret_cast<__half2 *>(&u.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ void store4(__half *p, float4 v) {
+        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<unsigned *>(&a);
+        u.y = *reinterpret_cast<unsigned *>(&b);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load4(const __nv_bfloat16 *p) {
+        uint2 u = *reinterpret_cast<const uint2 *>(p);
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ void store4(__nv_bfloat16 *p, float4 v) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<unsigned *>(&a);
+        u.y = *reinterpret_cast<unsigned *>(&b);
+        *reinterpret_cast<uint2 *>(p) = u;
+    }
+};
+
+// ---- layout ------------------------------------------------------------------
+struct MxLayout {
+    RBLayout g;          // geometry (W2, W4, S, MW) and the free-cell bits MR/MB
+    double *x;           // FP64 master, [ny][nx]
+    void *e[2][2];       // [buffer][colour] correction planes, ny x S entries
+    void *q[2];          // [colour] scaled right-hand side planes
+    int esize;           // bytes per stored entry
+};
+
+static int storage_bytes(int storage) { return storage == HP_STORE_F32 ? 4 : 2; }
+
 size_t carve_mixed(Carver &cv, int nx, int ny, int storage, RelaxLayout *R) {
-    (void)storage;
-    carve_rb(cv, nx, ny, R ? &R->rb : nullptr, true);
+    RBLayout g = rb_layout(nx, ny);
+    const size_t plane = (size_t)ny * g.S * storage_bytes(storage);
+    double *x = cv.take<double>((size_t)nx * ny);
+    g.MR = cv.take<uint32_t>((size_t)ny * g.MW);
+    g.MB = cv.take<uint32_t>((size_t)ny * g.MW);
+    void *e00 = cv.take<char>(plane), *e01 = cv.take<char>(plane);
+    void *e10 = cv.take<char>(plane), *e11 = cv.take<char>(plane);
+    void *q0 = cv.take<char>(plane), *q1 = cv.take<char>(plane);
+    if (R) {
+        R->rb = g;
+        R->mx.x = x;
+        R->mx.e_r = e00; R->mx.e_b = e01; R->mx.e_r2 = e10; R->mx.e_b2 = e11;
+        R->mx.q_r = q0; R->mx.q_b = q1;
+    }
     return cv.need;
 }
 
-int relax_mixed(const uint8_t *, int, int, int, int, float *, int, const hp_params *, hp_stats *,
-                RelaxLayout &, cudaStream_t) {
-    return TW_EINVAL;
+// ---- kernels -------------------------------------------------------------------
+
+// Free-cell bits and the FP64 master's initial value.
+// mode 0: planner (occ + goal; cold 0.5 unless warm); mode 1: general Dirichlet.
+__global__ void mx_init_kernel(const uint8_t *__restrict__ occ, const float *__restrict__ u_in, int nx, int ny,
+                               int gx, int gy, int mode, int warm, RBLayout g, double *__restrict__ x) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int color = 0; color < 2; color++) {
+        int xx = 2 * k + ((y + color) & 1);
+        bool free_cell = false;
+        if (k < g.W2 && xx < nx) {
+            size_t c = (size_t)y * nx + xx;
+            bool border = xx == 0 || y == 0 || xx == nx - 1 || y == ny - 1;
+            double v;
+            if (mode == 0) {
+                bool goal = (xx == gx && y == gy);
+                bool fixed = goal || border || occ[c] != 0;
+                free_cell = !fixed;
+                v = goal ? 1.0 : (fixed ? 0.0 : (warm ? (double)u_in[c] : 0.5));
+            } else {
+                free_cell = !(border || occ[c] != 0);
+                v = (double)u_in[c];
+            }
+            x[c] = v;
+        }
+        unsigned bits = __ballot_sync(0xffffffffu, free_cell);
+        if (lane == 0) {
+            uint32_t *M = color ? g.MB : g.MR;
+            int w = k >> 5;
+            if (w < g.MW) M[(size_t)y * g.MW + w] = bits;
+        }
+    }
+}
+
+__device__ __forceinline__ bool mx_free(const RBLayout &g, int x, int y) {
+    const int color = (x + y) & 1, k = x >> 1;
+    const uint32_t *M = color ? g.MB : g.MR;
+    return (M[(size_t)y * g.MW + (k >> 5)] >> (k & 31)) & 1u;
+}
+
+// FP64 residual of the master: max |r| (pass 0) or q = r / s into the planes (pass 1).
+template <class S>
+__global__ void __launch_bounds__(256) mx_residual_kernel(RBLayout g, const double *__restrict__ x, int nx, int ny,
+                                                          int pass, const double *__restrict__ scale,
+                                                          S *__restrict__ qr, S *__restrict__ qb,
+                                                          unsigned long long *__restrict__ out_max) {
+    // one thread per 4 entries of one colour row; both colours
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    double rmax = 0.0;
+    if (k4 < g.W4) {
+#pragma unroll
+        for (int color = 0; color < 2; color++) {
+            float4 qv;
+            float *qa = &qv.x;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int k = 4 * k4 + e;
+                const int xx = 2 * k + ((y + color) & 1);
+                double r = 0.0;
+                if (xx > 0 && xx < nx - 1 && y > 0 && y < ny - 1 && mx_free(g, xx, y)) {
+                    const size_t c = (size_t)y * nx + xx;
+                    r = 0.25 * (((x[c + 1] + x[c - 1]) + x[c + nx]) + x[c - nx]) - x[c];
+                }
+                rmax = fmax(rmax, fabs(r));
+                qa[e] = pass ? (float)(r / *scale) : 0.0f;
+            }
+            if (pass) {
+                S *q = color ? qb : qr;
+                Store<S>::store4(q + (size_t)y * g.S + 4 + 4 * k4, qv);
+            }
+        }
+    }
+    if (pass == 0) block_max_sum_f64(rmax, out_max, reinterpret_cast<double *>(out_max + 1));
+}
+
+// x += s * e (FP64), e read from the colour-split planes.
+template <class S>
+__global__ void mx_update_kernel(RBLayout g, double *__restrict__ x, int nx, int ny, const double *__restrict__ scale,
+                                 const S *__restrict__ er, const S *__restrict__ eb) {
+    const int xx = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (xx >= nx || y >= ny) return;
+    const int color = (xx + y) & 1, k = xx >> 1;
+    const S *e = color ? eb : er;
+    float4 q4 = Store<S>::load4(e + (size_t)y * g.S + 4 + (k & ~3));
+    const float ev = (&q4.x)[k & 3];
+    if (mx_free(g, xx, y)) x[(size_t)y * nx + xx] += *scale * (double)ev;
+}
+
+__global__ void mx_output_kernel(const double *__restrict__ x, float *__restrict__ out, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)x[i];
+}
+
+// Inner residual max |(1/4) sum e_n + q - e| over free cells (FP32 from storage).
+template <class S>
+__global__ void __launch_bounds__(256) mx_inner_residual_kernel(RBLayout g, int ny, const S *__restrict__ er,
+                                                                const S *__restrict__ eb, const S *__restrict__ qr,
+                                                                const S *__restrict__ qb,
+                                                                unsigned int *__restrict__ out_max) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    float r = 0.0f;
+    if (k4 < g.W4 && y < ny - 1) {
+        const int k = 4 * k4;
+#pragma unroll
+        for (int color = 0; color < 2; color++) {
+            const S *U = color ? eb : er;
+            const S *V = color ? er : eb;
+            const S *Q = color ? qb : qr;
+            const uint32_t *M = color ? g.MB : g.MR;
+            const uint32_t bits = (M[(size_t)y * g.MW + (k >> 5)] >> (k & 31)) & 0xFu;
+            if (!bits) continue;
+            const int s = (y + color) & 1;
+            const S *row = V + (size_t)y * g.S + 4;
+            const float4 mid = Store<S>::load4(row + k);
+            const float4 up = Store<S>::load4(row - g.S + k), dn = Store<S>::load4(row + g.S + k);
+            float4 ex4 = Store<S>::load4(row + (s ? k + 4 : k - 4));
+            const float ex = s ? ex4.x : ex4.w;
+            const float4 c = Store<S>::load4(U + (size_t)y * g.S + 4 + k);
+            const float4 q = Store<S>::load4(Q + (size_t)y * g.S + 4 + k);
+            float l[4], rr[4];
+            if (s) { l[0] = mid.x; l[1] = mid.y; l[2] = mid.z; l[3] = mid.w; rr[0] = mid.y; rr[1] = mid.z; rr[2] = mid.w; rr[3] = ex; }
+            else { l[0] = ex; l[1] = mid.x; l[2] = mid.y; l[3] = mid.z; rr[0] = mid.x; rr[1] = mid.y; rr[2] = mid.z; rr[3] = mid.w; }
+            const float cu[4] = {up.x, up.y, up.z, up.w}, cd[4] = {dn.x, dn.y, dn.z, dn.w};
+            const float cc[4] = {c.x, c.y, c.z, c.w}, cq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (bits & (1u << e))
+                    r = fmaxf(r, fabsf(fmaf(0.25f, (l[e] + rr[e]) + (cu[e] + cd[e]), cq[e] - cc[e])));
+        }
+    }
+    block_max_atomic(r, out_max);
+}
+
+// T-fused SOR sweeps of the correction equation, storage S, FP32 arithmetic.
+// Same register blocking as the FP32 kernel (8 rows x float4 of both colours
+// per thread, 8 warps, halo 2T rows / ceil((T+1)/4) float4 columns); the
+// right-hand side is read through the L1 cache (the tile's rows repeat every
+// half-sweep, so after the first one they hit L1).
+constexpr int kMxRows = 8, kMxWarps = 8;
+
+template <int T, class S>
+__global__ void __launch_bounds__(kMxWarps * 32)
+mx_tb_kernel(const S *__restrict__ Rin, const S *__restrict__ Bin, S *__restrict__ Rout, S *__restrict__ Bout,
+             const S *__restrict__ Qr, const S *__restrict__ Qb, const uint32_t *__restrict__ MR,
+             const uint32_t *__restrict__ MB, int ny, int W4, int Sst, int MW, const float *__restrict__ omega_p) {
+    constexpr int RB = kMxRows, WARPS = kMxWarps;
+    constexpr int HK4 = (T + 1 + 3) / 4, HY = 2 * T, KI4 = 32 - 2 * HK4, YI = WARPS * RB - 2 * HY;
+    __shared__ float4 s_top[2][WARPS][32];
+    __shared__ float4 s_bot[2][WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k4 = (int)blockIdx.x * KI4 - HK4 + lane;
+    const int y_tile = (int)blockIdx.y * YI;
+    const int y0 = y_tile - HY + warp * RB;
+    const bool kin = (k4 >= 0) && (k4 < W4);
+    const int k = 4 * k4;
+    const float omega = *omega_p;
+    float4 v[2][RB];
+    uint32_t m[2] = {0u, 0u};
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+        const int y = y0 + r;
+        const bool in = kin && y >= 0 && y < ny;
+        const size_t off = (size_t)(in ? y : 0) * Sst + 4 + (in ? k : 0);
+        v[0][r] = in ? Store<S>::load4(Rin + off) : z4;
+        v[1][r] = in ? Store<S>::load4(Bin + off) : z4;
+        if (in) {
+            const size_t w = (size_t)y * MW + (k >> 5);
+            m[0] |= ((MR[w] >> (k & 31)) & 0xFu) << (4 * r);
+            m[1] |= ((MB[w] >> (k & 31)) & 0xFu) << (4 * r);
+        }
+    }
+#pragma unroll 1
+    for (int p = 0; p < 2 * T; p++) {
+        const int c = p & 1, o = 1 - c, buf = p & 1;
+        s_top[buf][warp][lane] = v[o][0];
+        s_bot[buf][warp][lane] = v[o][RB - 1];
+        __syncthreads();
+        const float4 above = warp > 0 ? s_bot[buf][warp - 1][lane] : z4;
+        const float4 below = warp < WARPS - 1 ? s_top[buf][warp + 1][lane] : z4;
+#pragma unroll
+        for (int r = 0; r < RB; r++) {
+            const float4 mid = v[o][r];
+            const float4 up = r == 0 ? above : v[o][r - 1];
+            const float4 dn = r == RB - 1 ? below : v[o][r + 1];
+            const int s = (r + c) & 1;   // rows start even
+            float l0, l1, l2, l3, r0, r1, r2, r3;
+            if (s) {
+                const float ex = __shfl_down_sync(0xffffffffu, mid.x, 1);
+                l0 = mid.x; l1 = mid.y; l2 = mid.z; l3 = mid.w; r0 = mid.y; r1 = mid.z; r2 = mid.w; r3 = ex;
+            } else {
+                const float ex = __shfl_up_sync(0xffffffffu, mid.w, 1);
+                l0 = ex; l1 = mid.x; l2 = mid.y; l3 = mid.z; r0 = mid.x; r1 = mid.y; r2 = mid.z; r3 = mid.w;
+            }
+            const int yq = y0 + r;
+            const bool qin = kin && yq >= 0 && yq < ny;
+            const float4 q = qin ? Store<S>::load4((c ? Qb : Qr) + (size_t)yq * Sst + 4 + k) : z4;
+            float4 cv = v[c][r];
+            const uint32_t bits = ((c ? m[1] : m[0]) >> (4 * r)) & 0xFu;
+            const float n0 = fmaf(omega, fmaf(0.25f, (l0 + r0) + (up.x + dn.x), q.x - cv.x), cv.x);
+            const float n1 = fmaf(omega, fmaf(0.25f, (l1 + r1) + (up.y + dn.y), q.y - cv.y), cv.y);
+            const float n2 = fmaf(omega, fmaf(0.25f, (l2 + r2) + (up.z + dn.z), q.z - cv.z), cv.z);
+            const float n3 = fmaf(omega, fmaf(0.25f, (l3 + r3) + (up.w + dn.w), q.w - cv.w), cv.w);
+            cv.x = (bits & 1u) ? n0 : cv.x;
+            cv.y = (bits & 2u) ? n1 : cv.y;
+            cv.z = (bits & 4u) ? n2 : cv.z;
+            cv.w = (bits & 8u) ? n3 : cv.w;
+            v[c][r] = cv;
+        }
+    }
+    const bool kint = lane >= HK4 && lane < 32 - HK4 && kin;
+    if (kint) {
+#pragma unroll
+        for (int r = 0; r < RB; r++) {
+            const int y = y0 + r;
+            if (y >= y_tile && y < y_tile + YI && y < ny) {
+                const size_t off = (size_t)y * Sst + 4 + k;
+                Store<S>::store4(Rout + off, v[0][r]);
+                Store<S>::store4(Bout + off, v[1][r]);
+            }
+        }
+    }
+}
+
+// ---- driver ----------------------------------------------------------------------
+
+template <class S>
+static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, int mode, const hp_params *p,
+                       hp_stats *st, RelaxLayout &R, cudaStream_t s) {
+    RBLayout g = R.rb;
+    S *e[2][2] = {{(S *)R.mx.e_r, (S *)R.mx.e_b}, {(S *)R.mx.e_r2, (S *)R.mx.e_b2}};
+    S *q[2] = {(S *)R.mx.q_r, (S *)R.mx.q_b};
+    double *x = R.mx.x;
+    RelaxScalars *sc = R.scal;
+    const size_t plane = (size_t)ny * g.S * sizeof(S);
+    for (int i = 0; i < 2; i++) {
+        TW_CUDA(cudaMemsetAsync(q[i], 0, plane, s));
+        TW_CUDA(cudaMemsetAsync(e[0][i], 0, plane, s));
+        TW_CUDA(cudaMemsetAsync(e[1][i], 0, plane, s));
+    }
+    TW_LAUNCH(mx_init_kernel, dim3(ceil_div(g.W2 + 31, 128), ny), 128, 0, s, occ, u, nx, ny, gx, gy, mode,
+              (p->flags & HP_WARM_START) ? 1 : 0, g, x);
+    TW_CHECK_LAUNCH();
+    const int T = 4, K = 32;
+    // inner solves relax the correction residual by this factor (bounded by the storage precision)
+    const double inner_drop = (sizeof(S) == 4) ? 1e-4 : (std::is_same<S, __half>::value ? 2e-3 : 1e-2);
+    RelaxCtl c;   // omega state carried across the inner solves
+    memset(&c, 0, sizeof(c));
+    c.adapt = p->omega == 0.0;
+    c.omega = c.adapt ? sor_initial_omega(nx, ny) : p->omega;
+    int sweeps = 0, launches = 0, checks = 0, outer = 0;
+    double r_inf = 0.0;
+    st->status = TW_NOT_CONVERGED;
+    const dim3 rgrid(ceil_div(g.W4, 128), ny), rblock(128);
+    const int KI4 = 32 - 2 * ((T + 4) / 4), YI = kMxWarps * kMxRows - 4 * T;
+    const dim3 tgrid(ceil_div(g.W4, KI4), ceil_div(ny, YI));
+    for (;;) {
+        // 1. FP64 residual max of the master
+        TW_CUDA(cudaMemsetAsync(&sc->max64, 0, sizeof(sc->max64) + sizeof(sc->sum64), s));
+        TW_LAUNCH((mx_residual_kernel<S>), rgrid, rblock, 0, s, g, x, nx, ny, 0, (const double *)nullptr,
+                  (S *)nullptr, (S *)nullptr, &sc->max64);
+        TW_CHECK_LAUNCH();
+        unsigned long long mb = 0;
+        TW_CUDA(cudaMemcpyAsync(&mb, &sc->max64, sizeof(mb), cudaMemcpyDeviceToHost, s));
+        TW_CUDA(cudaStreamSynchronize(s));
+        memcpy(&r_inf, &mb, sizeof(double));
+        double sum = 0.0;
+        TW_CUDA(cudaMemcpyAsync(&sum, &sc->sum64, sizeof(sum), cudaMemcpyDeviceToHost, s));
+        TW_CUDA(cudaStreamSynchronize(s));
+        st->resid_l2 = sqrt(sum);
+        checks++;
+        if ((p->tol > 0.0 && r_inf <= p->tol) || r_inf == 0.0) { st->status = TW_OK; break; }
+        if (sweeps >= p->max_sweeps) break;
+        // 2. q = r / s in storage precision (s kept on the device in pad1[0])
+        double *scale = &sc->pad1[0];
+        TW_CUDA(cudaMemcpyAsync(scale, &r_inf, sizeof(double), cudaMemcpyHostToDevice, s));
+        TW_LAUNCH((mx_residual_kernel<S>), rgrid, rblock, 0, s, g, x, nx, ny, 1, (const double *)scale, q[0], q[1],
+                  &sc->max64);
+        // 3. inner SOR on e (cold start at 0)
+        TW_CUDA(cudaMemsetAsync(e[0][0], 0, plane, s));
+        TW_CUDA(cudaMemsetAsync(e[0][1], 0, plane, s));
+        int cur = 0;
+        c.r_prev = -1.0;
+        c.same_iv = 0;
+        c.K = K;
+        c.tol = inner_drop;    // |q| <= 1, so this is the relative drop
+        c.status = TW_NOT_CONVERGED;
+        c.omega_f = (float)c.omega;
+        float *omega_dev = &sc->ctl.omega_f;
+        for (int it = 0; sweeps < p->max_sweeps; it++) {
+            TW_CUDA(cudaMemcpyAsync(omega_dev, &c.omega_f, sizeof(float), cudaMemcpyHostToDevice, s));
+            int n = p->max_sweeps - sweeps < K ? p->max_sweeps - sweeps : K;
+            for (int done = 0; done < n; done += T) {
+                // a partial last launch is rounded up to T sweeps (the cap may be exceeded by < T)
+                TW_LAUNCH((mx_tb_kernel<T, S>), tgrid, kMxWarps * 32, 0, s, e[cur][0], e[cur][1], e[1 - cur][0],
+                          e[1 - cur][1], q[0], q[1], g.MR, g.MB, ny, g.W4, g.S, g.MW, (const float *)omega_dev);
+                cur = 1 - cur;
+                launches++;
+            }
+            TW_CHECK_LAUNCH();
+            sweeps += ((n + T - 1) / T) * T;
+            TW_CUDA(cudaMemsetAsync(&sc->max32, 0, sizeof(unsigned int), s));
+            TW_LAUNCH((mx_inner_residual_kernel<S>), dim3(ceil_div(g.W4, 64), ceil_div(ny, 4)), dim3(64, 4), 0, s, g,
+                      ny, e[cur][0], e[cur][1], q[0], q[1], &sc->max32);
+            float rf;
+            int er = read_max_f32(&sc->max32, s, &rf);
+            if (er) return er;
+            checks++;
+            const double prev = c.r_prev;
+            if (!relax_control(c, (double)rf, n)) break;
+            if (prev > 0.0 && it > 4 && rf > 0.98 * prev) break;   // storage floor reached
+        }
+        // 4. x += s e
+        TW_LAUNCH((mx_update_kernel<S>), dim3(ceil_div(nx, 256), ny), 256, 0, s, g, x, nx, ny, (const double *)scale,
+                  e[cur][0], e[cur][1]);
+        TW_CHECK_LAUNCH();
+        outer++;
+        if (outer > 64) break;
+    }
+    const size_t n = (size_t)nx * ny;
+    TW_LAUNCH(mx_output_kernel, ceil_div(n, 256), 256, 0, s, x, u, n);
+    TW_CHECK_LAUNCH();
+    st->sweeps = sweeps;
+    st->checks = checks;
+    st->omega = c.omega;
+    st->sweep_launches = launches;
+    st->tblock = T;
+    st->resid_inf = r_inf;   // the FP64 master's residual (the FP32 output rounds it)
+    return TW_OK;
+}
+
+int relax_mixed(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, int mode, const hp_params *p,
+                hp_stats *st, RelaxLayout &R, cudaStream_t s) {
+    switch (p->storage) {
+        case HP_STORE_F16: return mixed_solve<__half>(occ, nx, ny, gx, gy, u, mode, p, st, R, s);
+        case HP_STORE_BF16: return mixed_solve<__nv_bfloat16>(occ, nx, ny, gx, gy, u, mode, p, st, R, s);
+        default: return mixed_solve<float>(occ, nx, ny, gx, gy, u, mode, p, st, R, s);
+    }
 }
 
 }  // namespace tw

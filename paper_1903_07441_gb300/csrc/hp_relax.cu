@@ -433,9 +433,11 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
         e = relax_mixed(occ, nx, ny, gx, gy, u, mode, p, &local, R, s);
     }
     if (e) return e;
-    e = final_residual_full(occ, nx, ny, mode == 1 ? -1 : gx, mode == 1 ? -1 : gy, u, R.scal, s,
-                            &local.resid_inf, &local.resid_l2);
-    if (e) return e;
+    if (p->method != HP_MIXED) {   // HP_MIXED reports the residual of its FP64 master
+        e = final_residual_full(occ, nx, ny, mode == 1 ? -1 : gx, mode == 1 ? -1 : gy, u, R.scal, s,
+                                &local.resid_inf, &local.resid_l2);
+        if (e) return e;
+    }
     if (mode == 0 && (p->flags & HP_OUT_PHI)) {
         size_t n = (size_t)nx * ny;
         TW_LAUNCH(to_phi_kernel, ceil_div(n, 256), 256, 0, s, u, n);
