@@ -363,6 +363,34 @@ def run_twgrid(args, rank, world, dist):
                                                  "time-to-solution is a lower bound",
                  "wall_s": time.perf_counter() - p0}
 
+    # ---- the other forms of the relaxation on the same scene and tolerance
+    forms = None
+    if not args.no_forms and rank == 0:
+        forms = {}
+        tw.tw_build_grid(grid, sc.robot, sc.tracks, sc.law, static_occ=static_d, occ=occ)
+        for name, prm in (("rbsor_fp32_graph", params),
+                          ("rbsor_fp32_host_loop", tw.Params(tol=args.tol, max_sweeps=args.max_sweeps,
+                                                             flags=tw.HP_HOST_LOOP)),
+                          ("mixed_fp16", tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_F16, tol=args.tol,
+                                                   max_sweeps=args.max_sweeps)),
+                          ("mixed_bf16", tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_BF16, tol=args.tol,
+                                                   max_sweeps=args.max_sweeps))):
+            tw.hp_relax(grid, occ, sc.goal, field=u, params=prm)   # warm
+            times, fst = [], None
+            for _ in range(5):
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                _, fst = tw.hp_relax(grid, occ, sc.goal, field=u, params=prm)
+                b_.record(stream)
+                torch.cuda.synchronize()
+                times.append(a_.elapsed_time(b_))
+            t_med = float(np.median(times))
+            forms[name] = {"ms_to_solution": t_med, "solves_per_s": 1e3 / t_med, "sweeps": fst["sweeps"],
+                           "resid_inf": fst["resid_inf"], "converged": fst["status"] == tw.TW_OK}
+        if plain and plain["converged"]:
+            for f_ in forms.values():
+                f_["speedup_vs_plain_fp32"] = plain["seconds"] * 1e3 / f_["ms_to_solution"]
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -374,7 +402,7 @@ def run_twgrid(args, rank, world, dist):
            "resid_inf_max": max(resid) if resid else None, "relax_status": sorted(set(status)),
            "path_status": sorted(set(path_status)), "path_len": [n for _, _, n in stats_log][:1],
            "omega": stats_log[0][0]["omega"] if stats_log else None,
-           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain,
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms,
            "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": min(step_ms), "max": max(step_ms), "host_p50": float(np.percentile(host_ms, 50))},
            "wall_s": wall, "clocks": clocks}
@@ -454,6 +482,7 @@ def main():
     ap.add_argument("--plain-max-sweeps", type=int, default=400000)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

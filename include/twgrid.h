@@ -203,6 +203,31 @@ int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *fi
 int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *field_dev,
                      const hp_params *p, hp_stats *stats, void *stream);
 
+/* hp_relax_batched: many planners solved together (uneven grids).  Each
+ * instance is the hp_relax problem of its own occupancy and goal; all of them
+ * are relaxed by red-black SOR inside one CUDA graph whose sweep kernel is a
+ * persistent, grid-stride kernel over the tiles of every still-active
+ * instance, with per-instance omega, residual and convergence (converged
+ * instances drop out).  The blocking depth T is autotuned per batch shape
+ * (p->tblock 2 or 4 forces it; the tuning sweeps count towards the solve).
+ * n: 1..1024 instances.  p: method HP_RBSOR, FP32; tol, max_sweeps, omega
+ * (0 = adaptive) and check_every apply to every instance; HP_WARM_START reads
+ * u from field_dev, HP_OUT_PHI writes phi (not both).  stats: host array of n,
+ * latency_ms: host array of n or NULL -- the time from the start of the
+ * relaxation to each instance's convergence, measured on the device
+ * (%globaltimer).  Returns TW_OK, TW_NOT_CONVERGED if any instance hit the
+ * cap, or the first error (per-instance status in stats[i].status, e.g.
+ * TW_EGOAL_BLOCKED).  Synchronises `stream`. */
+typedef struct {
+    int nx, ny;              /* grid of this instance (3..65536) */
+    const uint8_t *occ_dev;  /* device uint8 [ny][nx] occupancy (nonzero = obstacle) */
+    int gx, gy;              /* goal cell */
+    float *field_dev;        /* device float [ny][nx]: the field (u unless HP_OUT_PHI) */
+} hp_instance;
+size_t hp_relax_batched_workspace_size(int n, const hp_instance *inst, const hp_params *p);
+int hp_relax_batched(int n, const hp_instance *inst, const hp_params *p, hp_stats *stats,
+                     double *latency_ms, void *workspace, size_t workspace_bytes, void *stream);
+
 /* hp_relax_dirichlet: the same solver on a general Dirichlet problem: cells
  * with fixed_dev != 0 keep their value of u_dev, the others satisfy the
  * discrete Laplace equation.  Every border cell must be fixed.  u_dev is read

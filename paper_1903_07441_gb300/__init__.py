@@ -32,6 +32,7 @@ HP_WARM_START, HP_OUT_PHI, HP_TIMING, HP_HOST_LOOP = 1, 2, 4, 8
 EXPORTS = (
     "tw_build_grid_workspace_size", "tw_build_grid", "tw_ring_count",
     "hp_relax_workspace_size", "hp_relax", "hp_relax_noalloc", "hp_relax_dirichlet", "hp_residual",
+    "hp_relax_batched_workspace_size", "hp_relax_batched",
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
     "kf_update", "kf_init", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
 )
@@ -67,6 +68,11 @@ class hp_params(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("storage", ctypes.c_int), ("omega", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("tblock", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class hp_instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("occ_dev", ctypes.c_void_p),
+                ("gx", ctypes.c_int), ("gy", ctypes.c_int), ("field_dev", ctypes.c_void_p)]
 
 
 class hp_stats(ctypes.Structure):
@@ -126,6 +132,10 @@ def load() -> ctypes.CDLL:
     lib.hp_relax.restype = I
     lib.hp_relax_noalloc.argtypes = [P, P, I, I, P, P, P, P]
     lib.hp_relax_noalloc.restype = I
+    lib.hp_relax_batched_workspace_size.argtypes = [I, P, P]
+    lib.hp_relax_batched_workspace_size.restype = Z
+    lib.hp_relax_batched.argtypes = [I, P, P, P, P, P, Z, P]
+    lib.hp_relax_batched.restype = I
     lib.hp_relax_dirichlet.argtypes = [I, I, P, P, P, P, P, Z, P]
     lib.hp_relax_dirichlet.restype = I
     lib.hp_residual.argtypes = [I, I, P, P, P, P, P, Z, P]
@@ -271,6 +281,29 @@ def hp_relax_noalloc(grid: tw_grid, occ, goal, field=None, params: Optional[Para
                                  ctypes.byref(cp), ctypes.byref(stats), _stream(occ.device))
     _check("hp_relax_noalloc", st, ok=(TW_OK, TW_NOT_CONVERGED))
     return field, stats.as_dict()
+
+
+def hp_relax_batched(occs, goals, fields=None, params: Optional[Params] = None):
+    """Relax many planners together.  occs: list of device uint8 [ny][nx];
+    goals: list of (gx, gy).  Returns (fields, list of stats dicts, latency_ms array)."""
+    torch = _torch()
+    lib = load()
+    params = params or Params()
+    n = len(occs)
+    if fields is None:
+        fields = [torch.empty(o.shape, dtype=torch.float32, device=o.device) for o in occs]
+    arr = (hp_instance * n)()
+    for i, (o, g, f) in enumerate(zip(occs, goals, fields)):
+        arr[i] = hp_instance(int(o.shape[1]), int(o.shape[0]), o.data_ptr(), int(g[0]), int(g[1]), f.data_ptr())
+    cp = params.c()
+    ws = workspace(lib.hp_relax_batched_workspace_size(n, arr, ctypes.byref(cp)), occs[0].device, "batch")
+    stats = (hp_stats * n)()
+    lat = np.zeros(n, np.float64)
+    st = lib.hp_relax_batched(n, arr, ctypes.byref(cp), stats, lat.ctypes.data_as(ctypes.c_void_p), _ptr(ws),
+                              ws.numel(), _stream(occs[0].device))
+    if st < 0 and all(s_.status < 0 for s_ in stats):
+        raise TwError("hp_relax_batched", st)
+    return fields, [s_.as_dict() for s_ in stats], lat
 
 
 def hp_relax_dirichlet(fixed, u, params: Optional[Params] = None):

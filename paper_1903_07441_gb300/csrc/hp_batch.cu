@@ -1,0 +1,548 @@
+// Batched relaxation: many planners with uneven grids solved together.
+//
+// Every instance gets its own colour-split planes, free-cell bits and
+// convergence state (RelaxCtl: omega, residual history, sweeps).  One CUDA
+// graph with a conditional while-node runs the check intervals for the whole
+// batch:
+//   * batch_tb_kernel: a persistent, grid-stride kernel (one wave of CTAs,
+//     sized from the occupancy calculator) that walks a device-side list of
+//     the tiles of every still-active instance and applies the T-fused
+//     red-black SOR tile update (the same tile code as the single-field
+//     kernel) with that instance's omega;
+//   * batch_residual_kernel: per-instance FP32 residual max over the same list;
+//   * batch_control_kernel: one thread per instance applies relax_control,
+//     retires converged (or capped) instances with their completion time
+//     (%globaltimer, for the per-instance latency), compacts the tile list of
+//     the remaining ones and sets the loop condition.
+// The blocking depth T is chosen per batch shape by a small autotuner that
+// times the candidates on the batch itself (Gauss-Seidel sweeps that count
+// towards the solve) and caches the choice.
+#include <float.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "hp_internal.cuh"
+#include "hp_tile.cuh"
+
+namespace tw {
+
+constexpr int kBRows = 8, kBWarps = 8;
+constexpr int kMaxBatch = 1024;
+
+struct BatchInst {
+    int nx, ny, gx, gy;
+    int W2, W4, S, MW;
+    int tx, ty, pad0, pad1;           // tiles per row / column for the chosen T
+    float *P[2][2];                   // [buffer][colour] planes
+    uint32_t *MR, *MB;
+    const uint8_t *occ;
+    float *field;
+    unsigned int rmax;                // FP32 residual max (bits) of the current interval
+    int active;                       // 1 while the instance is being relaxed
+    int error;                        // TW_EGOAL_BLOCKED if the goal cell is occupied
+    int pad2;
+    unsigned long long t_done;        // %globaltimer at retirement
+    unsigned long long max64;         // final FP64 residual max (bits) and sum of squares
+    double sum64;
+    RelaxCtl ctl;
+};
+
+struct BatchHdr {
+    int n, n_active, rounds, T;
+    unsigned long long t_start;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int T>
+struct BShape {
+    static constexpr int HK4 = (T + 1 + 3) / 4, HY = 2 * T;
+    static constexpr int KI4 = 32 - 2 * HK4, YI = kBWarps * kBRows - 2 * HY;
+};
+
+static void tiles_for(int T, int W4, int ny, int *tx, int *ty) {
+    int KI4 = 32 - 2 * ((T + 4) / 4), YI = kBWarps * kBRows - 4 * T;
+    *tx = (W4 + KI4 - 1) / KI4;
+    *ty = (ny + YI - 1) / YI;
+}
+
+// ---- kernels ---------------------------------------------------------------------
+
+__global__ void batch_pack_kernel(BatchInst *I, int warm) {
+    BatchInst &b = I[blockIdx.z];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (y >= b.ny) return;   // uniform per block
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int color = 0; color < 2; color++) {
+        const int x = 2 * k + ((y + color) & 1);
+        float v = 0.0f;
+        bool free_cell = false;
+        if (k < b.W2 && x < b.nx) {
+            const size_t c = (size_t)y * b.nx + x;
+            const bool goal = (x == b.gx && y == b.gy);
+            if (goal && b.occ[c] != 0) b.error = TW_EGOAL_BLOCKED;
+            const bool fixed = goal || x == 0 || y == 0 || x == b.nx - 1 || y == b.ny - 1 || b.occ[c] != 0;
+            free_cell = !fixed;
+            v = goal ? 1.0f : (fixed ? 0.0f : (warm ? b.field[c] : 0.5f));
+        }
+        const unsigned bits = __ballot_sync(0xffffffffu, free_cell);
+        if (k < b.W2) b.P[0][color][(size_t)y * b.S + 4 + k] = v;
+        if (lane == 0 && (k >> 5) < b.MW) (color ? b.MB : b.MR)[(size_t)y * b.MW + (k >> 5)] = bits;
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kBWarps * 32)
+batch_tb_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const BatchHdr *__restrict__ H,
+                int parity) {
+    __shared__ float4 s_top[2][kBWarps][32];
+    __shared__ float4 s_bot[2][kBWarps][32];
+    const int n_active = H->n_active;
+    for (int t = blockIdx.x; t < n_active; t += gridDim.x) {
+        __syncthreads();   // the previous tile's exchange buffers are free again
+        const int2 it = list[t];
+        const BatchInst &b = I[it.x];
+        const int bx = it.y % b.tx, by = it.y / b.tx;
+        tb_tile<T, kBRows, kBWarps>(b.P[parity][0], b.P[parity][1], b.P[1 - parity][0],
+                                           b.P[1 - parity][1], b.MR, b.MB, b.ny, b.W4, b.S, b.MW,
+                                           b.ctl.omega_f, bx, by, s_top, s_bot);
+    }
+}
+
+// FP32 residual max of each active tile's interior, one atomic per CTA and tile.
+template <int T>
+__global__ void __launch_bounds__(256)
+batch_residual_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const BatchHdr *__restrict__ H) {
+    using Sh = BShape<T>;
+    const int n_active = H->n_active;
+    for (int t = blockIdx.x; t < n_active; t += gridDim.x) {
+        const int2 it = list[t];
+        BatchInst &b = I[it.x];
+        const int bx = it.y % b.tx, by = it.y / b.tx;
+        float r = 0.0f;
+        for (int idx = threadIdx.x; idx < Sh::KI4 * Sh::YI; idx += blockDim.x) {
+            const int k4 = bx * Sh::KI4 + idx % Sh::KI4;
+            const int y = by * Sh::YI + idx / Sh::KI4;
+            if (k4 >= b.W4 || y < 1 || y >= b.ny - 1) continue;
+            const int k = 4 * k4;
+#pragma unroll
+            for (int color = 0; color < 2; color++) {
+                const float *U = b.P[0][color], *V = b.P[0][1 - color];
+                const uint32_t bits = ((color ? b.MB : b.MR)[(size_t)y * b.MW + (k >> 5)] >> (k & 31)) & 0xFu;
+                if (!bits) continue;
+                float4 nb[4];
+                rb_load_neighbours(V, b.S, y, k, (y + color) & 1, nb);
+                const float4 c = *reinterpret_cast<const float4 *>(U + (size_t)y * b.S + 4 + k);
+                if (bits & 1u) r = fmaxf(r, fabsf(rb_avg(nb, 0) - c.x));
+                if (bits & 2u) r = fmaxf(r, fabsf(rb_avg(nb, 1) - c.y));
+                if (bits & 4u) r = fmaxf(r, fabsf(rb_avg(nb, 2) - c.z));
+                if (bits & 8u) r = fmaxf(r, fabsf(rb_avg(nb, 3) - c.w));
+            }
+        }
+        block_max_atomic(r, &b.rmax);
+        __syncthreads();
+    }
+}
+
+// Per-instance control and tile-list compaction (one block, one thread per instance).
+__global__ void __launch_bounds__(kMaxBatch)
+batch_control_kernel(BatchInst *__restrict__ I, BatchHdr *__restrict__ H, int2 *__restrict__ list, int max_rounds,
+                     int final_check, cudaGraphConditionalHandle handle, int use_handle) {
+    __shared__ int s_scan[kMaxBatch];
+    const int i = threadIdx.x;
+    const int n = H->n;
+    int my_tiles = 0;
+    if (i < n) {
+        BatchInst &b = I[i];
+        if (b.active) {
+            RelaxCtl c = b.ctl;
+            const float rf = __uint_as_float(b.rmax);
+            b.rmax = 0u;
+            c.sweeps += c.K;
+            int go = relax_control(c, (double)rf, c.K);
+            if (c.sweeps + c.K > c.max_sweeps || final_check) go = 0;
+            if (b.error) go = 0;
+            c.omega_f = (float)c.omega;
+            b.ctl = c;
+            if (!go) {
+                b.active = 0;
+                b.t_done = globaltimer();
+            } else {
+                my_tiles = b.tx * b.ty;
+            }
+        }
+    }
+    // exclusive scan of the active instances' tile counts
+    s_scan[i] = my_tiles;
+    __syncthreads();
+    for (int off = 1; off < kMaxBatch; off <<= 1) {
+        const int v = i >= off ? s_scan[i - off] : 0;
+        __syncthreads();
+        s_scan[i] += v;
+        __syncthreads();
+    }
+    const int end = s_scan[i], start = end - my_tiles;
+    for (int t = 0; t < my_tiles; t++) list[start + t] = make_int2(i, t);
+    if (i == kMaxBatch - 1) {
+        H->n_active = end;
+        H->rounds += 1;
+        const int go = end > 0 && H->rounds < max_rounds;
+        if (use_handle) cudaGraphSetConditional(handle, go ? 1u : 0u);
+    }
+}
+
+__global__ void batch_unpack_kernel(BatchInst *I, int to_phi) {
+    const BatchInst &b = I[blockIdx.z];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= b.nx || y >= b.ny) return;
+    const float v = b.P[0][(x + y) & 1][(size_t)y * b.S + 4 + (x >> 1)];
+    b.field[(size_t)y * b.nx + x] = to_phi ? 1.0f - v : v;
+}
+
+__global__ void __launch_bounds__(256) batch_final_residual_kernel(BatchInst *I) {
+    BatchInst &b = I[blockIdx.z];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    double r = 0.0;
+    if (x > 0 && y > 0 && x < b.nx - 1 && y < b.ny - 1) {
+        const size_t c = (size_t)y * b.nx + x;
+        const bool fixed = b.occ[c] != 0 || (x == b.gx && y == b.gy);
+        if (!fixed) {
+            const float *u = b.field;
+            const double a = 0.25 * ((((double)u[c + 1] + (double)u[c - 1]) + (double)u[c + b.nx]) + (double)u[c - b.nx]);
+            r = fabs(a - (double)u[c]);
+        }
+    }
+    block_max_sum_f64(r, &b.max64, &b.sum64);
+}
+
+__global__ void batch_start_kernel(BatchHdr *H) { H->t_start = globaltimer(); }
+
+// ---- host side ------------------------------------------------------------------------
+
+struct BatchLayout {
+    BatchHdr *hdr;
+    BatchInst *inst;
+    int2 *list;
+    size_t max_tiles;
+};
+
+static size_t carve_batch(Carver &cv, int n, const hp_instance *in, std::vector<BatchInst> *host,
+                          BatchLayout *L) {
+    BatchLayout l;
+    l.hdr = cv.take<BatchHdr>(1);
+    l.inst = cv.take<BatchInst>(n > 0 ? n : 1);
+    size_t max_tiles = 0;
+    for (int i = 0; i < n; i++) {
+        RBLayout g = rb_layout(in[i].nx, in[i].ny);
+        int tx2, ty2;
+        tiles_for(4, g.W4, in[i].ny, &tx2, &ty2);   // the deepest candidate has the most tiles
+        max_tiles += (size_t)tx2 * ty2;
+    }
+    l.list = cv.take<int2>(max_tiles > 0 ? max_tiles : 1);
+    l.max_tiles = max_tiles;
+    for (int i = 0; i < n; i++) {
+        RBLayout g = rb_layout(in[i].nx, in[i].ny);
+        const size_t plane = (size_t)in[i].ny * g.S;
+        BatchInst b;
+        memset(&b, 0, sizeof(b));
+        b.nx = in[i].nx; b.ny = in[i].ny; b.gx = in[i].gx; b.gy = in[i].gy;
+        b.W2 = g.W2; b.W4 = g.W4; b.S = g.S; b.MW = g.MW;
+        b.P[0][0] = cv.take<float>(plane); b.P[0][1] = cv.take<float>(plane);
+        b.P[1][0] = cv.take<float>(plane); b.P[1][1] = cv.take<float>(plane);
+        b.MR = cv.take<uint32_t>((size_t)in[i].ny * g.MW);
+        b.MB = cv.take<uint32_t>((size_t)in[i].ny * g.MW);
+        b.occ = in[i].occ_dev;
+        b.field = in[i].field_dev;
+        if (host) host->push_back(b);
+    }
+    if (L) *L = l;
+    return cv.need;
+}
+
+static std::mutex g_batch_mutex;
+static std::map<std::tuple<int, const void *, int, size_t>, int> g_tuned_T;   // (dev, ws, n, cells) -> T
+
+struct BatchGraph {
+    int dev, T, K, rounds;
+    const void *ws;
+    int n;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+static std::vector<BatchGraph> g_batch_graphs;
+
+static int persistent_grid(const void *func, int threads) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, func, threads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+template <int T>
+static void launch_batch_sweep(BatchLayout &L, int parity, cudaStream_t s) {
+    const int grid = persistent_grid((const void *)batch_tb_kernel<T>, kBWarps * 32);
+    TW_LAUNCH((batch_tb_kernel<T>), grid, kBWarps * 32, 0, s, L.inst, L.list, L.hdr, parity);
+}
+
+static void launch_batch_sweep_T(int T, BatchLayout &L, int parity, cudaStream_t s) {
+    if (T == 4) launch_batch_sweep<4>(L, parity, s);
+    else launch_batch_sweep<2>(L, parity, s);
+}
+
+static void launch_batch_residual_T(int T, BatchLayout &L, cudaStream_t s) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (T == 4) TW_LAUNCH((batch_residual_kernel<4>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
+    else TW_LAUNCH((batch_residual_kernel<2>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
+}
+
+static int build_batch_graph(BatchLayout L, int T, int K, int max_rounds, BatchGraph *out) {
+    cudaGraph_t g;
+    TW_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return 1; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    e = cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return 1; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // capture the body from a private stream (the launch helpers are stream-based)
+    cudaStream_t cs;
+    TW_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); cudaGraphDestroy(g); set_cuda_error(e); return 1; }
+    for (int i = 0; i < K / T; i++) launch_batch_sweep_T(T, L, i & 1, cs);
+    launch_batch_residual_T(T, L, cs);
+    TW_LAUNCH(batch_control_kernel, 1, kMaxBatch, 0, cs, L.inst, L.hdr, L.list, max_rounds, 0, h, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return 1; }
+    out->graph = g;
+    out->exec = exec;
+    return TW_OK;
+}
+
+// Autotuner: time each candidate depth with two launches of Gauss-Seidel
+// sweeps (omega = 1) on the batch; the sweeps count towards the solve.
+static int autotune(BatchLayout &L, std::vector<BatchInst> &hb, int n, cudaStream_t s, int *T_out, int *gs_sweeps) {
+    const int cands[2] = {2, 4};
+    float best = FLT_MAX;
+    int bestT = 4;
+    cudaEvent_t a, b;
+    TW_CUDA(cudaEventCreate(&a));
+    TW_CUDA(cudaEventCreate(&b));
+    *gs_sweeps = 0;
+    for (int ci = 0; ci < 2; ci++) {
+        const int T = cands[ci];
+        std::vector<int2> lst;
+        for (int i = 0; i < n; i++) {
+            tiles_for(T, hb[i].W4, hb[i].ny, &hb[i].tx, &hb[i].ty);
+            for (int t = 0; t < hb[i].tx * hb[i].ty; t++) lst.push_back(make_int2(i, t));
+        }
+        BatchHdr h = {n, (int)lst.size(), 0, T, 0ull};
+        TW_CUDA(cudaMemcpyAsync(L.inst, hb.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s));
+        TW_CUDA(cudaMemcpyAsync(L.list, lst.data(), sizeof(int2) * lst.size(), cudaMemcpyHostToDevice, s));
+        TW_CUDA(cudaMemcpyAsync(L.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+        TW_CUDA(cudaEventRecord(a, s));
+        launch_batch_sweep_T(T, L, 0, s);
+        launch_batch_sweep_T(T, L, 1, s);
+        TW_CUDA(cudaEventRecord(b, s));
+        TW_CUDA(cudaEventSynchronize(b));
+        float ms = 0.0f;
+        TW_CUDA(cudaEventElapsedTime(&ms, a, b));
+        *gs_sweeps += 2 * T;
+        const float per_sweep = ms / (2 * T);
+        if (per_sweep < best) { best = per_sweep; bestT = T; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *T_out = bestT;
+    return TW_OK;
+}
+
+}  // namespace tw
+
+using namespace tw;
+
+extern "C" size_t hp_relax_batched_workspace_size(int n, const hp_instance *inst, const hp_params *p) {
+    (void)p;
+    if (n < 1 || n > kMaxBatch || !inst) return 0;
+    Carver cv;
+    return carve_batch(cv, n, inst, nullptr, nullptr);
+}
+
+extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params *p, hp_stats *stats,
+                                double *latency_ms, void *workspace, size_t workspace_bytes, void *stream) {
+    if (n < 1 || n > kMaxBatch || !inst || !p || !stats) return TW_EINVAL;
+    if (p->method != HP_RBSOR || !(p->tol >= 0.0) || p->max_sweeps < 1 ||
+        ((p->flags & HP_WARM_START) && (p->flags & HP_OUT_PHI)) ||
+        !(p->omega == 0.0 || (p->omega > 0.0 && p->omega < 2.0)))
+        return TW_EINVAL;
+    size_t cells = 0;
+    for (int i = 0; i < n; i++) {
+        const hp_instance &q = inst[i];
+        if (q.nx < 3 || q.ny < 3 || q.nx > 65536 || q.ny > 65536 || !q.occ_dev || !q.field_dev) return TW_EINVAL;
+        if (q.gx < 1 || q.gy < 1 || q.gx > q.nx - 2 || q.gy > q.ny - 2) return TW_EGOAL_BLOCKED;
+        cells += (size_t)q.nx * q.ny;
+    }
+    if (!workspace || !ws_aligned(workspace)) return TW_EWORKSPACE;
+    Carver cv(workspace, workspace_bytes);
+    std::vector<BatchInst> hb;
+    BatchLayout L;
+    carve_batch(cv, n, inst, &hb, &L);
+    if (!cv.ok()) return TW_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int maxW2 = 0, maxNy = 0, maxNx = 0;
+    for (int i = 0; i < n; i++) {
+        if (hb[i].W2 > maxW2) maxW2 = hb[i].W2;
+        if (hb[i].ny > maxNy) maxNy = hb[i].ny;
+        if (hb[i].nx > maxNx) maxNx = hb[i].nx;
+        for (int bb = 0; bb < 2; bb++)
+            for (int c = 0; c < 2; c++)
+                TW_CUDA(cudaMemsetAsync(hb[i].P[bb][c], 0, sizeof(float) * (size_t)hb[i].ny * hb[i].S, s));
+        hb[i].active = 1;
+        hb[i].ctl.omega = 1.0;
+        hb[i].ctl.omega_f = 1.0f;
+    }
+    TW_CUDA(cudaMemcpyAsync(L.inst, hb.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s));
+    TW_LAUNCH(batch_pack_kernel, dim3(ceil_div(maxW2 + 31, 128), maxNy, n), 128, 0, s, L.inst,
+              (p->flags & HP_WARM_START) ? 1 : 0);
+    TW_CHECK_LAUNCH();
+    {   // goal checks made by the pack kernel
+        std::vector<BatchInst> dev_copy(n);
+        TW_CUDA(cudaMemcpyAsync(dev_copy.data(), L.inst, sizeof(BatchInst) * n, cudaMemcpyDeviceToHost, s));
+        TW_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; i++) hb[i].error = dev_copy[i].error;
+    }
+
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    int dev = 0;
+    TW_CUDA(cudaGetDevice(&dev));
+    // pick the blocking depth (cached per batch shape)
+    int T = p->tblock;
+    int gs_sweeps = 0;
+    if (T != 2 && T != 4) {
+        auto key = std::make_tuple(dev, (const void *)workspace, n, cells);
+        auto f = g_tuned_T.find(key);
+        if (f != g_tuned_T.end()) {
+            T = f->second;
+        } else {
+            int e = autotune(L, hb, n, s, &T, &gs_sweeps);
+            if (e) return e;
+            g_tuned_T[key] = T;
+        }
+    }
+    const int K0 = p->check_every > 0 ? p->check_every : 32;
+    const int K = K0 / (2 * T) > 0 ? K0 / (2 * T) * (2 * T) : 2 * T;   // an even number of launches
+    // control state and the initial tile list for T
+    std::vector<int2> lst;
+    for (int i = 0; i < n; i++) {
+        tiles_for(T, hb[i].W4, hb[i].ny, &hb[i].tx, &hb[i].ty);
+        RelaxCtl &c = hb[i].ctl;
+        memset(&c, 0, sizeof(c));
+        c.adapt = p->omega == 0.0;
+        c.omega = c.adapt ? sor_initial_omega(hb[i].nx, hb[i].ny) : p->omega;
+        c.omega_f = (float)c.omega;
+        c.r_prev = -1.0;
+        c.tol = p->tol;
+        c.K = K;
+        c.max_sweeps = p->max_sweeps;
+        c.sweeps = gs_sweeps;
+        c.status = TW_NOT_CONVERGED;
+        hb[i].active = hb[i].error ? 0 : 1;
+        hb[i].rmax = 0;
+        if (hb[i].active)
+            for (int t = 0; t < hb[i].tx * hb[i].ty; t++) lst.push_back(make_int2(i, t));
+    }
+    BatchHdr h = {n, (int)lst.size(), 0, T, 0ull};
+    TW_CUDA(cudaMemcpyAsync(L.inst, hb.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s));
+    if (!lst.empty())
+        TW_CUDA(cudaMemcpyAsync(L.list, lst.data(), sizeof(int2) * lst.size(), cudaMemcpyHostToDevice, s));
+    TW_CUDA(cudaMemcpyAsync(L.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    TW_LAUNCH(batch_start_kernel, 1, 1, 0, s, L.hdr);
+
+    const int max_rounds = (p->max_sweeps - gs_sweeps) / K > 0 ? (p->max_sweeps - gs_sweeps) / K : 1;
+    BatchGraph *gr = nullptr;
+    for (auto &g : g_batch_graphs)
+        if (g.dev == dev && g.ws == workspace && g.n == n && g.T == T && g.K == K && g.rounds == max_rounds) gr = &g;
+    if (!gr) {
+        if (g_batch_graphs.size() >= 8) {
+            cudaGraphExecDestroy(g_batch_graphs.front().exec);
+            cudaGraphDestroy(g_batch_graphs.front().graph);
+            g_batch_graphs.erase(g_batch_graphs.begin());
+        }
+        BatchGraph ng;
+        ng.dev = dev; ng.T = T; ng.K = K; ng.rounds = max_rounds; ng.ws = workspace; ng.n = n;
+        int e = build_batch_graph(L, T, K, max_rounds, &ng);
+        if (e < 0) return e;
+        if (e == 0) { g_batch_graphs.push_back(ng); gr = &g_batch_graphs.back(); }
+    }
+    if (lst.empty()) {
+        // every instance failed its checks: nothing to relax
+    } else if (gr) {
+        TW_CUDA(cudaGraphLaunch(gr->exec, s));
+    } else {   // no graph support: the same intervals driven from the host
+        for (int r = 0; r < max_rounds; r++) {
+            for (int i = 0; i < K / T; i++) launch_batch_sweep_T(T, L, i & 1, s);
+            launch_batch_residual_T(T, L, s);
+            TW_LAUNCH(batch_control_kernel, 1, kMaxBatch, 0, s, L.inst, L.hdr, L.list, max_rounds, 0,
+                      (cudaGraphConditionalHandle)0, 0);
+            BatchHdr hh;
+            TW_CUDA(cudaMemcpyAsync(&hh, L.hdr, sizeof(hh), cudaMemcpyDeviceToHost, s));
+            TW_CUDA(cudaStreamSynchronize(s));
+            if (hh.n_active == 0) break;
+        }
+    }
+    TW_LAUNCH(batch_unpack_kernel, dim3(ceil_div(maxNx, 256), maxNy, n), 256, 0, s, L.inst,
+              (p->flags & HP_OUT_PHI) ? 1 : 0);
+    TW_LAUNCH(batch_final_residual_kernel, dim3(ceil_div(maxNx, 32), ceil_div(maxNy, 8), n), dim3(32, 8), 0, s,
+              L.inst);
+    TW_CHECK_LAUNCH();
+    BatchHdr hh;
+    TW_CUDA(cudaMemcpyAsync(hb.data(), L.inst, sizeof(BatchInst) * n, cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaMemcpyAsync(&hh, L.hdr, sizeof(hh), cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaStreamSynchronize(s));
+    // launches run inside the graph: rounds x (K/T sweeps + residual + control)
+    count_launches((unsigned long long)hh.rounds * (K / T + 2));
+    int worst = TW_OK;
+    for (int i = 0; i < n; i++) {
+        const BatchInst &b = hb[i];
+        hp_stats &st = stats[i];
+        memset(&st, 0, sizeof(st));
+        double rinf;
+        memcpy(&rinf, &b.max64, sizeof(double));
+        st.resid_inf = rinf;
+        st.resid_l2 = sqrt(b.sum64);
+        st.sweeps = b.ctl.sweeps;
+        st.checks = b.ctl.checks;
+        st.omega = b.ctl.omega;
+        st.tblock = T;
+        st.status = b.error ? b.error : ((p->tol > 0.0 && rinf <= p->tol) ? TW_OK : TW_NOT_CONVERGED);
+        if (latency_ms) latency_ms[i] = b.t_done > hh.t_start ? (double)(b.t_done - hh.t_start) * 1e-6 : 0.0;
+        if (st.status < 0) worst = st.status;
+        else if (st.status > 0 && worst == TW_OK) worst = st.status;
+    }
+    return worst;
+}

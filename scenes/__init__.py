@@ -341,6 +341,41 @@ def batch_instance(seed: int) -> Scene:
     return sc
 
 
+def batch_fast(seed: int, side_lo: int = 64, side_hi: int = 1024) -> Scene:
+    """One planner of the batched form drawn in a single painting pass: side
+    U{side_lo..side_hi}, target occupancy U[5 %, 35 %] reached by adding
+    shapes (rectangles sides U{4..20}, disks radius U{3..10}) until the
+    painted fraction reaches it; 10-300 tracks and its own ring law.  The
+    robot (5 %, 5 %) and goal (95 %, 95 %) cells are kept free; connectivity is
+    not enforced (an enclosed goal is still a valid relaxation)."""
+    st = Stream(seed)
+    side = int(st.integers(side_lo, side_hi, 1)[0])
+    target = float(st.uniform(1, 0.05, 0.35)[0])
+    n_obs = int(st.integers(10, 300, 1)[0])
+    growth = float(st.uniform(1, 1.2, 1.4)[0])
+    r0 = float(st.uniform(1, 0.3, 0.7)[0])
+    start = (max(1, side // 20), max(1, side // 20))
+    goal = (side - 1 - start[0], side - 1 - start[1])
+    occ = np.zeros((side, side), np.uint8)
+    cells = float(side * side)
+    painted = 0
+    while painted < target * cells:
+        batch = _shapes(st, 16, side, side, 1.0, keep_free=(start, goal))
+        for kind, p in batch:
+            (_paint_rect if kind == 0 else _paint_disk)(occ, *p)
+        painted = int(occ.sum())
+    cell = 0.05
+    rxy = ((start[0] + 0.5) * cell, (start[1] + 0.5) * cell)
+    gxy = ((goal[0] + 0.5) * cell, (goal[1] + 0.5) * cell)
+    L = side * cell
+    radius, tp, tv, meas = _simulate_tracks(st, n_obs, (0.0, 0.0, L, L), 1, 0.1, 0.05,
+                                            avoid=(np.array(rxy), np.array(gxy)), clearance=1.0)
+    sc = Scene("batch", seed, side, side, cell, static_occ=occ, start=start, goal=goal,
+               robot=_robot_pose(rxy, gxy, 0.75), tracks=synth_tracks(st, tp[0], tv[0], radius),
+               law=RingLaw(r0=r0, growth=growth), radius=radius)
+    return sc
+
+
 def by_name(name: str, seed: Optional[int] = None) -> Scene:
     table = {"static128": (static128, 1000), "dynamic512": (dynamic512, 1001),
              "static2048": (static2048, 1002), "dynamic1024": (dynamic1024, 1004)}

@@ -1,0 +1,82 @@
+"""Batched relaxation (hp_relax_batched): uneven planners solved together in
+one graph-driven persistent launch, each checked against the FP64 oracle with
+the a-posteriori bound and against the single-field solver."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1903_07441_gb300 as tw
+import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_07441_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _batch(n, seed0, lo=40, hi=260):
+    out = []
+    for i in range(n):
+        sc = scenes.batch_fast(seed0 + i, side_lo=lo, side_hi=hi)
+        occ, _, _ = oracle.build_grid(sc)
+        if occ[sc.goal[1], sc.goal[0]] != 0:
+            free = np.argwhere(occ == 0)
+            d = np.hypot(free[:, 1] - sc.goal[0], free[:, 0] - sc.goal[1])
+            j = int(np.argmin(d))
+            sc.goal = (int(free[j, 1]), int(free[j, 0]))
+        out.append((sc, occ))
+    return out
+
+
+@pytest.mark.parametrize("tblock", [0, 2, 4])
+def test_batched_matches_oracle_and_single_solver(dev, tblock):
+    cases = _batch(10, 8100)
+    occs = [torch.from_numpy(o).to(dev) for _, o in cases]
+    goals = [sc.goal for sc, _ in cases]
+    fields, stats, lat = tw.hp_relax_batched(occs, goals, params=tw.Params(tol=1e-6, tblock=tblock))
+    torch.cuda.synchronize()
+    for (sc, occ), f, st, l in zip(cases, fields, stats, lat):
+        assert st["status"] == tw.TW_OK and st["resid_inf"] <= 1e-6, st
+        u = f.cpu().numpy().astype(np.float64)
+        ustar, fixed = oracle.solve_field(occ, sc.goal, tol=1e-13)
+        tau = oracle.exit_time(fixed).max()
+        assert np.abs(u - ustar).max() <= tau * st["resid_inf"] * 1.001 + 1e-7
+        single, s1 = tw.hp_relax(tw.make_grid(sc.nx, sc.ny, sc.cell), torch.from_numpy(occ).to(dev), sc.goal,
+                                 params=tw.Params(tol=1e-6))
+        assert np.abs(u - single.cpu().numpy()).max() <= tau * 2e-6 + 1e-7
+        assert l > 0.0
+    if tblock in (2, 4):
+        assert all(st["tblock"] == tblock for st in stats)
+
+
+def test_batched_blocked_goal_is_reported_per_instance(dev):
+    cases = _batch(4, 8200)
+    occs = [torch.from_numpy(o).to(dev) for _, o in cases]
+    goals = [sc.goal for sc, _ in cases]
+    sc1, occ1 = cases[1]
+    blocked = tuple(int(v) for v in np.argwhere(occ1[1:-1, 1:-1] != 0)[0][::-1] + 1)
+    goals[1] = blocked
+    fields, stats, lat = tw.hp_relax_batched(occs, goals, params=tw.Params(tol=1e-6))
+    assert stats[1]["status"] == tw.TW_EGOAL_BLOCKED
+    for i in (0, 2, 3):
+        assert stats[i]["status"] == tw.TW_OK
+
+
+def test_batched_cap_and_repeat_calls(dev):
+    cases = _batch(6, 8300)
+    occs = [torch.from_numpy(o).to(dev) for _, o in cases]
+    goals = [sc.goal for sc, _ in cases]
+    _, stats, _ = tw.hp_relax_batched(occs, goals, params=tw.Params(tol=1e-12, max_sweeps=64, tblock=4))
+    assert all(st["status"] == tw.TW_NOT_CONVERGED and st["sweeps"] <= 64 for st in stats)
+    a, sa, _ = tw.hp_relax_batched(occs, goals, params=tw.Params(tol=1e-6, tblock=4))
+    b, sb, _ = tw.hp_relax_batched(occs, goals, params=tw.Params(tol=1e-6, tblock=4))
+    for x, y, p, q in zip(a, b, sa, sb):
+        assert p["sweeps"] == q["sweeps"]
+        assert torch.equal(x, y)
