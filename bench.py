@@ -391,6 +391,8 @@ def run_twgrid(args, rank, world, dist):
             for f_ in forms.values():
                 f_["speedup_vs_plain_fp32"] = plain["seconds"] * 1e3 / f_["ms_to_solution"]
 
+    batched = run_batched(args, dev, tw) if (not args.no_batch and rank == 0) else None
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -402,11 +404,85 @@ def run_twgrid(args, rank, world, dist):
            "resid_inf_max": max(resid) if resid else None, "relax_status": sorted(set(status)),
            "path_status": sorted(set(path_status)), "path_len": [n for _, _, n in stats_log][:1],
            "omega": stats_log[0][0]["omega"] if stats_log else None,
-           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms,
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms, "batched": batched,
            "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": min(step_ms), "max": max(step_ms), "host_p50": float(np.percentile(host_ms, 50))},
            "wall_s": wall, "clocks": clocks}
     return out
+
+
+def run_batched(args, dev, tw):
+    """The batched form on 256 uneven planners (side U{64..1024}, 5-35 % occupancy,
+    10-300 tracks, own ring law each): per repetition, every planner's raster,
+    then one hp_relax_batched call; compared with the same planners relaxed one
+    by one with hp_relax."""
+    import torch
+    n = args.batch
+    scs = [scenes.batch_fast(7000 + i) for i in range(n)]
+    grids = [tw.make_grid(sc.nx, sc.ny, sc.cell) for sc in scs]
+    statics = [torch.from_numpy(sc.static_occ).to(dev) for sc in scs]
+    occs = [torch.empty((sc.ny, sc.nx), dtype=torch.uint8, device=dev) for sc in scs]
+    fields = [torch.empty((sc.ny, sc.nx), dtype=torch.float32, device=dev) for sc in scs]
+    cells = sum(sc.nx * sc.ny for sc in scs)
+
+    def rasters():
+        for sc, g, st_, o in zip(scs, grids, statics, occs):
+            tw.tw_build_grid(g, sc.robot, sc.tracks, sc.law, static_occ=st_, occ=o)
+
+    rasters()
+    torch.cuda.synchronize()
+    goals = []
+    for sc, o in zip(scs, occs):
+        # predicted obstacles may cover the nominal goal: take the nearest free interior cell
+        gx, gy = sc.goal
+        if o[gy, gx].item() != 0:
+            free = torch.nonzero(o[1:-1, 1:-1] == 0)
+            if len(free):
+                d = (free[:, 0] + 1 - gy) ** 2 + (free[:, 1] + 1 - gx) ** 2
+                j = int(torch.argmin(d).item())
+                gy, gx = int(free[j, 0].item()) + 1, int(free[j, 1].item()) + 1
+        goals.append((gx, gy))
+    prm = tw.Params(tol=args.tol, max_sweeps=args.max_sweeps)
+    tw.hp_relax_batched(occs, goals, fields, prm)   # warm: autotune + graph build
+    stream = torch.cuda.current_stream()
+    times, lats, stats = [], [], None
+    for _ in range(args.batch_reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rasters()
+        _, stats, lat = tw.hp_relax_batched(occs, goals, fields, prm)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+        lats.extend(lat.tolist())
+    t = float(np.median(times))
+    ok = sum(1 for st in stats if st["status"] == tw.TW_OK)
+    sweeps = [st["sweeps"] for st in stats]
+    updates = sum(st["sweeps"] * sc.nx * sc.ny for st, sc in zip(stats, scs))
+    # the same planners one by one (single-field graph-driven solver)
+    valid = [i for i, st in enumerate(stats) if st["status"] >= 0]
+    for i in valid[:2]:
+        tw.hp_relax(grids[i], occs[i], goals[i], field=fields[i], params=prm)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    rasters()
+    for i in valid:
+        tw.hp_relax(grids[i], occs[i], goals[i], field=fields[i], params=prm)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b) / 1e3
+    T = stats[0]["tblock"]
+    return {"instances": n, "total_cells": cells, "converged": ok, "seconds_per_batch": t,
+            "solves_per_s": ok / t, "latency_ms": {"p50": float(np.percentile(lats, 50)),
+                                                 "p99": float(np.percentile(lats, 99)),
+                                                 "max": float(np.max(lats))},
+            "sweeps": {"min": min(sweeps), "median": float(np.median(sweeps)), "max": max(sweeps)},
+            "tblock_autotuned": T, "cell_updates_per_s": updates / t,
+            "effective_gbs": updates / t * (2 * STORAGE_BYTES + MASK_BYTES) / T / 1e9,
+            "sequential_seconds": t_seq, "sequential_solves_per_s": len(valid) / t_seq,
+            "speedup_vs_sequential": (t_seq / max(len(valid), 1)) / (t / max(ok, 1)),
+            "note": "per repetition: 256 rasters + one hp_relax_batched call; latency = start of the batched "
+                    "relaxation to each instance's convergence (device clock)"}
 
 
 # ---------------------------------------------------------------------------
@@ -472,7 +548,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--warmup-seconds", type=float, default=1.0)
+    ap.add_argument("--warmup-seconds", type=float, default=3.0)
     ap.add_argument("--impl", default="twgrid", choices=["twgrid", "reference"])
     ap.add_argument("--method", default="rbsor", choices=["rbsor", "jacobi", "mixed"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
@@ -483,6 +559,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--batch-reps", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

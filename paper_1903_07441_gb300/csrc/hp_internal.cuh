@@ -35,7 +35,7 @@ struct RelaxCtl {
 
 struct RelaxScalars {
     unsigned int max32;
-    unsigned int pad0;
+    int goal_blocked;      // set on the device when the goal cell is occupied
     unsigned long long max64;
     double sum64;
     double pad1[5];
@@ -96,8 +96,9 @@ struct SweepTimer {
         if (b) cudaEventDestroy(b);
     }
 };
+// *ctl_on_device = 1 when the final loop state is only on the device (in scal->ctl)
 int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
-             cudaStream_t s);
+             cudaStream_t s, int *ctl_on_device);
 double sor_initial_omega(int nx, int ny);
 int read_max_f32(unsigned int *dmax, cudaStream_t s, float *out);
 int final_residual_full(const uint8_t *occ, int nx, int ny, int gx, int gy, const float *u,

@@ -96,6 +96,10 @@ __global__ void __launch_bounds__(256) full_residual_f64_kernel(const uint8_t *_
     block_max_sum_f64(r, out_max, out_sum);
 }
 
+__global__ void goal_check_kernel(const uint8_t *__restrict__ occ, int nx, int gx, int gy, int *flag) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *flag = occ[(size_t)gy * nx + gx] != 0;
+}
+
 __global__ void to_phi_kernel(float *__restrict__ u, size_t n) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) u[i] = 1.0f - u[i];
@@ -325,7 +329,8 @@ void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, cudaStream_t s) 
 // residual, control" on the device); the host loop below finishes any
 // remainder and serves HP_TIMING / HP_HOST_LOOP.
 int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
-             cudaStream_t s) {
+             cudaStream_t s, int *ctl_on_device) {
+    *ctl_on_device = 0;
     int T = p->tblock > 0 ? p->tblock : kDefaultTBlock;
     if (T > 4) T = 4;
     int K = p->check_every > 0 ? p->check_every : 32;
@@ -349,6 +354,13 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
         TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
         int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, scal, s, &launches);
         if (e < 0) return e;
+        if (e == TW_OK && p->max_sweeps % K == 0) {
+            // the graph runs every interval the cap allows: no remainder can follow, so the
+            // loop state is read back later together with the final residual (one sync)
+            *ctl_on_device = 1;
+            st->tblock = T;
+            return TW_OK;
+        }
         if (e == TW_OK) {
             TW_CUDA(cudaMemcpyAsync(&c, &scal->ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
             TW_CUDA(cudaStreamSynchronize(s));
@@ -389,7 +401,7 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
 }
 
 static int relax_rbsor(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, int mode,
-                       const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s) {
+                       const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s, int *ctl_dev) {
     RBLayout &L = R.rb;
     TW_CUDA(cudaMemsetAsync(L.R, 0, sizeof(float) * (size_t)ny * L.S, s));
     TW_CUDA(cudaMemsetAsync(L.B, 0, sizeof(float) * (size_t)ny * L.S, s));
@@ -400,7 +412,7 @@ static int relax_rbsor(const uint8_t *occ, int nx, int ny, int gx, int gy, float
     TW_LAUNCH(rb_pack_kernel, dim3(ceil_div(L.W2 + 31, 128), ny), 128, 0, s,
               occ, u, nx, ny, gx, gy, mode, (p->flags & HP_WARM_START) ? 1 : 0, L);
     TW_CHECK_LAUNCH();
-    int e = rb_solve(L, nx, ny, p, R.scal, st, s);
+    int e = rb_solve(L, nx, ny, p, R.scal, st, s, ctl_dev);
     if (e) return e;
     TW_LAUNCH(rb_unpack_kernel, dim3(ceil_div(nx, 256), ny), 256, 0, s, L, nx, ny, u, 0);
     TW_CHECK_LAUNCH();
@@ -416,11 +428,13 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
     if (!cv.ok()) return TW_EWORKSPACE;
     hp_stats local;
     memset(&local, 0, sizeof(local));
-    int e;
+    // goal check on the device: read back with the final results (no extra sync)
+    TW_CUDA(cudaMemsetAsync(&R.scal->goal_blocked, 0, sizeof(int), s));
+    if (mode == 0) TW_LAUNCH(goal_check_kernel, 1, 32, 0, s, occ, nx, gx, gy, &R.scal->goal_blocked);
+    int e, ctl_dev = 0;
     if (p->method == HP_JACOBI) {
         if (mode == 1) {
             // the general Dirichlet form keeps the caller's fixed values
-            e = TW_OK;
             hp_params q = *p;
             q.flags |= HP_WARM_START;
             e = relax_jacobi(occ, nx, ny, -1, -1, u, &q, &local, R, s);
@@ -428,21 +442,41 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
             e = relax_jacobi(occ, nx, ny, gx, gy, u, p, &local, R, s);
         }
     } else if (p->method == HP_RBSOR) {
-        e = relax_rbsor(occ, nx, ny, gx, gy, u, mode, p, &local, R, s);
+        e = relax_rbsor(occ, nx, ny, gx, gy, u, mode, p, &local, R, s, &ctl_dev);
     } else {
         e = relax_mixed(occ, nx, ny, gx, gy, u, mode, p, &local, R, s);
     }
     if (e) return e;
     if (p->method != HP_MIXED) {   // HP_MIXED reports the residual of its FP64 master
-        e = final_residual_full(occ, nx, ny, mode == 1 ? -1 : gx, mode == 1 ? -1 : gy, u, R.scal, s,
-                                &local.resid_inf, &local.resid_l2);
-        if (e) return e;
+        TW_CUDA(cudaMemsetAsync(&R.scal->max64, 0, sizeof(R.scal->max64) + sizeof(R.scal->sum64), s));
+        dim3 b(32, 8), gr(ceil_div(nx, 32), ceil_div(ny, 8));
+        TW_LAUNCH(full_residual_f64_kernel, gr, b, 0, s, occ, nx, ny, mode == 1 ? -1 : gx, mode == 1 ? -1 : gy, u,
+                  &R.scal->max64, &R.scal->sum64);
+        TW_CHECK_LAUNCH();
     }
     if (mode == 0 && (p->flags & HP_OUT_PHI)) {
         size_t n = (size_t)nx * ny;
         TW_LAUNCH(to_phi_kernel, ceil_div(n, 256), 256, 0, s, u, n);
         TW_CHECK_LAUNCH();
-        TW_CUDA(cudaStreamSynchronize(s));
+    }
+    // the one synchronisation of the call: loop state, goal flag and final residual
+    RelaxScalars hs;
+    TW_CUDA(cudaMemcpyAsync(&hs, R.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaStreamSynchronize(s));
+    if (hs.goal_blocked) return TW_EGOAL_BLOCKED;
+    if (ctl_dev) {
+        const RelaxCtl &c = hs.ctl;
+        const int KT = local.tblock > 1 ? c.K / local.tblock : c.K;
+        local.status = c.status;
+        local.sweeps = c.sweeps;
+        local.checks = c.checks;
+        local.omega = c.omega;
+        local.sweep_launches = c.checks * KT;
+        count_launches((unsigned long long)c.checks * (KT + 2));
+    }
+    if (p->method != HP_MIXED) {
+        memcpy(&local.resid_inf, &hs.max64, sizeof(double));
+        local.resid_l2 = sqrt(hs.sum64);
     }
     if (p->tol > 0.0 && local.resid_inf <= p->tol) local.status = TW_OK;
     if (st) *st = local;
@@ -468,10 +502,6 @@ extern "C" int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy
     int nx = g->nx, ny = g->ny;
     if (gx < 1 || gy < 1 || gx > nx - 2 || gy > ny - 2) return TW_EGOAL_BLOCKED;
     cudaStream_t s = (cudaStream_t)stream;
-    uint8_t gocc = 0;
-    TW_CUDA(cudaMemcpyAsync(&gocc, occ_dev + (size_t)gy * nx + gx, 1, cudaMemcpyDeviceToHost, s));
-    TW_CUDA(cudaStreamSynchronize(s));
-    if (gocc != 0) return TW_EGOAL_BLOCKED;
     if ((p->flags & HP_WARM_START) && (p->flags & HP_OUT_PHI)) {
         // warm start given as phi: convert to u in place first
         size_t n = (size_t)nx * ny;
