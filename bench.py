@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # DRAM traffic of the dominant kernel from one ncu capture, valid only while
 # the kernel source is unchanged (sha256 of the file that holds it).
-TRAFFIC = {"5bf8cc205240ea68": 17452032 + 2048}   # rb_tb_kernel<4,8,8>, profiles/rb_tb_kernel_static2048.md
+TRAFFIC = {"5e3432727f8fc078": 17452032 + 1280}   # rb_tb_kernel<4,8,8,1>, profiles/rb_tb_kernel_static2048.md
 
 
 def _env_int(k, d):
@@ -308,8 +308,10 @@ def run_twgrid(args, rank, world, dist):
     sweeps_per_launch = roof_sweeps / max(sweep_launches, 1)
     bytes_per_launch = cells * (2 * STORAGE_BYTES + MASK_BYTES) * min(1.0, sweeps_per_launch)
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    src = os.path.join(ROOT, "paper_1903_07441_gb300", "csrc", "hp_sweeps.cu")
-    src_hash = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h_ = hashlib.sha256()
+    for name in ("hp_sweeps.cu", "hp_tile.cuh"):   # the files that define the sweep kernel
+        h_.update(open(os.path.join(ROOT, "paper_1903_07441_gb300", "csrc", name), "rb").read())
+    src_hash = h_.hexdigest()[:16]
     traffic = TRAFFIC.get(src_hash)
     roofline = {"bound": "hbm", "kernel": "red-black SOR sweep (hp_sweeps.cu)", "achieved": achieved,
                 "peak": hbm, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": achieved / hbm,
