@@ -218,8 +218,7 @@ __global__ void __launch_bounds__(256) batch_final_residual_kernel(BatchInst *I)
         const bool fixed = b.occ[c] != 0 || (x == b.gx && y == b.gy);
         if (!fixed) {
             const float *u = b.field;
-            const double a = 0.25 * ((((double)u[c + 1] + (double)u[c - 1]) + (double)u[c + b.nx]) + (double)u[c - b.nx]);
-            r = fabs(a - (double)u[c]);
+            r = resid_exact(u[c + 1], u[c - 1], u[c + b.nx], u[c - b.nx], u[c]);
         }
     }
     block_max_sum_f64(r, &b.max64, &b.sum64);

@@ -176,6 +176,29 @@ __device__ __forceinline__ void block_max_atomic(float r, unsigned int *out) {
     }
 }
 
+// Knuth's TwoSum: s + e == a + b exactly (s = fl(a + b)).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// |(1/4)(l + r + u + d) - c| for FP32 inputs, evaluated in compensated FP32
+// (TwoSum on every addition, the scaling by 1/4 is exact) and returned as a
+// double: accurate to about 2^-45 relative to the inputs' magnitude, i.e. the
+// FP64 evaluation of the residual at a fraction of the FP64 operations (FP64
+// throughput is a small fraction of FP32 on this GPU).
+__device__ __forceinline__ double resid_exact(float l, float r, float u, float d, float c) {
+    float s1, e1, s2, e2, s3, e3, dd, e4;
+    two_sum(l, r, s1, e1);
+    two_sum(u, d, s2, e2);
+    two_sum(s1, s2, s3, e3);
+    const float lo = __fadd_rn(__fadd_rn(e1, e2), e3);
+    two_sum(__fmul_rn(0.25f, s3), -c, dd, e4);
+    const float tail = __fadd_rn(__fmul_rn(0.25f, lo), e4);
+    return fabs((double)dd + (double)tail);
+}
+
 // Block-wide FP64 max (atomicMax on the bits of a non-negative double) and sum.
 __device__ __forceinline__ void block_max_sum_f64(double r, unsigned long long *out_max, double *out_sum) {
     __shared__ double smx[32], sms[32];

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) full_residual_kernel(const uint8_t *__res
     block_max_atomic(r, out_max);
 }
 
-// FP64 residual (max and sum of squares) of a full-layout FP32 field.
+// FP64-accurate residual (max and sum of squares) of a full-layout FP32 field.
 __global__ void __launch_bounds__(256) full_residual_f64_kernel(const uint8_t *__restrict__ occ, int nx, int ny,
                                                                 int gx, int gy, const float *__restrict__ u,
                                                                 unsigned long long *__restrict__ out_max,
@@ -88,10 +88,7 @@ __global__ void __launch_bounds__(256) full_residual_f64_kernel(const uint8_t *_
     double r = 0.0;
     if (x > 0 && y > 0 && x < nx - 1 && y < ny - 1) {
         size_t c = (size_t)y * nx + x;
-        if (!(occ[c] != 0 || (x == gx && y == gy))) {
-            double a = 0.25 * ((((double)u[c + 1] + (double)u[c - 1]) + (double)u[c + nx]) + (double)u[c - nx]);
-            r = fabs(a - (double)u[c]);
-        }
+        if (!(occ[c] != 0 || (x == gx && y == gy))) r = resid_exact(u[c + 1], u[c - 1], u[c + nx], u[c - nx], u[c]);
     }
     block_max_sum_f64(r, out_max, out_sum);
 }

@@ -54,38 +54,40 @@ __device__ __forceinline__ long long qpos(double v, double origin, double cell) 
     return qclamp(__dmul_rn(__ddiv_rn(__dsub_rn(v, origin), cell), 256.0), -kCoordClamp, kCoordClamp);
 }
 
+// One thread per ring: thread j repeats the recurrence R_j = growth * R_{j-1}
+// from r0 (the same rounded products as a serial loop), so the whole table
+// costs one ring's latency.  The ring count J is the number of rings below
+// the reach plus one (the radii increase).
 __global__ void tw_ring_table_kernel(Params p, RingTab *tab) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = threadIdx.x;   // blockDim.x == kMaxRings
     double w = __dmul_rn((double)p.nx, p.cell), h = __dmul_rn((double)p.ny, p.cell);
     double reach = __dsqrt_rn(__dadd_rn(__dmul_rn(w, w), __dmul_rn(h, h)));
     if (p.kind == TW_RING_ELLIPTIC) reach = __dmul_rn(reach, 10.0);
-    double R[kMaxRings];
-    int J = 0;
-    double r = p.r0;
-    for (;;) {
-        if (J >= kMaxRings) { tab->J = -1; return; }
-        R[J] = r;
-        J++;
-        if (p.n_rings > 0) { if (J == p.n_rings) break; }
-        else if (r >= reach) break;
+    double r = p.r0, rprev = 0.0;
+    for (int i = 0; i < j; i++) {
+        rprev = r;
         r = __dmul_rn(r, p.growth);
     }
-    tab->J = J;
-    tab->kind = p.kind;
-    tab->mark = p.mark;
-    for (int j = 0; j < J; j++) {
-        double t;
-        if (p.time_outer) t = __ddiv_rn(R[j], p.speed);
-        else t = (j == 0) ? 0.0 : __ddiv_rn(R[j - 1], p.speed);
-        tab->t[j] = t;
-        tab->Rq[j] = qclamp(__dmul_rn(__ddiv_rn(R[j], p.cell), 256.0), 0, kRadiusClamp);
-        tab->Aq[j] = qclamp(__dmul_rn(__ddiv_rn(R[j], p.cell), 268435456.0), 0, 1LL << 52);
-        tab->Cq[j] = qclamp(__dmul_rn(__ddiv_rn(__dmul_rn(0.9, R[j]), p.cell), 268435456.0), 0, 1LL << 52);
+    const int below = __syncthreads_count(r < reach);
+    int J = (p.n_rings > 0) ? p.n_rings : below + 1;
+    if (J > kMaxRings) J = -1;
+    if (j == 0) {
+        tab->J = J;
+        tab->kind = p.kind;
+        tab->mark = p.mark;
+        tab->rxq = qpos(p.rx, p.ox, p.cell);
+        tab->ryq = qpos(p.ry, p.oy, p.cell);
+        tab->hxq = qclamp(__dmul_rn(p.hx, 1048576.0), -1048576, 1048576);
+        tab->hyq = qclamp(__dmul_rn(p.hy, 1048576.0), -1048576, 1048576);
     }
-    tab->rxq = qpos(p.rx, p.ox, p.cell);
-    tab->ryq = qpos(p.ry, p.oy, p.cell);
-    tab->hxq = qclamp(__dmul_rn(p.hx, 1048576.0), -1048576, 1048576);
-    tab->hyq = qclamp(__dmul_rn(p.hy, 1048576.0), -1048576, 1048576);
+    if (J < 0 || j >= J) return;
+    double t;
+    if (p.time_outer) t = __ddiv_rn(r, p.speed);
+    else t = (j == 0) ? 0.0 : __ddiv_rn(rprev, p.speed);
+    tab->t[j] = t;
+    tab->Rq[j] = qclamp(__dmul_rn(__ddiv_rn(r, p.cell), 256.0), 0, kRadiusClamp);
+    tab->Aq[j] = qclamp(__dmul_rn(__ddiv_rn(r, p.cell), 268435456.0), 0, 1LL << 52);
+    tab->Cq[j] = qclamp(__dmul_rn(__ddiv_rn(__dmul_rn(0.9, r), p.cell), 268435456.0), 0, 1LL << 52);
 }
 
 // Smallest ring containing the fixed-point offset (dx, dy); the last ring otherwise.
@@ -93,9 +95,16 @@ __device__ __forceinline__ int ring_index(int kind, int J, long long dx, long lo
                                           const long long *Rq, const long long *Aq,
                                           const long long *Cq, long long hxq, long long hyq) {
     if (kind == TW_RING_CIRCULAR) {
-        long long d2 = dx * dx + dy * dy;
-        for (int j = 0; j < J; j++)
-            if (d2 <= Rq[j] * Rq[j]) return j;
+        // the radii increase: binary search for the first ring with d2 <= Rq_j^2
+        const long long d2 = dx * dx + dy * dy;
+        if (d2 > Rq[J - 1] * Rq[J - 1]) return J - 1;
+        int lo = 0, hi = J - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (d2 <= Rq[mid] * Rq[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        return lo;
     } else {
         __int128 u = (__int128)(hxq * dx + hyq * dy);
         __int128 v = (__int128)(hxq * dy - hyq * dx);
@@ -365,7 +374,7 @@ extern "C" int tw_build_grid(const tw_grid *g, const tw_pose *robot, const tw_tr
     if (n_tracks > 0)
         TW_CUDA(cudaMemcpyAsync(L.tracks, tracks, sizeof(tw_track) * (size_t)n_tracks,
                                 cudaMemcpyHostToDevice, s));
-    TW_LAUNCH(tw_ring_table_kernel, 1, 32, 0, s, p, L.tab);
+    TW_LAUNCH(tw_ring_table_kernel, 1, kMaxRings, 0, s, p, L.tab);
     TW_CHECK_LAUNCH();
     if (n_tracks > 0) {
         TW_LAUNCH(tw_predict_kernel, ceil_div((size_t)n_tracks * kMaxRings, 128), 128, 0, s, p, L.tab,
