@@ -394,6 +394,7 @@ def run_twgrid(args, rank, world, dist):
                 f_["speedup_vs_plain_fp32"] = plain["seconds"] * 1e3 / f_["ms_to_solution"]
 
     batched = run_batched(args, dev, tw) if (not args.no_batch and rank == 0) else None
+    dynamic = run_dynamic(args, dev, tw) if (not args.no_dynamic and rank == 0) else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
@@ -407,6 +408,7 @@ def run_twgrid(args, rank, world, dist):
            "path_status": sorted(set(path_status)), "path_len": [n for _, _, n in stats_log][:1],
            "omega": stats_log[0][0]["omega"] if stats_log else None,
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms, "batched": batched,
+           "dynamic": dynamic,
            "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": min(step_ms), "max": max(step_ms), "host_p50": float(np.percentile(host_ms, 50))},
            "wall_s": wall, "clocks": clocks}
@@ -487,6 +489,55 @@ def run_batched(args, dev, tw):
                     "relaxation to each instance's convergence (device clock)"}
 
 
+def run_dynamic(args, dev, tw):
+    """The dynamic 512x512 configuration: 200 Kalman-tracked disks, rings 0.5 m x 1.3^j,
+    100 replanning frames at 10 Hz (Kalman update + raster + warm-started relaxation
+    + path + robot motion per frame)."""
+    import torch
+    from paper_1903_07441_gb300 import replan
+    sc = scenes.dynamic(seed=1001, side=512, n_obs=200, frames=101)
+    replan.run(sc, frames=3, device=dev)   # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = replan.run(sc, frames=100, device=dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    sweeps = [f.relax.get("sweeps", 0) for f in res.frames if f.relax]
+    out = {"workload": "dynamic512: 512x512, 5 cm, 200 moving disks (Kalman-tracked), 100 frames at 10 Hz",
+           "frames": len(res.frames), "seconds": t, "frames_per_s": len(res.frames) / t,
+           "ms_per_frame": t / max(len(res.frames), 1) * 1e3,
+           "sweeps_per_frame_median": float(np.median(sweeps)) if sweeps else None,
+           "path_ok_frames": sum(1 for f in res.frames if f.path_status == tw.TW_OK),
+           "collision_free": res.collision_free, "min_clearance_m": res.min_clearance}
+    if args.dynamic_eval:
+        out["evaluation"] = dynamic_eval(dev, tw)
+    return out
+
+
+def dynamic_eval(dev, tw, seeds=5, frames=700):
+    """Success / collision-free rates and turning angles for 1-16 moving obstacles
+    (the paper's Table 1 setting, on synthetic 512x512 scenes with 8 static shapes)."""
+    from paper_1903_07441_gb300 import replan
+    table = {}
+    for n_obs in (1, 2, 4, 8, 16):
+        reached = free = 0
+        lengths, angles = [], []
+        for k in range(seeds):
+            sc = scenes.dynamic(seed=5000 + 97 * k + n_obs, side=512, n_obs=n_obs, frames=frames + 1,
+                                static_shapes=8)
+            res = replan.run(sc, frames=frames, device=dev)
+            reached += int(res.reached)
+            free += int(res.collision_free)
+            lengths.append(res.path_length())
+            angles.extend(res.turning_angles().tolist())
+        hist, edges = np.histogram(angles, bins=[0, 5, 10, 20, 45, 90, 180])
+        table[str(n_obs)] = {"runs": seeds, "reached_goal": reached, "collision_free": free,
+                             "path_length_m_mean": float(np.mean(lengths)),
+                             "turning_angle_hist_deg": {f"{int(a)}-{int(b)}": int(h)
+                                                        for a, b, h in zip(edges[:-1], edges[1:], hist)}}
+    return table
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
@@ -562,6 +613,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-dynamic", action="store_true")
+    ap.add_argument("--dynamic-eval", action="store_true",
+                    help="also run the success / collision-free evaluation over 1-16 moving obstacles")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-reps", type=int, default=3)
     args = ap.parse_args()

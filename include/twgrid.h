@@ -115,6 +115,16 @@ int tw_build_grid(const tw_grid *g, const tw_pose *robot, const tw_track *tracks
                   const tw_ring_law *law, const uint8_t *static_occ_dev, uint8_t *occ_dev,
                   int16_t *ring_dev, void *workspace, size_t workspace_bytes, void *stream);
 
+/* tw_nearest_free: the free (occ == 0), non-border cell nearest to (x, y)
+ * (squared Euclidean distance in cells; ties go to the lowest row-major index),
+ * written to host xy_host[0..1].  A replanning loop uses it as the goal when
+ * predicted obstacles cover the nominal goal.  workspace: >= 8 bytes of
+ * device scratch.  Synchronises `stream`.  (x, y) must lie in the grid and
+ * nx^2 + ny^2 < 2^32.  TW_OK, TW_NO_PATH (no free cell), TW_EINVAL,
+ * TW_EWORKSPACE, TW_ECUDA. */
+int tw_nearest_free(const tw_grid *g, const uint8_t *occ_dev, int x, int y, int *xy_host, void *workspace,
+                    size_t workspace_bytes, void *stream);
+
 /* Number of rings tw_build_grid uses for this grid, pose and law (> 0), or TW_EINVAL. */
 int tw_ring_count(const tw_grid *g, const tw_pose *robot, const tw_ring_law *law);
 

@@ -30,7 +30,7 @@ HP_STORE_F32, HP_STORE_F16, HP_STORE_BF16 = 0, 1, 2
 HP_WARM_START, HP_OUT_PHI, HP_TIMING, HP_HOST_LOOP = 1, 2, 4, 8
 
 EXPORTS = (
-    "tw_build_grid_workspace_size", "tw_build_grid", "tw_ring_count",
+    "tw_build_grid_workspace_size", "tw_build_grid", "tw_ring_count", "tw_nearest_free",
     "hp_relax_workspace_size", "hp_relax", "hp_relax_noalloc", "hp_relax_dirichlet", "hp_residual",
     "hp_relax_batched_workspace_size", "hp_relax_batched",
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
@@ -124,6 +124,8 @@ def load() -> ctypes.CDLL:
     lib.tw_build_grid_workspace_size.restype = Z
     lib.tw_build_grid.argtypes = [P, P, P, I, P, P, P, P, P, Z, P]
     lib.tw_build_grid.restype = I
+    lib.tw_nearest_free.argtypes = [P, P, I, I, P, P, Z, P]
+    lib.tw_nearest_free.restype = I
     lib.tw_ring_count.argtypes = [P, P, P]
     lib.tw_ring_count.restype = I
     lib.hp_relax_workspace_size.argtypes = [I, I, P]
@@ -251,6 +253,16 @@ def tw_build_grid(grid: tw_grid, robot, tracks: np.ndarray, law, static_occ=None
                            _stream(occ.device))
     _check("tw_build_grid", st)
     return occ, ring
+
+
+def tw_nearest_free(grid: tw_grid, occ, x, y):
+    """Nearest free non-border cell to (x, y), or None if there is none."""
+    ws = workspace(256, occ.device, "nearest")
+    xy = (ctypes.c_int * 2)()
+    st = load().tw_nearest_free(ctypes.byref(grid), _ptr(occ), int(x), int(y), xy, _ptr(ws), ws.numel(),
+                                _stream(occ.device))
+    _check("tw_nearest_free", st, ok=(TW_OK, TW_NO_PATH))
+    return (int(xy[0]), int(xy[1])) if st == TW_OK else None
 
 
 def hp_relax(grid: tw_grid, occ, goal, field=None, params: Optional[Params] = None):

@@ -331,7 +331,63 @@ static size_t carve_grid(Carver &cv, int n_tracks, int J, GridLayout *out) {
 
 }  // namespace tw
 
+namespace tw {
+
+// Nearest free, non-border cell to (x, y): one block scans the grid and keeps
+// the minimum of (squared distance << 32 | linear index) -- ties go to the
+// lowest index, so the answer is deterministic.
+__global__ void __launch_bounds__(1024) nearest_free_kernel(const uint8_t *__restrict__ occ, int nx, int ny, int x,
+                                                            int y, unsigned long long *out) {
+    __shared__ unsigned long long sm[32];
+    unsigned long long best = ~0ull;
+    const long long n = (long long)nx * ny;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const int cx = (int)(i % nx), cy = (int)(i / nx);
+        if (cx == 0 || cy == 0 || cx == nx - 1 || cy == ny - 1 || occ[i] != 0) continue;
+        const unsigned long long d2 = (unsigned long long)((long long)(cx - x) * (cx - x) + (long long)(cy - y) * (cy - y));
+        const unsigned long long key = (d2 << 32) | (unsigned long long)i;
+        if (key < best) best = key;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        if (v < best) best = v;
+    }
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        best = sm[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            if (v < best) best = v;
+        }
+        if (threadIdx.x == 0) *out = best;
+    }
+}
+
+}  // namespace tw
+
 using namespace tw;
+
+extern "C" int tw_nearest_free(const tw_grid *g, const uint8_t *occ_dev, int x, int y, int *xy_host, void *workspace,
+                               size_t workspace_bytes, void *stream) {
+    // the (squared distance, index) key packs both in 32 bits each
+    if (!valid_grid(g) || !occ_dev || !xy_host || x < 0 || y < 0 || x >= g->nx || y >= g->ny ||
+        (double)g->nx * g->nx + (double)g->ny * g->ny >= 4294967296.0)
+        return TW_EINVAL;
+    if (!workspace || !ws_aligned(workspace) || workspace_bytes < sizeof(unsigned long long)) return TW_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *dkey = (unsigned long long *)workspace;
+    TW_LAUNCH(nearest_free_kernel, 1, 1024, 0, s, occ_dev, g->nx, g->ny, x, y, dkey);
+    TW_CHECK_LAUNCH();
+    unsigned long long key = 0;
+    TW_CUDA(cudaMemcpyAsync(&key, dkey, sizeof(key), cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaStreamSynchronize(s));
+    if (key == ~0ull) return TW_NO_PATH;
+    const unsigned long long idx = key & 0xffffffffull;
+    xy_host[0] = (int)(idx % (unsigned long long)g->nx);
+    xy_host[1] = (int)(idx / (unsigned long long)g->nx);
+    return TW_OK;
+}
 
 extern "C" int tw_ring_count(const tw_grid *g, const tw_pose *robot, const tw_ring_law *law) {
     return ring_count(g, robot, law);

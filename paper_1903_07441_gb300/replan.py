@@ -8,10 +8,10 @@ occupancy is rebuilt, the field persists), and the path is extracted and
 smoothed (plan_path, Eq. 3 and Eqs. 4-6).  The robot then moves along the path
 by one frame's travel (Alg. 1: move to the next cell of the current path).
 
-If a predicted obstacle covers the goal cell, the frame aims at the nearest
-statically free cell around the goal that is free in this frame's raster (the
-robot keeps heading towards the goal region instead of stopping).  If the
-robot's own cell is covered, it holds its position for the frame.
+If predicted obstacles cover the goal cell, the frame aims at the nearest cell
+that is free in this frame's raster (the robot keeps heading towards the goal
+region instead of stopping).  If the robot's own cell is covered, or no path
+exists, it holds its position for the frame.
 """
 from __future__ import annotations
 
@@ -21,8 +21,8 @@ from typing import List, Optional
 
 import numpy as np
 
-from . import (HP_WARM_START, TW_ESTART_BLOCKED, TW_NO_PATH, TW_OK, Params, hp_relax, kf_init, kf_update,
-               make_grid, plan_path, tw_build_grid)
+from . import (HP_WARM_START, TW_NO_PATH, TW_OK, Params, hp_relax, kf_init, kf_update, make_grid, plan_path,
+               tw_build_grid, tw_nearest_free)
 
 
 @dataclass
@@ -130,13 +130,16 @@ def run(scene, frames: int, law=None, params: Optional[Params] = None, rubber_it
         pose = robot.copy()
         tw_build_grid(grid, pose, tracks, law, static_occ=static, occ=occ)
         free = (occ.view(-1)[cand_idx] == 0).nonzero()
-        goal = cands[int(free[0].item())] if len(free) else scene.goal
+        if len(free):
+            goal = cands[int(free[0].item())]
+        else:
+            goal = tw_nearest_free(grid, occ, scene.goal[0], scene.goal[1])
         sx = min(max(int((robot[0] - scene.ox) / scene.cell), 0), scene.nx - 1)
         sy = min(max(int((robot[1] - scene.oy) / scene.cell), 0), scene.ny - 1)
         moved = 0.0
         relax = {}
         pst, plen = TW_NO_PATH, 0
-        if len(free):
+        if goal is not None:
             p = Params(**{**params.__dict__})
             p.flags = params.flags | (HP_WARM_START if warm else 0)
             _, relax = hp_relax(grid, occ, goal, field=u, params=p)
@@ -150,7 +153,7 @@ def run(scene, frames: int, law=None, params: Optional[Params] = None, rubber_it
                 if head is not None:
                     robot[0:2] = pos
                     robot[2:4] = head
-        res.frames.append(FrameLog(f, pose, tracks.copy(), goal, relax, pst, plen, moved))
+        res.frames.append(FrameLog(f, pose, tracks.copy(), goal or scene.goal, relax, pst, plen, moved))
         res.trajectory.append((robot[0], robot[1]))
         # collision with the true obstacles at the next frame's time
         tf = min(f + 1, scene.truth_pos.shape[0] - 1)

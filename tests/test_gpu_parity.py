@@ -349,6 +349,18 @@ def test_path_static128(dev, polished128, rubber):
     assert _hausdorff(path, opath) <= 2.0
 
 
+def test_nearest_free(dev):
+    occ = np.ones((20, 30), np.uint8)
+    occ[5, 7] = occ[15, 25] = occ[9, 12] = 0
+    occ_t = torch.from_numpy(occ).to(dev)
+    grid = tw.make_grid(30, 20, 0.05)
+    assert tw.tw_nearest_free(grid, occ_t, 12, 9) == (12, 9)
+    assert tw.tw_nearest_free(grid, occ_t, 24, 14) == (25, 15)
+    assert tw.tw_nearest_free(grid, occ_t, 1, 1) == (7, 5)
+    occ[:] = 1
+    assert tw.tw_nearest_free(grid, torch.from_numpy(occ).to(dev), 3, 3) is None
+
+
 def test_path_errors(dev):
     n = 40
     occ = np.zeros((n, n), np.uint8)
