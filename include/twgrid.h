@@ -274,6 +274,36 @@ int plan_path_ex(const tw_grid *g, const float *u_dev, const uint8_t *occ_dev, i
                  int32_t *path_xy_host, int *len_out, void *workspace, size_t workspace_bytes,
                  void *stream);
 
+/* ---- learned warm start --------------------------------------------------------
+ * A fully convolutional encoder-decoder (4 levels, 32/64/128/128 channels,
+ * 3x3 convolutions, 2x2 average pooling, nearest upsampling, additive skips,
+ * ReLU; 15 convolutions) predicts p = log(u) / 30 from two input maps: the
+ * occupancy (1 where occ != 0) and the distance to the goal over the grid
+ * diagonal.  Activations and gradients are stored in BF16, weights in FP32
+ * (rounded to BF16 when used), all products accumulate in FP32.  The network
+ * is not in the paper: the field it predicts is only a starting point for
+ * hp_relax (HP_WARM_START), which finishes the solve to its tolerance.
+ * H and W: multiples of 8 in [16, 8192].  params/grads/adam_m/adam_v: device
+ * FP32 arrays of ws_unet_param_count() values.  occ: device uint8 [H][W];
+ * (gx, gy) the goal.  workspace: ws_unet_workspace_size(H, W) bytes. */
+size_t ws_unet_param_count(void);
+size_t ws_unet_workspace_size(int H, int W);
+/* He-normal weights from a counter-based generator seeded with `seed`, zero biases. */
+int ws_unet_init(float *params, unsigned long long seed, void *stream);
+/* target[i] = max(log(max(u[i], 1e-30)), log(1e-30)) / 30 for a relaxed field u (device, n values). */
+int ws_make_target(const float *u, size_t n, float *target, void *stream);
+/* Forward pass.  u_out (nullable): the warm start u = exp(30 p) clipped to <= 1,
+ * 0 on occupied cells, 1 at the goal.  pred_out (nullable): p itself. */
+int ws_unet_forward(const float *params, const uint8_t *occ, int H, int W, int gx, int gy, float *u_out,
+                    float *pred_out, void *workspace, size_t workspace_bytes, void *stream);
+/* One training step on one field: masked mean-squared error between p and
+ * target over free cells (occ == 0, not the goal), gradients into `grads`,
+ * then Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected with `step` >= 1,
+ * learning rate lr) when adam_m != NULL.  loss_host (nullable) receives the loss. */
+int ws_unet_train_step(float *params, float *grads, float *adam_m, float *adam_v, int step, float lr,
+                       const uint8_t *occ, int H, int W, int gx, int gy, const float *target, float *loss_host,
+                       void *workspace, size_t workspace_bytes, void *stream);
+
 /* ---- Kalman filter (host) ----------------------------------------------------
  * kf_update: one step of the constant-velocity filter of Sec. 3.5 for n host
  * tracks: predict by dt (Eqs. 9-10, A(dt), Q(dt) = q_accel x white-noise

@@ -34,7 +34,8 @@ EXPORTS = (
     "hp_relax_workspace_size", "hp_relax", "hp_relax_noalloc", "hp_relax_dirichlet", "hp_residual",
     "hp_relax_batched_workspace_size", "hp_relax_batched",
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
-    "kf_update", "kf_init", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
+    "kf_update", "kf_init", "ws_unet_param_count", "ws_unet_workspace_size", "ws_unet_init", "ws_make_target",
+    "ws_unet_forward", "ws_unet_train_step", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
 )
 
 
@@ -152,6 +153,17 @@ def load() -> ctypes.CDLL:
     lib.kf_update.restype = I
     lib.kf_init.argtypes = [P, I, P, P, D, D]
     lib.kf_init.restype = I
+    lib.ws_unet_param_count.restype = Z
+    lib.ws_unet_workspace_size.argtypes = [I, I]
+    lib.ws_unet_workspace_size.restype = Z
+    lib.ws_unet_init.argtypes = [P, ctypes.c_ulonglong, P]
+    lib.ws_unet_init.restype = I
+    lib.ws_make_target.argtypes = [P, Z, P, P]
+    lib.ws_make_target.restype = I
+    lib.ws_unet_forward.argtypes = [P, P, I, I, I, I, P, P, P, Z, P]
+    lib.ws_unet_forward.restype = I
+    lib.ws_unet_train_step.argtypes = [P, P, P, P, I, ctypes.c_float, P, I, I, I, I, P, P, P, Z, P]
+    lib.ws_unet_train_step.restype = I
     lib.tw_status_string.argtypes = [I]
     lib.tw_status_string.restype = ctypes.c_char_p
     lib.tw_last_cuda_error.restype = I
@@ -376,3 +388,65 @@ def kf_init(z: np.ndarray, radius: np.ndarray, r_meas=0.05, p_vel=1.0) -> np.nda
                                      zz.ctypes.data_as(ctypes.c_void_p), rr.ctypes.data_as(ctypes.c_void_p),
                                      float(r_meas), float(p_vel)))
     return T
+
+
+# ---------------------------------------------------------------------------
+# learned warm start
+# ---------------------------------------------------------------------------
+
+class WarmStartNet:
+    """Parameters and Adam state of the warm-start network, on one device."""
+
+    def __init__(self, device="cuda", seed=1):
+        torch = _torch()
+        lib = load()
+        self.n = int(lib.ws_unet_param_count())
+        self.device = torch.device(device)
+        self.params = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step_count = 0
+        _check("ws_unet_init", lib.ws_unet_init(_ptr(self.params), int(seed), _stream(self.device)))
+
+    def _ws(self, H, W):
+        return workspace(load().ws_unet_workspace_size(int(H), int(W)), self.device, "unet")
+
+    def target(self, u):
+        torch = _torch()
+        t = torch.empty(u.shape, dtype=torch.float32, device=u.device)
+        _check("ws_make_target", load().ws_make_target(_ptr(u), u.numel(), _ptr(t), _stream(u.device)))
+        return t
+
+    def forward(self, occ, goal, u_out=True):
+        """Returns (u warm start or None, prediction p = log(u) / 30)."""
+        torch = _torch()
+        H, W = occ.shape
+        u = torch.empty((H, W), dtype=torch.float32, device=occ.device) if u_out else None
+        p = torch.empty((H, W), dtype=torch.float32, device=occ.device)
+        ws = self._ws(H, W)
+        _check("ws_unet_forward", load().ws_unet_forward(_ptr(self.params), _ptr(occ), H, W, int(goal[0]),
+                                                          int(goal[1]), _ptr(u) if u is not None else None, _ptr(p),
+                                                          _ptr(ws), ws.numel(), _stream(occ.device)))
+        return u, p
+
+    def gradients(self, occ, goal, target):
+        """Loss and gradients for one field (no parameter update)."""
+        H, W = occ.shape
+        ws = self._ws(H, W)
+        loss = ctypes.c_float()
+        _check("ws_unet_train_step", load().ws_unet_train_step(
+            _ptr(self.params), _ptr(self.grads), None, None, 0, 0.0, _ptr(occ), H, W, int(goal[0]), int(goal[1]),
+            _ptr(target), ctypes.byref(loss), _ptr(ws), ws.numel(), _stream(occ.device)))
+        return loss.value, self.grads
+
+    def train_step(self, occ, goal, target, lr=1e-3):
+        H, W = occ.shape
+        ws = self._ws(H, W)
+        self.step_count += 1
+        loss = ctypes.c_float()
+        _check("ws_unet_train_step", load().ws_unet_train_step(
+            _ptr(self.params), _ptr(self.grads), _ptr(self.m), _ptr(self.v), self.step_count, float(lr), _ptr(occ),
+            H, W, int(goal[0]), int(goal[1]), _ptr(target), ctypes.byref(loss), _ptr(ws), ws.numel(),
+            _stream(occ.device)))
+        return loss.value

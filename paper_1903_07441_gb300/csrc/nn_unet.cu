@@ -1,0 +1,575 @@
+// Learned warm start: a small encoder-decoder network that predicts
+// log(u) (u = 1 - phi) from the occupancy and a goal-distance map, trained on
+// fields the relaxation itself produced.  The relaxation then finishes from
+// the prediction (hp_relax with HP_WARM_START), so it stays both the fallback
+// and the judge of the error.
+//
+// Network (fully convolutional, input H and W multiples of 8):
+//   enc0  conv3x3 2->32, conv 32->32            @ H     (ReLU after every conv but the head)
+//   enc1  avgpool2, conv 32->64, conv 64->64    @ H/2
+//   enc2  avgpool2, conv 64->128, conv 128->128 @ H/4
+//   enc3  avgpool2, conv 128->128, conv 128->128 @ H/8
+//   dec2  up2, conv 128->128 (+ enc2, ReLU), conv 128->128 @ H/4
+//   dec1  up2, conv 128->64  (+ enc1, ReLU), conv 64->64   @ H/2
+//   dec0  up2, conv 64->32   (+ enc0, ReLU), conv 32->32   @ H
+//   head  conv 32->1 (linear): the prediction p = log(u) / 30
+// Inputs: channel 0 = 1 on obstacles/border/goal-free... (1 where occupied),
+// channel 1 = distance to the goal / grid diagonal.
+// Storage: activations and their gradients in BF16, weights in FP32 (rounded
+// to BF16 when loaded), every product accumulated in FP32.
+//
+// Kernels are direct convolutions on CUDA cores: each CTA computes a 16x16
+// pixel tile for 16 output channels, staging an 18x18 input tile per chunk of
+// 8 input channels and the matching weights in shared memory.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace tw {
+namespace nn {
+
+typedef __nv_bfloat16 bf16;
+
+struct ConvSpec { int cin, cout, level; };
+// layer order: enc0a enc0b enc1a enc1b enc2a enc2b enc3a enc3b dec2a dec2b dec1a dec1b dec0a dec0b head
+static const ConvSpec kConvs[15] = {
+    {2, 32, 0},    {32, 32, 0},  {32, 64, 1},   {64, 64, 1},   {64, 128, 2},  {128, 128, 2},
+    {128, 128, 3}, {128, 128, 3}, {128, 128, 2}, {128, 128, 2}, {128, 64, 1},  {64, 64, 1},
+    {64, 32, 0},   {32, 32, 0},  {32, 1, 0}};
+constexpr int kNumConvs = 15;
+
+static size_t conv_params(int i) { return (size_t)kConvs[i].cout * kConvs[i].cin * 9 + kConvs[i].cout; }
+static size_t param_offset(int i) {
+    size_t o = 0;
+    for (int k = 0; k < i; k++) o += conv_params(k);
+    return o;
+}
+static size_t total_params() { return param_offset(kNumConvs); }
+
+// ---- kernels ----------------------------------------------------------------------
+
+constexpr int TS = 16;   // pixel tile side
+constexpr int COB = 16;  // output channels per CTA
+constexpr int CIB = 8;   // input channels per staged chunk
+
+__device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16(v)); }
+
+// Y = act(conv3x3(X) + b + S): X [cin][H][W] bf16, Wt [cout][cin][3][3] fp32 (rounded to bf16),
+// b [cout] (nullable), S [cout][H][W] bf16 (nullable), Y [cout][H][W] bf16.
+__global__ void __launch_bounds__(256) conv3x3_fwd_kernel(const bf16 *__restrict__ X, const float *__restrict__ Wt,
+                                                          const float *__restrict__ b, const bf16 *__restrict__ S,
+                                                          bf16 *__restrict__ Y, int cin, int cout, int H, int W,
+                                                          int relu) {
+    __shared__ float xs[CIB][TS + 2][TS + 2];
+    __shared__ float ws[COB][CIB][9];
+    const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;
+    const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS, co0 = blockIdx.z * COB;
+    const int x = x0 + tx, y = y0 + ty;
+    float acc[COB];
+#pragma unroll
+    for (int c = 0; c < COB; c++) acc[c] = 0.0f;
+    for (int ci0 = 0; ci0 < cin; ci0 += CIB) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < CIB * (TS + 2) * (TS + 2); i += 256) {
+            const int c = i / ((TS + 2) * (TS + 2)), r = i % ((TS + 2) * (TS + 2));
+            const int yy = y0 + r / (TS + 2) - 1, xx = x0 + r % (TS + 2) - 1;
+            float v = 0.0f;
+            if (ci0 + c < cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = __bfloat162float(X[((size_t)(ci0 + c) * H + yy) * W + xx]);
+            xs[c][r / (TS + 2)][r % (TS + 2)] = v;
+        }
+        for (int i = threadIdx.x; i < COB * CIB * 9; i += 256) {
+            const int co = i / (CIB * 9), r = i % (CIB * 9), c = r / 9, k = r % 9;
+            float v = 0.0f;
+            if (co0 + co < cout && ci0 + c < cin) v = bf(Wt[((size_t)(co0 + co) * cin + ci0 + c) * 9 + k]);
+            ws[co][c][k] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < CIB; c++) {
+            float in[9];
+#pragma unroll
+            for (int k = 0; k < 9; k++) in[k] = xs[c][ty + k / 3][tx + k % 3];
+#pragma unroll
+            for (int co = 0; co < COB; co++) {
+                float a = acc[co];
+#pragma unroll
+                for (int k = 0; k < 9; k++) a = fmaf(in[k], ws[co][c][k], a);
+                acc[co] = a;
+            }
+        }
+    }
+    if (x >= W || y >= H) return;
+#pragma unroll
+    for (int co = 0; co < COB; co++) {
+        const int oc = co0 + co;
+        if (oc >= cout) break;
+        float v = acc[co] + (b ? b[oc] : 0.0f);
+        const size_t o = ((size_t)oc * H + y) * W + x;
+        if (S) v += __bfloat162float(S[o]);
+        if (relu) v = fmaxf(v, 0.0f);
+        Y[o] = __float2bfloat16(v);
+    }
+}
+
+// weight transform for the data gradient: Wt'[ci][co][8 - k] = Wt[co][ci][k]
+__global__ void conv_transpose_weights_kernel(const float *__restrict__ Wt, float *__restrict__ Wtt, int cin, int cout) {
+    const size_t n = (size_t)cin * cout * 9;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % 9), ci = (int)((i / 9) % cin), co = (int)(i / 9 / cin);
+        Wtt[((size_t)ci * cout + co) * 9 + (8 - k)] = Wt[i];
+    }
+}
+
+// dW[co][ci][k] += sum_p dY[co][p] X[ci][p + k - (1,1)], db[co] += sum_p dY[co][p].
+// CTA: one output channel block (16) x one input channel block (8) x a chunk of rows.
+__global__ void __launch_bounds__(256) conv3x3_bwd_weight_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ dY,
+                                                                 float *__restrict__ dW, float *__restrict__ db, int cin,
+                                                                 int cout, int H, int W, int rows_per_cta) {
+    // thread t: weight index (co, c, k) = t for t < COB*CIB*9/...; accumulate over pixels
+    const int co0 = blockIdx.x * COB, ci0 = blockIdx.y * CIB;
+    const int ya = blockIdx.z * rows_per_cta, yb = min(H, ya + rows_per_cta);
+    __shared__ float sdy[COB][TS * 4];
+    __shared__ float sx[CIB][3][TS * 4 + 2];
+    // 16*8*9 = 1152 weights; 256 threads hold 4.5 -> use 5 slots each
+    float acc[5];
+    float accb = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 5; j++) acc[j] = 0.0f;
+    for (int y = ya; y < yb; y++) {
+        for (int xs0 = 0; xs0 < W; xs0 += TS * 4) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < COB * TS * 4; i += 256) {
+                const int co = i / (TS * 4), xx = xs0 + i % (TS * 4);
+                sdy[co][i % (TS * 4)] = (co0 + co < cout && xx < W)
+                                            ? __bfloat162float(dY[((size_t)(co0 + co) * H + y) * W + xx]) : 0.0f;
+            }
+            for (int i = threadIdx.x; i < CIB * 3 * (TS * 4 + 2); i += 256) {
+                const int c = i / (3 * (TS * 4 + 2)), r = (i / (TS * 4 + 2)) % 3, xx = xs0 + i % (TS * 4 + 2) - 1;
+                const int yy = y + r - 1;
+                sx[c][r][i % (TS * 4 + 2)] = (ci0 + c < cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                                                 ? __bfloat162float(X[((size_t)(ci0 + c) * H + yy) * W + xx]) : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 5; j++) {
+                const int t = threadIdx.x + 256 * j;
+                if (t >= COB * CIB * 9) break;
+                const int co = t / (CIB * 9), c = (t / 9) % CIB, k = t % 9, ky = k / 3, kx = k % 3;
+                float a = acc[j];
+                for (int p = 0; p < TS * 4; p++) a = fmaf(sdy[co][p], sx[c][ky][p + kx], a);
+                acc[j] = a;
+            }
+            if (blockIdx.y == 0 && threadIdx.x < COB)
+                for (int p = 0; p < TS * 4; p++) accb += sdy[threadIdx.x][p];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        const int t = threadIdx.x + 256 * j;
+        if (t >= COB * CIB * 9) break;
+        const int co = t / (CIB * 9), c = (t / 9) % CIB, k = t % 9;
+        if (co0 + co < cout && ci0 + c < cin) atomicAdd(&dW[((size_t)(co0 + co) * cin + ci0 + c) * 9 + k], acc[j]);
+    }
+    if (blockIdx.y == 0 && threadIdx.x < COB && co0 + threadIdx.x < cout && db) atomicAdd(&db[co0 + threadIdx.x], accb);
+}
+
+// dA = dY * (A > 0) in place on dY (A: the post-ReLU activation)
+__global__ void relu_bwd_kernel(const bf16 *__restrict__ A, bf16 *__restrict__ dY, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(A[i]) > 0.0f)) dY[i] = __float2bfloat16(0.0f);
+}
+
+__global__ void pool2_fwd_kernel(const bf16 *__restrict__ X, bf16 *__restrict__ Y, int C, int H, int W) {
+    const int h = H / 2, w = W / 2;
+    const size_t n = (size_t)C * h * w;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % w), y = (int)((i / w) % h), c = (int)(i / w / h);
+        const bf16 *p = X + ((size_t)c * H + 2 * y) * W + 2 * x;
+        const float v = (__bfloat162float(p[0]) + __bfloat162float(p[1])) +
+                        (__bfloat162float(p[W]) + __bfloat162float(p[W + 1]));
+        Y[i] = __float2bfloat16(0.25f * v);
+    }
+}
+
+// gradient of the 2x2 average pool, accumulated into dX (dX += dY / 4 spread over the window)
+__global__ void pool2_bwd_kernel(const bf16 *__restrict__ dY, bf16 *__restrict__ dX, int C, int H, int W) {
+    const size_t n = (size_t)C * H * W;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W), y = (int)((i / W) % H), c = (int)(i / W / H);
+        const float g = 0.25f * __bfloat162float(dY[((size_t)c * (H / 2) + y / 2) * (W / 2) + x / 2]);
+        dX[i] = __float2bfloat16(__bfloat162float(dX[i]) + g);
+    }
+}
+
+__global__ void up2_fwd_kernel(const bf16 *__restrict__ X, bf16 *__restrict__ Y, int C, int H, int W) {
+    // X [C][H/2][W/2] -> Y [C][H][W] (nearest)
+    const size_t n = (size_t)C * H * W;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W), y = (int)((i / W) % H), c = (int)(i / W / H);
+        Y[i] = X[((size_t)c * (H / 2) + y / 2) * (W / 2) + x / 2];
+    }
+}
+
+__global__ void up2_bwd_kernel(const bf16 *__restrict__ dY, bf16 *__restrict__ dX, int C, int H, int W) {
+    // dX [C][H/2][W/2] = sum of the 4 children of dY [C][H][W]
+    const int h = H / 2, w = W / 2;
+    const size_t n = (size_t)C * h * w;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % w), y = (int)((i / w) % h), c = (int)(i / w / h);
+        const bf16 *p = dY + ((size_t)c * H + 2 * y) * W + 2 * x;
+        dX[i] = __float2bfloat16((__bfloat162float(p[0]) + __bfloat162float(p[1])) +
+                                 (__bfloat162float(p[W]) + __bfloat162float(p[W + 1])));
+    }
+}
+
+__global__ void add_inplace_kernel(bf16 *__restrict__ A, const bf16 *__restrict__ B, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        A[i] = __float2bfloat16(__bfloat162float(A[i]) + __bfloat162float(B[i]));
+}
+
+// Input features: channel 0 = occupied (occ != 0), channel 1 = goal distance / diagonal.
+__global__ void features_kernel(const uint8_t *__restrict__ occ, int H, int W, int gx, int gy, bf16 *__restrict__ X) {
+    const size_t n = (size_t)H * W;
+    const float diag = sqrtf((float)H * H + (float)W * W);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W), y = (int)(i / W);
+        X[i] = __float2bfloat16(occ[i] != 0 ? 1.0f : 0.0f);
+        X[n + i] = __float2bfloat16(sqrtf((float)(x - gx) * (x - gx) + (float)(y - gy) * (y - gy)) / diag);
+    }
+}
+
+// Masked MSE over free cells: loss = sum m (p - t)^2 / sum m; dP = 2 m (p - t) / sum m (bf16).
+__global__ void __launch_bounds__(256) mse_kernel(const bf16 *__restrict__ P, const float *__restrict__ T,
+                                                  const uint8_t *__restrict__ occ, int gx, int gy, int W, size_t n,
+                                                  float inv_count, bf16 *__restrict__ dP, float *__restrict__ loss) {
+    float s = 0.0f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const bool m = occ[i] == 0 && !((int)(i % W) == gx && (int)(i / W) == gy);
+        const float d = m ? (__bfloat162float(P[i]) - T[i]) : 0.0f;
+        s += d * d;
+        dP[i] = __float2bfloat16(2.0f * d * inv_count);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv_count);
+}
+
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// He-normal initialisation from a counter-based generator (SplitMix64 + Box-Muller), biases 0.
+__device__ __forceinline__ unsigned long long splitmix(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+__global__ void init_kernel(float *__restrict__ w, size_t n_w, size_t n_total, float stdv, unsigned long long seed,
+                            size_t offset) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_total; i += (size_t)gridDim.x * blockDim.x) {
+        if (i >= n_w) { w[i] = 0.0f; continue; }
+        const unsigned long long a = splitmix(seed * 0x100000001B3ull + 2 * (offset + i));
+        const unsigned long long b = splitmix(seed * 0x100000001B3ull + 2 * (offset + i) + 1);
+        const float u1 = ((a >> 40) + 1) * (1.0f / 16777217.0f), u2 = (b >> 40) * (1.0f / 16777216.0f);
+        w[i] = stdv * sqrtf(-2.0f * logf(u1)) * cosf(6.2831853f * u2);
+    }
+}
+
+__global__ void to_u_kernel(const bf16 *__restrict__ P, const uint8_t *__restrict__ occ, int gx, int gy, int W,
+                            size_t n, float *__restrict__ u) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const bool goal = (int)(i % W) == gx && (int)(i / W) == gy;
+        float v = occ[i] != 0 ? 0.0f : expf(fminf(30.0f * __bfloat162float(P[i]), 0.0f));
+        u[i] = goal ? 1.0f : v;
+    }
+}
+
+// ---- host-side network -------------------------------------------------------------
+
+struct Act {   // activation buffers per level (bf16 [C][h][w])
+    bf16 *in;                          // features [2][H][W]
+    bf16 *e[4][2];                     // encoder conv outputs per level (a, b)
+    bf16 *p[3];                        // pooled inputs of levels 1..3
+    bf16 *u[3];                        // upsampled decoder inputs at levels 2, 1, 0
+    bf16 *d[3][2];                     // decoder conv outputs at levels 2, 1, 0
+    bf16 *out;                         // head output [1][H][W]
+    bf16 *g0, *g1, *g2;                // gradient scratch (64 x H x W each)
+    bf16 *sk[3];                       // gradients into the skip sources e[2][1], e[1][1], e[0][1]
+    float *target;                     // [H][W] training target (log u / 30)
+    float *wt;                         // transposed weights scratch
+    float *loss;
+};
+
+static size_t lvl_px(int H, int W, int l) { return (size_t)(H >> l) * (W >> l); }
+
+static size_t carve_act(Carver &cv, int H, int W, Act *A) {
+    Act a;
+    a.in = cv.take<bf16>(2 * lvl_px(H, W, 0));
+    const int ch[4] = {32, 64, 128, 128};
+    for (int l = 0; l < 4; l++) {
+        a.e[l][0] = cv.take<bf16>(ch[l] * lvl_px(H, W, l));
+        a.e[l][1] = cv.take<bf16>(ch[l] * lvl_px(H, W, l));
+    }
+    for (int l = 1; l < 4; l++) a.p[l - 1] = cv.take<bf16>(ch[l - 1] * lvl_px(H, W, l));
+    const int uc[3] = {128, 128, 64};   // channels entering dec2, dec1, dec0
+    const int ul[3] = {2, 1, 0};
+    const int dc[3] = {128, 64, 32};
+    for (int j = 0; j < 3; j++) {
+        a.u[j] = cv.take<bf16>(uc[j] * lvl_px(H, W, ul[j]));
+        a.d[j][0] = cv.take<bf16>(dc[j] * lvl_px(H, W, ul[j]));
+        a.d[j][1] = cv.take<bf16>(dc[j] * lvl_px(H, W, ul[j]));
+    }
+    a.out = cv.take<bf16>(lvl_px(H, W, 0));
+    const size_t gm = 64 * lvl_px(H, W, 0);   // the largest activation gradient (u[2]: 64 ch at full size)
+    a.g0 = cv.take<bf16>(gm);
+    a.g1 = cv.take<bf16>(gm);
+    a.g2 = cv.take<bf16>(gm);
+    a.sk[0] = cv.take<bf16>(128 * lvl_px(H, W, 2));
+    a.sk[1] = cv.take<bf16>(64 * lvl_px(H, W, 1));
+    a.sk[2] = cv.take<bf16>(32 * lvl_px(H, W, 0));
+    a.target = cv.take<float>(lvl_px(H, W, 0));
+    a.wt = cv.take<float>(128 * 128 * 9);
+    a.loss = cv.take<float>(64);
+    if (A) *A = a;
+    return cv.need;
+}
+
+static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256); }
+
+static void conv_fwd(const bf16 *X, const float *params, int li, const bf16 *S, bf16 *Y, int H, int W, int relu,
+                     cudaStream_t s, bool bias = true) {
+    const ConvSpec &c = kConvs[li];
+    const float *Wt = params + param_offset(li);
+    const float *b = bias ? Wt + (size_t)c.cout * c.cin * 9 : nullptr;
+    dim3 grid(ceil_div(W, TS), ceil_div(H, TS), ceil_div(c.cout, COB));
+    TW_LAUNCH(conv3x3_fwd_kernel, grid, 256, 0, s, X, Wt, b, S, Y, c.cin, c.cout, H, W, relu);
+}
+
+// The forward pass; every intermediate is kept for the backward pass.
+static void forward(const float *P, Act &A, int H, int W, cudaStream_t s) {
+    const int ch[4] = {32, 64, 128, 128};
+    // encoder
+    conv_fwd(A.in, P, 0, nullptr, A.e[0][0], H, W, 1, s);
+    conv_fwd(A.e[0][0], P, 1, nullptr, A.e[0][1], H, W, 1, s);
+    for (int l = 1; l < 4; l++) {
+        const int h = H >> l, w = W >> l;
+        TW_LAUNCH(pool2_fwd_kernel, blocks_for(ch[l - 1] * lvl_px(H, W, l)), 256, 0, s, A.e[l - 1][1], A.p[l - 1],
+                  ch[l - 1], H >> (l - 1), W >> (l - 1));
+        conv_fwd(A.p[l - 1], P, 2 * l, nullptr, A.e[l][0], h, w, 1, s);
+        conv_fwd(A.e[l][0], P, 2 * l + 1, nullptr, A.e[l][1], h, w, 1, s);
+    }
+    // decoder: level 2, 1, 0
+    const bf16 *prev = A.e[3][1];
+    const int pc[3] = {128, 128, 64};
+    for (int j = 0; j < 3; j++) {
+        const int l = 2 - j, h = H >> l, w = W >> l;
+        TW_LAUNCH(up2_fwd_kernel, blocks_for(pc[j] * lvl_px(H, W, l)), 256, 0, s, prev, A.u[j], pc[j], h, w);
+        conv_fwd(A.u[j], P, 8 + 2 * j, A.e[l][1], A.d[j][0], h, w, 1, s);
+        conv_fwd(A.d[j][0], P, 9 + 2 * j, nullptr, A.d[j][1], h, w, 1, s);
+        prev = A.d[j][1];
+    }
+    conv_fwd(A.d[2][1], P, 14, nullptr, A.out, H, W, 0, s);
+}
+
+// Gradient through one conv layer: dY (its output gradient, ReLU already applied)
+// -> dX (overwritten, or accumulated when accumulate != 0) and dW/db (accumulated).
+static void conv_bwd(const bf16 *X, const float *P, float *G, int li, const bf16 *dY, bf16 *dX, bf16 *tmp, int H,
+                     int W, float *wt, int accumulate, cudaStream_t s) {
+    const ConvSpec &c = kConvs[li];
+    const float *Wt = P + param_offset(li);
+    float *dW = G + param_offset(li);
+    float *db = dW + (size_t)c.cout * c.cin * 9;
+    const int rows = H < 16 ? H : 16;
+    dim3 gw(ceil_div(c.cout, COB), ceil_div(c.cin, CIB), ceil_div(H, rows));
+    TW_LAUNCH(conv3x3_bwd_weight_kernel, gw, 256, 0, s, X, dY, dW, db, c.cin, c.cout, H, W, rows);
+    if (!dX) return;
+    TW_LAUNCH(conv_transpose_weights_kernel, blocks_for((size_t)c.cin * c.cout * 9), 256, 0, s, Wt, wt, c.cin, c.cout);
+    // dX = conv3x3(dY, W^T) with cin/cout swapped: a forward conv of the transposed layer
+    dim3 grid(ceil_div(W, TS), ceil_div(H, TS), ceil_div(c.cin, COB));
+    bf16 *dst = accumulate ? tmp : dX;
+    TW_LAUNCH(conv3x3_fwd_kernel, grid, 256, 0, s, dY, wt, (const float *)nullptr, (const bf16 *)nullptr, dst, c.cout,
+              c.cin, H, W, 0);
+    if (accumulate)
+        TW_LAUNCH(add_inplace_kernel, blocks_for((size_t)c.cin * H * W), 256, 0, s, dX, tmp, (size_t)c.cin * H * W);
+}
+
+// Backward pass from dOut (gradient of the head output) to the parameter gradients G.
+static void backward(const float *P, float *G, Act &A, int H, int W, cudaStream_t s, bf16 *d_out,
+                     std::vector<bf16 *> &scratch) {
+    // scratch buffers: dA (current), dB, skip gradients per level, tmp
+    bf16 *dcur = scratch[0], *dnext = scratch[1], *tmp = scratch[2];
+    bf16 *dskip[3] = {scratch[3], scratch[4], scratch[5]};   // gradients into e[2][1], e[1][1], e[0][1]
+    // head (linear): dOut -> d(d[2][1])
+    conv_bwd(A.d[2][1], P, G, 14, d_out, dcur, tmp, H, W, A.wt, 0, s);
+    const int dc[3] = {128, 64, 32}, pc[3] = {128, 128, 64};
+    for (int j = 2; j >= 0; j--) {
+        const int l = 2 - j, h = H >> l, w = W >> l;
+        // dcur: gradient of d[j][1] (post-ReLU output of conv 9 + 2j)
+        TW_LAUNCH(relu_bwd_kernel, blocks_for(dc[j] * lvl_px(H, W, l)), 256, 0, s, A.d[j][1], dcur,
+                  (size_t)dc[j] * lvl_px(H, W, l));
+        conv_bwd(A.d[j][0], P, G, 9 + 2 * j, dcur, dnext, tmp, h, w, A.wt, 0, s);   // -> grad of d[j][0]
+        TW_LAUNCH(relu_bwd_kernel, blocks_for(dc[j] * lvl_px(H, W, l)), 256, 0, s, A.d[j][0], dnext,
+                  (size_t)dc[j] * lvl_px(H, W, l));
+        // d[j][0] = relu(conv(u[j]) + e[l][1]): the skip receives the same gradient
+        cudaMemcpyAsync(dskip[j], dnext, sizeof(bf16) * dc[j] * lvl_px(H, W, l), cudaMemcpyDeviceToDevice, s);
+        conv_bwd(A.u[j], P, G, 8 + 2 * j, dnext, dcur, tmp, h, w, A.wt, 0, s);      // -> grad of u[j]
+        // u[j] = up2(prev): gradient to prev (level l + 1)
+        TW_LAUNCH(up2_bwd_kernel, blocks_for(pc[j] * lvl_px(H, W, l + 1)), 256, 0, s, dcur, dnext, pc[j], h, w);
+        bf16 *t = dcur; dcur = dnext; dnext = t;   // dcur: gradient of the previous decoder output
+    }
+    // dcur: gradient of e[3][1]; walk the encoder down, adding the skip gradients
+    const int ch[4] = {32, 64, 128, 128};
+    for (int l = 3; l >= 0; l--) {
+        const int h = H >> l, w = W >> l;
+        if (l <= 2)
+            TW_LAUNCH(add_inplace_kernel, blocks_for(ch[l] * lvl_px(H, W, l)), 256, 0, s, dcur, dskip[2 - l],
+                      (size_t)ch[l] * lvl_px(H, W, l));
+        TW_LAUNCH(relu_bwd_kernel, blocks_for(ch[l] * lvl_px(H, W, l)), 256, 0, s, A.e[l][1], dcur,
+                  (size_t)ch[l] * lvl_px(H, W, l));
+        conv_bwd(A.e[l][0], P, G, 2 * l + 1, dcur, dnext, tmp, h, w, A.wt, 0, s);   // grad of e[l][0]
+        TW_LAUNCH(relu_bwd_kernel, blocks_for(ch[l] * lvl_px(H, W, l)), 256, 0, s, A.e[l][0], dnext,
+                  (size_t)ch[l] * lvl_px(H, W, l));
+        const bf16 *xin = l == 0 ? A.in : A.p[l - 1];
+        if (l == 0) {
+            conv_bwd(xin, P, G, 0, dnext, nullptr, tmp, h, w, A.wt, 0, s);
+        } else {
+            conv_bwd(xin, P, G, 2 * l, dnext, dcur, tmp, h, w, A.wt, 0, s);          // grad of p[l-1]
+            // p[l-1] = pool2(e[l-1][1]): spread into a zeroed gradient of e[l-1][1]
+            cudaMemsetAsync(dnext, 0, sizeof(bf16) * ch[l - 1] * lvl_px(H, W, l - 1), s);
+            TW_LAUNCH(pool2_bwd_kernel, blocks_for(ch[l - 1] * lvl_px(H, W, l - 1)), 256, 0, s, dcur, dnext,
+                      ch[l - 1], H >> (l - 1), W >> (l - 1));
+            bf16 *t = dcur; dcur = dnext; dnext = t;
+        }
+    }
+}
+
+__global__ void make_target_kernel(const float *__restrict__ u, float *__restrict__ t, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        t[i] = fmaxf(logf(fmaxf(u[i], 1e-30f)), -30.0f * 2.302585093f) / 30.0f;
+}
+
+__global__ void bf16_to_f32_kernel(const bf16 *__restrict__ a, float *__restrict__ b, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = __bfloat162float(a[i]);
+}
+__global__ void count_free_kernel(const uint8_t *__restrict__ occ, int gx, int gy, int W, size_t n, float *out) {
+    float c = 0.0f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        c += (occ[i] == 0 && !((int)(i % W) == gx && (int)(i / W) == gy)) ? 1.0f : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
+
+static bool valid_hw(int H, int W) { return H >= 16 && W >= 16 && H % 8 == 0 && W % 8 == 0 && H <= 8192 && W <= 8192; }
+
+}  // namespace nn
+}  // namespace tw
+
+using namespace tw;
+using namespace tw::nn;
+
+extern "C" size_t ws_unet_param_count(void) { return total_params(); }
+
+extern "C" size_t ws_unet_workspace_size(int H, int W) {
+    if (!valid_hw(H, W)) return 0;
+    Carver cv;
+    return carve_act(cv, H, W, nullptr);
+}
+
+extern "C" int ws_unet_init(float *params, unsigned long long seed, void *stream) {
+    if (!params) return TW_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < kNumConvs; i++) {
+        const ConvSpec &c = kConvs[i];
+        const size_t nw = (size_t)c.cout * c.cin * 9;
+        const float stdv = (i == kNumConvs - 1) ? sqrtf(1.0f / (9.0f * c.cin)) : sqrtf(2.0f / (9.0f * c.cin));
+        TW_LAUNCH(init_kernel, blocks_for(conv_params(i)), 256, 0, s, params + param_offset(i), nw, conv_params(i),
+                  stdv, seed, param_offset(i));
+    }
+    TW_CHECK_LAUNCH();
+    return TW_OK;
+}
+
+extern "C" int ws_make_target(const float *u, size_t n, float *target, void *stream) {
+    if (!u || !target) return TW_EINVAL;
+    TW_LAUNCH(make_target_kernel, blocks_for(n), 256, 0, (cudaStream_t)stream, u, target, n);
+    TW_CHECK_LAUNCH();
+    return TW_OK;
+}
+
+extern "C" int ws_unet_forward(const float *params, const uint8_t *occ, int H, int W, int gx, int gy, float *u_out,
+                               float *pred_out, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!params || !occ || !valid_hw(H, W) || gx < 0 || gy < 0 || gx >= W || gy >= H) return TW_EINVAL;
+    if (!workspace || !ws_aligned(workspace)) return TW_EWORKSPACE;
+    Carver cv(workspace, workspace_bytes);
+    Act A;
+    carve_act(cv, H, W, &A);
+    if (!cv.ok()) return TW_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)H * W;
+    TW_LAUNCH(features_kernel, blocks_for(n), 256, 0, s, occ, H, W, gx, gy, A.in);
+    forward(params, A, H, W, s);
+    if (u_out) TW_LAUNCH(to_u_kernel, blocks_for(n), 256, 0, s, A.out, occ, gx, gy, W, n, u_out);
+    if (pred_out) {
+        TW_LAUNCH(bf16_to_f32_kernel, blocks_for(n), 256, 0, s, A.out, pred_out, n);
+    }
+    TW_CHECK_LAUNCH();
+    return TW_OK;
+}
+
+extern "C" int ws_unet_train_step(float *params, float *grads, float *adam_m, float *adam_v, int step, float lr,
+                                  const uint8_t *occ, int H, int W, int gx, int gy, const float *target,
+                                  float *loss_host, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!params || !grads || !occ || !target || !valid_hw(H, W) || gx < 0 || gy < 0 || gx >= W || gy >= H ||
+        (adam_m && (!adam_v || step < 1 || !(lr > 0.0f))))
+        return TW_EINVAL;
+    if (!workspace || !ws_aligned(workspace)) return TW_EWORKSPACE;
+    Carver cv(workspace, workspace_bytes);
+    Act A;
+    carve_act(cv, H, W, &A);
+    if (!cv.ok()) return TW_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)H * W;
+    TW_LAUNCH(features_kernel, blocks_for(n), 256, 0, s, occ, H, W, gx, gy, A.in);
+    forward(params, A, H, W, s);
+    // free-cell count for the loss normalisation (the mask: occ == 0 and not the goal)
+    TW_CUDA(cudaMemsetAsync(A.loss, 0, 2 * sizeof(float), s));
+    TW_LAUNCH(count_free_kernel, blocks_for(n), 256, 0, s, occ, gx, gy, W, n, A.loss + 1);
+    float cnt = 0.0f;
+    TW_CUDA(cudaMemcpyAsync(&cnt, A.loss + 1, sizeof(float), cudaMemcpyDeviceToHost, s));
+    TW_CUDA(cudaStreamSynchronize(s));
+    const float inv = cnt > 0.0f ? 1.0f / cnt : 0.0f;
+    bf16 *d_out = A.g2;   // head-output gradient
+    TW_LAUNCH(mse_kernel, blocks_for(n), 256, 0, s, A.out, target, occ, gx, gy, W, n, inv, d_out, A.loss);
+    TW_CUDA(cudaMemsetAsync(grads, 0, sizeof(float) * total_params(), s));
+    // backward needs its own scratch: dcur, dnext, tmp (64 x H x W), and the skip gradients
+    std::vector<bf16 *> scratch = {A.g0, A.g1, A.g2, A.sk[0], A.sk[1], A.sk[2]};
+    backward(params, grads, A, H, W, s, d_out, scratch);
+    if (adam_m) {
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+        TW_LAUNCH(adam_kernel, blocks_for(total_params()), 256, 0, s, params, grads, adam_m, adam_v, total_params(),
+                  lr, b1, b2, 1e-8f, c1, c2);
+    }
+    TW_CHECK_LAUNCH();
+    if (loss_host) {
+        TW_CUDA(cudaMemcpyAsync(loss_host, A.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        TW_CUDA(cudaStreamSynchronize(s));
+    }
+    return TW_OK;
+}
+

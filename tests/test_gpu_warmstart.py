@@ -1,0 +1,101 @@
+"""Learned warm start: the library's BF16 network kernels against the FP64
+reference network (forward and gradients), training on fields the method
+generates, and the gain the trained network gives the relaxation (fewer sweeps
+to the same tolerance, with the final field still checked against the oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1903_07441_gb300 as tw
+import scenes
+from oracle import nn_oracle as nn
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_07441_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _scene(seed, side):
+    """Dynamic-style training scene: static shapes plus time-warped predicted disks."""
+    sc = scenes.dynamic(seed=seed, side=side, n_obs=12, frames=1, static_shapes=10)
+    occ, _, _ = oracle.build_grid(sc)
+    if occ[sc.goal[1], sc.goal[0]] != 0:
+        free = np.argwhere(occ == 0)
+        j = int(np.argmin(np.hypot(free[:, 1] - sc.goal[0], free[:, 0] - sc.goal[1])))
+        sc.goal = (int(free[j, 1]), int(free[j, 0]))
+    return sc, occ
+
+
+def test_forward_and_gradients_match_fp64_reference(dev):
+    net = tw.WarmStartNet(dev, seed=7)
+    sc, occ = _scene(9100, 32)
+    occ_t = torch.from_numpy(occ).to(dev)
+    p = net.params.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(1)
+    # perturb the biases so that every unit is active somewhere
+    _, pred = net.forward(occ_t, sc.goal)
+    ref, _ = nn.forward(p, occ, sc.goal)
+    g = pred.cpu().numpy()
+    scale = np.abs(ref).max()
+    assert scale > 0
+    assert np.abs(g - ref).max() <= 0.05 * scale + 1e-3
+    target = (rng.standard_normal(occ.shape) * 0.1 - 0.3).astype(np.float32)
+    loss, grads = net.gradients(occ_t, sc.goal, torch.from_numpy(target).to(dev))
+    loss_ref, g_ref = nn.loss_and_grads(p, occ, sc.goal, target.astype(np.float64))
+    assert abs(loss - loss_ref) <= 0.03 * loss_ref
+    gg = grads.cpu().numpy().astype(np.float64)
+    cos = gg @ g_ref / (np.linalg.norm(gg) * np.linalg.norm(g_ref))
+    assert cos >= 0.99, cos
+    o = 0
+    for ci, co in nn.LAYERS:
+        k = co * ci * 9 + co
+        a, b = gg[o:o + k], g_ref[o:o + k]
+        assert np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(b) + 1e-6, (ci, co)
+        o += k
+
+
+def _fields(dev, seeds, side):
+    out = []
+    for s in seeds:
+        sc, occ = _scene(s, side)
+        occ_t = torch.from_numpy(occ).to(dev)
+        grid = tw.make_grid(side, side, sc.cell)
+        u, st = tw.hp_relax(grid, occ_t, sc.goal, params=tw.Params(omega=1.0, tol=0.0, max_sweeps=6000))
+        out.append((sc, occ, occ_t, u))
+    return out
+
+
+def test_training_reduces_loss_and_warm_start_saves_sweeps(dev):
+    side = 128
+    train = _fields(dev, range(9200, 9240), side)
+    net = tw.WarmStartNet(dev, seed=3)
+    targets = [net.target(u) for _, _, _, u in train]
+    first = np.mean([net.gradients(o, sc.goal, t)[0] for (sc, _, o, _), t in zip(train[:8], targets[:8])])
+    for it in range(800):
+        i = it % len(train)
+        sc, _, o, _ = train[i]
+        net.train_step(o, sc.goal, targets[i], lr=1e-3 if it < 600 else 3e-4)
+    last = np.mean([net.gradients(o, sc.goal, t)[0] for (sc, _, o, _), t in zip(train[:8], targets[:8])])
+    assert last < 0.2 * first, (first, last)
+    # held-out scenes: sweeps to 1e-6 from the network's field vs the cold start
+    cold, warm = [], []
+    for sc, occ, occ_t, _ in _fields(dev, range(9300, 9306), side):
+        grid = tw.make_grid(side, side, sc.cell)
+        _, s0 = tw.hp_relax(grid, occ_t, sc.goal, params=tw.Params(tol=1e-6))
+        u0, _ = net.forward(occ_t, sc.goal)
+        u1, s1 = tw.hp_relax(grid, occ_t, sc.goal, field=u0, params=tw.Params(tol=1e-6, flags=tw.HP_WARM_START))
+        assert s1["status"] == tw.TW_OK
+        ustar, fixed = oracle.solve_field(occ, sc.goal, tol=1e-13)
+        tau = oracle.exit_time(fixed).max()
+        assert np.abs(u1.cpu().numpy() - ustar).max() <= tau * s1["resid_inf"] * 1.001 + 1e-7
+        cold.append(s0["sweeps"])
+        warm.append(s1["sweeps"])
+    assert np.mean(warm) < np.mean(cold), (cold, warm)

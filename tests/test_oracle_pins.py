@@ -482,3 +482,48 @@ def test_enclosed_goal_has_no_path_and_blocked_start():
     assert st == oracle.NO_PATH
     st, _ = oracle.descent(u, fixed, (10, 12), (15, 15))
     assert st == oracle.ESTART
+
+
+# ---------------------------------------------------------------------------
+# warm-start network reference
+# ---------------------------------------------------------------------------
+
+def test_nn_oracle_gradients_match_finite_differences():
+    from oracle import nn_oracle as nn
+    rng = np.random.default_rng(3)
+    H = W = 16
+    occ = (rng.random((H, W)) < 0.2).astype(np.uint8)
+    goal = (9, 6)
+    occ[goal[1], goal[0]] = 0
+    p = np.zeros(nn.param_count())
+    o = 0
+    for ci, co in nn.LAYERS:   # He-scaled weights, small biases: every ReLU sees both signs
+        p[o:o + co * ci * 9] = rng.standard_normal(co * ci * 9) * np.sqrt(2.0 / (9 * ci))
+        o += co * ci * 9
+        p[o:o + co] = 0.05 * rng.standard_normal(co)
+        o += co
+    target = rng.standard_normal((H, W)) * 0.3
+    loss, g = nn.loss_and_grads(p, occ, goal, target)
+    assert loss > 0
+    idx = rng.choice(len(p), 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        num = (nn.loss_and_grads(pp, occ, goal, target)[0] - nn.loss_and_grads(pm, occ, goal, target)[0]) / (2 * h)
+        assert abs(num - g[i]) <= 1e-5 * max(1.0, abs(num)) + 1e-8, (i, num, g[i])
+
+
+def test_nn_oracle_conv_delta_reproduces_kernel():
+    from oracle import nn_oracle as nn
+    rng = np.random.default_rng(4)
+    Wt = rng.standard_normal((3, 2, 3, 3))
+    b = rng.standard_normal(3)
+    X = np.zeros((2, 7, 7))
+    X[1, 3, 3] = 1.0
+    Y = nn.conv(X, Wt, b)
+    # a unit impulse at (3, 3) of channel 1 leaves the flipped kernel around (3, 3)
+    for ky in range(3):
+        for kx in range(3):
+            assert np.allclose(Y[:, 3 + 1 - ky, 3 + 1 - kx], Wt[:, 1, ky, kx] + b)
