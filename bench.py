@@ -395,6 +395,7 @@ def run_twgrid(args, rank, world, dist):
 
     batched = run_batched(args, dev, tw) if (not args.no_batch and rank == 0) else None
     dynamic = run_dynamic(args, dev, tw) if (not args.no_dynamic and rank == 0) else None
+    learned = run_learned(args, dev, tw) if (not args.no_learned and rank == 0) else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
@@ -408,7 +409,7 @@ def run_twgrid(args, rank, world, dist):
            "path_status": sorted(set(path_status)), "path_len": [n for _, _, n in stats_log][:1],
            "omega": stats_log[0][0]["omega"] if stats_log else None,
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms, "batched": batched,
-           "dynamic": dynamic,
+           "dynamic": dynamic, "learned_warm_start": learned,
            "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": min(step_ms), "max": max(step_ms), "host_p50": float(np.percentile(host_ms, 50))},
            "wall_s": wall, "clocks": clocks}
@@ -514,6 +515,79 @@ def run_dynamic(args, dev, tw):
     return out
 
 
+def run_learned(args, dev, tw):
+    """Learned warm start: the network is trained on fields the relaxation generates
+    (dynamic-style 256x256 scenes: static shapes + time-warped predicted disks),
+    then warm-starts the relaxation on held-out scenes at 256x256 and 1024x1024."""
+    import torch
+
+    def scene(seed, side):
+        sc = scenes.dynamic(seed=seed, side=side, n_obs=12, frames=1, static_shapes=10)
+        grid = tw.make_grid(side, side, sc.cell)
+        occ, _ = tw.tw_build_grid(grid, sc.robot, sc.tracks, sc.law,
+                                  static_occ=torch.from_numpy(sc.static_occ).to(dev))
+        goal = sc.goal
+        if occ[goal[1], goal[0]].item() != 0:
+            goal = tw.tw_nearest_free(grid, occ, goal[0], goal[1])
+        return grid, occ, goal
+
+    side = 256
+    t0 = time.perf_counter()
+    data = []
+    for s in range(args.learn_fields):
+        grid, occ, goal = scene(20000 + s, side)
+        u, _ = tw.hp_relax(grid, occ, goal, params=tw.Params(omega=1.0, tol=0.0, max_sweeps=8000))
+        data.append((occ, goal, None, u))
+    net = tw.WarmStartNet(dev, seed=11)
+    data = [(o, g, net.target(u), None) for o, g, _, u in data]
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = []
+    for it in range(args.learn_steps):
+        o, g, t, _ = data[it % len(data)]
+        lr = 1e-3 if it < 0.75 * args.learn_steps else 3e-4
+        losses.append(net.train_step(o, g, t, lr=lr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = {"train_fields": len(data), "train_size": side, "train_steps": args.learn_steps,
+           "data_seconds": t_gen, "train_seconds": t_train, "train_steps_per_s": args.learn_steps / t_train,
+           "loss_first_100": float(np.mean(losses[:100])), "loss_last_100": float(np.mean(losses[-100:])),
+           "params": net.n}
+    ev = {}
+    for sz, seeds in ((256, range(30000, 30008)), (1024, range(31000, 31004))):
+        cold_s, warm_s, cold_t, warm_t, fwd_t = [], [], [], [], []
+        for sd in seeds:
+            grid, occ, goal = scene(sd, sz)
+            prm = tw.Params(tol=args.tol)
+            tw.hp_relax(grid, occ, goal, params=prm)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, s0 = tw.hp_relax(grid, occ, goal, params=prm)
+            b.record()
+            torch.cuda.synchronize()
+            cold_t.append(a.elapsed_time(b))
+            net.forward(occ, goal)
+            a.record()
+            u0, _ = net.forward(occ, goal)
+            m_ = torch.cuda.Event(enable_timing=True)
+            m_.record()
+            _, s1 = tw.hp_relax(grid, occ, goal, field=u0,
+                                params=tw.Params(tol=args.tol, flags=tw.HP_WARM_START))
+            b.record()
+            torch.cuda.synchronize()
+            warm_t.append(a.elapsed_time(b))
+            fwd_t.append(a.elapsed_time(m_))
+            cold_s.append(s0["sweeps"])
+            warm_s.append(s1["sweeps"])
+        ev[str(sz)] = {"scenes": len(cold_s), "cold_sweeps": float(np.mean(cold_s)), "warm_sweeps": float(np.mean(warm_s)),
+                       "cold_ms": float(np.mean(cold_t)), "warm_ms_incl_network": float(np.mean(warm_t)),
+                       "network_forward_ms": float(np.mean(fwd_t)),
+                       "sweep_reduction": 1.0 - float(np.mean(warm_s)) / float(np.mean(cold_s))}
+    out["evaluation"] = ev
+    return out
+
+
 def dynamic_eval(dev, tw, seeds=5, frames=700):
     """Success / collision-free rates and turning angles for 1-16 moving obstacles
     (the paper's Table 1 setting, on synthetic 512x512 scenes with 8 static shapes)."""
@@ -614,6 +688,9 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-dynamic", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learn-fields", type=int, default=256)
+    ap.add_argument("--learn-steps", type=int, default=3000)
     ap.add_argument("--dynamic-eval", action="store_true",
                     help="also run the success / collision-free evaluation over 1-16 moving obstacles")
     ap.add_argument("--batch", type=int, default=256)
