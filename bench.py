@@ -245,6 +245,7 @@ def run_twgrid(args, rank, world, dist):
     tw0 = time.perf_counter()
     n_warm = 0
     while n_warm < args.warmup or time.perf_counter() - tw0 < args.warmup_seconds:
+        flush.zero_()   # as in the timed loop: the buffer's first use costs ~0.25 s on a fresh GPU
         step(static_d)
         torch.cuda.synchronize()
         n_warm += 1
