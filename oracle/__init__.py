@@ -19,6 +19,11 @@ Functions and the passage each follows:
 
 The field is handled as u = 1 - phi (goal 1, obstacles and border 0), the
 same linear equation, which keeps relative precision where phi is near 1.
+
+Parity unpinned: ``rubber_band``.  The paper gives the rubber band only
+qualitatively (Eqs. 4-5 and a figure); the energy and move rule here are a
+reading, checked by invariants (the path stays an 8-connected chain of free
+cells, the energy never increases) but not by any value the paper fixes.
 """
 from __future__ import annotations
 

@@ -428,7 +428,8 @@ int or_descent(const double *u, const uint8_t *fixed, int nx, int ny,
 }
 
 /* ------------------------------------------------------------------------
- * Rubber band (Sec. 3.2, Eqs. 4-6).  Reading used: node energy
+ * Rubber band (Sec. 3.2, Eqs. 4-6) -- parity unpinned: the paper gives no
+ * tension law, so this is a reading checked only by invariants.  Node energy
  *   E_i(q) = w / u(q) + (k/2) (|q - p_{i-1}|^2 + |q - p_{i+1}|^2)
  * (w/u is the potential term of Eq. 6 in the u = 1 - phi form, the
  * quadratic terms the tensions of the two adjacent nodes).  A sweep moves
