@@ -151,8 +151,12 @@ typedef struct {
     double omega;      /* SOR factor in (0, 2); 0 = adaptive estimate (HP_RBSOR, HP_MIXED) */
     double tol;        /* stop when the residual r_inf <= tol (0: run max_sweeps) */
     int max_sweeps;    /* hard cap on full sweeps, >= 1 */
-    int check_every;   /* residual check period in sweeps (0 = library default) */
-    int tblock;        /* temporal-blocking depth T (0 = library default) */
+    int check_every;   /* residual check period in sweeps, rounded up to whole launches (0 = library
+                          default: the largest even number of T-sweep launches within 32 sweeps) */
+    int tblock;        /* temporal-blocking depth T, sweeps fused per launch (0 = library default):
+                          HP_RBSOR takes 1..7 (default 7 on deep tiles when the field has at least
+                          96 of them -- about 2048 x 1400 cells and up -- else 4); hp_relax_batched
+                          takes 2 or 4 (anything else: autotuned) */
     int flags;         /* HP_WARM_START | HP_OUT_PHI */
 } hp_params;
 
@@ -167,7 +171,13 @@ typedef struct {
     int sweep_launches;/* launches of the sweep kernel */
     double sweep_ms;   /* HP_TIMING: summed CUDA-event time of the sweep launches (ms) */
     int tblock;        /* temporal-blocking depth used (sweeps fused per launch) */
+    int loop;          /* how the convergence loop ran: HP_LOOP_HOST or HP_LOOP_GRAPH */
 } hp_stats;
+
+#define HP_LOOP_HOST 0     /* host-driven: HP_HOST_LOOP, HP_TIMING, HP_JACOBI, HP_MIXED, or a cap
+                              below one check interval */
+#define HP_LOOP_GRAPH 1    /* CUDA graph whose conditional while-node runs the check intervals
+                              (the host finishes a cap that is not a whole number of intervals) */
 
 /* hp_relax: the harmonic field of the occupancy grid (Sec. 3.1).  Cells with
  * occ != 0 and the border are Dirichlet cells at phi = 1, the goal cell is

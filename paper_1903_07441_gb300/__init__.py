@@ -28,6 +28,7 @@ TW_FREE, TW_STATIC, TW_DYNAMIC, TW_BORDER = 0, 1, 2, 3
 HP_JACOBI, HP_RBSOR, HP_MIXED = 0, 1, 2
 HP_STORE_F32, HP_STORE_F16, HP_STORE_BF16 = 0, 1, 2
 HP_WARM_START, HP_OUT_PHI, HP_TIMING, HP_HOST_LOOP = 1, 2, 4, 8
+HP_LOOP_HOST, HP_LOOP_GRAPH = 0, 1
 
 EXPORTS = (
     "tw_build_grid_workspace_size", "tw_build_grid", "tw_ring_count", "tw_nearest_free",
@@ -79,7 +80,8 @@ class hp_instance(ctypes.Structure):
 class hp_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("status", ctypes.c_int), ("resid_inf", ctypes.c_double),
                 ("resid_l2", ctypes.c_double), ("omega", ctypes.c_double), ("checks", ctypes.c_int),
-                ("sweep_launches", ctypes.c_int), ("sweep_ms", ctypes.c_double), ("tblock", ctypes.c_int)]
+                ("sweep_launches", ctypes.c_int), ("sweep_ms", ctypes.c_double), ("tblock", ctypes.c_int),
+                ("loop", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

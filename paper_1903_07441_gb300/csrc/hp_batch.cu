@@ -143,10 +143,10 @@ batch_residual_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, 
                 float4 nb[4];
                 rb_load_neighbours(V, b.S, y, k, (y + color) & 1, nb);
                 const float4 c = *reinterpret_cast<const float4 *>(U + (size_t)y * b.S + 4 + k);
-                if (bits & 1u) r = fmaxf(r, fabsf(rb_avg(nb, 0) - c.x));
-                if (bits & 2u) r = fmaxf(r, fabsf(rb_avg(nb, 1) - c.y));
-                if (bits & 4u) r = fmaxf(r, fabsf(rb_avg(nb, 2) - c.z));
-                if (bits & 8u) r = fmaxf(r, fabsf(rb_avg(nb, 3) - c.w));
+                if (bits & 1u) r = fmaxf(r, fabsf(rb_step(c.x, nb[0].x, nb[1].x, nb[2].x, nb[3].x)));
+                if (bits & 2u) r = fmaxf(r, fabsf(rb_step(c.y, nb[0].y, nb[1].y, nb[2].y, nb[3].y)));
+                if (bits & 4u) r = fmaxf(r, fabsf(rb_step(c.z, nb[0].z, nb[1].z, nb[2].z, nb[3].z)));
+                if (bits & 8u) r = fmaxf(r, fabsf(rb_step(c.w, nb[0].w, nb[1].w, nb[2].w, nb[3].w)));
             }
         }
         block_max_atomic(r, &b.rmax);
@@ -538,6 +538,7 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
         st.checks = b.ctl.checks;
         st.omega = b.ctl.omega;
         st.tblock = T;
+        st.loop = HP_LOOP_GRAPH;
         st.status = b.error ? b.error : ((p->tol > 0.0 && rinf <= p->tol) ? TW_OK : TW_NOT_CONVERGED);
         if (latency_ms) latency_ms[i] = b.t_done > hh.t_start ? (double)(b.t_done - hh.t_start) * 1e-6 : 0.0;
         if (st.status < 0) worst = st.status;

@@ -28,6 +28,7 @@ void *rb_residual_kernel_ptr();
 
 __global__ void relax_control_kernel(RelaxCtl *ctl, unsigned int *rmax, int max_intervals,
                                      cudaGraphConditionalHandle handle) {
+    pdl_wait();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     RelaxCtl c = *ctl;
     const float rf = __uint_as_float(*rmax);
@@ -37,6 +38,24 @@ __global__ void relax_control_kernel(RelaxCtl *ctl, unsigned int *rmax, int max_
     if (c.checks >= max_intervals || c.sweeps + c.K > c.max_sweeps) go = 0;
     *ctl = c;
     cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
+// Add a kernel node after `prev` (if any) with a programmatic edge: the node
+// may launch while `prev` finishes and waits (griddepcontrol.wait) for it.
+static cudaError_t add_kernel_after(cudaGraphNode_t *node, cudaGraph_t g, cudaGraphNode_t prev,
+                                    const cudaKernelNodeParams &kp) {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeKernel;
+    np.kernel.func = kp.func;
+    np.kernel.gridDim = kp.gridDim;
+    np.kernel.blockDim = kp.blockDim;
+    np.kernel.sharedMemBytes = kp.sharedMemBytes;
+    np.kernel.kernelParams = kp.kernelParams;
+    cudaGraphEdgeData ed;
+    memset(&ed, 0, sizeof(ed));
+    ed.from_port = cudaGraphKernelNodePortProgrammatic;
+    ed.type = cudaGraphDependencyTypeProgrammatic;
+    return cudaGraphAddNode(node, g, prev ? &prev : nullptr, prev ? &ed : nullptr, prev ? 1 : 0, &np);
 }
 
 struct GraphEntry {
@@ -94,7 +113,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         kp.sharedMemBytes = 0;
         kp.kernelParams = args;
         cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        e = add_kernel_after(&node, body, prev, kp);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
         prev = node;
         float *t = R; R = R2; R2 = t;
@@ -113,7 +132,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         kp.blockDim = dim3(64, 4);
         kp.kernelParams = args;
         cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, body, &prev, 1, &kp);
+        e = add_kernel_after(&node, body, prev, kp);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
         prev = node;
     }
@@ -129,7 +148,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         kp.blockDim = dim3(32);
         kp.kernelParams = args;
         cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, body, &prev, 1, &kp);
+        e = add_kernel_after(&node, body, prev, kp);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
     }
     cudaGraphExec_t exec;

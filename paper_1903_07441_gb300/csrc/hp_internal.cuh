@@ -6,7 +6,9 @@
 
 namespace tw {
 
-constexpr int kDefaultTBlock = 4;
+constexpr int kDefaultTBlock = 4;   // blocking depth of small fields
+constexpr int kDeepTBlock = 7;      // blocking depth of fields that fill the GPU with deep tiles
+constexpr int kMaxTBlock = 7;
 
 // Colour-split layout: red cells (x + y even) and black cells in two arrays
 // of ny rows; row y of colour c holds cells x = 2k + ((y + c) & 1), k < W2.
@@ -64,6 +66,8 @@ int relax_mixed(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, in
                 const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s);
 // n full red-black SOR sweeps, T fused per launch; *launches += launches made
 int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream_t s, int *launches);
+// Number of tiles (CTAs) of one T-fused launch over an nx x ny field.
+int tb_tiles(int T, int nx, int ny);
 // Graph-driven loop: up to max_intervals check intervals of K sweeps (K/T even)
 // run on the device; ctl_dev must hold the initial state.  Returns TW_OK, or
 // a positive value when graphs are unavailable (the caller uses the host loop).
@@ -156,6 +160,15 @@ __host__ __device__ inline int relax_control(RelaxCtl &c, double r, int n) {
     return 1;
 }
 
+// Programmatic dependent launch.  In the graph-driven loop consecutive
+// kernels are joined by programmatic edges: a kernel lets its successor be
+// launched as soon as all of its own CTAs have started (launch_dependents),
+// and every kernel waits for its predecessors to complete, with their memory
+// visible, before it reads what they wrote (wait).  Outside such an edge (plain
+// stream launches) both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // NaN or overflow must never look converged: map them to +inf before a max.
 __device__ __forceinline__ float sane(float r) { return (r <= FLT_MAX) ? r : __int_as_float(0x7f800000); }
 __device__ __forceinline__ double sane(double r) { return (r <= DBL_MAX) ? r : __longlong_as_double(0x7ff0000000000000LL); }
@@ -243,15 +256,6 @@ __device__ __forceinline__ void rb_load_neighbours(const float *V, int S, int y,
         nb[0] = make_float4(extra, mid.x, mid.y, mid.z);
         nb[1] = mid;
     }
-}
-
-__device__ __forceinline__ float comp(const float4 &v, int e) {
-    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
-}
-
-// (1/4)((left + right) + (up + down)), the Eq. 1 average in a fixed order.
-__device__ __forceinline__ float rb_avg(const float4 nb[4], int e) {
-    return 0.25f * ((comp(nb[0], e) + comp(nb[1], e)) + (comp(nb[2], e) + comp(nb[3], e)));
 }
 
 }  // namespace tw

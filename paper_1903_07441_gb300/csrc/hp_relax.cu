@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "hp_internal.cuh"
+#include "hp_tile.cuh"
 
 namespace tw {
 
@@ -159,6 +160,8 @@ __global__ void rb_unpack_kernel(RBLayout L, int nx, int ny, float *__restrict__
 
 // FP32 residual max over both colours of the split layout.
 __global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, unsigned int *out_max) {
+    pdl_launch_dependents();
+    pdl_wait();
     int k4 = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
     float r = 0.0f;
@@ -175,10 +178,10 @@ __global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, un
             float4 nb[4];
             rb_load_neighbours(V, L.S, y, k, s, nb);
             float4 c = *reinterpret_cast<const float4 *>(U + (size_t)y * L.S + 4 + k);
-            if (bits & 1u) r = fmaxf(r, fabsf(rb_avg(nb, 0) - c.x));
-            if (bits & 2u) r = fmaxf(r, fabsf(rb_avg(nb, 1) - c.y));
-            if (bits & 4u) r = fmaxf(r, fabsf(rb_avg(nb, 2) - c.z));
-            if (bits & 8u) r = fmaxf(r, fabsf(rb_avg(nb, 3) - c.w));
+            if (bits & 1u) r = fmaxf(r, fabsf(rb_step(c.x, nb[0].x, nb[1].x, nb[2].x, nb[3].x)));
+            if (bits & 2u) r = fmaxf(r, fabsf(rb_step(c.y, nb[0].y, nb[1].y, nb[2].y, nb[3].y)));
+            if (bits & 4u) r = fmaxf(r, fabsf(rb_step(c.z, nb[0].z, nb[1].z, nb[2].z, nb[3].z)));
+            if (bits & 8u) r = fmaxf(r, fabsf(rb_step(c.w, nb[0].w, nb[1].w, nb[2].w, nb[3].w)));
         }
     }
     block_max_atomic(r, out_max);
@@ -328,10 +331,20 @@ void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, cudaStream_t s) 
 int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
              cudaStream_t s, int *ctl_on_device) {
     *ctl_on_device = 0;
-    int T = p->tblock > 0 ? p->tblock : kDefaultTBlock;
-    if (T > 4) T = 4;
-    int K = p->check_every > 0 ? p->check_every : 32;
-    if (T > 1 && K % T) K += T - K % T;   // whole launches per check interval
+    // Blocking depth: the deep tiles when they fill most of a GB300 (152 SMs)
+    // in one launch, else the small tiles.
+    int T = p->tblock > 0 ? p->tblock : (tb_tiles(kDeepTBlock, nx, ny) >= 96 ? kDeepTBlock : kDefaultTBlock);
+    if (T > kMaxTBlock) T = kMaxTBlock;
+    // Check interval: check_every rounded up to whole launches; by default the
+    // largest even number of launches within 32 sweeps (the graph body needs
+    // an even count to end on the same ping-pong planes).
+    int K;
+    if (p->check_every > 0) {
+        K = p->check_every;
+        if (T > 1 && K % T) K += T - K % T;
+    } else {
+        K = T > 1 ? 2 * T * (32 / (2 * T) > 0 ? 32 / (2 * T) : 1) : 32;
+    }
     const bool checks = p->tol > 0.0 || p->omega == 0.0;
     RelaxCtl c;
     memset(&c, 0, sizeof(c));
@@ -351,6 +364,7 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
         TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
         int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, scal, s, &launches);
         if (e < 0) return e;
+        if (e == TW_OK) st->loop = HP_LOOP_GRAPH;
         if (e == TW_OK && p->max_sweeps % K == 0) {
             // the graph runs every interval the cap allows: no remainder can follow, so the
             // loop state is read back later together with the final residual (one sync)

@@ -72,22 +72,33 @@ rb_tb_kernel(const float *__restrict__ Rin, const float *__restrict__ Bin, float
              int ny, int W4, int S, int MW, float omega_arg, const float *__restrict__ omega_dev) {
     __shared__ float4 s_top[2][WARPS][32];
     __shared__ float4 s_bot[2][WARPS][32];
+    pdl_launch_dependents();
+    pdl_wait();   // the previous sweep (or the control kernel's omega) must be complete
     // the graph-driven loop keeps omega in device memory (it adapts on the device)
     const float omega = omega_dev ? *omega_dev : omega_arg;
     tb_tile<T, RB, WARPS>(Rin, Bin, Rout, Bout, MR, MB, ny, W4, S, MW, omega, (int)blockIdx.x, (int)blockIdx.y,
                           s_top, s_bot);
 }
 
-constexpr int kTBRows = 8;    // rows per thread
-constexpr int kTBWarps = 8;   // warps per CTA
-constexpr int kTBMinBlocks = 1;
+// Tile shape per blocking depth.  T <= 4: 8 rows x 8 warps (256 x 64 cells
+// with halo, two CTAs per SM).  5 <= T <= 7: 14 rows x 12 warps (256 x 168
+// cells, one CTA per SM, up to 168 registers a thread): the column halo is two
+// float4 for every T in 4..7 (T + 1 <= 8 entries) and the taller tile keeps
+// the row halo (2T per side) to 1.2x, so a 2048 x 2048 field is 10 x 15 = 150
+// tiles -- one wave on 152 SMs -- and each launch carries 7 sweeps.
+template <int T>
+struct TBCfg {
+    static constexpr int RB = T <= 4 ? 8 : 14;
+    static constexpr int WARPS = T <= 4 ? 8 : 12;
+    using Sh = TBShape<T, RB, WARPS>;
+};
 
 template <int T>
 static void launch_tb(RBLayout &L, int ny, float omega, cudaStream_t s) {
-    using Sh = TBShape<T, kTBRows, kTBWarps>;
-    dim3 grid(ceil_div(L.W4, Sh::KI4), ceil_div(ny, Sh::YI));
-    TW_LAUNCH((rb_tb_kernel<T, kTBRows, kTBWarps, kTBMinBlocks>), grid, kTBWarps * 32, 0, s, L.R, L.B, L.R2,
-              L.B2, L.MR, L.MB, ny, L.W4, L.S, L.MW, omega, (const float *)nullptr);
+    using C = TBCfg<T>;
+    dim3 grid(ceil_div(L.W4, C::Sh::KI4), ceil_div(ny, C::Sh::YI));
+    TW_LAUNCH((rb_tb_kernel<T, C::RB, C::WARPS, 1>), grid, C::WARPS * 32, 0, s, L.R, L.B, L.R2, L.B2, L.MR, L.MB,
+              ny, L.W4, L.S, L.MW, omega, (const float *)nullptr);
     float *t = L.R; L.R = L.R2; L.R2 = t;
     t = L.B; L.B = L.B2; L.B2 = t;
 }
@@ -95,14 +106,19 @@ static void launch_tb(RBLayout &L, int ny, float omega, cudaStream_t s) {
 int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream_t s, int *launches) {
     (void)nx;
     if (T <= 1 || !L.R2) return rb_sweeps_simple(L, ny, n, omega, s, launches);
-    if (T > 4) T = 4;
+    if (T > kMaxTBlock) T = kMaxTBlock;
     int left = n;
     while (left > 0) {
         int t = left >= T ? T : left;
-        if (t == 4) launch_tb<4>(L, ny, omega, s);
-        else if (t == 3) launch_tb<3>(L, ny, omega, s);
-        else if (t == 2) launch_tb<2>(L, ny, omega, s);
-        else launch_tb<1>(L, ny, omega, s);
+        switch (t) {
+            case 7: launch_tb<7>(L, ny, omega, s); break;
+            case 6: launch_tb<6>(L, ny, omega, s); break;
+            case 5: launch_tb<5>(L, ny, omega, s); break;
+            case 4: launch_tb<4>(L, ny, omega, s); break;
+            case 3: launch_tb<3>(L, ny, omega, s); break;
+            case 2: launch_tb<2>(L, ny, omega, s); break;
+            default: launch_tb<1>(L, ny, omega, s); break;
+        }
         left -= t;
         (*launches)++;
     }
@@ -110,20 +126,38 @@ int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream
     return TW_OK;
 }
 
+int tb_tiles(int T, int nx, int ny) {
+    RBLayout L = rb_layout(nx, ny);
+    int kx, yi;
+    switch (T) {
+        case 7: kx = TBCfg<7>::Sh::KI4; yi = TBCfg<7>::Sh::YI; break;
+        case 6: kx = TBCfg<6>::Sh::KI4; yi = TBCfg<6>::Sh::YI; break;
+        case 5: kx = TBCfg<5>::Sh::KI4; yi = TBCfg<5>::Sh::YI; break;
+        case 4: kx = TBCfg<4>::Sh::KI4; yi = TBCfg<4>::Sh::YI; break;
+        case 3: kx = TBCfg<3>::Sh::KI4; yi = TBCfg<3>::Sh::YI; break;
+        default: kx = TBCfg<2>::Sh::KI4; yi = TBCfg<2>::Sh::YI; break;
+    }
+    return (int)(ceil_div(L.W4, kx) * ceil_div(ny, yi));
+}
+
+template <int T>
+static void node_of(RBLayout &L, int ny, void **func, dim3 *grid, dim3 *block) {
+    using C = TBCfg<T>;
+    *func = (void *)rb_tb_kernel<T, C::RB, C::WARPS, 1>;
+    *grid = dim3(ceil_div(L.W4, C::Sh::KI4), ceil_div(ny, C::Sh::YI));
+    *block = dim3(C::WARPS * 32);
+}
+
 // Kernel entry and launch shape of the T-fused sweep, for graph construction.
 void tb_kernel_node(int T, RBLayout &L, int ny, void **func, dim3 *grid, dim3 *block) {
     switch (T) {
-        case 4: { using Sh = TBShape<4, kTBRows, kTBWarps>;
-                  *func = (void *)rb_tb_kernel<4, kTBRows, kTBWarps, kTBMinBlocks>;
-                  *grid = dim3(ceil_div(L.W4, Sh::KI4), ceil_div(ny, Sh::YI)); break; }
-        case 3: { using Sh = TBShape<3, kTBRows, kTBWarps>;
-                  *func = (void *)rb_tb_kernel<3, kTBRows, kTBWarps, kTBMinBlocks>;
-                  *grid = dim3(ceil_div(L.W4, Sh::KI4), ceil_div(ny, Sh::YI)); break; }
-        default: { using Sh = TBShape<2, kTBRows, kTBWarps>;
-                   *func = (void *)rb_tb_kernel<2, kTBRows, kTBWarps, kTBMinBlocks>;
-                   *grid = dim3(ceil_div(L.W4, Sh::KI4), ceil_div(ny, Sh::YI)); break; }
+        case 7: node_of<7>(L, ny, func, grid, block); break;
+        case 6: node_of<6>(L, ny, func, grid, block); break;
+        case 5: node_of<5>(L, ny, func, grid, block); break;
+        case 4: node_of<4>(L, ny, func, grid, block); break;
+        case 3: node_of<3>(L, ny, func, grid, block); break;
+        default: node_of<2>(L, ny, func, grid, block); break;
     }
-    *block = dim3(kTBWarps * 32);
 }
 
 }  // namespace tw

@@ -1,13 +1,22 @@
 // Register-blocked, temporally blocked red-black SOR tile (shared by the
 // single-field and the batched sweep kernels; see hp_sweeps.cu for the design).
 #pragma once
+#include <type_traits>
+
 #include "hp_internal.cuh"
 
 namespace tw {
 
+// One Eq. 1 update's size, (1/4)((l + r) + (u + d)) - c: the SOR step before
+// the factor omega, and (in magnitude) the residual of the cell.  Every kernel
+// of the split layout evaluates it in this form so that their residuals agree
+// bit for bit.
+__device__ __forceinline__ float rb_step(float c, float l, float r, float u, float d) {
+    return fmaf(0.25f, (l + r) + (u + d), -c);
+}
+
 __device__ __forceinline__ float sor1(float c, float l, float r, float u, float d, float omega) {
-    const float t = fmaf(0.25f, (l + r) + (u + d), -c);
-    return fmaf(omega, t, c);
+    return fmaf(omega, rb_step(c, l, r, u, d), c);
 }
 
 // SOR update of one float4 row; S = parity of the row for the colour updated
@@ -37,6 +46,28 @@ __device__ __forceinline__ float4 sor_row(float4 c, const float4 mid, const floa
     return c;
 }
 
+// Residual max over the masked cells of one float4 row (same neighbour
+// pattern as sor_row).
+template <int S>
+__device__ __forceinline__ float resid_row(const float4 c, const float4 mid, const float4 up, const float4 dn,
+                                           uint32_t bits, float acc) {
+    float l0, l1, l2, l3, r0, r1, r2, r3;
+    if (S) {
+        const float ex = __shfl_down_sync(0xffffffffu, mid.x, 1);
+        l0 = mid.x; l1 = mid.y; l2 = mid.z; l3 = mid.w;
+        r0 = mid.y; r1 = mid.z; r2 = mid.w; r3 = ex;
+    } else {
+        const float ex = __shfl_up_sync(0xffffffffu, mid.w, 1);
+        l0 = ex; l1 = mid.x; l2 = mid.y; l3 = mid.z;
+        r0 = mid.x; r1 = mid.y; r2 = mid.z; r3 = mid.w;
+    }
+    if (bits & 1u) acc = fmaxf(acc, fabsf(rb_step(c.x, l0, r0, up.x, dn.x)));
+    if (bits & 2u) acc = fmaxf(acc, fabsf(rb_step(c.y, l1, r1, up.y, dn.y)));
+    if (bits & 4u) acc = fmaxf(acc, fabsf(rb_step(c.z, l2, r2, up.z, dn.z)));
+    if (bits & 8u) acc = fmaxf(acc, fabsf(rb_step(c.w, l3, r3, up.w, dn.w)));
+    return acc;
+}
+
 template <int T, int RB, int WARPS>
 struct TBShape {
     static constexpr int HK4 = (T + 1 + 3) / 4;       // halo, float4 columns per side
@@ -48,8 +79,13 @@ struct TBShape {
     static_assert(YI % 2 == 0 && HY % 2 == 0 && RB % 2 == 0, "thread rows must start on even rows");
 };
 
+// Free-cell bits of a thread's rows, 4 per row: one 32-bit word per colour up
+// to 8 rows, 64 bits beyond.
+template <int RB>
+using TBMask = typename std::conditional<(RB > 8), unsigned long long, uint32_t>::type;
+
 template <int COLOR, int RB, int WARPS>
-__device__ __forceinline__ void tb_half_sweep(float4 (&v)[2][RB], const uint32_t m, float4 above, float4 below,
+__device__ __forceinline__ void tb_half_sweep(float4 (&v)[2][RB], const TBMask<RB> m, float4 above, float4 below,
                                               float omega) {
     constexpr int O = 1 - COLOR;
 #pragma unroll
@@ -58,9 +94,73 @@ __device__ __forceinline__ void tb_half_sweep(float4 (&v)[2][RB], const uint32_t
         const float4 dn = (r == RB - 1) ? below : v[O][r + 1];
         // rows start even, so the parity of row r for colour COLOR is (r + COLOR) & 1
         if (((r + COLOR) & 1) != 0)
-            v[COLOR][r] = sor_row<1>(v[COLOR][r], v[O][r], up, dn, (m >> (4 * r)) & 0xFu, omega);
+            v[COLOR][r] = sor_row<1>(v[COLOR][r], v[O][r], up, dn, (uint32_t)(m >> (4 * r)) & 0xFu, omega);
         else
-            v[COLOR][r] = sor_row<0>(v[COLOR][r], v[O][r], up, dn, (m >> (4 * r)) & 0xFu, omega);
+            v[COLOR][r] = sor_row<0>(v[COLOR][r], v[O][r], up, dn, (uint32_t)(m >> (4 * r)) & 0xFu, omega);
+    }
+}
+
+// Load a thread's RB rows of float4 column k4 of both colours, and their
+// free-cell bits (bit 4*r + e: cell e of row r is free).  Rows and columns
+// outside the field read as zero with no free bit, so they never change.
+template <int RB>
+__device__ __forceinline__ void tb_load(float4 (&v)[2][RB], TBMask<RB> (&m)[2], const float *__restrict__ Rin,
+                                        const float *__restrict__ Bin, const uint32_t *__restrict__ MR,
+                                        const uint32_t *__restrict__ MB, int y0, int k4, bool kin, int ny, int S,
+                                        int MW) {
+    static_assert(RB <= 16, "free-cell bits of a thread's rows are kept in one 64-bit word per colour");
+    const int k = 4 * k4;
+    m[0] = 0u;
+    m[1] = 0u;
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+        const int y = y0 + r;
+        const bool in = kin && y >= 0 && y < ny;
+        const size_t off = (size_t)(in ? y : 0) * S + 4 + (in ? k : 0);
+        v[0][r] = in ? __ldg(reinterpret_cast<const float4 *>(Rin + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[1][r] = in ? __ldg(reinterpret_cast<const float4 *>(Bin + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in) {
+            const size_t w = (size_t)y * MW + (k >> 5);
+            m[0] |= (TBMask<RB>)((__ldg(MR + w) >> (k & 31)) & 0xFu) << (4 * r);
+            m[1] |= (TBMask<RB>)((__ldg(MB + w) >> (k & 31)) & 0xFu) << (4 * r);
+        }
+    }
+}
+
+// One full red-black sweep of the CTA's registers: each half-sweep first
+// exchanges the other colour's first/last rows with the warps above/below
+// through shared memory (double-buffered by colour, one barrier each).
+template <int RB, int WARPS>
+__device__ __forceinline__ void tb_full_sweep(float4 (&v)[2][RB], const TBMask<RB> (&m)[2], float omega,
+                                              float4 (&s_top)[2][WARPS][32], float4 (&s_bot)[2][WARPS][32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    s_top[0][warp][lane] = v[1][0];
+    s_bot[0][warp][lane] = v[1][RB - 1];
+    __syncthreads();
+    tb_half_sweep<0, RB, WARPS>(v, m[0], warp > 0 ? s_bot[0][warp - 1][lane] : zero,
+                                warp < WARPS - 1 ? s_top[0][warp + 1][lane] : zero, omega);
+    s_top[1][warp][lane] = v[0][0];
+    s_bot[1][warp][lane] = v[0][RB - 1];
+    __syncthreads();
+    tb_half_sweep<1, RB, WARPS>(v, m[1], warp > 0 ? s_bot[1][warp - 1][lane] : zero,
+                                warp < WARPS - 1 ? s_top[1][warp + 1][lane] : zero, omega);
+}
+
+// Store the rows of the tile interior [y_tile, y_tile + YI) held by the thread.
+template <int RB>
+__device__ __forceinline__ void tb_store(const float4 (&v)[2][RB], float *__restrict__ Rout,
+                                         float *__restrict__ Bout, int y0, int y_tile, int YI, int k4,
+                                         bool lane_int, int ny, int S) {
+    if (!lane_int) return;
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+        const int y = y0 + r;
+        if (y >= y_tile && y < y_tile + YI && y < ny) {
+            const size_t off = (size_t)y * S + 4 + 4 * k4;
+            *reinterpret_cast<float4 *>(Rout + off) = v[0][r];
+            *reinterpret_cast<float4 *>(Bout + off) = v[1][r];
+        }
     }
 }
 
@@ -78,54 +178,13 @@ __device__ __forceinline__ void tb_tile(const float *__restrict__ Rin, const flo
     const int y_tile = by * Sh::YI;
     const int y0 = y_tile - Sh::HY + warp * RB;   // even
     const bool kin = (k4 >= 0) && (k4 < W4);
-    const int k = 4 * k4;
 
     float4 v[2][RB];
-    uint32_t m[2] = {0u, 0u};  // bit 4*r + e: cell e of row r is free
-#pragma unroll
-    for (int r = 0; r < RB; r++) {
-        const int y = y0 + r;
-        const bool in = kin && y >= 0 && y < ny;
-        const size_t off = (size_t)(in ? y : 0) * S + 4 + (in ? k : 0);
-        v[0][r] = in ? __ldg(reinterpret_cast<const float4 *>(Rin + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[1][r] = in ? __ldg(reinterpret_cast<const float4 *>(Bin + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (in) {
-            const size_t w = (size_t)y * MW + (k >> 5);
-            m[0] |= ((__ldg(MR + w) >> (k & 31)) & 0xFu) << (4 * r);
-            m[1] |= ((__ldg(MB + w) >> (k & 31)) & 0xFu) << (4 * r);
-        }
-    }
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-
+    TBMask<RB> m[2];
+    tb_load<RB>(v, m, Rin, Bin, MR, MB, y0, k4, kin, ny, S, MW);
 #pragma unroll 1
-    for (int p = 0; p < T; p++) {
-        // red half-sweep: exchange black's first/last rows with the warps above/below
-        s_top[0][warp][lane] = v[1][0];
-        s_bot[0][warp][lane] = v[1][RB - 1];
-        __syncthreads();
-        tb_half_sweep<0, RB, WARPS>(v, m[0], warp > 0 ? s_bot[0][warp - 1][lane] : zero,
-                                    warp < WARPS - 1 ? s_top[0][warp + 1][lane] : zero, omega);
-        // black half-sweep: exchange red's first/last rows
-        s_top[1][warp][lane] = v[0][0];
-        s_bot[1][warp][lane] = v[0][RB - 1];
-        __syncthreads();
-        tb_half_sweep<1, RB, WARPS>(v, m[1], warp > 0 ? s_bot[1][warp - 1][lane] : zero,
-                                    warp < WARPS - 1 ? s_top[1][warp + 1][lane] : zero, omega);
-    }
-
-    // store the interior
-    const bool kint = lane >= Sh::HK4 && lane < 32 - Sh::HK4 && kin;
-    if (kint) {
-#pragma unroll
-        for (int r = 0; r < RB; r++) {
-            const int y = y0 + r;
-            if (y >= y_tile && y < y_tile + Sh::YI && y < ny) {
-                const size_t off = (size_t)y * S + 4 + k;
-                *reinterpret_cast<float4 *>(Rout + off) = v[0][r];
-                *reinterpret_cast<float4 *>(Bout + off) = v[1][r];
-            }
-        }
-    }
+    for (int p = 0; p < T; p++) tb_full_sweep<RB, WARPS>(v, m, omega, s_top, s_bot);
+    tb_store<RB>(v, Rout, Bout, y0, y_tile, Sh::YI, k4, kin && lane >= Sh::HK4 && lane < 32 - Sh::HK4, ny, S);
 }
 
 }  // namespace tw
