@@ -169,7 +169,7 @@ batch_control_kernel(BatchInst *__restrict__ I, BatchHdr *__restrict__ H, int2 *
             const float rf = __uint_as_float(b.rmax);
             b.rmax = 0u;
             c.sweeps += c.K;
-            int go = relax_control(c, (double)rf, c.K);
+            int go = relax_control(c, (double)rf, -1.0, c.K);
             if (c.sweeps + c.K > c.max_sweeps || final_check) go = 0;
             if (b.error) go = 0;
             c.omega_f = (float)c.omega;

@@ -26,36 +26,19 @@ namespace tw {
 void tb_kernel_node(int T, RBLayout &L, int ny, void **func, dim3 *grid, dim3 *block);
 void *rb_residual_kernel_ptr();
 
-__global__ void relax_control_kernel(RelaxCtl *ctl, unsigned int *rmax, int max_intervals,
-                                     cudaGraphConditionalHandle handle) {
-    pdl_wait();
+__global__ void relax_control_kernel(RelaxCtl *ctl, unsigned int *rmax, const float *l2part, int n_part,
+                                     int max_intervals, cudaGraphConditionalHandle handle) {
+    // one warp: the 2-norm from the residual kernel's per-CTA partials, then lane 0 decides
+    const double e = l2part ? sqrt(warp_sum_partials(l2part, n_part)) : -1.0;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     RelaxCtl c = *ctl;
     const float rf = __uint_as_float(*rmax);
     *rmax = 0u;
     c.sweeps += c.K;
-    int go = relax_control(c, (double)rf, c.K);
+    int go = relax_control(c, (double)rf, e, c.K);
     if (c.checks >= max_intervals || c.sweeps + c.K > c.max_sweeps) go = 0;
     *ctl = c;
     cudaGraphSetConditional(handle, go ? 1u : 0u);
-}
-
-// Add a kernel node after `prev` (if any) with a programmatic edge: the node
-// may launch while `prev` finishes and waits (griddepcontrol.wait) for it.
-static cudaError_t add_kernel_after(cudaGraphNode_t *node, cudaGraph_t g, cudaGraphNode_t prev,
-                                    const cudaKernelNodeParams &kp) {
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeKernel;
-    np.kernel.func = kp.func;
-    np.kernel.gridDim = kp.gridDim;
-    np.kernel.blockDim = kp.blockDim;
-    np.kernel.sharedMemBytes = kp.sharedMemBytes;
-    np.kernel.kernelParams = kp.kernelParams;
-    cudaGraphEdgeData ed;
-    memset(&ed, 0, sizeof(ed));
-    ed.from_port = cudaGraphKernelNodePortProgrammatic;
-    ed.type = cudaGraphDependencyTypeProgrammatic;
-    return cudaGraphAddNode(node, g, prev ? &prev : nullptr, prev ? &ed : nullptr, prev ? 1 : 0, &np);
 }
 
 struct GraphEntry {
@@ -70,7 +53,7 @@ static std::vector<GraphEntry> g_graphs;
 constexpr size_t kMaxCachedGraphs = 16;
 
 static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_intervals, RelaxScalars *scal,
-                       GraphEntry *out) {
+                       float *l2part, GraphEntry *out) {
     (void)nx;
     cudaGraph_t g = nullptr;
     TW_CUDA(cudaGraphCreate(&g, 0));
@@ -113,7 +96,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         kp.sharedMemBytes = 0;
         kp.kernelParams = args;
         cudaGraphNode_t node;
-        e = add_kernel_after(&node, body, prev, kp);
+        e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
         prev = node;
         float *t = R; R = R2; R2 = t;
@@ -124,7 +107,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         Lc.R = R; Lc.B = B;
         int ny_ = ny;
         unsigned int *rmax = &scal->max32;
-        void *args[] = {(void *)&Lc, (void *)&ny_, (void *)&rmax};
+        void *args[] = {(void *)&Lc, (void *)&ny_, (void *)&rmax, (void *)&l2part};
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof(kp));
         kp.func = rb_residual_kernel_ptr();
@@ -132,15 +115,17 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         kp.blockDim = dim3(64, 4);
         kp.kernelParams = args;
         cudaGraphNode_t node;
-        e = add_kernel_after(&node, body, prev, kp);
+        e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
         prev = node;
     }
     {   // control
         RelaxCtl *ctl = &scal->ctl;
         unsigned int *rmax = &scal->max32;
+        const float *part = l2part;
+        int n_part = rb_residual_blocks(L, ny);
         int mi = max_intervals;
-        void *args[] = {(void *)&ctl, (void *)&rmax, (void *)&mi, (void *)&h};
+        void *args[] = {(void *)&ctl, (void *)&rmax, (void *)&part, (void *)&n_part, (void *)&mi, (void *)&h};
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof(kp));
         kp.func = (void *)relax_control_kernel;
@@ -148,7 +133,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         kp.blockDim = dim3(32);
         kp.kernelParams = args;
         cudaGraphNode_t node;
-        e = add_kernel_after(&node, body, prev, kp);
+        e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
     }
     cudaGraphExec_t exec;
@@ -160,7 +145,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
 }
 
 int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, RelaxScalars *scal,
-                   cudaStream_t s, int *launches) {
+                   float *l2part, cudaStream_t s, int *launches) {
     if (max_intervals < 1) return 1;
     int dev = 0;
     TW_CUDA(cudaGetDevice(&dev));
@@ -179,7 +164,7 @@ int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals,
         GraphEntry ne;
         ne.dev = dev; ne.nx = nx; ne.ny = ny; ne.T = T; ne.K = K; ne.max_intervals = max_intervals;
         ne.key = (const void *)scal;
-        int e = build_graph(L, nx, ny, T, K, max_intervals, scal, &ne);
+        int e = build_graph(L, nx, ny, T, K, max_intervals, scal, l2part, &ne);
         if (e) return e;
         g_graphs.push_back(ne);
         ent = &g_graphs.back();

@@ -32,6 +32,7 @@ struct RelaxCtl {
     unsigned int rmax;     // FP32 residual max accumulator (bits); reset after each check
     int sweeps, checks, status, adapt, same_iv, K, max_sweeps, pad;
     double omega, r_prev, tol, r_last;
+    double e_prev;         // residual 2-norm at the previous check (<= 0: not measured)
 };
 
 
@@ -40,7 +41,8 @@ struct RelaxScalars {
     int goal_blocked;      // set on the device when the goal cell is occupied
     unsigned long long max64;
     double sum64;
-    double pad1[5];
+    double l2;             // residual 2-norm of the last check (host-driven loop)
+    double pad1[4];
     RelaxCtl ctl;
 };
 
@@ -57,6 +59,7 @@ struct RelaxLayout {
     float *tmp;        // Jacobi ping-pong buffer
     RBLayout rb;
     MixedLayout mx;
+    float *l2part;     // per-CTA sums of squared residuals of rb_residual_kernel
 };
 
 RBLayout rb_layout(int nx, int ny);
@@ -72,8 +75,11 @@ int tb_tiles(int T, int nx, int ny);
 // run on the device; ctl_dev must hold the initial state.  Returns TW_OK, or
 // a positive value when graphs are unavailable (the caller uses the host loop).
 int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, RelaxScalars *scal,
-                   cudaStream_t s, int *launches);
-void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, cudaStream_t s);
+                   float *l2part, cudaStream_t s, int *launches);
+// FP32 residual max (atomicMax into *out) and, if l2part is given, the sum of
+// squared residuals of every CTA in l2part[rb_residual_blocks(L, ny)].
+void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s);
+int rb_residual_blocks(const RBLayout &L, int ny);
 
 // Optional CUDA-event timing of the sweep kernels (HP_TIMING).
 struct SweepTimer {
@@ -101,7 +107,7 @@ struct SweepTimer {
     }
 };
 // *ctl_on_device = 1 when the final loop state is only on the device (in scal->ctl)
-int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
+int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, float *l2part, hp_stats *st,
              cudaStream_t s, int *ctl_on_device);
 double sor_initial_omega(int nx, int ny);
 int read_max_f32(unsigned int *dmax, cudaStream_t s, float *out);
@@ -128,9 +134,23 @@ __host__ __device__ inline double sor_adapt(double omega, double lambda) {
     return (w > omega) ? w : omega;
 }
 
+// Deterministic sum of per-CTA partials by one full warp (every lane returns
+// the same value: lane-strided sums in index order, then a butterfly whose
+// pairwise additions are the same in every lane).
+__device__ inline double warp_sum_partials(const float *part, int n) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += (double)part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // One residual check: stop test, over-relaxation back-off at the rounding
-// floor, adaptive omega.  Returns 1 to continue, 0 when converged.
-__host__ __device__ inline int relax_control(RelaxCtl &c, double r, int n) {
+// floor, adaptive omega.  r is the residual max (the stopping quantity); e,
+// when positive, its 2-norm, from which the decay rate that drives omega is
+// estimated (smoother than the max, whose location jumps between cells).
+// Returns 1 to continue, 0 when converged.
+__host__ __device__ inline int relax_control(RelaxCtl &c, double r, double e, int n) {
     c.checks++;
     c.r_last = r;
     if (c.tol > 0.0 && r <= c.tol) {
@@ -149,25 +169,18 @@ __host__ __device__ inline int relax_control(RelaxCtl &c, double r, int n) {
         c.same_iv = 0;
     } else if (c.adapt) {
         if (c.r_prev > 0.0 && c.same_iv >= 1 && n == c.K) {
-            double lambda = pow(r / c.r_prev, 1.0 / n);
+            const bool l2 = e > 0.0 && c.e_prev > 0.0;
+            double lambda = pow(l2 ? e / c.e_prev : r / c.r_prev, 1.0 / n);
             double w = sor_adapt(c.omega, lambda);
             if (w > c.omega + 1e-4) { c.omega = w; c.same_iv = -1; }
         }
         c.same_iv++;
     }
     c.r_prev = r;
+    c.e_prev = e;
     c.omega_f = (float)c.omega;
     return 1;
 }
-
-// Programmatic dependent launch.  In the graph-driven loop consecutive
-// kernels are joined by programmatic edges: a kernel lets its successor be
-// launched as soon as all of its own CTAs have started (launch_dependents),
-// and every kernel waits for its predecessors to complete, with their memory
-// visible, before it reads what they wrote (wait).  Outside such an edge (plain
-// stream launches) both are no-ops.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // NaN or overflow must never look converged: map them to +inf before a max.
 __device__ __forceinline__ float sane(float r) { return (r <= FLT_MAX) ? r : __int_as_float(0x7f800000); }

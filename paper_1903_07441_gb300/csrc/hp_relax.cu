@@ -158,13 +158,12 @@ __global__ void rb_unpack_kernel(RBLayout L, int nx, int ny, float *__restrict__
     out[(size_t)y * nx + x] = to_phi ? 1.0f - v : v;
 }
 
-// FP32 residual max over both colours of the split layout.
-__global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, unsigned int *out_max) {
-    pdl_launch_dependents();
-    pdl_wait();
+// FP32 residual max over both colours of the split layout (one atomicMax per
+// CTA) and, if l2part is given, each CTA's sum of squared residuals.
+__global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, unsigned int *out_max, float *l2part) {
     int k4 = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    float r = 0.0f;
+    float r = 0.0f, q = 0.0f;
     if (k4 < L.W4 && y < ny - 1) {
         int k = 4 * k4;
 #pragma unroll
@@ -178,13 +177,35 @@ __global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, un
             float4 nb[4];
             rb_load_neighbours(V, L.S, y, k, s, nb);
             float4 c = *reinterpret_cast<const float4 *>(U + (size_t)y * L.S + 4 + k);
-            if (bits & 1u) r = fmaxf(r, fabsf(rb_step(c.x, nb[0].x, nb[1].x, nb[2].x, nb[3].x)));
-            if (bits & 2u) r = fmaxf(r, fabsf(rb_step(c.y, nb[0].y, nb[1].y, nb[2].y, nb[3].y)));
-            if (bits & 4u) r = fmaxf(r, fabsf(rb_step(c.z, nb[0].z, nb[1].z, nb[2].z, nb[3].z)));
-            if (bits & 8u) r = fmaxf(r, fabsf(rb_step(c.w, nb[0].w, nb[1].w, nb[2].w, nb[3].w)));
+            const float t0 = rb_step(c.x, nb[0].x, nb[1].x, nb[2].x, nb[3].x);
+            const float t1 = rb_step(c.y, nb[0].y, nb[1].y, nb[2].y, nb[3].y);
+            const float t2 = rb_step(c.z, nb[0].z, nb[1].z, nb[2].z, nb[3].z);
+            const float t3 = rb_step(c.w, nb[0].w, nb[1].w, nb[2].w, nb[3].w);
+            if (bits & 1u) { r = fmaxf(r, fabsf(t0)); q = fmaf(t0, t0, q); }
+            if (bits & 2u) { r = fmaxf(r, fabsf(t1)); q = fmaf(t1, t1, q); }
+            if (bits & 4u) { r = fmaxf(r, fabsf(t2)); q = fmaf(t2, t2, q); }
+            if (bits & 8u) { r = fmaxf(r, fabsf(t3)); q = fmaf(t3, t3, q); }
+        }
+    }
+    if (l2part) {   // fixed-order CTA sum: the same partials in every run
+        __shared__ float sq[8];
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        const int t = threadIdx.y * blockDim.x + threadIdx.x;
+        if ((t & 31) == 0) sq[t >> 5] = q;
+        __syncthreads();
+        if (t < 32) {
+            float v = t < (int)((blockDim.x * blockDim.y + 31) / 32) ? sq[t] : 0.0f;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (t == 0) l2part[blockIdx.y * gridDim.x + blockIdx.x] = v;
         }
     }
     block_max_atomic(r, out_max);
+}
+
+// The 2-norm of the last check's residual from its per-CTA partials (one warp).
+__global__ void l2_finalize_kernel(const float *__restrict__ part, int n, double *out) {
+    const double s = warp_sum_partials(part, n);
+    if (threadIdx.x == 0) *out = sqrt(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -226,6 +247,7 @@ static size_t carve_relax(Carver &cv, int nx, int ny, const hp_params *p, RelaxL
         R.tmp = cv.take<float>((size_t)nx * ny);
     } else if (method == HP_RBSOR) {
         carve_rb(cv, nx, ny, &R.rb, true);
+        R.l2part = cv.take<float>((size_t)rb_residual_blocks(R.rb, ny));
     } else {
         carve_mixed(cv, nx, ny, p ? p->storage : HP_STORE_F16, &R);
     }
@@ -319,16 +341,18 @@ static int relax_jacobi(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
 // Red-black SOR driver on the split layout (pack -> sweeps -> unpack).
 void *rb_residual_kernel_ptr() { return (void *)rb_residual_kernel; }
 
-void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, cudaStream_t s) {
+int rb_residual_blocks(const RBLayout &L, int ny) { return (int)(ceil_div(L.W4, 64) * ceil_div(ny, 4)); }
+
+void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s) {
     dim3 b(64, 4), gr(ceil_div(L.W4, 64), ceil_div(ny, 4));
-    TW_LAUNCH(rb_residual_kernel, gr, b, 0, s, L, ny, out);
+    TW_LAUNCH(rb_residual_kernel, gr, b, 0, s, L, ny, out, l2part);
 }
 
 // Red-black SOR driver on the split layout.  By default the check intervals
 // run inside one CUDA graph (a conditional while-node re-runs "K sweeps,
 // residual, control" on the device); the host loop below finishes any
 // remainder and serves HP_TIMING / HP_HOST_LOOP.
-int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, hp_stats *st,
+int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, float *l2part, hp_stats *st,
              cudaStream_t s, int *ctl_on_device) {
     *ctl_on_device = 0;
     // Blocking depth: the deep tiles when they fill most of a GB300 (152 SMs)
@@ -362,7 +386,7 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
     if (checks && !host_loop && T > 1 && (K / T) % 2 == 0 && p->max_sweeps >= K) {
         TW_CUDA(cudaMemcpyAsync(&scal->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s));
         TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
-        int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, scal, s, &launches);
+        int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, scal, l2part, s, &launches);
         if (e < 0) return e;
         if (e == TW_OK) st->loop = HP_LOOP_GRAPH;
         if (e == TW_OK && p->max_sweeps % K == 0) {
@@ -393,12 +417,15 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
         c.sweeps += n;
         if (checks) {
             TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
-            rb_residual_launch(L, ny, &scal->max32, s);
+            rb_residual_launch(L, ny, &scal->max32, l2part, s);
+            if (l2part) TW_LAUNCH(l2_finalize_kernel, 1, 32, 0, s, l2part, rb_residual_blocks(L, ny), &scal->l2);
             TW_CHECK_LAUNCH();
+            RelaxScalars hs;
+            TW_CUDA(cudaMemcpyAsync(&hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+            TW_CUDA(cudaStreamSynchronize(s));
             float rf;
-            e = read_max_f32(&scal->max32, s, &rf);
-            if (e) return e;
-            if (!relax_control(c, (double)rf, n)) done = true;
+            memcpy(&rf, &hs.max32, sizeof(rf));
+            if (!relax_control(c, (double)rf, l2part ? hs.l2 : -1.0, n)) done = true;
         }
     }
     st->status = c.status;
@@ -423,7 +450,7 @@ static int relax_rbsor(const uint8_t *occ, int nx, int ny, int gx, int gy, float
     TW_LAUNCH(rb_pack_kernel, dim3(ceil_div(L.W2 + 31, 128), ny), 128, 0, s,
               occ, u, nx, ny, gx, gy, mode, (p->flags & HP_WARM_START) ? 1 : 0, L);
     TW_CHECK_LAUNCH();
-    int e = rb_solve(L, nx, ny, p, R.scal, st, s, ctl_dev);
+    int e = rb_solve(L, nx, ny, p, R.scal, R.l2part, st, s, ctl_dev);
     if (e) return e;
     TW_LAUNCH(rb_unpack_kernel, dim3(ceil_div(nx, 256), ny), 256, 0, s, L, nx, ny, u, 0);
     TW_CHECK_LAUNCH();

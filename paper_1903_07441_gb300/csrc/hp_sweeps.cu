@@ -72,8 +72,6 @@ rb_tb_kernel(const float *__restrict__ Rin, const float *__restrict__ Bin, float
              int ny, int W4, int S, int MW, float omega_arg, const float *__restrict__ omega_dev) {
     __shared__ float4 s_top[2][WARPS][32];
     __shared__ float4 s_bot[2][WARPS][32];
-    pdl_launch_dependents();
-    pdl_wait();   // the previous sweep (or the control kernel's omega) must be complete
     // the graph-driven loop keeps omega in device memory (it adapts on the device)
     const float omega = omega_dev ? *omega_dev : omega_arg;
     tb_tile<T, RB, WARPS>(Rin, Bin, Rout, Bout, MR, MB, ny, W4, S, MW, omega, (int)blockIdx.x, (int)blockIdx.y,
