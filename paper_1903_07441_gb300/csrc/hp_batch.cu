@@ -212,16 +212,16 @@ __global__ void batch_unpack_kernel(BatchInst *I, int to_phi) {
 __global__ void __launch_bounds__(256) batch_final_residual_kernel(BatchInst *I) {
     BatchInst &b = I[blockIdx.z];
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    double r = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     if (x > 0 && y > 0 && x < b.nx - 1 && y < b.ny - 1) {
         const size_t c = (size_t)y * b.nx + x;
         const bool fixed = b.occ[c] != 0 || (x == b.gx && y == b.gy);
         if (!fixed) {
             const float *u = b.field;
-            r = resid_exact(u[c + 1], u[c - 1], u[c + b.nx], u[c - b.nx], u[c]);
+            resid_pair(u[c + 1], u[c - 1], u[c + b.nx], u[c - b.nx], u[c], hi, lo);
         }
     }
-    block_max_sum_f64(r, &b.max64, &b.sum64);
+    block_max_sum_pair(hi, lo, hi * hi, &b.max64, &b.sum64);
 }
 
 __global__ void batch_start_kernel(BatchHdr *H) { H->t_start = globaltimer(); }

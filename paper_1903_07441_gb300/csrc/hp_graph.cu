@@ -28,8 +28,8 @@ void *rb_residual_kernel_ptr();
 
 __global__ void relax_control_kernel(RelaxCtl *ctl, unsigned int *rmax, const float *l2part, int n_part,
                                      int max_intervals, cudaGraphConditionalHandle handle) {
-    // one warp: the 2-norm from the residual kernel's per-CTA partials, then lane 0 decides
-    const double e = l2part ? sqrt(warp_sum_partials(l2part, n_part)) : -1.0;
+    // the 2-norm from the residual kernel's per-CTA partials (whole CTA), then thread 0 decides
+    const double e = l2part ? sqrt(block_sum_partials(l2part, n_part, threadIdx.x)) : -1.0;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     RelaxCtl c = *ctl;
     const float rf = __uint_as_float(*rmax);
@@ -130,7 +130,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         memset(&kp, 0, sizeof(kp));
         kp.func = (void *)relax_control_kernel;
         kp.gridDim = dim3(1);
-        kp.blockDim = dim3(32);
+        kp.blockDim = dim3(kPartThreads);
         kp.kernelParams = args;
         cudaGraphNode_t node;
         e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);

@@ -134,15 +134,23 @@ __host__ __device__ inline double sor_adapt(double omega, double lambda) {
     return (w > omega) ? w : omega;
 }
 
-// Deterministic sum of per-CTA partials by one full warp (every lane returns
-// the same value: lane-strided sums in index order, then a butterfly whose
-// pairwise additions are the same in every lane).
-__device__ inline double warp_sum_partials(const float *part, int n) {
-    const int lane = threadIdx.x & 31;
+// Deterministic sum of per-CTA partials by one CTA of kPartThreads threads:
+// each thread sums its strided partials in index order, then a fixed-shape
+// tree in shared memory; every thread returns the same value.
+// t is the thread's linear index in its CTA.  Partials are read through L2, so
+// values other CTAs of the same grid have just written are seen.
+constexpr int kPartThreads = 256;
+__device__ inline double block_sum_partials(const float *part, int n, int t) {
+    __shared__ double sm[kPartThreads];
     double s = 0.0;
-    for (int i = lane; i < n; i += 32) s += (double)part[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
+    for (int i = t; i < n; i += kPartThreads) s += (double)__ldcg(part + i);
+    sm[t] = s;
+    __syncthreads();
+    for (int w = kPartThreads / 2; w > 0; w >>= 1) {
+        if (t < w) sm[t] += sm[t + w];
+        __syncthreads();
+    }
+    return sm[0];
 }
 
 // One residual check: stop test, over-relaxation back-off at the rounding
@@ -209,20 +217,70 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// |(1/4)(l + r + u + d) - c| for FP32 inputs, evaluated in compensated FP32
-// (TwoSum on every addition, the scaling by 1/4 is exact) and returned as a
-// double: accurate to about 2^-45 relative to the inputs' magnitude, i.e. the
-// FP64 evaluation of the residual at a fraction of the FP64 operations (FP64
-// throughput is a small fraction of FP32 on this GPU).
-__device__ __forceinline__ double resid_exact(float l, float r, float u, float d, float c) {
+// |(1/4)(l + r + u + d) - c| for FP32 inputs in compensated FP32: TwoSum on
+// every addition (the scaling by 1/4 is exact), the result kept as an
+// unevaluated pair hi + lo of floats (hi >= 0, |lo| <= ulp(hi) / 2, so pairs
+// order lexicographically as their exact values do).  hi + lo is the FP64
+// evaluation of the residual to about 2^-45 relative to the inputs' magnitude,
+// at FP32 cost (FP64 throughput is a small fraction of FP32 on this GPU);
+// only the CTA's maximum is converted to FP64.
+__device__ __forceinline__ void resid_pair(float l, float r, float u, float d, float c, float &hi, float &lo) {
     float s1, e1, s2, e2, s3, e3, dd, e4;
     two_sum(l, r, s1, e1);
     two_sum(u, d, s2, e2);
     two_sum(s1, s2, s3, e3);
-    const float lo = __fadd_rn(__fadd_rn(e1, e2), e3);
+    const float low = __fadd_rn(__fadd_rn(e1, e2), e3);
     two_sum(__fmul_rn(0.25f, s3), -c, dd, e4);
-    const float tail = __fadd_rn(__fmul_rn(0.25f, lo), e4);
-    return fabs((double)dd + (double)tail);
+    two_sum(dd, __fadd_rn(__fmul_rn(0.25f, low), e4), hi, lo);
+    if (hi < 0.0f || (hi == 0.0f && lo < 0.0f)) {
+        hi = -hi;
+        lo = -lo;
+    }
+    if (!(hi <= FLT_MAX)) {   // NaN or overflow must never look converged
+        hi = __int_as_float(0x7f800000);
+        lo = 0.0f;
+    }
+}
+
+__device__ __forceinline__ void pair_max(float &hi, float &lo, float h2, float l2) {
+    if (h2 > hi || (h2 == hi && l2 > lo)) {
+        hi = h2;
+        lo = l2;
+    }
+}
+
+// Block-wide max of residual pairs and sum of squares: FP32 shuffles, then one
+// FP64 atomicMax (bits of a non-negative double) and one FP64 atomicAdd per CTA.
+__device__ __forceinline__ void block_max_sum_pair(float hi, float lo, float q, unsigned long long *out_max,
+                                                   double *out_sum) {
+    __shared__ float sh[32], sl[32], sq[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        pair_max(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y;
+    if ((t & 31) == 0) {
+        sh[t >> 5] = hi;
+        sl[t >> 5] = lo;
+        sq[t >> 5] = q;
+    }
+    __syncthreads();
+    if (t < 32) {
+        const bool in = t < (nt + 31) / 32;
+        hi = in ? sh[t] : 0.0f;
+        lo = in ? sl[t] : 0.0f;
+        q = in ? sq[t] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) {
+            pair_max(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+            q += __shfl_xor_sync(0xffffffffu, q, o);
+        }
+        if (t == 0) {
+            const double r = (double)hi + (double)lo;
+            if (r > 0.0) atomicMax(out_max, (unsigned long long)__double_as_longlong(r));
+            if (q != 0.0f) atomicAdd(out_sum, (double)q);
+        }
+    }
 }
 
 // Block-wide FP64 max (atomicMax on the bits of a non-negative double) and sum.

@@ -81,17 +81,29 @@ __global__ void __launch_bounds__(256) full_residual_kernel(const uint8_t *__res
 }
 
 // FP64-accurate residual (max and sum of squares) of a full-layout FP32 field.
+// A 32 x 8 CTA covers 32 x (8 * kResRows) cells, kResRows rows per thread, so
+// that the block reduction is amortised over several cells.
+constexpr int kResRows = 4;
 __global__ void __launch_bounds__(256) full_residual_f64_kernel(const uint8_t *__restrict__ occ, int nx, int ny,
                                                                 int gx, int gy, const float *__restrict__ u,
                                                                 unsigned long long *__restrict__ out_max,
                                                                 double *__restrict__ out_sum) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    double r = 0.0;
-    if (x > 0 && y > 0 && x < nx - 1 && y < ny - 1) {
-        size_t c = (size_t)y * nx + x;
-        if (!(occ[c] != 0 || (x == gx && y == gy))) r = resid_exact(u[c + 1], u[c - 1], u[c + nx], u[c - nx], u[c]);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    float hi = 0.0f, lo = 0.0f, q = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kResRows; i++) {
+        const int y = (blockIdx.y * kResRows + i) * blockDim.y + threadIdx.y;
+        if (x > 0 && y > 0 && x < nx - 1 && y < ny - 1) {
+            const size_t c = (size_t)y * nx + x;
+            if (!(occ[c] != 0 || (x == gx && y == gy))) {
+                float h, l;
+                resid_pair(u[c + 1], u[c - 1], u[c + nx], u[c - nx], u[c], h, l);
+                pair_max(hi, lo, h, l);
+                q = fmaf(h, h, q);
+            }
+        }
     }
-    block_max_sum_f64(r, out_max, out_sum);
+    block_max_sum_pair(hi, lo, q, out_max, out_sum);
 }
 
 __global__ void goal_check_kernel(const uint8_t *__restrict__ occ, int nx, int gx, int gy, int *flag) {
@@ -161,50 +173,14 @@ __global__ void rb_unpack_kernel(RBLayout L, int nx, int ny, float *__restrict__
 // FP32 residual max over both colours of the split layout (one atomicMax per
 // CTA) and, if l2part is given, each CTA's sum of squared residuals.
 __global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, unsigned int *out_max, float *l2part) {
-    int k4 = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
-    float r = 0.0f, q = 0.0f;
-    if (k4 < L.W4 && y < ny - 1) {
-        int k = 4 * k4;
-#pragma unroll
-        for (int color = 0; color < 2; color++) {
-            const float *U = color ? L.B : L.R;
-            const float *V = color ? L.R : L.B;
-            const uint32_t *M = color ? L.MB : L.MR;
-            uint32_t bits = (M[(size_t)y * L.MW + (k >> 5)] >> (k & 31)) & 0xFu;
-            if (!bits) continue;
-            int s = (y + color) & 1;
-            float4 nb[4];
-            rb_load_neighbours(V, L.S, y, k, s, nb);
-            float4 c = *reinterpret_cast<const float4 *>(U + (size_t)y * L.S + 4 + k);
-            const float t0 = rb_step(c.x, nb[0].x, nb[1].x, nb[2].x, nb[3].x);
-            const float t1 = rb_step(c.y, nb[0].y, nb[1].y, nb[2].y, nb[3].y);
-            const float t2 = rb_step(c.z, nb[0].z, nb[1].z, nb[2].z, nb[3].z);
-            const float t3 = rb_step(c.w, nb[0].w, nb[1].w, nb[2].w, nb[3].w);
-            if (bits & 1u) { r = fmaxf(r, fabsf(t0)); q = fmaf(t0, t0, q); }
-            if (bits & 2u) { r = fmaxf(r, fabsf(t1)); q = fmaf(t1, t1, q); }
-            if (bits & 4u) { r = fmaxf(r, fabsf(t2)); q = fmaf(t2, t2, q); }
-            if (bits & 8u) { r = fmaxf(r, fabsf(t3)); q = fmaf(t3, t3, q); }
-        }
-    }
-    if (l2part) {   // fixed-order CTA sum: the same partials in every run
-        __shared__ float sq[8];
-        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-        const int t = threadIdx.y * blockDim.x + threadIdx.x;
-        if ((t & 31) == 0) sq[t >> 5] = q;
-        __syncthreads();
-        if (t < 32) {
-            float v = t < (int)((blockDim.x * blockDim.y + 31) / 32) ? sq[t] : 0.0f;
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (t == 0) l2part[blockIdx.y * gridDim.x + blockIdx.x] = v;
-        }
-    }
-    block_max_atomic(r, out_max);
+    rb_residual_cta(L, ny, out_max, l2part);
 }
 
-// The 2-norm of the last check's residual from its per-CTA partials (one warp).
-__global__ void l2_finalize_kernel(const float *__restrict__ part, int n, double *out) {
-    const double s = warp_sum_partials(part, n);
+// The 2-norm of the last check's residual from its per-CTA partials (one CTA
+// of kPartThreads threads, the reduction the graph's control kernel uses).
+__global__ void __launch_bounds__(kPartThreads) l2_finalize_kernel(const float *__restrict__ part, int n,
+                                                                   double *out) {
+    const double s = block_sum_partials(part, n, threadIdx.x);
     if (threadIdx.x == 0) *out = sqrt(s);
 }
 
@@ -279,7 +255,7 @@ int read_max_f32(unsigned int *dmax, cudaStream_t s, float *out) {
 int final_residual_full(const uint8_t *occ, int nx, int ny, int gx, int gy, const float *u,
                         RelaxScalars *scal, cudaStream_t s, double *r_inf, double *r_l2) {
     TW_CUDA(cudaMemsetAsync(&scal->max64, 0, sizeof(scal->max64) + sizeof(scal->sum64), s));
-    dim3 b(32, 8), gr(ceil_div(nx, 32), ceil_div(ny, 8));
+    dim3 b(32, 8), gr(ceil_div(nx, 32), ceil_div(ny, 8 * kResRows));
     TW_LAUNCH(full_residual_f64_kernel, gr, b, 0, s, occ, nx, ny, gx, gy, u, &scal->max64, &scal->sum64);
     TW_CHECK_LAUNCH();
     unsigned long long m = 0;
@@ -339,9 +315,9 @@ static int relax_jacobi(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
 }
 
 // Red-black SOR driver on the split layout (pack -> sweeps -> unpack).
-void *rb_residual_kernel_ptr() { return (void *)rb_residual_kernel; }
-
 int rb_residual_blocks(const RBLayout &L, int ny) { return (int)(ceil_div(L.W4, 64) * ceil_div(ny, 4)); }
+
+void *rb_residual_kernel_ptr() { return (void *)rb_residual_kernel; }
 
 void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s) {
     dim3 b(64, 4), gr(ceil_div(L.W4, 64), ceil_div(ny, 4));
@@ -418,7 +394,8 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
         if (checks) {
             TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
             rb_residual_launch(L, ny, &scal->max32, l2part, s);
-            if (l2part) TW_LAUNCH(l2_finalize_kernel, 1, 32, 0, s, l2part, rb_residual_blocks(L, ny), &scal->l2);
+            if (l2part)
+                TW_LAUNCH(l2_finalize_kernel, 1, kPartThreads, 0, s, l2part, rb_residual_blocks(L, ny), &scal->l2);
             TW_CHECK_LAUNCH();
             RelaxScalars hs;
             TW_CUDA(cudaMemcpyAsync(&hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -487,7 +464,7 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
     if (e) return e;
     if (p->method != HP_MIXED) {   // HP_MIXED reports the residual of its FP64 master
         TW_CUDA(cudaMemsetAsync(&R.scal->max64, 0, sizeof(R.scal->max64) + sizeof(R.scal->sum64), s));
-        dim3 b(32, 8), gr(ceil_div(nx, 32), ceil_div(ny, 8));
+        dim3 b(32, 8), gr(ceil_div(nx, 32), ceil_div(ny, 8 * kResRows));
         TW_LAUNCH(full_residual_f64_kernel, gr, b, 0, s, occ, nx, ny, mode == 1 ? -1 : gx, mode == 1 ? -1 : gy, u,
                   &R.scal->max64, &R.scal->sum64);
         TW_CHECK_LAUNCH();

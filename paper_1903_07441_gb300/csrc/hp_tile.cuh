@@ -68,6 +68,52 @@ __device__ __forceinline__ float resid_row(const float4 c, const float4 mid, con
     return acc;
 }
 
+// One CTA (64 x 4 threads, one float4 of each colour per thread) of the FP32
+// residual check: atomicMax of the CTA's residual max into *out_max and, if
+// l2part is given, the CTA's sum of squared residuals, reduced in a fixed order,
+// into l2part[CTA index].
+__device__ __forceinline__ void rb_residual_cta(const RBLayout &L, int ny, unsigned int *out_max, float *l2part) {
+    const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    float r = 0.0f, q = 0.0f;
+    if (k4 < L.W4 && y < ny - 1) {
+        const int k = 4 * k4;
+#pragma unroll
+        for (int color = 0; color < 2; color++) {
+            const float *U = color ? L.B : L.R;
+            const float *V = color ? L.R : L.B;
+            const uint32_t *M = color ? L.MB : L.MR;
+            const uint32_t bits = (M[(size_t)y * L.MW + (k >> 5)] >> (k & 31)) & 0xFu;
+            if (!bits) continue;
+            const int s = (y + color) & 1;
+            float4 nb[4];
+            rb_load_neighbours(V, L.S, y, k, s, nb);
+            const float4 c = *reinterpret_cast<const float4 *>(U + (size_t)y * L.S + 4 + k);
+            const float t0 = rb_step(c.x, nb[0].x, nb[1].x, nb[2].x, nb[3].x);
+            const float t1 = rb_step(c.y, nb[0].y, nb[1].y, nb[2].y, nb[3].y);
+            const float t2 = rb_step(c.z, nb[0].z, nb[1].z, nb[2].z, nb[3].z);
+            const float t3 = rb_step(c.w, nb[0].w, nb[1].w, nb[2].w, nb[3].w);
+            if (bits & 1u) { r = fmaxf(r, fabsf(t0)); q = fmaf(t0, t0, q); }
+            if (bits & 2u) { r = fmaxf(r, fabsf(t1)); q = fmaf(t1, t1, q); }
+            if (bits & 4u) { r = fmaxf(r, fabsf(t2)); q = fmaf(t2, t2, q); }
+            if (bits & 8u) { r = fmaxf(r, fabsf(t3)); q = fmaf(t3, t3, q); }
+        }
+    }
+    if (l2part) {   // fixed-order CTA sum: the same partials in every run
+        __shared__ float sq[8];
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        const int t = threadIdx.y * blockDim.x + threadIdx.x;
+        if ((t & 31) == 0) sq[t >> 5] = q;
+        __syncthreads();
+        if (t < 32) {
+            float v = t < (int)((blockDim.x * blockDim.y + 31) / 32) ? sq[t] : 0.0f;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (t == 0) l2part[blockIdx.y * gridDim.x + blockIdx.x] = v;
+        }
+    }
+    block_max_atomic(r, out_max);
+}
+
 template <int T, int RB, int WARPS>
 struct TBShape {
     static constexpr int HK4 = (T + 1 + 3) / 4;       // halo, float4 columns per side
