@@ -314,6 +314,22 @@ int ws_unet_train_step(float *params, float *grads, float *adam_m, float *adam_v
                        const uint8_t *occ, int H, int W, int gx, int gy, const float *target, float *loss_host,
                        void *workspace, size_t workspace_bytes, void *stream);
 
+/* ws_conv3x3: one convolution layer of the network, Y = act(conv3x3(X, Wt) + b + S)
+ * with zero padding (stride 1).  X: device BF16 [cin][H][W]; Wt: device FP32
+ * [cout][cin][3][3], rounded to BF16 when used; b: device FP32 [cout] or NULL;
+ * S: device BF16 [cout][H][W] added before the activation, or NULL; Y: device
+ * BF16 [cout][H][W]; relu: 1 for ReLU, 0 for none.  impl: WS_CONV_AUTO (BF16
+ * tensor cores where cin % 16 == 0 and cout % 32 == 0, else CUDA cores),
+ * WS_CONV_SIMT (direct convolution on CUDA cores) or WS_CONV_MMA (tensor cores,
+ * mma.sync m16n8k16, FP32 accumulation; TW_EINVAL when the channel counts do not
+ * allow it).  Both accumulate every product in FP32; they differ only in the
+ * order of the sums.  Enqueued on `stream`.  Errors: TW_EINVAL, TW_ECUDA. */
+#define WS_CONV_AUTO 0
+#define WS_CONV_SIMT 1
+#define WS_CONV_MMA 2
+int ws_conv3x3(const void *X, const float *Wt, const float *b, const void *S, void *Y, int cin, int cout, int H, int W,
+               int relu, int impl, void *stream);
+
 /* ---- Kalman filter (host) ----------------------------------------------------
  * kf_update: one step of the constant-velocity filter of Sec. 3.5 for n host
  * tracks: predict by dt (Eqs. 9-10, A(dt), Q(dt) = q_accel x white-noise

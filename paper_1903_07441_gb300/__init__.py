@@ -29,6 +29,7 @@ HP_JACOBI, HP_RBSOR, HP_MIXED = 0, 1, 2
 HP_STORE_F32, HP_STORE_F16, HP_STORE_BF16 = 0, 1, 2
 HP_WARM_START, HP_OUT_PHI, HP_TIMING, HP_HOST_LOOP = 1, 2, 4, 8
 HP_LOOP_HOST, HP_LOOP_GRAPH = 0, 1
+WS_CONV_AUTO, WS_CONV_SIMT, WS_CONV_MMA = 0, 1, 2
 
 EXPORTS = (
     "tw_build_grid_workspace_size", "tw_build_grid", "tw_ring_count", "tw_nearest_free",
@@ -36,7 +37,7 @@ EXPORTS = (
     "hp_relax_batched_workspace_size", "hp_relax_batched",
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
     "kf_update", "kf_init", "ws_unet_param_count", "ws_unet_workspace_size", "ws_unet_init", "ws_make_target",
-    "ws_unet_forward", "ws_unet_train_step", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
+    "ws_unet_forward", "ws_unet_train_step", "ws_conv3x3", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
 )
 
 
@@ -166,6 +167,8 @@ def load() -> ctypes.CDLL:
     lib.ws_unet_forward.restype = I
     lib.ws_unet_train_step.argtypes = [P, P, P, P, I, ctypes.c_float, P, I, I, I, I, P, P, P, Z, P]
     lib.ws_unet_train_step.restype = I
+    lib.ws_conv3x3.argtypes = [P, P, P, P, P, I, I, I, I, I, I, P]
+    lib.ws_conv3x3.restype = I
     lib.tw_status_string.argtypes = [I]
     lib.tw_status_string.restype = ctypes.c_char_p
     lib.tw_last_cuda_error.restype = I
@@ -395,6 +398,20 @@ def kf_init(z: np.ndarray, radius: np.ndarray, r_meas=0.05, p_vel=1.0) -> np.nda
 # ---------------------------------------------------------------------------
 # learned warm start
 # ---------------------------------------------------------------------------
+
+def ws_conv3x3(x, w, b=None, skip=None, relu=False, impl=WS_CONV_AUTO):
+    """One convolution layer of the warm-start network: x bf16 [cin, H, W] (device),
+    w fp32 [cout, cin, 3, 3], b fp32 [cout] or None, skip bf16 [cout, H, W] or None.
+    Returns y bf16 [cout, H, W]."""
+    torch = _torch()
+    cin, H, W = x.shape
+    cout = w.shape[0]
+    y = torch.empty((cout, H, W), dtype=torch.bfloat16, device=x.device)
+    _check("ws_conv3x3", load().ws_conv3x3(_ptr(x), _ptr(w), _ptr(b) if b is not None else None,
+                                           _ptr(skip) if skip is not None else None, _ptr(y), cin, cout, H, W,
+                                           1 if relu else 0, int(impl), _stream(x.device)))
+    return y
+
 
 class WarmStartNet:
     """Parameters and Adam state of the warm-start network, on one device."""

@@ -53,13 +53,16 @@ static size_t total_params() { return param_offset(kNumConvs); }
 // ---- kernels ----------------------------------------------------------------------
 
 constexpr int TS = 16;   // pixel tile side
-constexpr int COB = 16;  // output channels per CTA
+constexpr int COB = 16;  // output channels per CTA (CUDA-core kernels)
 constexpr int CIB = 8;   // input channels per staged chunk
 
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16(v)); }
 
 // Y = act(conv3x3(X) + b + S): X [cin][H][W] bf16, Wt [cout][cin][3][3] fp32 (rounded to bf16),
 // b [cout] (nullable), S [cout][H][W] bf16 (nullable), Y [cout][H][W] bf16.
+// COB output channels per CTA, CIB input channels per staged chunk (the
+// network's first layer has 2 input channels, its head 1 output channel).
+template <int COB, int CIB>
 __global__ void __launch_bounds__(256) conv3x3_fwd_kernel(const bf16 *__restrict__ X, const float *__restrict__ Wt,
                                                           const float *__restrict__ b, const bf16 *__restrict__ S,
                                                           bf16 *__restrict__ Y, int cin, int cout, int H, int W,
@@ -113,6 +116,111 @@ __global__ void __launch_bounds__(256) conv3x3_fwd_kernel(const bf16 *__restrict
         if (S) v += __bfloat162float(S[o]);
         if (relu) v = fmaxf(v, 0.0f);
         Y[o] = __float2bfloat16(v);
+    }
+}
+
+// Tensor-core form of conv3x3_fwd_kernel (the same Y, up to FP32 summation
+// order) for cin a multiple of 16 and cout a multiple of NB: an implicit GEMM
+// with M = pixels, N = output channels, K = 9 taps x cin, on BF16
+// mma.sync.m16n8k16 with FP32 accumulators.  A CTA computes a 16 x 16 pixel
+// tile for NB output channels; warp w owns pixel rows 2w and 2w + 1 (one m16
+// tile each: 16 pixels along x) and all NB channels.  Per chunk of 16 input
+// channels the 18 x 18 input tile is staged channel-last (a pixel's 16
+// channels contiguous, stride 24 BF16 so that fragment loads are
+// conflict-free) and the weights as [tap][co][ci]; a fragment register is
+// then one 32-bit shared load.  Fragment layouts (m16n8k16, BF16): A row = pixel
+// g or g + 8 of the lane's group g = lane / 4, columns 2t, 2t + 1 (+ 8) with
+// t = lane % 4; B column = channel g, rows 2t, 2t + 1 (+ 8); C rows g, g + 8,
+// columns 2t, 2t + 1.
+constexpr int kTcStride = 24;   // BF16 per staged pixel / weight row (16 used)
+
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256) conv3x3_fwd_mma_kernel(const bf16 *__restrict__ X, const float *__restrict__ Wt,
+                                                              const float *__restrict__ b, const bf16 *__restrict__ S,
+                                                              bf16 *__restrict__ Y, int cin, int cout, int H, int W,
+                                                              int relu) {
+    constexpr int NT = NB / 8;
+    __shared__ __align__(16) bf16 xs[(TS + 2) * (TS + 2) * kTcStride];
+    __shared__ __align__(16) bf16 ws[9 * NB * kTcStride];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS, co0 = blockIdx.z * NB;
+    float acc[2][NT][4];
+#pragma unroll
+    for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int n = 0; n < NT; n++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) acc[m][n][e] = 0.0f;
+
+    for (int ci0 = 0; ci0 < cin; ci0 += 16) {
+        __syncthreads();
+        // input tile, channel-last: xs[(yy * 18 + xx) * 24 + c]
+        for (int i = threadIdx.x; i < 16 * (TS + 2) * (TS + 2); i += 256) {
+            const int c = i / ((TS + 2) * (TS + 2)), r = i % ((TS + 2) * (TS + 2));
+            const int yy = y0 + r / (TS + 2) - 1, xx = x0 + r % (TS + 2) - 1;
+            bf16 v = __float2bfloat16(0.0f);
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = X[((size_t)(ci0 + c) * H + yy) * W + xx];
+            xs[r * kTcStride + c] = v;
+        }
+        // weights as [tap][co][ci], rounded to BF16
+        for (int i = threadIdx.x; i < NB * 16 * 9; i += 256) {
+            const int co = i / (16 * 9), r = i % (16 * 9), c = r / 9, k = r % 9;
+            const float v = Wt[((size_t)(co0 + co) * cin + ci0 + c) * 9 + k];
+            ws[(k * NB + co) * kTcStride + c] = __float2bfloat16(v);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const int dy = k / 3, dx = k % 3;
+            uint32_t a[2][4];
+#pragma unroll
+            for (int m = 0; m < 2; m++) {
+                const int row = 2 * warp + m + dy;
+                const bf16 *p0 = xs + (row * (TS + 2) + g + dx) * kTcStride + 2 * t4;
+                const bf16 *p1 = p0 + 8 * kTcStride;   // pixel g + 8
+                a[m][0] = *reinterpret_cast<const uint32_t *>(p0);
+                a[m][1] = *reinterpret_cast<const uint32_t *>(p1);
+                a[m][2] = *reinterpret_cast<const uint32_t *>(p0 + 8);
+                a[m][3] = *reinterpret_cast<const uint32_t *>(p1 + 8);
+            }
+#pragma unroll
+            for (int n = 0; n < NT; n++) {
+                const bf16 *q = ws + (k * NB + n * 8 + g) * kTcStride + 2 * t4;
+                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(q);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(q + 8);
+                mma_bf16_16816(acc[0][n], a[0], b0, b1);
+                mma_bf16_16816(acc[1][n], a[1], b0, b1);
+            }
+        }
+    }
+    // epilogue: bias, skip, ReLU, BF16 store
+#pragma unroll
+    for (int m = 0; m < 2; m++) {
+        const int y = y0 + 2 * warp + m;
+        if (y >= H) continue;
+#pragma unroll
+        for (int n = 0; n < NT; n++) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int x = x0 + g + (e >= 2 ? 8 : 0);
+                const int oc = co0 + n * 8 + 2 * t4 + (e & 1);
+                if (x >= W) continue;
+                float v = acc[m][n][e] + (b ? b[oc] : 0.0f);
+                const size_t o = ((size_t)oc * H + y) * W + x;
+                if (S) v += __bfloat162float(S[o]);
+                if (relu) v = fmaxf(v, 0.0f);
+                Y[o] = __float2bfloat16(v);
+            }
+        }
     }
 }
 
@@ -350,13 +458,41 @@ static size_t carve_act(Carver &cv, int H, int W, Act *A) {
 
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256); }
 
+// One 3x3 convolution: the tensor-core kernel where the channel counts allow
+// it (impl WS_CONV_AUTO), or the one asked for.
+static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
+                   int W, int relu, int impl, cudaStream_t s) {
+    const bool mma_ok = cin % 16 == 0 && cout % 32 == 0;
+    if (impl == WS_CONV_MMA && !mma_ok) return TW_EINVAL;
+    if (impl != WS_CONV_SIMT && mma_ok) {
+        if (cout % 64 == 0) {
+            dim3 grid(ceil_div(W, TS), ceil_div(H, TS), cout / 64);
+            TW_LAUNCH(conv3x3_fwd_mma_kernel<64>, grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu);
+        } else {
+            dim3 grid(ceil_div(W, TS), ceil_div(H, TS), cout / 32);
+            TW_LAUNCH(conv3x3_fwd_mma_kernel<32>, grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu);
+        }
+        return TW_OK;
+    }
+    if (cout < 8) {
+        dim3 grid(ceil_div(W, TS), ceil_div(H, TS), cout);
+        TW_LAUNCH((conv3x3_fwd_kernel<1, CIB>), grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu);
+    } else if (cin <= 2) {
+        dim3 grid(ceil_div(W, TS), ceil_div(H, TS), ceil_div(cout, COB));
+        TW_LAUNCH((conv3x3_fwd_kernel<COB, 2>), grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu);
+    } else {
+        dim3 grid(ceil_div(W, TS), ceil_div(H, TS), ceil_div(cout, COB));
+        TW_LAUNCH((conv3x3_fwd_kernel<COB, CIB>), grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu);
+    }
+    return TW_OK;
+}
+
 static void conv_fwd(const bf16 *X, const float *params, int li, const bf16 *S, bf16 *Y, int H, int W, int relu,
                      cudaStream_t s, bool bias = true) {
     const ConvSpec &c = kConvs[li];
     const float *Wt = params + param_offset(li);
     const float *b = bias ? Wt + (size_t)c.cout * c.cin * 9 : nullptr;
-    dim3 grid(ceil_div(W, TS), ceil_div(H, TS), ceil_div(c.cout, COB));
-    TW_LAUNCH(conv3x3_fwd_kernel, grid, 256, 0, s, X, Wt, b, S, Y, c.cin, c.cout, H, W, relu);
+    conv3x3(X, Wt, b, S, Y, c.cin, c.cout, H, W, relu, WS_CONV_AUTO, s);
 }
 
 // The forward pass; every intermediate is kept for the backward pass.
@@ -399,10 +535,8 @@ static void conv_bwd(const bf16 *X, const float *P, float *G, int li, const bf16
     if (!dX) return;
     TW_LAUNCH(conv_transpose_weights_kernel, blocks_for((size_t)c.cin * c.cout * 9), 256, 0, s, Wt, wt, c.cin, c.cout);
     // dX = conv3x3(dY, W^T) with cin/cout swapped: a forward conv of the transposed layer
-    dim3 grid(ceil_div(W, TS), ceil_div(H, TS), ceil_div(c.cin, COB));
     bf16 *dst = accumulate ? tmp : dX;
-    TW_LAUNCH(conv3x3_fwd_kernel, grid, 256, 0, s, dY, wt, (const float *)nullptr, (const bf16 *)nullptr, dst, c.cout,
-              c.cin, H, W, 0);
+    conv3x3(dY, wt, nullptr, nullptr, dst, c.cout, c.cin, H, W, 0, WS_CONV_AUTO, s);
     if (accumulate)
         TW_LAUNCH(add_inplace_kernel, blocks_for((size_t)c.cin * H * W), 256, 0, s, dX, tmp, (size_t)c.cin * H * W);
 }
@@ -573,3 +707,15 @@ extern "C" int ws_unet_train_step(float *params, float *grads, float *adam_m, fl
     return TW_OK;
 }
 
+extern "C" int ws_conv3x3(const void *X, const float *Wt, const float *b, const void *S, void *Y, int cin, int cout,
+                          int H, int W, int relu, int impl, void *stream) {
+    using namespace tw::nn;
+    if (!X || !Wt || !Y || cin < 1 || cout < 1 || H < 1 || W < 1 || H > 65536 || W > 65536 ||
+        (impl != WS_CONV_AUTO && impl != WS_CONV_SIMT && impl != WS_CONV_MMA))
+        return TW_EINVAL;
+    int e = conv3x3((const bf16 *)X, Wt, b, (const bf16 *)S, (bf16 *)Y, cin, cout, H, W, relu ? 1 : 0, impl,
+                    (cudaStream_t)stream);
+    if (e) return e;
+    TW_CHECK_LAUNCH();
+    return TW_OK;
+}

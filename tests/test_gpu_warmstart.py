@@ -34,6 +34,45 @@ def _scene(seed, side):
     return sc, occ
 
 
+@pytest.mark.parametrize("cin,cout", [(32, 32), (32, 64), (64, 128), (128, 128), (128, 64), (64, 32), (16, 96)])
+@pytest.mark.parametrize("H,W", [(16, 16), (24, 40), (48, 72)])
+def test_conv3x3_tensor_core_matches_cuda_core_and_fp64(dev, cin, cout, H, W):
+    """The BF16 tensor-core convolution (mma.sync implicit GEMM) and the CUDA-core
+    direct convolution compute the same layer: against the FP64 convolution of the
+    same BF16-rounded inputs and weights, both stay within BF16 output rounding
+    (plus FP32 summation noise), and they differ from each other by at most one
+    BF16 ulp -- ragged tiles in x and y, bias, skip and ReLU included."""
+    g = torch.Generator(device="cpu").manual_seed(cin * 1000 + cout * 10 + H + W)
+    x = (torch.randn((cin, H, W), generator=g)).to(torch.bfloat16).to(dev)
+    w = (torch.randn((cout, cin, 3, 3), generator=g) / (3.0 * cin ** 0.5)).to(dev)
+    b = (0.1 * torch.randn((cout,), generator=g)).to(dev)
+    skip = torch.randn((cout, H, W), generator=g).to(torch.bfloat16).to(dev)
+    outs = {}
+    for impl in (tw.WS_CONV_SIMT, tw.WS_CONV_MMA, tw.WS_CONV_AUTO):
+        outs[impl] = tw.ws_conv3x3(x, w, b, skip, relu=True, impl=impl).float().cpu().numpy()
+    xr = x.float().cpu().numpy().astype(np.float64)
+    wr = w.to(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+    ref = nn.conv(xr, wr, b.cpu().numpy().astype(np.float64)) + skip.float().cpu().numpy()
+    ref = np.maximum(ref, 0.0)
+    scale = np.abs(ref) + 1e-2
+    for impl, y in outs.items():
+        assert np.all(np.abs(y - ref) <= 2.0 ** -7 * scale), (impl, np.abs(y - ref).max())
+    # one BF16 ulp apart, except where the FP32 sums cancel to near zero (and ReLU may cut either)
+    both = np.maximum(np.abs(outs[tw.WS_CONV_SIMT]), np.abs(outs[tw.WS_CONV_MMA]))
+    assert np.all(np.abs(outs[tw.WS_CONV_MMA] - outs[tw.WS_CONV_SIMT]) <= 2.0 ** -7 * (both + 1e-2))
+    assert np.array_equal(outs[tw.WS_CONV_AUTO], outs[tw.WS_CONV_MMA])
+
+
+def test_conv3x3_rejects_tensor_core_shapes_it_cannot_take(dev):
+    x = torch.zeros((8, 16, 16), dtype=torch.bfloat16, device=dev)
+    w = torch.zeros((32, 8, 3, 3), dtype=torch.float32, device=dev)
+    with pytest.raises(tw.TwError) as e:
+        tw.ws_conv3x3(x, w, impl=tw.WS_CONV_MMA)
+    assert e.value.status == tw.TW_EINVAL
+    # the automatic choice falls back to the CUDA-core kernel
+    assert tw.ws_conv3x3(x, w, impl=tw.WS_CONV_AUTO).shape == (32, 16, 16)
+
+
 def test_forward_and_gradients_match_fp64_reference(dev):
     net = tw.WarmStartNet(dev, seed=7)
     sc, occ = _scene(9100, 32)
