@@ -292,47 +292,43 @@ __global__ void relu_bwd_kernel(const bf16 *__restrict__ A, bf16 *__restrict__ d
         if (!(__bfloat162float(A[i]) > 0.0f)) dY[i] = __float2bfloat16(0.0f);
 }
 
+// Pooling and upsampling kernels: grid (ceil(width / 256), rows, channels) of
+// the tensor they write, so a thread finds its element without divisions.
+
 __global__ void pool2_fwd_kernel(const bf16 *__restrict__ X, bf16 *__restrict__ Y, int C, int H, int W) {
     const int h = H / 2, w = W / 2;
-    const size_t n = (size_t)C * h * w;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % w), y = (int)((i / w) % h), c = (int)(i / w / h);
-        const bf16 *p = X + ((size_t)c * H + 2 * y) * W + 2 * x;
-        const float v = (__bfloat162float(p[0]) + __bfloat162float(p[1])) +
-                        (__bfloat162float(p[W]) + __bfloat162float(p[W + 1]));
-        Y[i] = __float2bfloat16(0.25f * v);
-    }
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, c = blockIdx.z;
+    if (x >= w) return;
+    const bf16 *p = X + ((size_t)c * H + 2 * y) * W + 2 * x;
+    const float v = (__bfloat162float(p[0]) + __bfloat162float(p[1])) +
+                    (__bfloat162float(p[W]) + __bfloat162float(p[W + 1]));
+    Y[((size_t)c * h + y) * w + x] = __float2bfloat16(0.25f * v);
 }
 
 // gradient of the 2x2 average pool, accumulated into dX (dX += dY / 4 spread over the window)
 __global__ void pool2_bwd_kernel(const bf16 *__restrict__ dY, bf16 *__restrict__ dX, int C, int H, int W) {
-    const size_t n = (size_t)C * H * W;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % W), y = (int)((i / W) % H), c = (int)(i / W / H);
-        const float g = 0.25f * __bfloat162float(dY[((size_t)c * (H / 2) + y / 2) * (W / 2) + x / 2]);
-        dX[i] = __float2bfloat16(__bfloat162float(dX[i]) + g);
-    }
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, c = blockIdx.z;
+    if (x >= W) return;
+    const float g = 0.25f * __bfloat162float(dY[((size_t)c * (H / 2) + y / 2) * (W / 2) + x / 2]);
+    const size_t i = ((size_t)c * H + y) * W + x;
+    dX[i] = __float2bfloat16(__bfloat162float(dX[i]) + g);
 }
 
+// X [C][H/2][W/2] -> Y [C][H][W] (nearest)
 __global__ void up2_fwd_kernel(const bf16 *__restrict__ X, bf16 *__restrict__ Y, int C, int H, int W) {
-    // X [C][H/2][W/2] -> Y [C][H][W] (nearest)
-    const size_t n = (size_t)C * H * W;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % W), y = (int)((i / W) % H), c = (int)(i / W / H);
-        Y[i] = X[((size_t)c * (H / 2) + y / 2) * (W / 2) + x / 2];
-    }
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, c = blockIdx.z;
+    if (x >= W) return;
+    Y[((size_t)c * H + y) * W + x] = X[((size_t)c * (H / 2) + y / 2) * (W / 2) + x / 2];
 }
 
+// dX [C][H/2][W/2] = sum of the 4 children of dY [C][H][W]
 __global__ void up2_bwd_kernel(const bf16 *__restrict__ dY, bf16 *__restrict__ dX, int C, int H, int W) {
-    // dX [C][H/2][W/2] = sum of the 4 children of dY [C][H][W]
     const int h = H / 2, w = W / 2;
-    const size_t n = (size_t)C * h * w;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % w), y = (int)((i / w) % h), c = (int)(i / w / h);
-        const bf16 *p = dY + ((size_t)c * H + 2 * y) * W + 2 * x;
-        dX[i] = __float2bfloat16((__bfloat162float(p[0]) + __bfloat162float(p[1])) +
-                                 (__bfloat162float(p[W]) + __bfloat162float(p[W + 1])));
-    }
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, c = blockIdx.z;
+    if (x >= w) return;
+    const bf16 *p = dY + ((size_t)c * H + 2 * y) * W + 2 * x;
+    dX[((size_t)c * h + y) * w + x] = __float2bfloat16((__bfloat162float(p[0]) + __bfloat162float(p[1])) +
+                                                       (__bfloat162float(p[W]) + __bfloat162float(p[W + 1])));
 }
 
 __global__ void add_inplace_kernel(bf16 *__restrict__ A, const bf16 *__restrict__ B, size_t n) {
@@ -503,7 +499,7 @@ static void forward(const float *P, Act &A, int H, int W, cudaStream_t s) {
     conv_fwd(A.e[0][0], P, 1, nullptr, A.e[0][1], H, W, 1, s);
     for (int l = 1; l < 4; l++) {
         const int h = H >> l, w = W >> l;
-        TW_LAUNCH(pool2_fwd_kernel, blocks_for(ch[l - 1] * lvl_px(H, W, l)), 256, 0, s, A.e[l - 1][1], A.p[l - 1],
+        TW_LAUNCH(pool2_fwd_kernel, dim3(ceil_div(w, 256), h, ch[l - 1]), 256, 0, s, A.e[l - 1][1], A.p[l - 1],
                   ch[l - 1], H >> (l - 1), W >> (l - 1));
         conv_fwd(A.p[l - 1], P, 2 * l, nullptr, A.e[l][0], h, w, 1, s);
         conv_fwd(A.e[l][0], P, 2 * l + 1, nullptr, A.e[l][1], h, w, 1, s);
@@ -513,7 +509,7 @@ static void forward(const float *P, Act &A, int H, int W, cudaStream_t s) {
     const int pc[3] = {128, 128, 64};
     for (int j = 0; j < 3; j++) {
         const int l = 2 - j, h = H >> l, w = W >> l;
-        TW_LAUNCH(up2_fwd_kernel, blocks_for(pc[j] * lvl_px(H, W, l)), 256, 0, s, prev, A.u[j], pc[j], h, w);
+        TW_LAUNCH(up2_fwd_kernel, dim3(ceil_div(w, 256), h, pc[j]), 256, 0, s, prev, A.u[j], pc[j], h, w);
         conv_fwd(A.u[j], P, 8 + 2 * j, A.e[l][1], A.d[j][0], h, w, 1, s);
         conv_fwd(A.d[j][0], P, 9 + 2 * j, nullptr, A.d[j][1], h, w, 1, s);
         prev = A.d[j][1];
@@ -562,7 +558,7 @@ static void backward(const float *P, float *G, Act &A, int H, int W, cudaStream_
         cudaMemcpyAsync(dskip[j], dnext, sizeof(bf16) * dc[j] * lvl_px(H, W, l), cudaMemcpyDeviceToDevice, s);
         conv_bwd(A.u[j], P, G, 8 + 2 * j, dnext, dcur, tmp, h, w, A.wt, 0, s);      // -> grad of u[j]
         // u[j] = up2(prev): gradient to prev (level l + 1)
-        TW_LAUNCH(up2_bwd_kernel, blocks_for(pc[j] * lvl_px(H, W, l + 1)), 256, 0, s, dcur, dnext, pc[j], h, w);
+        TW_LAUNCH(up2_bwd_kernel, dim3(ceil_div(w / 2, 256), h / 2, pc[j]), 256, 0, s, dcur, dnext, pc[j], h, w);
         bf16 *t = dcur; dcur = dnext; dnext = t;   // dcur: gradient of the previous decoder output
     }
     // dcur: gradient of e[3][1]; walk the encoder down, adding the skip gradients
@@ -584,8 +580,8 @@ static void backward(const float *P, float *G, Act &A, int H, int W, cudaStream_
             conv_bwd(xin, P, G, 2 * l, dnext, dcur, tmp, h, w, A.wt, 0, s);          // grad of p[l-1]
             // p[l-1] = pool2(e[l-1][1]): spread into a zeroed gradient of e[l-1][1]
             cudaMemsetAsync(dnext, 0, sizeof(bf16) * ch[l - 1] * lvl_px(H, W, l - 1), s);
-            TW_LAUNCH(pool2_bwd_kernel, blocks_for(ch[l - 1] * lvl_px(H, W, l - 1)), 256, 0, s, dcur, dnext,
-                      ch[l - 1], H >> (l - 1), W >> (l - 1));
+            TW_LAUNCH(pool2_bwd_kernel, dim3(ceil_div(W >> (l - 1), 256), H >> (l - 1), ch[l - 1]), 256, 0, s, dcur,
+                      dnext, ch[l - 1], H >> (l - 1), W >> (l - 1));
             bf16 *t = dcur; dcur = dnext; dnext = t;
         }
     }
