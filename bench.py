@@ -182,6 +182,32 @@ def scene_seed(rank: int) -> int:
     return 1002 + 100 * rank
 
 
+GOLDEN_FIELD = os.path.join(ROOT, "tests", "golden", "static2048_field.json")
+
+
+def field_accuracy(u, occ, sc, st):
+    """The solved field against the FP64 reference u* stored for this scene
+    (tests/golden/make_static2048_field.py: CG to 1e-12, exit time): the
+    a-posteriori bound tau_max * r_inf and the largest error at the stored
+    sample cells.  Outside the timed region."""
+    import json as _json
+    if not os.path.exists(GOLDEN_FIELD):
+        return {"note": "no stored reference"}
+    ref = _json.load(open(GOLDEN_FIELD))
+    occ_h = occ.cpu().numpy()
+    if (ref["nx"], ref["ny"]) != (sc.nx, sc.ny) or \
+            hashlib.sha256(np.ascontiguousarray(occ_h).tobytes()).hexdigest() != ref["occupancy_sha256"]:
+        return {"note": "stored reference belongs to another scene"}
+    cells = np.asarray(ref["cells"], dtype=np.int64)
+    ustar = np.asarray([float(v) for v in ref["u_star"]])
+    got = u[cells[:, 1], cells[:, 0]].double().cpu().numpy()
+    err = np.abs(got - ustar)
+    return {"reference": ref["reference"], "tau_max": ref["tau_max"], "resid_inf": st["resid_inf"],
+            "error_bound": ref["tau_max"] * st["resid_inf"], "sampled_cells": int(len(cells)),
+            "max_abs_error_sampled": float(err.max()), "mean_abs_error_sampled": float(err.mean()),
+            "u_start": float(got[0]), "u_star_start": float(ustar[0])}
+
+
 def max_over_ranks(x: float, dist, device=None) -> float:
     """Max of a per-rank scalar (the elapsed time) over all ranks; identity without a process group."""
     if dist is None:
@@ -327,6 +353,9 @@ def run_twgrid(args, rank, world, dist):
                           "further steps of the same workload run with the host-driven loop (HP_TIMING); "
                           "the timed steps above use the graph-driven loop"}
 
+    # ---- accuracy of the solved field against the stored FP64 reference of this scene
+    accuracy = field_accuracy(u, occ, sc, timed_log[-1][0]) if rank == 0 else None
+
     # ---- end to end through the C ABI with host buffers
     stats_log.clear()
     barrier()
@@ -413,7 +442,7 @@ def run_twgrid(args, rank, world, dist):
            "resid_inf_max": max(resid) if resid else None, "relax_status": sorted(set(status)),
            "path_status": sorted(set(path_status)), "path_len": [n for _, _, n in stats_log][:1],
            "omega": stats_log[0][0]["omega"] if stats_log else None,
-           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms, "batched": batched,
+           "roofline": roofline, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms, "batched": batched,
            "dynamic": dynamic, "learned_warm_start": learned,
            "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": min(step_ms), "max": max(step_ms), "host_p50": float(np.percentile(host_ms, 50))},

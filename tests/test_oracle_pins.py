@@ -527,3 +527,28 @@ def test_nn_oracle_conv_delta_reproduces_kernel():
     for ky in range(3):
         for kx in range(3):
             assert np.allclose(Y[:, 3 + 1 - ky, 3 + 1 - kx], Wt[:, 1, ky, kx] + b)
+
+
+def test_stored_static2048_reference_matches_the_scene():
+    """The stored FP64 reference of the measured workload (written by
+    tests/golden/make_static2048_field.py from the oracle) belongs to the scene
+    the generator makes today, and is self-consistent: the sampled u* lie in
+    (0, 1], the start cell is among them, and tau_max is at least the exit time
+    of a free cell next to the goal (1) and below the square of the grid side.
+    The sampled u* obey the maximum principle up to the reference's own error
+    bound tau_max * r* (most of this cluttered field is below 1e-8: the
+    potential decays exponentially away from the goal)."""
+    import hashlib
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "static2048_field.json")))
+    sc = scenes.static2048()
+    occ, _, _ = oracle.build_grid(sc)
+    assert hashlib.sha256(np.ascontiguousarray(occ).tobytes()).hexdigest() == ref["occupancy_sha256"]
+    assert (ref["nx"], ref["ny"]) == (sc.nx, sc.ny) and tuple(ref["goal"]) == tuple(sc.goal)
+    u = np.array([float(v) for v in ref["u_star"]])
+    noise = ref["tau_max"] * ref["reference_resid_inf"]
+    assert np.all((u >= -noise) & (u <= 1.0)) and ref["cells"][0] == list(sc.start)
+    cells = np.asarray(ref["cells"])
+    assert np.all(occ[cells[:, 1], cells[:, 0]] == 0)
+    assert 1.0 <= ref["tau_max"] < float(sc.nx) ** 2 and ref["reference_resid_inf"] <= 1e-12
