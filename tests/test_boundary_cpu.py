@@ -151,6 +151,24 @@ def test_relax_rejects_bad_params_and_goal_on_host(lib):
     assert call(tw.Params(), gx=64, gy=30) == tw.TW_EGOAL_BLOCKED    # out of range
 
 
+def test_warm_start_entry_points_reject_bad_input_on_host(lib):
+    """The network's entry points validate sizes and choices before any GPU work."""
+    P = ctypes.c_void_p(256)
+    # ws_conv3x3: unknown implementation, non-positive sizes, missing pointers
+    assert lib.ws_conv3x3(P, P, None, None, P, 32, 32, 16, 16, 1, 7, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 0, 32, 16, 16, 1, tw.WS_CONV_AUTO, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 32, 32, 0, 16, 1, tw.WS_CONV_AUTO, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(None, P, None, None, P, 32, 32, 16, 16, 1, tw.WS_CONV_AUTO, None) == tw.TW_EINVAL
+    # the tensor-core form needs cin % 16 == 0 and cout % 32 == 0
+    assert lib.ws_conv3x3(P, P, None, None, P, 8, 32, 16, 16, 1, tw.WS_CONV_MMA, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 32, 16, 16, 16, 1, tw.WS_CONV_MMA, None) == tw.TW_EINVAL
+    # the network: H and W multiples of 8, goal inside, workspace present
+    assert lib.ws_unet_workspace_size(64, 64) > lib.ws_unet_workspace_size(16, 16) > 0
+    assert lib.ws_unet_forward(P, P, 60, 64, 1, 1, None, None, P, 1 << 30, None) == tw.TW_EINVAL
+    assert lib.ws_unet_forward(P, P, 64, 64, 64, 1, None, None, P, 1 << 30, None) == tw.TW_EINVAL
+    assert lib.ws_unet_forward(P, P, 64, 64, 1, 1, None, None, None, 1 << 30, None) == tw.TW_EWORKSPACE
+
+
 def test_product_path_has_no_cpu_fallback():
     """The binding imports no oracle code and fails loudly without a GPU."""
     src = open(os.path.join(ROOT, "paper_1903_07441_gb300", "__init__.py")).read()
