@@ -306,6 +306,20 @@ int ws_make_target(const float *u, size_t n, float *target, void *stream);
  * 0 on occupied cells, 1 at the goal.  pred_out (nullable): p itself. */
 int ws_unet_forward(const float *params, const uint8_t *occ, int H, int W, int gx, int gy, float *u_out,
                     float *pred_out, void *workspace, size_t workspace_bytes, void *stream);
+/* The warm start for hp_relax (HP_WARM_START) from the network run at a coarser
+ * resolution: stride s in {1, 2, 4}; H/s and W/s must satisfy the network's
+ * size rule.  The occupancy is max-pooled by s (a coarse cell is occupied when
+ * any of its cells is, except the one holding the goal), the network predicts
+ * p on the H/s x W/s grid, and u_out (device FP32 [H][W]) receives
+ * exp(min(30 p, 0)) with p bilinearly interpolated at every cell centre, 0 on
+ * occupied cells and 1 at the goal.  s = 1 equals ws_unet_forward's u_out.
+ * The network is fully convolutional and trained at one size; a coarse run
+ * costs about s^2 times less and the relaxation restores the detail.
+ * workspace: ws_unet_warm_start_workspace_size(H, W, s) bytes.
+ * Errors: TW_EINVAL, TW_EWORKSPACE, TW_ECUDA. */
+size_t ws_unet_warm_start_workspace_size(int H, int W, int stride);
+int ws_unet_warm_start(const float *params, const uint8_t *occ, int H, int W, int gx, int gy, int stride,
+                       float *u_out, void *workspace, size_t workspace_bytes, void *stream);
 /* One training step on one field: masked mean-squared error between p and
  * target over free cells (occ == 0, not the goal), gradients into `grads`,
  * then Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected with `step` >= 1,

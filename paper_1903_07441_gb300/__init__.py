@@ -37,7 +37,8 @@ EXPORTS = (
     "hp_relax_batched_workspace_size", "hp_relax_batched",
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
     "kf_update", "kf_init", "ws_unet_param_count", "ws_unet_workspace_size", "ws_unet_init", "ws_make_target",
-    "ws_unet_forward", "ws_unet_train_step", "ws_conv3x3", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
+    "ws_unet_forward", "ws_unet_train_step", "ws_unet_warm_start_workspace_size", "ws_unet_warm_start",
+    "ws_conv3x3", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
 )
 
 
@@ -167,6 +168,10 @@ def load() -> ctypes.CDLL:
     lib.ws_unet_forward.restype = I
     lib.ws_unet_train_step.argtypes = [P, P, P, P, I, ctypes.c_float, P, I, I, I, I, P, P, P, Z, P]
     lib.ws_unet_train_step.restype = I
+    lib.ws_unet_warm_start_workspace_size.argtypes = [I, I, I]
+    lib.ws_unet_warm_start_workspace_size.restype = Z
+    lib.ws_unet_warm_start.argtypes = [P, P, I, I, I, I, I, P, P, Z, P]
+    lib.ws_unet_warm_start.restype = I
     lib.ws_conv3x3.argtypes = [P, P, P, P, P, I, I, I, I, I, I, P]
     lib.ws_conv3x3.restype = I
     lib.tw_status_string.argtypes = [I]
@@ -448,6 +453,20 @@ class WarmStartNet:
                                                           int(goal[1]), _ptr(u) if u is not None else None, _ptr(p),
                                                           _ptr(ws), ws.numel(), _stream(occ.device)))
         return u, p
+
+    def warm_start(self, occ, goal, stride=1, u=None):
+        """The warm start u for hp_relax from the network run at 1/stride of the
+        resolution (stride 1, 2 or 4), upsampled to the grid of `occ`."""
+        torch = _torch()
+        lib = load()
+        H, W = occ.shape
+        if u is None:
+            u = torch.empty((H, W), dtype=torch.float32, device=occ.device)
+        ws = workspace(lib.ws_unet_warm_start_workspace_size(int(H), int(W), int(stride)), self.device, "unet")
+        _check("ws_unet_warm_start", lib.ws_unet_warm_start(_ptr(self.params), _ptr(occ), H, W, int(goal[0]),
+                                                            int(goal[1]), int(stride), _ptr(u), _ptr(ws),
+                                                            ws.numel(), _stream(occ.device)))
+        return u
 
     def gradients(self, occ, goal, target):
         """Loss and gradients for one field (no parameter update)."""

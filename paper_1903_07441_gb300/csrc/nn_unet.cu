@@ -402,6 +402,41 @@ __global__ void to_u_kernel(const bf16 *__restrict__ P, const uint8_t *__restric
     }
 }
 
+// Coarse input for the warm start at stride s: a coarse cell is occupied when
+// any of its s x s cells is, except the cell holding the goal, which stays
+// free so that the network sees a reachable goal.
+__global__ void occ_pool_kernel(const uint8_t *__restrict__ occ, int W, int s, int gxc, int gyc,
+                                uint8_t *__restrict__ oc, int wc) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= wc) return;
+    uint8_t v = 0;
+    for (int dy = 0; dy < s; dy++)
+        for (int dx = 0; dx < s; dx++) v |= occ[(size_t)(y * s + dy) * W + x * s + dx];
+    oc[(size_t)y * wc + x] = (x == gxc && y == gyc) ? 0 : (v != 0);
+}
+
+// Full-resolution warm start from the coarse prediction: p bilinearly
+// interpolated at each cell centre (cell-centred grids, clamped at the edges),
+// u = exp(min(30 p, 0)), 0 on occupied cells, 1 at the goal.
+__global__ void upsample_to_u_kernel(const bf16 *__restrict__ P, int hc, int wc, int s,
+                                     const uint8_t *__restrict__ occ, int W, int gx, int gy,
+                                     float *__restrict__ u) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W) return;
+    const size_t i = (size_t)y * W + x;
+    if (occ[i] != 0) { u[i] = 0.0f; return; }
+    if (x == gx && y == gy) { u[i] = 1.0f; return; }
+    const float fx = fminf(fmaxf((x + 0.5f) / s - 0.5f, 0.0f), (float)(wc - 1));
+    const float fy = fminf(fmaxf((y + 0.5f) / s - 0.5f, 0.0f), (float)(hc - 1));
+    const int x0 = (int)fx, y0 = (int)fy;
+    const int x1 = x0 + 1 < wc ? x0 + 1 : x0, y1 = y0 + 1 < hc ? y0 + 1 : y0;
+    const float ax = fx - x0, ay = fy - y0;
+    const float p00 = __bfloat162float(P[(size_t)y0 * wc + x0]), p01 = __bfloat162float(P[(size_t)y0 * wc + x1]);
+    const float p10 = __bfloat162float(P[(size_t)y1 * wc + x0]), p11 = __bfloat162float(P[(size_t)y1 * wc + x1]);
+    const float p = (1.0f - ay) * ((1.0f - ax) * p00 + ax * p01) + ay * ((1.0f - ax) * p10 + ax * p11);
+    u[i] = expf(fminf(30.0f * p, 0.0f));
+}
+
 // ---- host-side network -------------------------------------------------------------
 
 struct Act {   // activation buffers per level (bf16 [C][h][w])
@@ -618,6 +653,51 @@ extern "C" size_t ws_unet_workspace_size(int H, int W) {
     if (!valid_hw(H, W)) return 0;
     Carver cv;
     return carve_act(cv, H, W, nullptr);
+}
+
+static bool valid_stride(int H, int W, int s) {
+    return (s == 1 || s == 2 || s == 4) && H % s == 0 && W % s == 0 && valid_hw(H / s, W / s) && H <= 8192 &&
+           W <= 8192;
+}
+
+// the network's buffers at the coarse size, then the coarse occupancy
+static size_t carve_warm(Carver &cv, int H, int W, int s, Act *A, uint8_t **oc) {
+    carve_act(cv, H / s, W / s, A);
+    uint8_t *o = cv.take<uint8_t>((size_t)(H / s) * (W / s));
+    if (oc) *oc = o;
+    return cv.need;
+}
+
+extern "C" size_t ws_unet_warm_start_workspace_size(int H, int W, int stride) {
+    if (!valid_stride(H, W, stride)) return 0;
+    Carver cv;
+    return carve_warm(cv, H, W, stride, nullptr, nullptr);
+}
+
+extern "C" int ws_unet_warm_start(const float *params, const uint8_t *occ, int H, int W, int gx, int gy, int stride,
+                                  float *u_out, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!params || !occ || !u_out || !valid_stride(H, W, stride) || gx < 0 || gy < 0 || gx >= W || gy >= H)
+        return TW_EINVAL;
+    if (!workspace || !ws_aligned(workspace)) return TW_EWORKSPACE;
+    Carver cv(workspace, workspace_bytes);
+    Act A;
+    uint8_t *oc = nullptr;
+    carve_warm(cv, H, W, stride, &A, &oc);
+    if (!cv.ok()) return TW_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int hc = H / stride, wc = W / stride, gxc = gx / stride, gyc = gy / stride;
+    const uint8_t *oin = occ;
+    if (stride > 1) {
+        TW_LAUNCH(occ_pool_kernel, dim3(ceil_div(wc, 256), hc), 256, 0, s, occ, W, stride, gxc, gyc, oc, wc);
+        oin = oc;
+    }
+    const size_t nc = (size_t)hc * wc;
+    TW_LAUNCH(features_kernel, blocks_for(nc), 256, 0, s, oin, hc, wc, gxc, gyc, A.in);
+    forward(params, A, hc, wc, s);
+    TW_LAUNCH(upsample_to_u_kernel, dim3(ceil_div(W, 256), H), 256, 0, s, A.out, hc, wc, stride, occ, W, gx, gy,
+              u_out);
+    TW_CHECK_LAUNCH();
+    return TW_OK;
 }
 
 extern "C" int ws_unet_init(float *params, unsigned long long seed, void *stream) {

@@ -125,11 +125,12 @@ def test_training_reduces_loss_and_warm_start_saves_sweeps(dev):
     last = np.mean([net.gradients(o, sc.goal, t)[0] for (sc, _, o, _), t in zip(train[:8], targets[:8])])
     assert last < 0.2 * first, (first, last)
     # held-out scenes: sweeps to 1e-6 from the network's field vs the cold start
-    cold, warm = [], []
+    cold, warm, coarse = [], [], []
     for sc, occ, occ_t, _ in _fields(dev, range(9300, 9306), side):
         grid = tw.make_grid(side, side, sc.cell)
         _, s0 = tw.hp_relax(grid, occ_t, sc.goal, params=tw.Params(tol=1e-6))
         u0, _ = net.forward(occ_t, sc.goal)
+        u0_h = u0.cpu().numpy()   # hp_relax overwrites its field argument
         u1, s1 = tw.hp_relax(grid, occ_t, sc.goal, field=u0, params=tw.Params(tol=1e-6, flags=tw.HP_WARM_START))
         assert s1["status"] == tw.TW_OK
         ustar, fixed = oracle.solve_field(occ, sc.goal, tol=1e-13)
@@ -137,4 +138,14 @@ def test_training_reduces_loss_and_warm_start_saves_sweeps(dev):
         assert np.abs(u1.cpu().numpy() - ustar).max() <= tau * s1["resid_inf"] * 1.001 + 1e-7
         cold.append(s0["sweeps"])
         warm.append(s1["sweeps"])
+        # the warm start at stride 1 is the forward pass's own u; at stride 2 (the network on a
+        # max-pooled 64 x 64 grid, its prediction interpolated back) it is a valid start too
+        assert np.array_equal(net.warm_start(occ_t, sc.goal, 1).cpu().numpy(), u0_h)
+        u2 = net.warm_start(occ_t, sc.goal, 2)
+        h = u2.cpu().numpy()
+        assert np.all((h >= 0.0) & (h <= 1.0)) and np.all(h[occ != 0] == 0.0) and h[sc.goal[1], sc.goal[0]] == 1.0
+        _, s2 = tw.hp_relax(grid, occ_t, sc.goal, field=u2, params=tw.Params(tol=1e-6, flags=tw.HP_WARM_START))
+        assert s2["status"] == tw.TW_OK
+        coarse.append(s2["sweeps"])
     assert np.mean(warm) < np.mean(cold), (cold, warm)
+    assert np.mean(coarse) < np.mean(cold), (cold, coarse)
