@@ -53,6 +53,7 @@ static size_t total_params() { return param_offset(kNumConvs); }
 // ---- kernels ----------------------------------------------------------------------
 
 constexpr int TS = 16;   // pixel tile side
+constexpr size_t kSplitKCap = (size_t)1 << 21;   // floats of split-K partial sums (8 MB of workspace)
 constexpr int COB = 16;  // output channels per CTA (CUDA-core kernels)
 constexpr int CIB = 8;   // input channels per staged chunk
 
@@ -142,17 +143,24 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Split K: with splits > 1, blockIdx.z = channel block + (cout / NB) x split,
+// each split takes its share of the 16-channel chunks and writes FP32 partial
+// sums to part[split][cout][H][W] (no bias, skip or activation), which
+// splitk_finalize_kernel adds up in split order.
 template <int NB>
 __global__ void __launch_bounds__(256) conv3x3_fwd_mma_kernel(const bf16 *__restrict__ X, const float *__restrict__ Wt,
                                                               const float *__restrict__ b, const bf16 *__restrict__ S,
                                                               bf16 *__restrict__ Y, int cin, int cout, int H, int W,
-                                                              int relu) {
+                                                              int relu, int splits, float *__restrict__ part) {
     constexpr int NT = NB / 8;
     __shared__ __align__(16) bf16 xs[(TS + 2) * (TS + 2) * kTcStride];
     __shared__ __align__(16) bf16 ws[9 * NB * kTcStride];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t4 = lane & 3;
-    const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS, co0 = blockIdx.z * NB;
+    const int nzb = cout / NB, sp = blockIdx.z / nzb;
+    const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS, co0 = (blockIdx.z % nzb) * NB;
+    const int chunks = cin / 16, per = (chunks + splits - 1) / splits;
+    const int c_begin = sp * per * 16, c_end = min(chunks, (sp + 1) * per) * 16;
     float acc[2][NT][4];
 #pragma unroll
     for (int m = 0; m < 2; m++)
@@ -161,7 +169,7 @@ __global__ void __launch_bounds__(256) conv3x3_fwd_mma_kernel(const bf16 *__rest
 #pragma unroll
             for (int e = 0; e < 4; e++) acc[m][n][e] = 0.0f;
 
-    for (int ci0 = 0; ci0 < cin; ci0 += 16) {
+    for (int ci0 = c_begin; ci0 < c_end; ci0 += 16) {
         __syncthreads();
         // input tile, channel-last: xs[(yy * 18 + xx) * 24 + c]
         for (int i = threadIdx.x; i < 16 * (TS + 2) * (TS + 2); i += 256) {
@@ -214,14 +222,33 @@ __global__ void __launch_bounds__(256) conv3x3_fwd_mma_kernel(const bf16 *__rest
                 const int x = x0 + g + (e >= 2 ? 8 : 0);
                 const int oc = co0 + n * 8 + 2 * t4 + (e & 1);
                 if (x >= W) continue;
-                float v = acc[m][n][e] + (b ? b[oc] : 0.0f);
                 const size_t o = ((size_t)oc * H + y) * W + x;
+                if (splits > 1) {
+                    part[(size_t)sp * cout * H * W + o] = acc[m][n][e];
+                    continue;
+                }
+                float v = acc[m][n][e] + (b ? b[oc] : 0.0f);
                 if (S) v += __bfloat162float(S[o]);
                 if (relu) v = fmaxf(v, 0.0f);
                 Y[o] = __float2bfloat16(v);
             }
         }
     }
+}
+
+// Y = act(sum over splits of part + b + S), the splits added in index order.
+__global__ void splitk_finalize_kernel(const float *__restrict__ part, int splits, const float *__restrict__ b,
+                                       const bf16 *__restrict__ S, bf16 *__restrict__ Y, int cout, int H, int W,
+                                       int relu) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, oc = blockIdx.z;
+    if (x >= W) return;
+    const size_t o = ((size_t)oc * H + y) * W + x, plane = (size_t)cout * H * W;
+    float v = 0.0f;
+    for (int sp = 0; sp < splits; sp++) v += part[sp * plane + o];
+    v += b ? b[oc] : 0.0f;
+    if (S) v += __bfloat162float(S[o]);
+    if (relu) v = fmaxf(v, 0.0f);
+    Y[o] = __float2bfloat16(v);
 }
 
 // weight transform for the data gradient: Wt'[ci][co][8 - k] = Wt[co][ci][k]
@@ -450,6 +477,7 @@ struct Act {   // activation buffers per level (bf16 [C][h][w])
     bf16 *sk[3];                       // gradients into the skip sources e[2][1], e[1][1], e[0][1]
     float *target;                     // [H][W] training target (log u / 30)
     float *wt;                         // transposed weights scratch
+    float *kpart;                      // split-K partial sums (kSplitKCap floats)
     float *loss;
 };
 
@@ -482,6 +510,7 @@ static size_t carve_act(Carver &cv, int H, int W, Act *A) {
     a.sk[2] = cv.take<bf16>(32 * lvl_px(H, W, 0));
     a.target = cv.take<float>(lvl_px(H, W, 0));
     a.wt = cv.take<float>(128 * 128 * 9);
+    a.kpart = cv.take<float>(kSplitKCap);
     a.loss = cv.take<float>(64);
     if (A) *A = a;
     return cv.need;
@@ -489,20 +518,42 @@ static size_t carve_act(Carver &cv, int H, int W, Act *A) {
 
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256); }
 
+// Split-K factor of a tensor-core convolution: enough CTAs for two per SM of a
+// 152-SM GPU when the pixel tiles alone are too few, at most one chunk of 16
+// input channels per split, and at most cap_floats of FP32 partials.
+static int splitk_plan(int cin, int cout, int H, int W, size_t cap_floats) {
+    const int nb = cout % 64 == 0 ? 64 : 32;
+    const long base = (long)ceil_div(W, TS) * ceil_div(H, TS) * (cout / nb);
+    if (base >= 152) return 1;
+    const int chunks = cin / 16;
+    int sp = (int)((304 + base - 1) / base);
+    if (sp > chunks) sp = chunks;
+    while (sp > 1 && (size_t)sp * cout * H * W > cap_floats) sp--;
+    if (sp < 1) return 1;
+    const int per = (chunks + sp - 1) / sp;   // no empty split
+    return (chunks + per - 1) / per;
+}
+
 // One 3x3 convolution: the tensor-core kernel where the channel counts allow
-// it (impl WS_CONV_AUTO), or the one asked for.
+// it (impl WS_CONV_AUTO), or the one asked for.  part (nullable): scratch for
+// split-K partial sums, part_floats long.
 static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
-                   int W, int relu, int impl, cudaStream_t s) {
+                   int W, int relu, int impl, cudaStream_t s, float *part = nullptr, size_t part_floats = 0) {
     const bool mma_ok = cin % 16 == 0 && cout % 32 == 0;
     if (impl == WS_CONV_MMA && !mma_ok) return TW_EINVAL;
     if (impl != WS_CONV_SIMT && mma_ok) {
+        const int sp = part ? splitk_plan(cin, cout, H, W, part_floats) : 1;
+        float *pp = sp > 1 ? part : nullptr;
         if (cout % 64 == 0) {
-            dim3 grid(ceil_div(W, TS), ceil_div(H, TS), cout / 64);
-            TW_LAUNCH(conv3x3_fwd_mma_kernel<64>, grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu);
+            dim3 grid(ceil_div(W, TS), ceil_div(H, TS), cout / 64 * sp);
+            TW_LAUNCH(conv3x3_fwd_mma_kernel<64>, grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu, sp, pp);
         } else {
-            dim3 grid(ceil_div(W, TS), ceil_div(H, TS), cout / 32);
-            TW_LAUNCH(conv3x3_fwd_mma_kernel<32>, grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu);
+            dim3 grid(ceil_div(W, TS), ceil_div(H, TS), cout / 32 * sp);
+            TW_LAUNCH(conv3x3_fwd_mma_kernel<32>, grid, 256, 0, s, X, Wt, b, S, Y, cin, cout, H, W, relu, sp, pp);
         }
+        if (sp > 1)
+            TW_LAUNCH(splitk_finalize_kernel, dim3(ceil_div(W, 256), H, cout), 256, 0, s, part, sp, b, S, Y, cout, H,
+                      W, relu);
         return TW_OK;
     }
     if (cout < 8) {
@@ -519,25 +570,25 @@ static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S
 }
 
 static void conv_fwd(const bf16 *X, const float *params, int li, const bf16 *S, bf16 *Y, int H, int W, int relu,
-                     cudaStream_t s, bool bias = true) {
+                     float *kpart, cudaStream_t s, bool bias = true) {
     const ConvSpec &c = kConvs[li];
     const float *Wt = params + param_offset(li);
     const float *b = bias ? Wt + (size_t)c.cout * c.cin * 9 : nullptr;
-    conv3x3(X, Wt, b, S, Y, c.cin, c.cout, H, W, relu, WS_CONV_AUTO, s);
+    conv3x3(X, Wt, b, S, Y, c.cin, c.cout, H, W, relu, WS_CONV_AUTO, s, kpart, kSplitKCap);
 }
 
 // The forward pass; every intermediate is kept for the backward pass.
 static void forward(const float *P, Act &A, int H, int W, cudaStream_t s) {
     const int ch[4] = {32, 64, 128, 128};
     // encoder
-    conv_fwd(A.in, P, 0, nullptr, A.e[0][0], H, W, 1, s);
-    conv_fwd(A.e[0][0], P, 1, nullptr, A.e[0][1], H, W, 1, s);
+    conv_fwd(A.in, P, 0, nullptr, A.e[0][0], H, W, 1, A.kpart, s);
+    conv_fwd(A.e[0][0], P, 1, nullptr, A.e[0][1], H, W, 1, A.kpart, s);
     for (int l = 1; l < 4; l++) {
         const int h = H >> l, w = W >> l;
         TW_LAUNCH(pool2_fwd_kernel, dim3(ceil_div(w, 256), h, ch[l - 1]), 256, 0, s, A.e[l - 1][1], A.p[l - 1],
                   ch[l - 1], H >> (l - 1), W >> (l - 1));
-        conv_fwd(A.p[l - 1], P, 2 * l, nullptr, A.e[l][0], h, w, 1, s);
-        conv_fwd(A.e[l][0], P, 2 * l + 1, nullptr, A.e[l][1], h, w, 1, s);
+        conv_fwd(A.p[l - 1], P, 2 * l, nullptr, A.e[l][0], h, w, 1, A.kpart, s);
+        conv_fwd(A.e[l][0], P, 2 * l + 1, nullptr, A.e[l][1], h, w, 1, A.kpart, s);
     }
     // decoder: level 2, 1, 0
     const bf16 *prev = A.e[3][1];
@@ -545,17 +596,17 @@ static void forward(const float *P, Act &A, int H, int W, cudaStream_t s) {
     for (int j = 0; j < 3; j++) {
         const int l = 2 - j, h = H >> l, w = W >> l;
         TW_LAUNCH(up2_fwd_kernel, dim3(ceil_div(w, 256), h, pc[j]), 256, 0, s, prev, A.u[j], pc[j], h, w);
-        conv_fwd(A.u[j], P, 8 + 2 * j, A.e[l][1], A.d[j][0], h, w, 1, s);
-        conv_fwd(A.d[j][0], P, 9 + 2 * j, nullptr, A.d[j][1], h, w, 1, s);
+        conv_fwd(A.u[j], P, 8 + 2 * j, A.e[l][1], A.d[j][0], h, w, 1, A.kpart, s);
+        conv_fwd(A.d[j][0], P, 9 + 2 * j, nullptr, A.d[j][1], h, w, 1, A.kpart, s);
         prev = A.d[j][1];
     }
-    conv_fwd(A.d[2][1], P, 14, nullptr, A.out, H, W, 0, s);
+    conv_fwd(A.d[2][1], P, 14, nullptr, A.out, H, W, 0, A.kpart, s);
 }
 
 // Gradient through one conv layer: dY (its output gradient, ReLU already applied)
 // -> dX (overwritten, or accumulated when accumulate != 0) and dW/db (accumulated).
 static void conv_bwd(const bf16 *X, const float *P, float *G, int li, const bf16 *dY, bf16 *dX, bf16 *tmp, int H,
-                     int W, float *wt, int accumulate, cudaStream_t s) {
+                     int W, float *wt, float *kpart, int accumulate, cudaStream_t s) {
     const ConvSpec &c = kConvs[li];
     const float *Wt = P + param_offset(li);
     float *dW = G + param_offset(li);
@@ -567,7 +618,7 @@ static void conv_bwd(const bf16 *X, const float *P, float *G, int li, const bf16
     TW_LAUNCH(conv_transpose_weights_kernel, blocks_for((size_t)c.cin * c.cout * 9), 256, 0, s, Wt, wt, c.cin, c.cout);
     // dX = conv3x3(dY, W^T) with cin/cout swapped: a forward conv of the transposed layer
     bf16 *dst = accumulate ? tmp : dX;
-    conv3x3(dY, wt, nullptr, nullptr, dst, c.cout, c.cin, H, W, 0, WS_CONV_AUTO, s);
+    conv3x3(dY, wt, nullptr, nullptr, dst, c.cout, c.cin, H, W, 0, WS_CONV_AUTO, s, kpart, kSplitKCap);
     if (accumulate)
         TW_LAUNCH(add_inplace_kernel, blocks_for((size_t)c.cin * H * W), 256, 0, s, dX, tmp, (size_t)c.cin * H * W);
 }
@@ -579,19 +630,19 @@ static void backward(const float *P, float *G, Act &A, int H, int W, cudaStream_
     bf16 *dcur = scratch[0], *dnext = scratch[1], *tmp = scratch[2];
     bf16 *dskip[3] = {scratch[3], scratch[4], scratch[5]};   // gradients into e[2][1], e[1][1], e[0][1]
     // head (linear): dOut -> d(d[2][1])
-    conv_bwd(A.d[2][1], P, G, 14, d_out, dcur, tmp, H, W, A.wt, 0, s);
+    conv_bwd(A.d[2][1], P, G, 14, d_out, dcur, tmp, H, W, A.wt, A.kpart, 0, s);
     const int dc[3] = {128, 64, 32}, pc[3] = {128, 128, 64};
     for (int j = 2; j >= 0; j--) {
         const int l = 2 - j, h = H >> l, w = W >> l;
         // dcur: gradient of d[j][1] (post-ReLU output of conv 9 + 2j)
         TW_LAUNCH(relu_bwd_kernel, blocks_for(dc[j] * lvl_px(H, W, l)), 256, 0, s, A.d[j][1], dcur,
                   (size_t)dc[j] * lvl_px(H, W, l));
-        conv_bwd(A.d[j][0], P, G, 9 + 2 * j, dcur, dnext, tmp, h, w, A.wt, 0, s);   // -> grad of d[j][0]
+        conv_bwd(A.d[j][0], P, G, 9 + 2 * j, dcur, dnext, tmp, h, w, A.wt, A.kpart, 0, s);   // -> grad of d[j][0]
         TW_LAUNCH(relu_bwd_kernel, blocks_for(dc[j] * lvl_px(H, W, l)), 256, 0, s, A.d[j][0], dnext,
                   (size_t)dc[j] * lvl_px(H, W, l));
         // d[j][0] = relu(conv(u[j]) + e[l][1]): the skip receives the same gradient
         cudaMemcpyAsync(dskip[j], dnext, sizeof(bf16) * dc[j] * lvl_px(H, W, l), cudaMemcpyDeviceToDevice, s);
-        conv_bwd(A.u[j], P, G, 8 + 2 * j, dnext, dcur, tmp, h, w, A.wt, 0, s);      // -> grad of u[j]
+        conv_bwd(A.u[j], P, G, 8 + 2 * j, dnext, dcur, tmp, h, w, A.wt, A.kpart, 0, s);      // -> grad of u[j]
         // u[j] = up2(prev): gradient to prev (level l + 1)
         TW_LAUNCH(up2_bwd_kernel, dim3(ceil_div(w / 2, 256), h / 2, pc[j]), 256, 0, s, dcur, dnext, pc[j], h, w);
         bf16 *t = dcur; dcur = dnext; dnext = t;   // dcur: gradient of the previous decoder output
@@ -605,14 +656,14 @@ static void backward(const float *P, float *G, Act &A, int H, int W, cudaStream_
                       (size_t)ch[l] * lvl_px(H, W, l));
         TW_LAUNCH(relu_bwd_kernel, blocks_for(ch[l] * lvl_px(H, W, l)), 256, 0, s, A.e[l][1], dcur,
                   (size_t)ch[l] * lvl_px(H, W, l));
-        conv_bwd(A.e[l][0], P, G, 2 * l + 1, dcur, dnext, tmp, h, w, A.wt, 0, s);   // grad of e[l][0]
+        conv_bwd(A.e[l][0], P, G, 2 * l + 1, dcur, dnext, tmp, h, w, A.wt, A.kpart, 0, s);   // grad of e[l][0]
         TW_LAUNCH(relu_bwd_kernel, blocks_for(ch[l] * lvl_px(H, W, l)), 256, 0, s, A.e[l][0], dnext,
                   (size_t)ch[l] * lvl_px(H, W, l));
         const bf16 *xin = l == 0 ? A.in : A.p[l - 1];
         if (l == 0) {
-            conv_bwd(xin, P, G, 0, dnext, nullptr, tmp, h, w, A.wt, 0, s);
+            conv_bwd(xin, P, G, 0, dnext, nullptr, tmp, h, w, A.wt, A.kpart, 0, s);
         } else {
-            conv_bwd(xin, P, G, 2 * l, dnext, dcur, tmp, h, w, A.wt, 0, s);          // grad of p[l-1]
+            conv_bwd(xin, P, G, 2 * l, dnext, dcur, tmp, h, w, A.wt, A.kpart, 0, s);          // grad of p[l-1]
             // p[l-1] = pool2(e[l-1][1]): spread into a zeroed gradient of e[l-1][1]
             cudaMemsetAsync(dnext, 0, sizeof(bf16) * ch[l - 1] * lvl_px(H, W, l - 1), s);
             TW_LAUNCH(pool2_bwd_kernel, dim3(ceil_div(W >> (l - 1), 256), H >> (l - 1), ch[l - 1]), 256, 0, s, dcur,
