@@ -421,8 +421,11 @@ def run_twgrid(args, rank, world, dist):
                 torch.cuda.synchronize()
                 times.append(a_.elapsed_time(b_))
             t_med = float(np.median(times))
+            acc = field_accuracy(u, occ, sc, fst)
             forms[name] = {"ms_to_solution": t_med, "solves_per_s": 1e3 / t_med, "sweeps": fst["sweeps"],
-                           "resid_inf": fst["resid_inf"], "converged": fst["status"] == tw.TW_OK}
+                           "resid_inf": fst["resid_inf"], "converged": fst["status"] == tw.TW_OK,
+                           "max_abs_error_sampled": acc.get("max_abs_error_sampled"),
+                           "error_bound": acc.get("error_bound")}
         if plain and plain["converged"]:
             for f_ in forms.values():
                 f_["speedup_vs_plain_fp32"] = plain["seconds"] * 1e3 / f_["ms_to_solution"]
