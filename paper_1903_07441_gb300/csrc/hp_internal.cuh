@@ -120,16 +120,25 @@ int final_residual_full(const uint8_t *occ, int nx, int ny, int gx, int gy, cons
 // (Young).  The observed residual decay over a check interval gives lambda,
 // hence mu and omega_opt = 2 / (1 + sqrt(1 - mu^2)).  Pre-asymptotic decay
 // underestimates mu, so omega approaches omega_opt from below.
+//
+// At or past omega_opt every eigenvalue has modulus omega - 1 and lambda says
+// nothing about mu, so omega is kept while lambda <= (omega - 1)^F, F = 3/4
+// (the form of test used by the adaptive SOR procedure of Hageman & Young,
+// Applied Iterative Methods, 1981).  The margin scales with 2 - omega, the
+// distance of omega - 1 from 1: a margin proportional to omega - 1 itself
+// would exceed 1 - lambda for every omega close to 2 and freeze omega below
+// its optimum (on a 2048^2 field with 30 % obstacles: 1.957 instead of about
+// 1.965, 532 sweeps instead of 420).
 __host__ __device__ inline double sor_adapt(double omega, double lambda) {
     if (!(lambda > 0.0) || lambda >= 1.0) return omega;
-    if (lambda <= (omega - 1.0) * 1.05) return omega;  // complex regime: at or past optimum
+    if (lambda <= pow(omega > 1.0 ? omega - 1.0 : 0.0, 0.75)) return omega;
     double mu = (lambda + omega - 1.0) / (omega * sqrt(lambda));
     if (!(mu > 0.0)) return omega;
     if (mu >= 0.999999999) mu = 0.999999999;
     double w = 2.0 / (1.0 + sqrt(1.0 - mu * mu));
     // Pre-asymptotic decay underestimates mu, and the SOR rate degrades much
-    // faster below omega_opt than above it: move 15 % of the way towards 2.
-    w = 2.0 - (2.0 - w) * 0.85;
+    // faster below omega_opt than above it: move 10 % of the way towards 2.
+    w = 2.0 - (2.0 - w) * 0.9;
     if (w > 1.9995) w = 1.9995;
     return (w > omega) ? w : omega;
 }

@@ -330,11 +330,13 @@ def test_field_full_size_2048(dev):
     assert st["status"] == tw.TW_OK and st["resid_inf"] <= 1e-6
     _, fixed = oracle.dirichlet_from_occ(occ, sc.goal)
     assert _np_residual(u, fixed) <= 1e-6
-    assert u.min() >= -1e-5 and u.max() <= 1.0
     ustar, _ = oracle.solve_field(occ, sc.goal, tol=1e-12)
     tau_max = oracle.exit_time(fixed, tol=1e-6).max()
+    bound = tau_max * st["resid_inf"] * 1.01 + 1e-6
+    # u* lies in [0, 1] (maximum principle), so u may leave it by the bound at most
+    assert u.min() >= -bound and u.max() <= 1.0
     err = np.abs(u - ustar).max()
-    assert err <= tau_max * st["resid_inf"] * 1.01 + 1e-6, (err, tau_max, st)
+    assert err <= bound, (err, tau_max, st)
 
 
 # ---------------------------------------------------------------------------
