@@ -407,6 +407,8 @@ def run_twgrid(args, rank, world, dist):
         for name, prm in (("rbsor_fp32_graph", params),
                           ("rbsor_fp32_host_loop", tw.Params(tol=args.tol, max_sweeps=args.max_sweeps,
                                                              flags=tw.HP_HOST_LOOP)),
+                          ("rbsor_fp32_graph_polish", tw.Params(tol=args.tol, max_sweeps=args.max_sweeps,
+                                                                flags=tw.HP_POLISH)),
                           ("mixed_fp16", tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_F16, tol=args.tol,
                                                    max_sweeps=args.max_sweeps)),
                           ("mixed_bf16", tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_BF16, tol=args.tol,
@@ -425,7 +427,11 @@ def run_twgrid(args, rank, world, dist):
             forms[name] = {"ms_to_solution": t_med, "solves_per_s": 1e3 / t_med, "sweeps": fst["sweeps"],
                            "resid_inf": fst["resid_inf"], "converged": fst["status"] == tw.TW_OK,
                            "max_abs_error_sampled": acc.get("max_abs_error_sampled"),
+                           "mean_abs_error_sampled": acc.get("mean_abs_error_sampled"),
                            "error_bound": acc.get("error_bound")}
+            if prm.flags & tw.HP_POLISH:
+                forms[name]["polishes"] = fst["polishes"]
+                forms[name]["polished"] = fst["polished"]
         if plain and plain["converged"]:
             for f_ in forms.values():
                 f_["speedup_vs_plain_fp32"] = plain["seconds"] * 1e3 / f_["ms_to_solution"]

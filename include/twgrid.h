@@ -144,6 +144,16 @@ int tw_ring_count(const tw_grid *g, const tw_pose *robot, const tw_ring_law *law
 #define HP_HOST_LOOP 8     /* drive the convergence loop from the host (one stream synchronisation per
                               residual check) instead of the default CUDA graph whose conditional
                               while-node runs the check intervals on the device */
+#define HP_POLISH 16       /* HP_RBSOR, T > 1: when a check finds r_inf < 100 tol at omega >= 1.5, one
+                              launch of T Gauss-Seidel sweeps (omega = 1) runs on a copy of the field;
+                              if the copy meets tol it is the result, otherwise it is dropped and SOR
+                              goes on unchanged.  At omega near 2 the residual max is dominated by
+                              oscillatory error that Gauss-Seidel removes in a few sweeps, so the
+                              tolerance is met one or more check intervals earlier -- but the smooth
+                              error SOR would have removed in those intervals stays: at the same tol
+                              the field is less accurate (still within tau_max * r_inf).  Off by
+                              default.  max_sweeps caps the SOR sweeps; polish sweeps are counted in
+                              hp_stats.sweeps on top. */
 
 typedef struct {
     int method;        /* HP_JACOBI, HP_RBSOR or HP_MIXED */
@@ -157,11 +167,11 @@ typedef struct {
                           HP_RBSOR takes 1..7 (default 7 on deep tiles when the field has at least
                           96 of them -- about 2048 x 1400 cells and up -- else 4); hp_relax_batched
                           takes 2 or 4 (anything else: autotuned) */
-    int flags;         /* HP_WARM_START | HP_OUT_PHI */
+    int flags;         /* HP_WARM_START | HP_OUT_PHI | HP_TIMING | HP_HOST_LOOP | HP_POLISH */
 } hp_params;
 
 typedef struct {
-    int sweeps;        /* full sweeps performed */
+    int sweeps;        /* full sweeps performed (HP_RBSOR: SOR sweeps plus polish sweeps) */
     int status;        /* TW_OK or TW_NOT_CONVERGED */
     double resid_inf;  /* FP64 residual max |(1/4) sum nbr - u| over free cells of the output
                           (HP_MIXED: of its FP64 master field, which the FP32 output rounds) */
@@ -172,6 +182,8 @@ typedef struct {
     double sweep_ms;   /* HP_TIMING: summed CUDA-event time of the sweep launches (ms) */
     int tblock;        /* temporal-blocking depth used (sweeps fused per launch) */
     int loop;          /* how the convergence loop ran: HP_LOOP_HOST or HP_LOOP_GRAPH */
+    int polishes;      /* polish launches tried (HP_POLISH) */
+    int polished;      /* 1: the output is the accepted polished copy */
 } hp_stats;
 
 #define HP_LOOP_HOST 0     /* host-driven: HP_HOST_LOOP, HP_TIMING, HP_JACOBI, HP_MIXED, or a cap

@@ -27,7 +27,7 @@ TW_MARK_PER_CELL, TW_MARK_PER_OBSTACLE = 0, 1
 TW_FREE, TW_STATIC, TW_DYNAMIC, TW_BORDER = 0, 1, 2, 3
 HP_JACOBI, HP_RBSOR, HP_MIXED = 0, 1, 2
 HP_STORE_F32, HP_STORE_F16, HP_STORE_BF16 = 0, 1, 2
-HP_WARM_START, HP_OUT_PHI, HP_TIMING, HP_HOST_LOOP = 1, 2, 4, 8
+HP_WARM_START, HP_OUT_PHI, HP_TIMING, HP_HOST_LOOP, HP_POLISH = 1, 2, 4, 8, 16
 HP_LOOP_HOST, HP_LOOP_GRAPH = 0, 1
 WS_CONV_AUTO, WS_CONV_SIMT, WS_CONV_MMA = 0, 1, 2
 
@@ -83,7 +83,8 @@ class hp_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("status", ctypes.c_int), ("resid_inf", ctypes.c_double),
                 ("resid_l2", ctypes.c_double), ("omega", ctypes.c_double), ("checks", ctypes.c_int),
                 ("sweep_launches", ctypes.c_int), ("sweep_ms", ctypes.c_double), ("tblock", ctypes.c_int),
-                ("loop", ctypes.c_int)]
+                ("loop", ctypes.c_int), ("polishes", ctypes.c_int),
+                ("polished", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -463,6 +463,7 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
         memset(&c, 0, sizeof(c));
         c.adapt = p->omega == 0.0;
         c.omega = c.adapt ? sor_initial_omega(hb[i].nx, hb[i].ny) : p->omega;
+        c.omega_max = sor_omega_cap(hb[i].nx, hb[i].ny);
         c.omega_f = (float)c.omega;
         c.r_prev = -1.0;
         c.tol = p->tol;

@@ -33,6 +33,14 @@ struct RelaxCtl {
     int sweeps, checks, status, adapt, same_iv, K, max_sweeps, pad;
     double omega, r_prev, tol, r_last;
     double e_prev;         // residual 2-norm at the previous check (<= 0: not measured)
+    double omega_max;      // cap on the adapted omega (<= 1: 1.9995)
+    int polish;            // 1: this check tries a polish launch
+    int in_alt;            // 1: the solution is the polished copy in the other ping-pong planes
+    int polishes, psweeps; // polish launches tried, and their sweeps
+    int go, T;             // continue flag of the last check; sweeps per launch
+    int polish_ok, pad2;   // polish enabled (HP_RBSOR with HP_POLISH and T > 1)
+    float one_f;           // 1.0f, the omega the polish launches read
+    float pad3;
 };
 
 
@@ -74,7 +82,7 @@ int tb_tiles(int T, int nx, int ny);
 // Graph-driven loop: up to max_intervals check intervals of K sweeps (K/T even)
 // run on the device; ctl_dev must hold the initial state.  Returns TW_OK, or
 // a positive value when graphs are unavailable (the caller uses the host loop).
-int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, RelaxScalars *scal,
+int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, int polish, RelaxScalars *scal,
                    float *l2part, cudaStream_t s, int *launches);
 // FP32 residual max (atomicMax into *out) and, if l2part is given, the sum of
 // squared residuals of every CTA in l2part[rb_residual_blocks(L, ny)].
@@ -110,6 +118,7 @@ struct SweepTimer {
 int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal, float *l2part, hp_stats *st,
              cudaStream_t s, int *ctl_on_device);
 double sor_initial_omega(int nx, int ny);
+double sor_omega_cap(int nx, int ny);
 int read_max_f32(unsigned int *dmax, cudaStream_t s, float *out);
 int final_residual_full(const uint8_t *occ, int nx, int ny, int gx, int gy, const float *u,
                         RelaxScalars *scal, cudaStream_t s, double *r_inf, double *r_l2);
@@ -129,7 +138,7 @@ int final_residual_full(const uint8_t *occ, int nx, int ny, int gx, int gy, cons
 // would exceed 1 - lambda for every omega close to 2 and freeze omega below
 // its optimum (on a 2048^2 field with 30 % obstacles: 1.957 instead of about
 // 1.965, 532 sweeps instead of 420).
-__host__ __device__ inline double sor_adapt(double omega, double lambda) {
+__host__ __device__ inline double sor_adapt(double omega, double lambda, double omega_max) {
     if (!(lambda > 0.0) || lambda >= 1.0) return omega;
     if (lambda <= pow(omega > 1.0 ? omega - 1.0 : 0.0, 0.75)) return omega;
     double mu = (lambda + omega - 1.0) / (omega * sqrt(lambda));
@@ -139,7 +148,8 @@ __host__ __device__ inline double sor_adapt(double omega, double lambda) {
     // Pre-asymptotic decay underestimates mu, and the SOR rate degrades much
     // faster below omega_opt than above it: move 10 % of the way towards 2.
     w = 2.0 - (2.0 - w) * 0.9;
-    if (w > 1.9995) w = 1.9995;
+    const double cap = omega_max > 1.0 ? omega_max : 1.9995;
+    if (w > cap) w = cap;
     return (w > omega) ? w : omega;
 }
 
@@ -188,7 +198,7 @@ __host__ __device__ inline int relax_control(RelaxCtl &c, double r, double e, in
         if (c.r_prev > 0.0 && c.same_iv >= 1 && n == c.K) {
             const bool l2 = e > 0.0 && c.e_prev > 0.0;
             double lambda = pow(l2 ? e / c.e_prev : r / c.r_prev, 1.0 / n);
-            double w = sor_adapt(c.omega, lambda);
+            double w = sor_adapt(c.omega, lambda, c.omega_max);
             if (w > c.omega + 1e-4) { c.omega = w; c.same_iv = -1; }
         }
         c.same_iv++;
@@ -196,6 +206,37 @@ __host__ __device__ inline int relax_control(RelaxCtl &c, double r, double e, in
     c.r_prev = r;
     c.e_prev = e;
     c.omega_f = (float)c.omega;
+    return 1;
+}
+
+// Polish (HP_POLISH): a stopping-test device beside the SOR iteration, not
+// part of it.  Near convergence at omega close to 2 the residual max is
+// dominated by oscillatory error that SOR damps only at the rate omega - 1
+// while Gauss-Seidel (omega = 1) removes it in a few sweeps.  When a check
+// finds r < kPolishFactor * tol, one launch of T sweeps at omega = 1 runs from
+// the current ping-pong planes into the other pair and its residual is
+// checked: at or below tol that copy is the solution; otherwise it is dropped
+// and SOR continues from the unpolished planes, whose sequence it leaves
+// untouched.  The smooth error stays, so at the same tol the polished field is
+// less accurate than the one SOR would reach.
+constexpr double kPolishFactor = 100.0;
+
+// After relax_control returned cont: decide whether this check polishes.
+__host__ __device__ inline int relax_polish_decide(RelaxCtl &c, int cont) {
+    c.polish = (cont && c.polish_ok && c.tol > 0.0 && c.r_last < kPolishFactor * c.tol && c.omega >= 1.5) ? 1 : 0;
+    return c.polish;
+}
+
+// The polished copy's residual r2: returns 0 when it meets the tolerance.
+__host__ __device__ inline int relax_polish_result(RelaxCtl &c, double r2) {
+    c.polishes++;
+    c.psweeps += c.T;
+    if (r2 <= c.tol) {
+        c.status = TW_OK;
+        c.in_alt = 1;
+        c.r_last = r2;
+        return 0;
+    }
     return 1;
 }
 

@@ -349,6 +349,7 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
     memset(&c, 0, sizeof(c));
     c.adapt = p->omega == 0.0;
     c.omega = c.adapt ? sor_initial_omega(nx, ny) : p->omega;
+    c.omega_max = sor_omega_cap(nx, ny);
     int sweeps = 0, launches = 0, checks = 0, outer = 0;
     double r_inf = 0.0;
     st->status = TW_NOT_CONVERGED;

@@ -160,12 +160,16 @@ __global__ void rb_pack_kernel(const uint8_t *__restrict__ occ, const float *__r
     }
 }
 
-__global__ void rb_unpack_kernel(RBLayout L, int nx, int ny, float *__restrict__ out, int to_phi) {
+// alt (nullable, device): when *alt != 0 the solution is in the second
+// ping-pong pair (a polished copy the graph-driven loop accepted).
+__global__ void rb_unpack_kernel(RBLayout L, int nx, int ny, float *__restrict__ out, int to_phi,
+                                 const int *__restrict__ alt) {
     int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= nx || y >= ny) return;
     int color = (x + y) & 1;
     int k = x >> 1;
-    const float *arr = color ? L.B : L.R;
+    const bool a = alt && *alt;
+    const float *arr = color ? (a ? L.B2 : L.B) : (a ? L.R2 : L.R);
     float v = arr[(size_t)y * L.S + 4 + k];
     out[(size_t)y * nx + x] = to_phi ? 1.0f - v : v;
 }
@@ -239,9 +243,28 @@ static bool valid_params(const hp_params *p) {
            p->tblock >= 0 && p->tblock <= 16;
 }
 
+// First omega of an adaptive solve, by the longer side n, and never above
+// sor_omega_cap.  The adaptation only raises omega, so the start stays below
+// the optimum of cluttered scenes (30-45 % obstacles: 1.94-1.97 at
+// 1024-2048, about 1.94 at 256-512).
 double sor_initial_omega(int nx, int ny) {
     int n = nx > ny ? nx : ny;
-    return n >= 1024 ? 1.9 : (n >= 256 ? 1.85 : 1.75);
+    const double w = n >= 1024 ? 1.9 : (n >= 256 ? 1.85 : 1.75);
+    const double cap = sor_omega_cap(nx, ny);
+    return w < cap ? w : cap;
+}
+
+// Upper bound on omega_opt for any occupancy of an nx x ny grid: the Jacobi
+// matrix of the free cells is a principal submatrix of the (nonnegative)
+// Jacobi matrix of the empty box, so its spectral radius is at most the box's,
+// mu = (cos(pi / (nx - 1)) + cos(pi / (ny - 1))) / 2 (Perron-Frobenius), and
+// omega_opt = 2 / (1 + sqrt(1 - mu^2)) grows with mu.  Without the cap the
+// pre-asymptotic estimates can drive omega past the optimum of open scenes,
+// where the rate omega - 1 gets close to 1.
+double sor_omega_cap(int nx, int ny) {
+    const double pi = 3.14159265358979323846;
+    const double mu = 0.5 * (cos(pi / (nx - 1)) + cos(pi / (ny - 1)));
+    return 2.0 / (1.0 + sqrt(1.0 - mu * mu));
 }
 
 int read_max_f32(unsigned int *dmax, cudaStream_t s, float *out) {
@@ -356,13 +379,17 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
     c.K = K;
     c.max_sweeps = p->max_sweeps;
     c.status = TW_NOT_CONVERGED;
+    c.omega_max = sor_omega_cap(nx, ny);
+    c.T = T;
+    c.polish_ok = (T > 1 && L.R2 && (p->flags & HP_POLISH)) ? 1 : 0;
+    c.one_f = 1.0f;
     int launches = 0;
     bool done = false;
     const bool host_loop = (p->flags & (HP_TIMING | HP_HOST_LOOP)) != 0;
     if (checks && !host_loop && T > 1 && (K / T) % 2 == 0 && p->max_sweeps >= K) {
         TW_CUDA(cudaMemcpyAsync(&scal->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s));
         TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
-        int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, scal, l2part, s, &launches);
+        int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, c.polish_ok, scal, l2part, s, &launches);
         if (e < 0) return e;
         if (e == TW_OK) st->loop = HP_LOOP_GRAPH;
         if (e == TW_OK && p->max_sweeps % K == 0) {
@@ -376,9 +403,14 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
             TW_CUDA(cudaMemcpyAsync(&c, &scal->ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
             TW_CUDA(cudaStreamSynchronize(s));
             done = c.status == TW_OK;
-            // every interval ran K/T sweep launches, the residual and the control kernel
-            launches += c.checks * (K / T);
-            count_launches((unsigned long long)c.checks * (K / T + 2));
+            if (c.in_alt) {   // a polished copy was accepted: it is in the second pair
+                float *t = L.R; L.R = L.R2; L.R2 = t;
+                t = L.B; L.B = L.B2; L.B2 = t;
+            }
+            // every interval ran K/T sweep launches, the residual and the control kernel (and with
+            // HP_POLISH the polish-result kernel); every polish one sweep launch and a residual
+            launches += c.checks * (K / T) + c.polishes;
+            count_launches((unsigned long long)c.checks * (K / T + 2 + c.polish_ok) + 2ull * c.polishes);
         }
     }
     SweepTimer timer;
@@ -402,11 +434,34 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
             TW_CUDA(cudaStreamSynchronize(s));
             float rf;
             memcpy(&rf, &hs.max32, sizeof(rf));
-            if (!relax_control(c, (double)rf, l2part ? hs.l2 : -1.0, n)) done = true;
+            const int cont = relax_control(c, (double)rf, l2part ? hs.l2 : -1.0, n);
+            if (!cont) {
+                done = true;
+            } else if (relax_polish_decide(c, cont)) {
+                // T sweeps at omega = 1 into the second pair; L keeps the SOR planes
+                RBLayout Lp = L;
+                timer.start(s);
+                e = rb_sweeps(Lp, nx, ny, T, T, 1.0f, s, &launches);
+                timer.stop(s);
+                if (e) return e;
+                timer.accumulate();
+                TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
+                rb_residual_launch(Lp, ny, &scal->max32, nullptr, s);
+                TW_CHECK_LAUNCH();
+                float r2;
+                e = read_max_f32(&scal->max32, s, &r2);
+                if (e) return e;
+                if (!relax_polish_result(c, (double)r2)) {
+                    done = true;
+                    L = Lp;
+                }
+            }
         }
     }
     st->status = c.status;
-    st->sweeps = c.sweeps;
+    st->sweeps = c.sweeps + c.psweeps;
+    st->polishes = c.polishes;
+    st->polished = c.in_alt;
     st->checks = c.checks;
     st->omega = c.omega;
     st->sweep_launches = launches;
@@ -429,7 +484,8 @@ static int relax_rbsor(const uint8_t *occ, int nx, int ny, int gx, int gy, float
     TW_CHECK_LAUNCH();
     int e = rb_solve(L, nx, ny, p, R.scal, R.l2part, st, s, ctl_dev);
     if (e) return e;
-    TW_LAUNCH(rb_unpack_kernel, dim3(ceil_div(nx, 256), ny), 256, 0, s, L, nx, ny, u, 0);
+    TW_LAUNCH(rb_unpack_kernel, dim3(ceil_div(nx, 256), ny), 256, 0, s, L, nx, ny, u, 0,
+              *ctl_dev ? (const int *)&R.scal->ctl.in_alt : (const int *)nullptr);
     TW_CHECK_LAUNCH();
     return TW_OK;
 }
@@ -483,11 +539,13 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
         const RelaxCtl &c = hs.ctl;
         const int KT = local.tblock > 1 ? c.K / local.tblock : c.K;
         local.status = c.status;
-        local.sweeps = c.sweeps;
+        local.sweeps = c.sweeps + c.psweeps;
+        local.polishes = c.polishes;
+        local.polished = c.in_alt;
         local.checks = c.checks;
         local.omega = c.omega;
-        local.sweep_launches = c.checks * KT;
-        count_launches((unsigned long long)c.checks * (KT + 2));
+        local.sweep_launches = c.checks * KT + c.polishes;
+        count_launches((unsigned long long)c.checks * (KT + 2 + c.polish_ok) + 2ull * c.polishes);
     }
     if (p->method != HP_MIXED) {
         memcpy(&local.resid_inf, &hs.max64, sizeof(double));

@@ -257,6 +257,7 @@ def test_graph_loop_matches_host_loop(dev):
         assert sa["loop"] == tw.HP_LOOP_GRAPH and sb["loop"] == tw.HP_LOOP_HOST
         assert sa["status"] == sb["status"] == tw.TW_OK
         assert sa["sweeps"] == sb["sweeps"] and sa["checks"] == sb["checks"]
+        assert sa["polishes"] == sb["polishes"] and sa["polished"] == sb["polished"]
         # omega adapts on the device (graph) or on the host: their libm may differ in the last bit
         assert abs(sa["omega"] - sb["omega"]) <= 1e-12
         assert np.array_equal(a, b)
@@ -281,7 +282,8 @@ def test_deep_tiles_graph_matches_host_loop(dev):
     b, sb = _relax(occ, goal, dev, tw.Params(tol=1e-6, flags=tw.HP_HOST_LOOP))
     assert sa["tblock"] == sb["tblock"] == 7 and sa["loop"] == tw.HP_LOOP_GRAPH
     assert sa["status"] == sb["status"] == tw.TW_OK and sa["sweeps"] == sb["sweeps"]
-    assert sa["sweeps"] % 28 == 0 and abs(sa["omega"] - sb["omega"]) <= 1e-12
+    assert sa["polishes"] == sb["polishes"] and sa["polished"] == sb["polished"]
+    assert (sa["sweeps"] - 7 * sa["polishes"]) % 28 == 0 and abs(sa["omega"] - sb["omega"]) <= 1e-12
     assert np.array_equal(a, b)
     c, sc_ = _relax(occ, goal, dev, tw.Params(tol=1e-12, max_sweeps=100))
     d, sd = _relax(occ, goal, dev, tw.Params(tol=1e-12, max_sweeps=100, flags=tw.HP_HOST_LOOP))
@@ -289,6 +291,51 @@ def test_deep_tiles_graph_matches_host_loop(dev):
     e, se = _relax(occ, goal, dev, tw.Params(tol=1e-6, tblock=4))
     assert se["tblock"] == 4 and se["status"] == tw.TW_OK
     assert np.abs(e - a).max() <= 1e-4   # both within their a-posteriori bounds of the same solution
+
+
+def _polish_scenes():
+    rng = np.random.default_rng(77)
+    occ = (rng.random((1500, 2048)) < 0.25).astype(np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+    occ[700, 1500] = 0
+    sc = scenes.static128()
+    occ128, _, _ = oracle.build_grid(sc)
+    s700 = scenes.static_occupancy(5, 700, 260, 0.25)
+    occ700, _, _ = oracle.build_grid(s700)
+    return [(occ128, sc.goal), (occ700, s700.goal), (occ, (1500, 700))]
+
+
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_polish_is_gauss_seidel_on_the_sor_planes(dev, case):
+    """HP_POLISH is a side branch: an accepted polished solve returns exactly
+    T Gauss-Seidel sweeps (omega = 1, same kernel) applied to the SOR field the
+    plain solve reaches after the same SOR sweeps, and the SOR sequence itself
+    is the plain one (same omega, same checks); graph and host loops agree."""
+    occ, goal = _polish_scenes()[case]
+    res = []
+    for flags in (0, tw.HP_HOST_LOOP):
+        a, sa = _relax(occ, goal, dev, tw.Params(tol=1e-6, flags=flags | tw.HP_POLISH))
+        res.append((a, sa))
+        n, sn = _relax(occ, goal, dev, tw.Params(tol=1e-6, flags=flags))
+        assert sa["status"] == sn["status"] == tw.TW_OK and sn["polishes"] == 0
+        assert sa["resid_inf"] <= 1e-6
+        T = sa["tblock"]
+        assert sa["polishes"] >= 1 and sa["polished"] == 1, sa
+        s_sor = sa["sweeps"] - T * sa["polishes"]
+        assert s_sor <= sn["sweeps"]
+        # the unpolished SOR field after s_sor sweeps, then T sweeps at omega = 1
+        b, sb = _relax(occ, goal, dev, tw.Params(tol=1e-6, max_sweeps=s_sor, flags=flags))
+        assert sb["sweeps"] == s_sor and abs(sb["omega"] - sa["omega"]) <= 1e-12
+        occ_t = torch.from_numpy(np.ascontiguousarray(occ)).to(dev)
+        grid = tw.make_grid(occ.shape[1], occ.shape[0], 0.05)
+        u = torch.from_numpy(b.astype(np.float32)).to(dev)
+        g, sg = tw.hp_relax(grid, occ_t, goal, field=u,
+                            params=tw.Params(omega=1.0, tol=0.0, max_sweeps=T, tblock=T, flags=tw.HP_WARM_START))
+        assert sg["sweeps"] == T and sg["sweep_launches"] == 1
+        assert np.array_equal(g.cpu().numpy().astype(np.float64), a)
+    (a, sa), (b, sb) = res
+    assert sa["loop"] == tw.HP_LOOP_GRAPH and sb["loop"] == tw.HP_LOOP_HOST
+    assert sa["sweeps"] == sb["sweeps"] and sa["polishes"] == sb["polishes"] and np.array_equal(a, b)
 
 
 def test_warm_start_and_phi_output(dev, ref128):
