@@ -9,7 +9,8 @@ r_inf <= 1e-6 (hp_relax), and the Eq. 3 path with rubber band (plan_path).
 Prints one JSON line (rank 0).  `value` is device-resident throughput (inputs
 already in HBM); `e2e` repeats the step through the same C ABI with host
 buffers (pinned H2D of the occupancy, D2H of the field and the path) inside
-the timed region.  Multi-GPU (torchrun): every rank solves its own scene, no
+the timed region, the copies on a second stream overlapping the neighbouring
+steps' compute (double buffers).  Multi-GPU (torchrun): every rank solves its own scene, no
 collective touches the data path; only a barrier and a max-reduce of the
 elapsed time are exchanged.  `--impl reference` times the FP64 CPU oracle on
 the host cores instead.
@@ -252,10 +253,11 @@ def run_twgrid(args, rank, world, dist):
     max_len = 4 * (sc.nx + sc.ny) * 4
     stats_log = []
 
-    def step(static_src, prm=None):
+    def step(static_src, prm=None, field=None):
+        field = u if field is None else field
         tw.tw_build_grid(grid, sc.robot, sc.tracks, sc.law, static_occ=static_src, occ=occ)
-        _, st = tw.hp_relax(grid, occ, sc.goal, field=u, params=prm or params)
-        pst, path = tw.plan_path(grid, u, occ, sc.start, sc.goal, rubber_iters=100, max_len=max_len)
+        _, st = tw.hp_relax(grid, occ, sc.goal, field=field, params=prm or params)
+        pst, path = tw.plan_path(grid, field, occ, sc.start, sc.goal, rubber_iters=100, max_len=max_len)
         stats_log.append((st, pst, len(path)))
         return path
 
@@ -356,25 +358,54 @@ def run_twgrid(args, rank, world, dist):
     # ---- accuracy of the solved field against the stored FP64 reference of this scene
     accuracy = field_accuracy(u, occ, sc, timed_log[-1][0]) if rank == 0 else None
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: every step copies its input map
+    # from pinned host memory and its field back, on a copy stream with double buffers so
+    # that step i's field goes back and step i+1's map comes in while step i+1 / i computes
     stats_log.clear()
+    copy_s = torch.cuda.Stream(device=dev)
+    u_b = [u, torch.empty_like(u)]
+    st_b = [static_d, torch.empty_like(static_d)]
+    uh_b = [u_h, torch.empty_like(u_h).pin_memory()]
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_out = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_free = [torch.cuda.Event(), torch.cuda.Event()]
     barrier()
     e0 = time.perf_counter()
     ev0.record(stream)
     h2d = d2h = 0
+    copy_s.wait_stream(stream)
+    with torch.cuda.stream(copy_s):
+        st_b[0].copy_(static_h, non_blocking=True)
+        ev_in[0].record(copy_s)
     for i in range(args.steps):
+        b = i & 1
         if i:
             flush.zero_()
-        static_d.copy_(static_h, non_blocking=True)
+        stream.wait_event(ev_in[b])
+        if i >= 2:
+            stream.wait_event(ev_free[b])   # the field buffer's previous copy-out is done
         h2d += static_h.numel() + sc.tracks.nbytes
-        path = step(static_d)
-        u_h.copy_(u, non_blocking=True)
+        path = step(st_b[b], field=u_b[b])
+        ev_out[b].record(stream)
+        with torch.cuda.stream(copy_s):
+            if i + 1 < args.steps:   # next step's input, once step i - 1 (its last reader) is done
+                if i >= 1:
+                    copy_s.wait_event(ev_out[1 - b])
+                st_b[1 - b].copy_(static_h, non_blocking=True)
+                ev_in[1 - b].record(copy_s)
+            copy_s.wait_event(ev_out[b])
+            uh_b[b].copy_(u_b[b], non_blocking=True)
+            ev_free[b].record(copy_s)
         d2h += u_h.numel() * 4 + path.nbytes
+    stream.wait_stream(copy_s)
     ev1.record(stream)
     torch.cuda.synchronize()
+    assert torch.equal(uh_b[(args.steps - 1) & 1], u_b[(args.steps - 1) & 1].cpu())
     e_el = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
     e2e = {"value": throughput(args.steps, world, e_el), "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
-           "d2h_bytes_per_step": d2h // args.steps, "wall_s": time.perf_counter() - e0}
+           "d2h_bytes_per_step": d2h // args.steps, "wall_s": time.perf_counter() - e0,
+           "copies": "pinned host buffers; a copy stream overlaps step i's field copy-out and step i+1's "
+                     "map copy-in with the compute (double-buffered); CUDA events around all steps"}
 
     # ---- plain FP32 Jacobi on the same scene (the comparison form)
     plain = None
