@@ -115,6 +115,30 @@ int tw_build_grid(const tw_grid *g, const tw_pose *robot, const tw_track *tracks
                   const tw_ring_law *law, const uint8_t *static_occ_dev, uint8_t *occ_dev,
                   int16_t *ring_dev, void *workspace, size_t workspace_bytes, void *stream);
 
+/* tw_build_grids: tw_build_grid for n planners at once (the batched form of
+ * Alg. 1 "Map Update", Sec. 3.4-3.5): every job gets exactly the occupancy
+ * and ring codes tw_build_grid gives it, from three launches in all (ring
+ * tables, predictions, raster over the concatenated tiles of every grid) and
+ * one host-to-device copy of all parameters and tracks.
+ * jobs: HOST array of n (1..65536) job descriptions; each tracks array is a
+ * HOST array of n_tracks (0 allowed).  The output buffers of different jobs
+ * must not overlap.  Asynchronous on `stream`; the host arrays may be reused
+ * on return.  Errors: TW_EINVAL (any job invalid as for tw_build_grid, or
+ * 2^31 tiles of 32 x 32 cells or more in total), TW_EWORKSPACE, TW_ECUDA.
+ * Nothing is launched when an argument is invalid. */
+typedef struct {
+    tw_grid grid;
+    tw_pose robot;
+    tw_ring_law law;
+    const tw_track *tracks;         /* HOST array of n_tracks */
+    int n_tracks;
+    const uint8_t *static_occ_dev;  /* device uint8 [ny][nx] or NULL */
+    uint8_t *occ_dev;               /* device uint8 [ny][nx] output */
+    int16_t *ring_dev;              /* device int16 [ny][nx] output or NULL */
+} tw_grid_job;
+size_t tw_build_grids_workspace_size(int n, const tw_grid_job *jobs);
+int tw_build_grids(int n, const tw_grid_job *jobs, void *workspace, size_t workspace_bytes, void *stream);
+
 /* tw_nearest_free: the free (occ == 0), non-border cell nearest to (x, y)
  * (squared Euclidean distance in cells; ties go to the lowest row-major index),
  * written to host xy_host[0..1].  A replanning loop uses it as the goal when

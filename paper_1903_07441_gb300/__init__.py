@@ -32,7 +32,8 @@ HP_LOOP_HOST, HP_LOOP_GRAPH = 0, 1
 WS_CONV_AUTO, WS_CONV_SIMT, WS_CONV_MMA = 0, 1, 2
 
 EXPORTS = (
-    "tw_build_grid_workspace_size", "tw_build_grid", "tw_ring_count", "tw_nearest_free",
+    "tw_build_grid_workspace_size", "tw_build_grid", "tw_build_grids_workspace_size", "tw_build_grids",
+    "tw_ring_count", "tw_nearest_free",
     "hp_relax_workspace_size", "hp_relax", "hp_relax_noalloc", "hp_relax_dirichlet", "hp_residual",
     "hp_relax_batched_workspace_size", "hp_relax_batched",
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
@@ -66,6 +67,12 @@ class tw_ring_law(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("mark", ctypes.c_int), ("r0", ctypes.c_double),
                 ("growth", ctypes.c_double), ("n_rings", ctypes.c_int), ("q_accel", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("d_safe", ctypes.c_double), ("time_outer", ctypes.c_int)]
+
+
+class tw_grid_job(ctypes.Structure):
+    _fields_ = [("grid", tw_grid), ("robot", tw_pose), ("law", tw_ring_law), ("tracks", ctypes.c_void_p),
+                ("n_tracks", ctypes.c_int), ("static_occ_dev", ctypes.c_void_p), ("occ_dev", ctypes.c_void_p),
+                ("ring_dev", ctypes.c_void_p)]
 
 
 class hp_params(ctypes.Structure):
@@ -130,6 +137,10 @@ def load() -> ctypes.CDLL:
     lib.tw_build_grid_workspace_size.restype = Z
     lib.tw_build_grid.argtypes = [P, P, P, I, P, P, P, P, P, Z, P]
     lib.tw_build_grid.restype = I
+    lib.tw_build_grids_workspace_size.argtypes = [I, P]
+    lib.tw_build_grids_workspace_size.restype = Z
+    lib.tw_build_grids.argtypes = [I, P, P, Z, P]
+    lib.tw_build_grids.restype = I
     lib.tw_nearest_free.argtypes = [P, P, I, I, P, P, Z, P]
     lib.tw_nearest_free.restype = I
     lib.tw_ring_count.argtypes = [P, P, P]
@@ -276,6 +287,37 @@ def tw_build_grid(grid: tw_grid, robot, tracks: np.ndarray, law, static_occ=None
                            _stream(occ.device))
     _check("tw_build_grid", st)
     return occ, ring
+
+
+def tw_build_grids(jobs, device="cuda"):
+    """Many time-warped rasters in one call.  jobs: list of dicts with keys grid,
+    robot, tracks (host float64 [n, 21]), law, and optionally static_occ, occ,
+    ring (device tensors).  Returns the list of (occ, ring)."""
+    torch = _torch()
+    lib = load()
+    n = len(jobs)
+    arr = (tw_grid_job * n)()
+    keep, outs = [], []
+    for i, j in enumerate(jobs):
+        g = j["grid"]
+        tr = np.ascontiguousarray(j.get("tracks") if j.get("tracks") is not None else np.zeros((0, 21)),
+                                  dtype=np.float64).reshape(-1, TRACK_DOUBLES)
+        keep.append(tr)
+        occ = j.get("occ")
+        if occ is None:
+            occ = torch.empty((g.ny, g.nx), dtype=torch.uint8, device=device)
+        ring = j.get("ring")
+        st_ = j.get("static_occ")
+        arr[i] = tw_grid_job(g, make_pose(j["robot"]), make_law(j["law"]),
+                             tr.ctypes.data if len(tr) else None, len(tr),
+                             _ptr(st_) if st_ is not None else None, _ptr(occ),
+                             _ptr(ring) if ring is not None else None)
+        outs.append((occ, ring))
+    dev = outs[0][0].device
+    ws = workspace(lib.tw_build_grids_workspace_size(n, arr), dev, "grids")
+    st = lib.tw_build_grids(n, arr, _ptr(ws), ws.numel(), _stream(dev))
+    _check("tw_build_grids", st)
+    return outs
 
 
 def tw_nearest_free(grid: tw_grid, occ, x, y):

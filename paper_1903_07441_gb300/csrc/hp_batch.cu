@@ -77,27 +77,56 @@ static void tiles_for(int T, int W4, int ny, int *tx, int *ty) {
 
 // ---- kernels ---------------------------------------------------------------------
 
-__global__ void batch_pack_kernel(BatchInst *I, int warm) {
-    BatchInst &b = I[blockIdx.z];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (y >= b.ny) return;   // uniform per block
+// Zero both ping-pong pairs of every instance, pad columns included (one
+// launch for the whole batch).
+__global__ void batch_zero_kernel(const BatchInst *I) {
+    const BatchInst &b = I[blockIdx.y];
+    const size_t n = (size_t)b.ny * b.S;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        b.P[0][0][i] = 0.0f;
+        b.P[0][1][i] = 0.0f;
+        b.P[1][0][i] = 0.0f;
+        b.P[1][1][i] = 0.0f;
+    }
+}
+
+// Instance and row of block `r` of a launch with one block per row of every
+// instance (row_off: prefix sums of the instances' ny, n + 1 entries).
+__device__ __forceinline__ int batch_row(const int *row_off, int n, int r, int *y) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    *y = r - row_off[lo];
+    return lo;
+}
+
+// One block per row of every instance (the grid holds exactly the rows).
+__global__ void batch_pack_kernel(BatchInst *I, const int *row_off, int n, int warm) {
+    int y;
+    BatchInst &b = I[batch_row(row_off, n, (int)blockIdx.x, &y)];
     const int lane = threadIdx.x & 31;
+    const int kend = (b.W2 + 31) & ~31;   // whole warps: the ballot below needs every lane
+    for (int k = threadIdx.x; k < kend; k += blockDim.x) {
 #pragma unroll
-    for (int color = 0; color < 2; color++) {
-        const int x = 2 * k + ((y + color) & 1);
-        float v = 0.0f;
-        bool free_cell = false;
-        if (k < b.W2 && x < b.nx) {
-            const size_t c = (size_t)y * b.nx + x;
-            const bool goal = (x == b.gx && y == b.gy);
-            if (goal && b.occ[c] != 0) b.error = TW_EGOAL_BLOCKED;
-            const bool fixed = goal || x == 0 || y == 0 || x == b.nx - 1 || y == b.ny - 1 || b.occ[c] != 0;
-            free_cell = !fixed;
-            v = goal ? 1.0f : (fixed ? 0.0f : (warm ? b.field[c] : 0.5f));
+        for (int color = 0; color < 2; color++) {
+            const int x = 2 * k + ((y + color) & 1);
+            float v = 0.0f;
+            bool free_cell = false;
+            if (k < b.W2 && x < b.nx) {
+                const size_t c = (size_t)y * b.nx + x;
+                const bool goal = (x == b.gx && y == b.gy);
+                if (goal && b.occ[c] != 0) b.error = TW_EGOAL_BLOCKED;
+                const bool fixed = goal || x == 0 || y == 0 || x == b.nx - 1 || y == b.ny - 1 || b.occ[c] != 0;
+                free_cell = !fixed;
+                v = goal ? 1.0f : (fixed ? 0.0f : (warm ? b.field[c] : 0.5f));
+            }
+            const unsigned bits = __ballot_sync(0xffffffffu, free_cell);
+            if (k < b.W2) b.P[0][color][(size_t)y * b.S + 4 + k] = v;
+            if (lane == 0 && (k >> 5) < b.MW) (color ? b.MB : b.MR)[(size_t)y * b.MW + (k >> 5)] = bits;
         }
-        const unsigned bits = __ballot_sync(0xffffffffu, free_cell);
-        if (k < b.W2) b.P[0][color][(size_t)y * b.S + 4 + k] = v;
-        if (lane == 0 && (k >> 5) < b.MW) (color ? b.MB : b.MR)[(size_t)y * b.MW + (k >> 5)] = bits;
     }
 }
 
@@ -201,27 +230,33 @@ batch_control_kernel(BatchInst *__restrict__ I, BatchHdr *__restrict__ H, int2 *
     }
 }
 
-__global__ void batch_unpack_kernel(BatchInst *I, int to_phi) {
-    const BatchInst &b = I[blockIdx.z];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= b.nx || y >= b.ny) return;
-    const float v = b.P[0][(x + y) & 1][(size_t)y * b.S + 4 + (x >> 1)];
-    b.field[(size_t)y * b.nx + x] = to_phi ? 1.0f - v : v;
+__global__ void batch_unpack_kernel(BatchInst *I, const int *row_off, int n, int to_phi) {
+    int y;
+    const BatchInst &b = I[batch_row(row_off, n, (int)blockIdx.x, &y)];
+    for (int x = threadIdx.x; x < b.nx; x += blockDim.x) {
+        const float v = b.P[0][(x + y) & 1][(size_t)y * b.S + 4 + (x >> 1)];
+        b.field[(size_t)y * b.nx + x] = to_phi ? 1.0f - v : v;
+    }
 }
 
-__global__ void __launch_bounds__(256) batch_final_residual_kernel(BatchInst *I) {
-    BatchInst &b = I[blockIdx.z];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    float hi = 0.0f, lo = 0.0f;
-    if (x > 0 && y > 0 && x < b.nx - 1 && y < b.ny - 1) {
-        const size_t c = (size_t)y * b.nx + x;
-        const bool fixed = b.occ[c] != 0 || (x == b.gx && y == b.gy);
-        if (!fixed) {
-            const float *u = b.field;
-            resid_pair(u[c + 1], u[c - 1], u[c + b.nx], u[c - b.nx], u[c], hi, lo);
+__global__ void __launch_bounds__(256) batch_final_residual_kernel(BatchInst *I, const int *row_off, int n) {
+    int y;
+    BatchInst &b = I[batch_row(row_off, n, (int)blockIdx.x, &y)];
+    float hi = 0.0f, lo = 0.0f, q = 0.0f;
+    if (y > 0 && y < b.ny - 1) {
+        for (int x = 1 + threadIdx.x; x < b.nx - 1; x += blockDim.x) {
+            const size_t c = (size_t)y * b.nx + x;
+            const bool fixed = b.occ[c] != 0 || (x == b.gx && y == b.gy);
+            if (!fixed) {
+                const float *u = b.field;
+                float h, l;
+                resid_pair(u[c + 1], u[c - 1], u[c + b.nx], u[c - b.nx], u[c], h, l);
+                pair_max(hi, lo, h, l);
+                q = fmaf(h, h, q);
+            }
         }
     }
-    block_max_sum_pair(hi, lo, hi * hi, &b.max64, &b.sum64);
+    block_max_sum_pair(hi, lo, q, &b.max64, &b.sum64);
 }
 
 __global__ void batch_start_kernel(BatchHdr *H) { H->t_start = globaltimer(); }
@@ -231,6 +266,7 @@ __global__ void batch_start_kernel(BatchHdr *H) { H->t_start = globaltimer(); }
 struct BatchLayout {
     BatchHdr *hdr;
     BatchInst *inst;
+    int *row_off;     // prefix sums of the instances' ny (n + 1 entries)
     int2 *list;
     size_t max_tiles;
 };
@@ -240,6 +276,7 @@ static size_t carve_batch(Carver &cv, int n, const hp_instance *in, std::vector<
     BatchLayout l;
     l.hdr = cv.take<BatchHdr>(1);
     l.inst = cv.take<BatchInst>(n > 0 ? n : 1);
+    l.row_off = cv.take<int>((size_t)(n > 0 ? n : 1) + 1);
     size_t max_tiles = 0;
     for (int i = 0; i < n; i++) {
         RBLayout g = rb_layout(in[i].nx, in[i].ny);
@@ -413,21 +450,18 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
     carve_batch(cv, n, inst, &hb, &L);
     if (!cv.ok()) return TW_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    int maxW2 = 0, maxNy = 0, maxNx = 0;
     for (int i = 0; i < n; i++) {
-        if (hb[i].W2 > maxW2) maxW2 = hb[i].W2;
-        if (hb[i].ny > maxNy) maxNy = hb[i].ny;
-        if (hb[i].nx > maxNx) maxNx = hb[i].nx;
-        for (int bb = 0; bb < 2; bb++)
-            for (int c = 0; c < 2; c++)
-                TW_CUDA(cudaMemsetAsync(hb[i].P[bb][c], 0, sizeof(float) * (size_t)hb[i].ny * hb[i].S, s));
         hb[i].active = 1;
         hb[i].ctl.omega = 1.0;
         hb[i].ctl.omega_f = 1.0f;
     }
+    std::vector<int> row_off(n + 1, 0);
+    for (int i = 0; i < n; i++) row_off[i + 1] = row_off[i] + hb[i].ny;
+    const int rows = row_off[n];
     TW_CUDA(cudaMemcpyAsync(L.inst, hb.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s));
-    TW_LAUNCH(batch_pack_kernel, dim3(ceil_div(maxW2 + 31, 128), maxNy, n), 128, 0, s, L.inst,
-              (p->flags & HP_WARM_START) ? 1 : 0);
+    TW_CUDA(cudaMemcpyAsync(L.row_off, row_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+    TW_LAUNCH(batch_zero_kernel, dim3(64, n), 256, 0, s, L.inst);
+    TW_LAUNCH(batch_pack_kernel, rows, 128, 0, s, L.inst, L.row_off, n, (p->flags & HP_WARM_START) ? 1 : 0);
     TW_CHECK_LAUNCH();
     {   // goal checks made by the pack kernel
         std::vector<BatchInst> dev_copy(n);
@@ -515,10 +549,8 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
             if (hh.n_active == 0) break;
         }
     }
-    TW_LAUNCH(batch_unpack_kernel, dim3(ceil_div(maxNx, 256), maxNy, n), 256, 0, s, L.inst,
-              (p->flags & HP_OUT_PHI) ? 1 : 0);
-    TW_LAUNCH(batch_final_residual_kernel, dim3(ceil_div(maxNx, 32), ceil_div(maxNy, 8), n), dim3(32, 8), 0, s,
-              L.inst);
+    TW_LAUNCH(batch_unpack_kernel, rows, 256, 0, s, L.inst, L.row_off, n, (p->flags & HP_OUT_PHI) ? 1 : 0);
+    TW_LAUNCH(batch_final_residual_kernel, rows, 256, 0, s, L.inst, L.row_off, n);
     TW_CHECK_LAUNCH();
     BatchHdr hh;
     TW_CUDA(cudaMemcpyAsync(hb.data(), L.inst, sizeof(BatchInst) * n, cudaMemcpyDeviceToHost, s));

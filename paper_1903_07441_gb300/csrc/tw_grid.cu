@@ -12,12 +12,16 @@
 //                         predicates, occupancy codes written once.
 // The raster is integer/ALU work (a few bytes of HBM per cell).
 #include <math.h>
+#include <string.h>
+
+#include <vector>
 
 #include "common.cuh"
 
 namespace tw {
 
 constexpr int kMaxRings = 64;
+constexpr int kMaxGridJobs = 1 << 16;
 constexpr long long kCoordClamp = 1LL << 30;
 constexpr long long kRadiusClamp = 1LL << 29;
 
@@ -58,7 +62,7 @@ __device__ __forceinline__ long long qpos(double v, double origin, double cell) 
 // from r0 (the same rounded products as a serial loop), so the whole table
 // costs one ring's latency.  The ring count J is the number of rings below
 // the reach plus one (the radii increase).
-__global__ void tw_ring_table_kernel(Params p, RingTab *tab) {
+__device__ __forceinline__ void ring_table_body(const Params &p, RingTab *tab) {
     const int j = threadIdx.x;   // blockDim.x == kMaxRings
     double w = __dmul_rn((double)p.nx, p.cell), h = __dmul_rn((double)p.ny, p.cell);
     double reach = __dsqrt_rn(__dadd_rn(__dmul_rn(w, w), __dmul_rn(h, h)));
@@ -89,6 +93,8 @@ __global__ void tw_ring_table_kernel(Params p, RingTab *tab) {
     tab->Aq[j] = qclamp(__dmul_rn(__ddiv_rn(r, p.cell), 268435456.0), 0, 1LL << 52);
     tab->Cq[j] = qclamp(__dmul_rn(__ddiv_rn(__dmul_rn(0.9, r), p.cell), 268435456.0), 0, 1LL << 52);
 }
+
+__global__ void tw_ring_table_kernel(Params p, RingTab *tab) { ring_table_body(p, tab); }
 
 // Smallest ring containing the fixed-point offset (dx, dy); the last ring otherwise.
 __device__ __forceinline__ int ring_index(int kind, int J, long long dx, long long dy,
@@ -139,11 +145,12 @@ __device__ Disk predict_disk(const tw_track &T, double t, const Params &p, int j
     return d;
 }
 
-__global__ void tw_predict_kernel(Params p, const RingTab *tab, const tw_track *tracks,
-                                  Disk *disks) {
+// Disk idx of one planner: per-cell marking, idx = track * J + ring over the
+// first n * J slots; per-obstacle marking, one disk per track.
+__device__ __forceinline__ void predict_body(const Params &p, const RingTab *tab, const tw_track *tracks,
+                                             Disk *disks, long long idx) {
     int J = tab->J;
     if (J <= 0) return;
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p.mark == TW_MARK_PER_CELL) {
         if (idx >= (long long)p.n * J) return;
         int o = (int)(idx / J), j = (int)(idx % J);
@@ -159,13 +166,18 @@ __global__ void tw_predict_kernel(Params p, const RingTab *tab, const tw_track *
     }
 }
 
+__global__ void tw_predict_kernel(Params p, const RingTab *tab, const tw_track *tracks, Disk *disks) {
+    predict_body(p, tab, tracks, disks, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 constexpr int kTile = 32;            // 32x32 cells per CTA
 constexpr int kRasterThreads = 256;  // 4 cells per thread
 constexpr int kChunk = 1024;         // disks examined per binning round
 
-__global__ void __launch_bounds__(kRasterThreads)
-tw_raster_kernel(Params p, const RingTab *tab, const Disk *disks, const uint8_t *static_occ, uint8_t *occ,
-                 int16_t *ring_out) {
+// Tile (bx, by) of one planner's raster (one CTA of kRasterThreads threads).
+__device__ __forceinline__ void raster_body(const Params &p, const RingTab *tab, const Disk *disks,
+                                            const uint8_t *static_occ, uint8_t *occ, int16_t *ring_out, int bx,
+                                            int by) {
     __shared__ long long sRq[kMaxRings], sAq[kMaxRings], sCq[kMaxRings];
     __shared__ Disk sList[kChunk];
     __shared__ int sCount, sJmin, sJmax;
@@ -183,7 +195,7 @@ tw_raster_kernel(Params p, const RingTab *tab, const Disk *disks, const uint8_t 
     if (tid == 0) { sJmin = 1 << 30; sJmax = -1; sCount = 0; }
     __syncthreads();
     const long long rxq = tab->rxq, ryq = tab->ryq, hxq = tab->hxq, hyq = tab->hyq;
-    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    const int x0 = bx * kTile, y0 = by * kTile;
     const int lx = tid % kTile;
     const int x = x0 + lx;
     int rj[4];
@@ -212,10 +224,16 @@ tw_raster_kernel(Params p, const RingTab *tab, const Disk *disks, const uint8_t 
     const long long bx1 = 256LL * min(x0 + kTile - 1, p.nx - 1) + 128;
     const long long by1 = 256LL * min(y0 + kTile - 1, p.ny - 1) + 128;
     if (tjmax >= 0) {
-        for (int base = 0; base < n_disks; base += kChunk) {
-            int lim = min(kChunk, n_disks - base);
+        // candidates: per-cell marking, only the disks of the tile's rings
+        // [tjmin, tjmax] (disk o * J + j), in index order; per obstacle, all
+        const bool per_cell = p.mark == TW_MARK_PER_CELL;
+        const int w = per_cell ? tjmax - tjmin + 1 : 1;
+        const int n_cand = per_cell ? p.n * w : n_disks;
+        for (int base = 0; base < n_cand; base += kChunk) {
+            int lim = min(kChunk, n_cand - base);
             for (int k = tid; k < lim; k += kRasterThreads) {
-                Disk d = disks[base + k];
+                const int c = base + k;
+                Disk d = disks[per_cell ? (c / w) * J + tjmin + c % w : c];
                 if (d.j >= 0 && (d.j < tjmin || d.j > tjmax)) continue;
                 long long ex = max(0LL, max(bx0 - (long long)d.px, (long long)d.px - bx1));
                 long long ey = max(0LL, max(by0 - (long long)d.py, (long long)d.py - by1));
@@ -252,6 +270,61 @@ tw_raster_kernel(Params p, const RingTab *tab, const Disk *disks, const uint8_t 
             if (ring_out) ring_out[c] = (int16_t)rj[r];
         }
     }
+}
+
+__global__ void __launch_bounds__(kRasterThreads)
+tw_raster_kernel(Params p, const RingTab *tab, const Disk *disks, const uint8_t *static_occ, uint8_t *occ,
+                 int16_t *ring_out) {
+    raster_body(p, tab, disks, static_occ, occ, ring_out, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// ---- many planners in three launches ----------------------------------------
+// Per planner: its parameters, ring table, output pointers and its ranges in
+// the concatenated tracks, disk slots (n_tracks * kMaxRings each) and tiles.
+struct JobPtrs {
+    const uint8_t *static_occ;
+    uint8_t *occ;
+    int16_t *ring;
+    long long track_off, slot_off;
+    int tile_off, tiles_x;
+};
+
+// Largest i in [0, n) with off[i] <= v (off non-decreasing, off[0] = 0 <= v).
+template <class I>
+__device__ __forceinline__ int job_of(const I *off, int n, long long v) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((long long)off[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void tw_ring_table_batch_kernel(const Params *P, RingTab *tabs) {
+    const Params p = P[blockIdx.x];
+    ring_table_body(p, tabs + blockIdx.x);
+}
+
+__global__ void tw_predict_batch_kernel(const Params *P, const RingTab *tabs, const tw_track *tracks, Disk *disks,
+                                        const long long *slot_off, const JobPtrs *jobs, int n) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= slot_off[n]) return;
+    // the planner whose slot range holds g (planners without tracks have empty ranges)
+    const int i = job_of(slot_off, n + 1, g);
+    const Params p = P[i];
+    predict_body(p, tabs + i, tracks + jobs[i].track_off, disks + slot_off[i], g - slot_off[i]);
+}
+
+__global__ void __launch_bounds__(kRasterThreads)
+tw_raster_batch_kernel(const Params *P, const RingTab *tabs, const Disk *disks, const int *tile_off,
+                       const JobPtrs *jobs, int n) {
+    const int t = (int)blockIdx.x;
+    const int i = job_of(tile_off, n + 1, t);
+    const Params p = P[i];
+    const JobPtrs J = jobs[i];
+    const int lt = t - J.tile_off;
+    raster_body(p, tabs + i, disks + J.slot_off, J.static_occ, J.occ, J.ring, lt % J.tiles_x, lt / J.tiles_x);
 }
 
 // ---------------------------------------------------------------------------
@@ -312,6 +385,55 @@ static int ring_count(const tw_grid *g, const tw_pose *robot, const tw_ring_law 
         r = r * L->growth;
     }
     return J;
+}
+
+static Params make_params(const tw_grid *g, const tw_pose *robot, const tw_ring_law *law, int n_tracks) {
+    Params p;
+    memset(&p, 0, sizeof(p));
+    p.nx = g->nx; p.ny = g->ny; p.n = n_tracks; p.mark = law->mark; p.kind = law->kind;
+    p.n_rings = law->n_rings; p.time_outer = law->time_outer;
+    p.cell = g->cell; p.ox = g->ox; p.oy = g->oy;
+    p.rx = robot->x; p.ry = robot->y; p.hx = robot->hx; p.hy = robot->hy; p.speed = robot->speed;
+    p.r0 = law->r0; p.growth = law->growth; p.q = law->q_accel; p.kappa = law->kappa;
+    p.d_safe = law->d_safe;
+    return p;
+}
+
+// Workspace of tw_build_grids: a head the host fills and copies in one transfer
+// (parameters, output pointers, range offsets, all tracks), then the ring
+// tables and the disk slots the kernels write.
+struct JobsLayout {
+    Params *P;
+    JobPtrs *jobs;
+    int *tile_off;
+    long long *slot_off;
+    tw_track *tracks;
+    size_t head_bytes;
+    RingTab *tabs;
+    Disk *disks;
+};
+
+static size_t carve_jobs(Carver &cv, int n, long long n_tracks, long long n_slots, JobsLayout *out) {
+    JobsLayout l;
+    l.P = cv.take<Params>(n);
+    l.jobs = cv.take<JobPtrs>(n);
+    l.tile_off = cv.take<int>(n + 1);
+    l.slot_off = cv.take<long long>(n + 1);
+    l.tracks = cv.take<tw_track>(n_tracks > 0 ? n_tracks : 1);
+    l.head_bytes = cv.need;
+    l.tabs = cv.take<RingTab>(n);
+    l.disks = cv.take<Disk>(n_slots > 0 ? n_slots : 1);
+    if (out) *out = l;
+    return cv.need;
+}
+
+static bool valid_job(const tw_grid_job &j) {
+    if (!valid_grid(&j.grid) || !valid_law(&j.law) || !valid_pose(&j.robot) || !j.occ_dev || j.n_tracks < 0 ||
+        (j.n_tracks > 0 && !j.tracks))
+        return false;
+    for (int o = 0; o < j.n_tracks; o++)
+        if (!valid_track(j.tracks[o])) return false;
+    return ring_count(&j.grid, &j.robot, &j.law) > 0;
 }
 
 struct GridLayout {
@@ -417,15 +539,7 @@ extern "C" int tw_build_grid(const tw_grid *g, const tw_pose *robot, const tw_tr
     carve_grid(cv, n_tracks, kMaxRings, &L);
     if (!cv.ok()) return TW_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-
-    Params p;
-    memset(&p, 0, sizeof(p));
-    p.nx = g->nx; p.ny = g->ny; p.n = n_tracks; p.mark = law->mark; p.kind = law->kind;
-    p.n_rings = law->n_rings; p.time_outer = law->time_outer;
-    p.cell = g->cell; p.ox = g->ox; p.oy = g->oy;
-    p.rx = robot->x; p.ry = robot->y; p.hx = robot->hx; p.hy = robot->hy; p.speed = robot->speed;
-    p.r0 = law->r0; p.growth = law->growth; p.q = law->q_accel; p.kappa = law->kappa;
-    p.d_safe = law->d_safe;
+    const Params p = make_params(g, robot, law, n_tracks);
 
     if (n_tracks > 0)
         TW_CUDA(cudaMemcpyAsync(L.tracks, tracks, sizeof(tw_track) * (size_t)n_tracks,
@@ -440,6 +554,72 @@ extern "C" int tw_build_grid(const tw_grid *g, const tw_pose *robot, const tw_tr
     dim3 grid(ceil_div(g->nx, kTile), ceil_div(g->ny, kTile));
     TW_LAUNCH(tw_raster_kernel, grid, kRasterThreads, 0, s, p, L.tab, L.disks, static_occ_dev, occ_dev,
               ring_dev);
+    TW_CHECK_LAUNCH();
+    return TW_OK;
+}
+
+extern "C" size_t tw_build_grids_workspace_size(int n, const tw_grid_job *jobs) {
+    if (n < 1 || !jobs) return 0;
+    long long nt = 0;
+    for (int i = 0; i < n; i++) nt += jobs[i].n_tracks > 0 ? jobs[i].n_tracks : 0;
+    Carver cv;
+    return carve_jobs(cv, n, nt, nt * kMaxRings, nullptr);
+}
+
+extern "C" int tw_build_grids(int n, const tw_grid_job *jobs, void *workspace, size_t workspace_bytes,
+                              void *stream) {
+    if (n < 1 || n > kMaxGridJobs || !jobs) return TW_EINVAL;
+    long long nt = 0, tiles = 0;
+    for (int i = 0; i < n; i++) {
+        if (!valid_job(jobs[i])) return TW_EINVAL;
+        nt += jobs[i].n_tracks;
+        tiles += (long long)ceil_div(jobs[i].grid.nx, kTile) * ceil_div(jobs[i].grid.ny, kTile);
+    }
+    if (tiles >= (1LL << 31)) return TW_EINVAL;
+    if (!workspace || !ws_aligned(workspace)) return TW_EWORKSPACE;
+    Carver cv(workspace, workspace_bytes);
+    JobsLayout D;
+    carve_jobs(cv, n, nt, nt * kMaxRings, &D);
+    if (!cv.ok()) return TW_EWORKSPACE;
+    // the head, laid out as on the device, filled on the host and copied once
+    std::vector<char> head(D.head_bytes);
+    Carver hc(head.data(), head.size());
+    JobsLayout H;
+    carve_jobs(hc, n, nt, nt * kMaxRings, &H);   // the head part of H lies in `head`
+    long long to = 0, so = 0;
+    int tf = 0;
+    for (int i = 0; i < n; i++) {
+        const tw_grid_job &j = jobs[i];
+        H.P[i] = make_params(&j.grid, &j.robot, &j.law, j.n_tracks);
+        JobPtrs q;
+        q.static_occ = j.static_occ_dev;
+        q.occ = j.occ_dev;
+        q.ring = j.ring_dev;
+        q.track_off = to;
+        q.slot_off = so;
+        q.tile_off = tf;
+        q.tiles_x = (int)ceil_div(j.grid.nx, kTile);
+        H.jobs[i] = q;
+        H.tile_off[i] = tf;
+        H.slot_off[i] = so;
+        if (j.n_tracks > 0) memcpy(H.tracks + to, j.tracks, sizeof(tw_track) * (size_t)j.n_tracks);
+        to += j.n_tracks;
+        so += (long long)j.n_tracks * kMaxRings;
+        tf += (int)(ceil_div(j.grid.nx, kTile) * ceil_div(j.grid.ny, kTile));
+    }
+    H.tile_off[n] = tf;
+    H.slot_off[n] = so;
+    cudaStream_t s = (cudaStream_t)stream;
+    TW_CUDA(cudaMemcpyAsync(workspace, head.data(), D.head_bytes, cudaMemcpyHostToDevice, s));
+    TW_LAUNCH(tw_ring_table_batch_kernel, n, kMaxRings, 0, s, D.P, D.tabs);
+    TW_CHECK_LAUNCH();
+    if (so > 0) {
+        TW_LAUNCH(tw_predict_batch_kernel, ceil_div((size_t)so, 128), 128, 0, s, D.P, D.tabs, D.tracks, D.disks,
+                  D.slot_off, D.jobs, n);
+        TW_CHECK_LAUNCH();
+    }
+    TW_LAUNCH(tw_raster_batch_kernel, (unsigned)tf, kRasterThreads, 0, s, D.P, D.tabs, D.disks, D.tile_off, D.jobs,
+              n);
     TW_CHECK_LAUNCH();
     return TW_OK;
 }

@@ -114,6 +114,40 @@ def test_build_grid_rejects_bad_input_on_host(lib):
     assert _bad_grid_call(lib, tracks=bad) == tw.TW_EINVAL
 
 
+def test_build_grids_rejects_bad_input_on_host(lib):
+    """The batched raster validates every job (as tw_build_grid does) before it
+    launches anything, so these calls never touch the (fake) device pointers."""
+    good = scenes.synth_tracks(scenes.rng.Stream(1), np.array([[1.0, 1.0]]), np.array([[0.1, 0.0]]),
+                               np.array([0.3]))
+    keep = []
+
+    def job(nx=64, cell=0.05, robot=(0.5, 0.5, 1.0, 0.0, 0.75), law=None, tracks=None, occ=256):
+        tr = np.ascontiguousarray(good if tracks is None else tracks, dtype=np.float64)
+        keep.append(tr)
+        return tw.tw_grid_job(tw.make_grid(nx, 64, cell), tw.make_pose(robot), tw.make_law(law or scenes.RingLaw()),
+                              tr.ctypes.data if len(tr) else None, len(tr), None, occ, None)
+
+    def call(*jobs, ws=256, nbytes=1 << 24):
+        arr = (tw.tw_grid_job * len(jobs))(*jobs)
+        return lib.tw_build_grids(len(jobs), arr, ctypes.c_void_p(ws), nbytes, None)
+
+    arr = (tw.tw_grid_job * 2)(job(), job(nx=100))
+    need = lib.tw_build_grids_workspace_size(2, arr)
+    assert need > lib.tw_build_grids_workspace_size(1, arr) > 0
+    assert lib.tw_build_grids(0, arr, ctypes.c_void_p(256), 1 << 20, None) == tw.TW_EINVAL
+    assert call(job(), job(nx=2)) == tw.TW_EINVAL
+    assert call(job(cell=0.0), job()) == tw.TW_EINVAL
+    assert call(job(), job(robot=(0.5, 0.5, 0.5, 0.0, 0.75))) == tw.TW_EINVAL
+    assert call(job(law=scenes.RingLaw(growth=1.0))) == tw.TW_EINVAL
+    bad = good.copy(); bad[0, 2] = np.nan
+    assert call(job(), job(tracks=bad)) == tw.TW_EINVAL
+    bad = good.copy(); bad[0, 4 + 2] = bad[0, 4 + 8] = 1.0    # not PSD
+    assert call(job(tracks=bad)) == tw.TW_EINVAL
+    assert call(job(occ=None)) == tw.TW_EINVAL
+    assert call(job(), job(), nbytes=need - 1) == tw.TW_EWORKSPACE
+    assert call(job(), ws=4096 + 8) == tw.TW_EWORKSPACE
+
+
 def test_workspace_errors_and_sizes(lib):
     g = tw.make_grid(64, 64, 0.05)
     robot = tw.make_pose([0.5, 0.5, 1.0, 0.0, 0.75])

@@ -95,6 +95,41 @@ def test_raster_batch_instances(dev):
         _assert_raster_equal(scenes.batch_instance(seed), dev)
 
 
+def test_raster_many_planners_in_one_call(dev):
+    """tw_build_grids: uneven planners (own sizes, laws, tracks; with and
+    without static map, ring output or tracks, both ring kinds and marking
+    modes) rastered in one call give the oracle's codes and rings bit for bit."""
+    scs = [scenes.batch_instance(5100 + i) for i in range(12)]
+    laws = [sc.law for sc in scs]
+    laws[1] = scenes.RingLaw(kind=scenes.RING_ELLIPTIC, r0=0.4, growth=1.25)
+    laws[2] = scenes.RingLaw(mark=scenes.MARK_PER_OBSTACLE)
+    laws[3] = scenes.RingLaw(kind=scenes.RING_ELLIPTIC, mark=scenes.MARK_PER_OBSTACLE, time_outer=1)
+    tracks = [sc.tracks for sc in scs]
+    tracks[4] = np.zeros((0, 21))
+    odd = scenes.Scene("odd", 0, 37, 5, 0.05, static_occ=None)
+    odd.robot = np.array([0.3, 0.1, 0.6, 0.8, 0.75])
+    scs.append(odd); laws.append(scenes.RingLaw(r0=0.1, growth=1.4)); tracks.append(scs[0].tracks[:7])
+    jobs = []
+    for i, (sc, law, tr) in enumerate(zip(scs, laws, tracks)):
+        static = None
+        if sc.static_occ is not None and i != 5:
+            static = torch.from_numpy(np.ascontiguousarray(sc.static_occ)).to(dev)
+        ring = torch.empty((sc.ny, sc.nx), dtype=torch.int16, device=dev) if i != 6 else None
+        jobs.append({"grid": tw.make_grid(sc.nx, sc.ny, sc.cell, sc.ox, sc.oy), "robot": sc.robot, "law": law,
+                     "tracks": tr, "static_occ": static, "ring": ring})
+    outs = tw.tw_build_grids(jobs)
+    torch.cuda.synchronize()
+    for i, ((occ, ring), sc, law, tr) in enumerate(zip(outs, scs, laws, tracks)):
+        so = "scene" if i != 5 else None
+        occ_ref, ring_ref, _ = oracle.build_grid(sc, law=law, tracks=tr, static_occ=so)
+        assert np.array_equal(occ.cpu().numpy(), occ_ref), i
+        if ring is not None:
+            assert np.array_equal(ring.cpu().numpy(), ring_ref), i
+    # a second call reusing the cached workspace, one job
+    (occ0, _), = tw.tw_build_grids(jobs[:1])
+    assert np.array_equal(occ0.cpu().numpy(), outs[0][0].cpu().numpy())
+
+
 def test_raster_full_size_2048_with_tracks(dev):
     sc = scenes.static2048()
     st = scenes.rng.Stream(42)
