@@ -190,7 +190,7 @@ typedef struct {
     int tblock;        /* temporal-blocking depth T, sweeps fused per launch (0 = library default):
                           HP_RBSOR takes 1..7 (default 7 on deep tiles when the field has at least
                           96 of them -- about 2048 x 1400 cells and up -- else 4); hp_relax_batched
-                          takes 2 or 4 (anything else: autotuned) */
+                          takes 2, 4 or 7 (anything else: autotuned) */
     int flags;         /* HP_WARM_START | HP_OUT_PHI | HP_TIMING | HP_HOST_LOOP | HP_POLISH */
 } hp_params;
 
@@ -265,7 +265,8 @@ int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, f
  * persistent, grid-stride kernel over the tiles of every still-active
  * instance, with per-instance omega, residual and convergence (converged
  * instances drop out).  The blocking depth T is autotuned per batch shape
- * (p->tblock 2 or 4 forces it; the tuning sweeps count towards the solve).
+ * among 2, 4 (8 x 8-row tiles) and 7 (12 x 14-row tiles) (p->tblock 2, 4
+ * or 7 forces it; the tuning sweeps count towards the solve).
  * n: 1..1024 instances.  p: method HP_RBSOR, FP32; tol, max_sweeps, omega
  * (0 = adaptive) and check_every apply to every instance; HP_WARM_START reads
  * u from field_dev, HP_OUT_PHI writes phi (not both).  stats: host array of n,

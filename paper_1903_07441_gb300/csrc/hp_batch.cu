@@ -31,8 +31,16 @@
 
 namespace tw {
 
-constexpr int kBRows = 8, kBWarps = 8;
 constexpr int kMaxBatch = 1024;
+
+// Tile configuration per blocking depth, as for the single field: T <= 4,
+// 8 rows x 8 warps (two CTAs per SM); T = 7, 14 rows x 12 warps (one CTA per
+// SM, half the bytes per update of T = 4 and a quarter of T = 2).
+template <int T>
+struct BCfg {
+    static constexpr int RB = T <= 4 ? 8 : 14;
+    static constexpr int WARPS = T <= 4 ? 8 : 12;
+};
 
 struct BatchInst {
     int nx, ny, gx, gy;
@@ -66,11 +74,12 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 template <int T>
 struct BShape {
     static constexpr int HK4 = (T + 1 + 3) / 4, HY = 2 * T;
-    static constexpr int KI4 = 32 - 2 * HK4, YI = kBWarps * kBRows - 2 * HY;
+    static constexpr int KI4 = 32 - 2 * HK4, YI = BCfg<T>::WARPS * BCfg<T>::RB - 2 * HY;
 };
 
 static void tiles_for(int T, int W4, int ny, int *tx, int *ty) {
-    int KI4 = 32 - 2 * ((T + 4) / 4), YI = kBWarps * kBRows - 4 * T;
+    const int rows = T <= 4 ? BCfg<4>::WARPS * BCfg<4>::RB : BCfg<7>::WARPS * BCfg<7>::RB;
+    int KI4 = 32 - 2 * ((T + 4) / 4), YI = rows - 4 * T;
     *tx = (W4 + KI4 - 1) / KI4;
     *ty = (ny + YI - 1) / YI;
 }
@@ -131,20 +140,20 @@ __global__ void batch_pack_kernel(BatchInst *I, const int *row_off, int n, int w
 }
 
 template <int T>
-__global__ void __launch_bounds__(kBWarps * 32)
+__global__ void __launch_bounds__(BCfg<T>::WARPS * 32, T <= 4 ? 2 : 1)
 batch_tb_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const BatchHdr *__restrict__ H,
                 int parity) {
-    __shared__ float4 s_top[2][kBWarps][32];
-    __shared__ float4 s_bot[2][kBWarps][32];
+    constexpr int RB = BCfg<T>::RB, WARPS = BCfg<T>::WARPS;
+    __shared__ float4 s_top[2][WARPS][32];
+    __shared__ float4 s_bot[2][WARPS][32];
     const int n_active = H->n_active;
     for (int t = blockIdx.x; t < n_active; t += gridDim.x) {
         __syncthreads();   // the previous tile's exchange buffers are free again
         const int2 it = list[t];
         const BatchInst &b = I[it.x];
         const int bx = it.y % b.tx, by = it.y / b.tx;
-        tb_tile<T, kBRows, kBWarps>(b.P[parity][0], b.P[parity][1], b.P[1 - parity][0],
-                                           b.P[1 - parity][1], b.MR, b.MB, b.ny, b.W4, b.S, b.MW,
-                                           b.ctl.omega_f, bx, by, s_top, s_bot);
+        tb_tile<T, RB, WARPS>(b.P[parity][0], b.P[parity][1], b.P[1 - parity][0], b.P[1 - parity][1], b.MR, b.MB,
+                              b.ny, b.W4, b.S, b.MW, b.ctl.omega_f, bx, by, s_top, s_bot);
     }
 }
 
@@ -317,23 +326,25 @@ struct BatchGraph {
 };
 static std::vector<BatchGraph> g_batch_graphs;
 
-static int persistent_grid(const void *func, int threads) {
+static int persistent_grid(const void *func, int threads, size_t smem) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, func, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, func, threads, smem);
     if (per < 1) per = 1;
     return sms * per;
 }
 
 template <int T>
 static void launch_batch_sweep(BatchLayout &L, int parity, cudaStream_t s) {
-    const int grid = persistent_grid((const void *)batch_tb_kernel<T>, kBWarps * 32);
-    TW_LAUNCH((batch_tb_kernel<T>), grid, kBWarps * 32, 0, s, L.inst, L.list, L.hdr, parity);
+    constexpr int threads = BCfg<T>::WARPS * 32;
+    const int grid = persistent_grid((const void *)batch_tb_kernel<T>, threads, 0);
+    TW_LAUNCH((batch_tb_kernel<T>), grid, threads, 0, s, L.inst, L.list, L.hdr, parity);
 }
 
 static void launch_batch_sweep_T(int T, BatchLayout &L, int parity, cudaStream_t s) {
-    if (T == 4) launch_batch_sweep<4>(L, parity, s);
+    if (T == 7) launch_batch_sweep<7>(L, parity, s);
+    else if (T == 4) launch_batch_sweep<4>(L, parity, s);
     else launch_batch_sweep<2>(L, parity, s);
 }
 
@@ -341,7 +352,8 @@ static void launch_batch_residual_T(int T, BatchLayout &L, cudaStream_t s) {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (T == 4) TW_LAUNCH((batch_residual_kernel<4>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
+    if (T == 7) TW_LAUNCH((batch_residual_kernel<7>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
+    else if (T == 4) TW_LAUNCH((batch_residual_kernel<4>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
     else TW_LAUNCH((batch_residual_kernel<2>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
 }
 
@@ -383,14 +395,14 @@ static int build_batch_graph(BatchLayout L, int T, int K, int max_rounds, BatchG
 // Autotuner: time each candidate depth with two launches of Gauss-Seidel
 // sweeps (omega = 1) on the batch; the sweeps count towards the solve.
 static int autotune(BatchLayout &L, std::vector<BatchInst> &hb, int n, cudaStream_t s, int *T_out, int *gs_sweeps) {
-    const int cands[2] = {2, 4};
+    const int cands[3] = {2, 4, 7};
     float best = FLT_MAX;
     int bestT = 4;
     cudaEvent_t a, b;
     TW_CUDA(cudaEventCreate(&a));
     TW_CUDA(cudaEventCreate(&b));
     *gs_sweeps = 0;
-    for (int ci = 0; ci < 2; ci++) {
+    for (int ci = 0; ci < 3; ci++) {
         const int T = cands[ci];
         std::vector<int2> lst;
         for (int i = 0; i < n; i++) {
@@ -476,7 +488,7 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
     // pick the blocking depth (cached per batch shape)
     int T = p->tblock;
     int gs_sweeps = 0;
-    if (T != 2 && T != 4) {
+    if (T != 2 && T != 4 && T != 7) {
         auto key = std::make_tuple(dev, (const void *)workspace, n, cells);
         auto f = g_tuned_T.find(key);
         if (f != g_tuned_T.end()) {

@@ -35,7 +35,7 @@ def _batch(n, seed0, lo=40, hi=260):
     return out
 
 
-@pytest.mark.parametrize("tblock", [0, 2, 4])
+@pytest.mark.parametrize("tblock", [0, 2, 4, 7])
 def test_batched_matches_oracle_and_single_solver(dev, tblock):
     cases = _batch(10, 8100)
     occs = [torch.from_numpy(o).to(dev) for _, o in cases]
@@ -52,8 +52,35 @@ def test_batched_matches_oracle_and_single_solver(dev, tblock):
                                  params=tw.Params(tol=1e-6))
         assert np.abs(u - single.cpu().numpy()).max() <= tau * 2e-6 + 1e-7
         assert l > 0.0
-    if tblock in (2, 4):
+    if tblock in (2, 4, 7):
         assert all(st["tblock"] == tblock for st in stats)
+
+
+@pytest.mark.parametrize("tblock", [2, 4, 7])
+def test_batched_sweeps_equal_single_field_sweeps(dev, tblock):
+    """At a fixed omega and sweep count the batched tile kernel (persistent, one
+    tile list over all instances) computes exactly what the single-field kernel
+    computes for each instance: the same bits, ragged tiles included."""
+    rng = np.random.default_rng(tblock)
+    shapes = [(300, 200), (700, 523), (1030, 67), (61, 1500), (9, 7), (2048, 300)]
+    occs, goals = [], []
+    for nx, ny in shapes:
+        occ = (rng.random((ny, nx)) < 0.2).astype(np.uint8)
+        g = (nx // 2, ny // 2)
+        occ[g[1], g[0]] = 0
+        occs.append(occ)
+        goals.append(g)
+    n_sw = 56 if tblock == 7 else 64   # two check intervals
+    prm = tw.Params(omega=1.9, tol=0.0, max_sweeps=n_sw, tblock=tblock)
+    occ_t = [torch.from_numpy(o).to(dev) for o in occs]
+    fields, stats, _ = tw.hp_relax_batched(occ_t, goals, params=prm)
+    torch.cuda.synchronize()
+    for o, g, f, st in zip(occ_t, goals, fields, stats):
+        assert st["sweeps"] == n_sw and st["tblock"] == tblock
+        ny, nx = o.shape
+        single, s1 = tw.hp_relax(tw.make_grid(nx, ny, 0.05), o, g, params=prm)
+        assert s1["sweeps"] == n_sw and s1["tblock"] == tblock
+        assert torch.equal(f, single), (nx, ny)
 
 
 def test_batched_blocked_goal_is_reported_per_instance(dev):
