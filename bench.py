@@ -511,8 +511,10 @@ def run_batched(args, dev, tw):
     jobs = [{"grid": g, "robot": sc.robot, "tracks": sc.tracks, "law": sc.law, "static_occ": st_, "occ": o}
             for sc, g, st_, o in zip(scs, grids, statics, occs)]
 
-    def rasters_batched():   # all planners in one call
-        tw.tw_build_grids(jobs)
+    gbatch = tw.GridBatch(jobs)
+
+    def rasters_batched():   # all planners in one call (job table prepared once)
+        gbatch.run()
 
     rasters()
     torch.cuda.synchronize()

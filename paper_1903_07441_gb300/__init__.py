@@ -289,35 +289,47 @@ def tw_build_grid(grid: tw_grid, robot, tracks: np.ndarray, law, static_occ=None
     return occ, ring
 
 
+class GridBatch:
+    """A prepared tw_build_grids call: the job table (grids, poses, laws, track
+    and buffer pointers) is built once and run() rasters every job.  The track
+    arrays are read at each run(), so a replanning loop updates them in place.
+    jobs: list of dicts with keys grid, robot, tracks (host float64 [n, 21]),
+    law, and optionally static_occ, occ, ring (device tensors)."""
+
+    def __init__(self, jobs, device="cuda"):
+        torch = _torch()
+        self._lib = load()
+        n = len(jobs)
+        self._arr = (tw_grid_job * n)()
+        self._keep, self.outputs = [], []
+        for i, j in enumerate(jobs):
+            g = j["grid"]
+            tr = np.ascontiguousarray(j.get("tracks") if j.get("tracks") is not None else np.zeros((0, 21)),
+                                      dtype=np.float64).reshape(-1, TRACK_DOUBLES)
+            occ = j.get("occ")
+            if occ is None:
+                occ = torch.empty((g.ny, g.nx), dtype=torch.uint8, device=device)
+            ring, st_ = j.get("ring"), j.get("static_occ")
+            self._keep.append((tr, st_))
+            self._arr[i] = tw_grid_job(g, make_pose(j["robot"]), make_law(j["law"]),
+                                       tr.ctypes.data if len(tr) else None, len(tr),
+                                       _ptr(st_) if st_ is not None else None, _ptr(occ),
+                                       _ptr(ring) if ring is not None else None)
+            self.outputs.append((occ, ring))
+        self.tracks = [k[0] for k in self._keep]
+        self._dev = self.outputs[0][0].device
+        self._ws = workspace(self._lib.tw_build_grids_workspace_size(n, self._arr), self._dev, "grids")
+
+    def run(self):
+        st = self._lib.tw_build_grids(len(self._arr), self._arr, _ptr(self._ws), self._ws.numel(),
+                                      _stream(self._dev))
+        _check("tw_build_grids", st)
+        return self.outputs
+
+
 def tw_build_grids(jobs, device="cuda"):
-    """Many time-warped rasters in one call.  jobs: list of dicts with keys grid,
-    robot, tracks (host float64 [n, 21]), law, and optionally static_occ, occ,
-    ring (device tensors).  Returns the list of (occ, ring)."""
-    torch = _torch()
-    lib = load()
-    n = len(jobs)
-    arr = (tw_grid_job * n)()
-    keep, outs = [], []
-    for i, j in enumerate(jobs):
-        g = j["grid"]
-        tr = np.ascontiguousarray(j.get("tracks") if j.get("tracks") is not None else np.zeros((0, 21)),
-                                  dtype=np.float64).reshape(-1, TRACK_DOUBLES)
-        keep.append(tr)
-        occ = j.get("occ")
-        if occ is None:
-            occ = torch.empty((g.ny, g.nx), dtype=torch.uint8, device=device)
-        ring = j.get("ring")
-        st_ = j.get("static_occ")
-        arr[i] = tw_grid_job(g, make_pose(j["robot"]), make_law(j["law"]),
-                             tr.ctypes.data if len(tr) else None, len(tr),
-                             _ptr(st_) if st_ is not None else None, _ptr(occ),
-                             _ptr(ring) if ring is not None else None)
-        outs.append((occ, ring))
-    dev = outs[0][0].device
-    ws = workspace(lib.tw_build_grids_workspace_size(n, arr), dev, "grids")
-    st = lib.tw_build_grids(n, arr, _ptr(ws), ws.numel(), _stream(dev))
-    _check("tw_build_grids", st)
-    return outs
+    """Many time-warped rasters in one call (see GridBatch).  Returns the list of (occ, ring)."""
+    return GridBatch(jobs, device).run()
 
 
 def tw_nearest_free(grid: tw_grid, occ, x, y):

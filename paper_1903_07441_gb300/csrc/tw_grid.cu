@@ -14,6 +14,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -181,6 +182,7 @@ __device__ __forceinline__ void raster_body(const Params &p, const RingTab *tab,
     __shared__ long long sRq[kMaxRings], sAq[kMaxRings], sCq[kMaxRings];
     __shared__ Disk sList[kChunk];
     __shared__ int sCount, sJmin, sJmax;
+    __shared__ unsigned int sCover[2];   // rings whose cells in this tile a disk covers entirely
     const int tid = threadIdx.x;
     const int J = tab->J;
     const int kind = tab->kind;
@@ -192,7 +194,7 @@ __device__ __forceinline__ void raster_body(const Params &p, const RingTab *tab,
         sAq[j] = tab->Aq[j];
         sCq[j] = tab->Cq[j];
     }
-    if (tid == 0) { sJmin = 1 << 30; sJmax = -1; sCount = 0; }
+    if (tid == 0) { sJmin = 1 << 30; sJmax = -1; sCount = 0; sCover[0] = 0u; sCover[1] = 0u; }
     __syncthreads();
     const long long rxq = tab->rxq, ryq = tab->ryq, hxq = tab->hxq, hyq = tab->hyq;
     const int x0 = bx * kTile, y0 = by * kTile;
@@ -238,15 +240,30 @@ __device__ __forceinline__ void raster_body(const Params &p, const RingTab *tab,
                 long long ex = max(0LL, max(bx0 - (long long)d.px, (long long)d.px - bx1));
                 long long ey = max(0LL, max(by0 - (long long)d.py, (long long)d.py - by1));
                 if (ex * ex + ey * ey <= d.r2) {
-                    int slot = atomicAdd(&sCount, 1);
-                    sList[slot] = d;
+                    // the farthest corner of the tile's cell-centre box inside the disk: the (convex)
+                    // disk holds every cell centre of the tile, so its ring is covered outright
+                    long long fx = max((long long)d.px - bx0, bx1 - (long long)d.px);
+                    long long fy = max((long long)d.py - by0, by1 - (long long)d.py);
+                    if (fx * fx + fy * fy <= d.r2) {
+                        if (d.j >= 0) {
+                            atomicOr(&sCover[d.j >> 5], 1u << (d.j & 31));
+                        } else {
+                            atomicOr(&sCover[0], ~0u);
+                            atomicOr(&sCover[1], ~0u);
+                        }
+                    } else {
+                        int slot = atomicAdd(&sCount, 1);
+                        sList[slot] = d;
+                    }
                 }
             }
             __syncthreads();
             const int cnt = sCount;
+            const unsigned int cov0 = sCover[0], cov1 = sCover[1];
 #pragma unroll
             for (int r = 0; r < 4; r++) {
                 if (code[r] != TW_FREE || rj[r] < 0) continue;
+                if (((rj[r] < 32 ? cov0 : cov1) >> (rj[r] & 31)) & 1u) { code[r] = TW_DYNAMIC; continue; }
                 int y = y0 + tid / kTile + 8 * r;
                 long long cx = 256LL * x + 128, cy = 256LL * y + 128;
                 for (int k = 0; k < cnt; k++) {
@@ -558,6 +575,55 @@ extern "C" int tw_build_grid(const tw_grid *g, const tw_pose *robot, const tw_tr
     return TW_OK;
 }
 
+// Pinned host staging for the head of tw_build_grids, one buffer per device,
+// reused across calls and held under a lock from filling to the copy: before
+// it is refilled, the copy that last read it has completed (an event recorded
+// after that copy).  Pinned memory lets the copy run asynchronously at full
+// link speed, where a pageable source would first be staged by the driver.
+namespace {
+struct PinnedStage {
+    int dev;
+    char *p;
+    size_t cap;
+    cudaEvent_t ev;
+    bool used;
+};
+std::mutex g_stage_mutex;
+std::vector<PinnedStage> g_stages;
+}  // namespace
+
+// Under the lock: a pinned buffer of `bytes` (contents undefined), fill(buf),
+// then one asynchronous copy to dst on s.
+template <class F>
+static int staged_copy(void *dst, size_t bytes, cudaStream_t s, F fill) {
+    int dev = 0;
+    TW_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_stage_mutex);
+    PinnedStage *st = nullptr;
+    for (auto &x : g_stages)
+        if (x.dev == dev) st = &x;
+    if (!st) {
+        PinnedStage ns = {dev, nullptr, 0, nullptr, false};
+        TW_CUDA(cudaEventCreateWithFlags(&ns.ev, cudaEventDisableTiming));
+        g_stages.push_back(ns);
+        st = &g_stages.back();
+    }
+    if (st->used) TW_CUDA(cudaEventSynchronize(st->ev));   // the last copy out of the buffer is done
+    if (st->cap < bytes) {
+        if (st->p) cudaFreeHost(st->p);
+        st->p = nullptr;
+        st->cap = 0;
+        const size_t cap = bytes + bytes / 2 + 4096;
+        TW_CUDA(cudaMallocHost((void **)&st->p, cap));
+        st->cap = cap;
+    }
+    fill(st->p);
+    TW_CUDA(cudaMemcpyAsync(dst, st->p, bytes, cudaMemcpyHostToDevice, s));
+    TW_CUDA(cudaEventRecord(st->ev, s));
+    st->used = true;
+    return TW_OK;
+}
+
 extern "C" size_t tw_build_grids_workspace_size(int n, const tw_grid_job *jobs) {
     if (n < 1 || !jobs) return 0;
     long long nt = 0;
@@ -581,36 +647,38 @@ extern "C" int tw_build_grids(int n, const tw_grid_job *jobs, void *workspace, s
     JobsLayout D;
     carve_jobs(cv, n, nt, nt * kMaxRings, &D);
     if (!cv.ok()) return TW_EWORKSPACE;
-    // the head, laid out as on the device, filled on the host and copied once
-    std::vector<char> head(D.head_bytes);
-    Carver hc(head.data(), head.size());
-    JobsLayout H;
-    carve_jobs(hc, n, nt, nt * kMaxRings, &H);   // the head part of H lies in `head`
-    long long to = 0, so = 0;
-    int tf = 0;
-    for (int i = 0; i < n; i++) {
-        const tw_grid_job &j = jobs[i];
-        H.P[i] = make_params(&j.grid, &j.robot, &j.law, j.n_tracks);
-        JobPtrs q;
-        q.static_occ = j.static_occ_dev;
-        q.occ = j.occ_dev;
-        q.ring = j.ring_dev;
-        q.track_off = to;
-        q.slot_off = so;
-        q.tile_off = tf;
-        q.tiles_x = (int)ceil_div(j.grid.nx, kTile);
-        H.jobs[i] = q;
-        H.tile_off[i] = tf;
-        H.slot_off[i] = so;
-        if (j.n_tracks > 0) memcpy(H.tracks + to, j.tracks, sizeof(tw_track) * (size_t)j.n_tracks);
-        to += j.n_tracks;
-        so += (long long)j.n_tracks * kMaxRings;
-        tf += (int)(ceil_div(j.grid.nx, kTile) * ceil_div(j.grid.ny, kTile));
-    }
-    H.tile_off[n] = tf;
-    H.slot_off[n] = so;
+    // the head, laid out as on the device, filled in pinned host memory and copied once
     cudaStream_t s = (cudaStream_t)stream;
-    TW_CUDA(cudaMemcpyAsync(workspace, head.data(), D.head_bytes, cudaMemcpyHostToDevice, s));
+    int tf = 0;
+    long long so = 0;
+    int e = staged_copy(workspace, D.head_bytes, s, [&](char *head) {
+        Carver hc(head, D.head_bytes);
+        JobsLayout H;
+        carve_jobs(hc, n, nt, nt * kMaxRings, &H);   // the head part of H lies in `head`
+        long long to = 0;
+        for (int i = 0; i < n; i++) {
+            const tw_grid_job &j = jobs[i];
+            H.P[i] = make_params(&j.grid, &j.robot, &j.law, j.n_tracks);
+            JobPtrs q;
+            q.static_occ = j.static_occ_dev;
+            q.occ = j.occ_dev;
+            q.ring = j.ring_dev;
+            q.track_off = to;
+            q.slot_off = so;
+            q.tile_off = tf;
+            q.tiles_x = (int)ceil_div(j.grid.nx, kTile);
+            H.jobs[i] = q;
+            H.tile_off[i] = tf;
+            H.slot_off[i] = so;
+            if (j.n_tracks > 0) memcpy(H.tracks + to, j.tracks, sizeof(tw_track) * (size_t)j.n_tracks);
+            to += j.n_tracks;
+            so += (long long)j.n_tracks * kMaxRings;
+            tf += (int)(ceil_div(j.grid.nx, kTile) * ceil_div(j.grid.ny, kTile));
+        }
+        H.tile_off[n] = tf;
+        H.slot_off[n] = so;
+    });
+    if (e) return e;
     TW_LAUNCH(tw_ring_table_batch_kernel, n, kMaxRings, 0, s, D.P, D.tabs);
     TW_CHECK_LAUNCH();
     if (so > 0) {

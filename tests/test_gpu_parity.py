@@ -128,6 +128,19 @@ def test_raster_many_planners_in_one_call(dev):
     # a second call reusing the cached workspace, one job
     (occ0, _), = tw.tw_build_grids(jobs[:1])
     assert np.array_equal(occ0.cpu().numpy(), outs[0][0].cpu().numpy())
+    # a prepared batch re-run after its tracks were updated in place (the next frame)
+    gb = tw.GridBatch(jobs[:3])
+    gb.run()
+    for k in range(3):
+        if len(gb.tracks[k]):
+            gb.tracks[k][:, 0] += 0.4
+            gb.tracks[k][:, 2] *= -1.0
+    outs2 = gb.run()
+    torch.cuda.synchronize()
+    for k in range(3):
+        so = "scene" if k != 5 else None
+        occ_ref, ring_ref, _ = oracle.build_grid(scs[k], law=laws[k], tracks=gb.tracks[k], static_occ=so)
+        assert np.array_equal(outs2[k][0].cpu().numpy(), occ_ref), k
 
 
 def test_raster_full_size_2048_with_tracks(dev):
