@@ -392,6 +392,23 @@ int kf_update(tw_track *tracks, int n, const double *z, double dt, double q_acce
 int kf_init(tw_track *tracks, int n, const double *z, const double *radius, double r_meas,
             double p_vel);
 
+/* hp_omega_update: one step of the adaptive SOR factor hp_relax uses
+ * (omega = 0 in hp_params), exposed for callers that drive their own
+ * red-black SOR and for tests.  omega: the factor of the last check interval;
+ * lambda: the observed decay rate of the residual per sweep over it (0..1);
+ * nx, ny: the grid.  Young's relation for consistently ordered matrices,
+ * (lambda + omega - 1)^2 = lambda omega^2 mu^2, gives the Jacobi spectral
+ * radius mu and omega_opt = 2 / (1 + sqrt(1 - mu^2)), moved 10 % of the way
+ * towards 2 (pre-asymptotic decay underestimates mu).  Returns the new factor:
+ * never below omega, never above the empty-box optimum for nx x ny (no
+ * occupancy has a larger one), and omega itself while lambda <= (omega - 1)^(3/4)
+ * (at or past the optimum, where lambda says nothing about mu) or lambda is
+ * outside (0, 1).  hp_omega_cap returns that upper bound;
+ * hp_omega_initial the first factor of an adaptive solve. */
+double hp_omega_update(double omega, double lambda, int nx, int ny);
+double hp_omega_cap(int nx, int ny);
+double hp_omega_initial(int nx, int ny);
+
 /* ---- diagnostics -------------------------------------------------------------- */
 const char *tw_status_string(int status);
 int tw_last_cuda_error(void);          /* last cudaError_t seen by the library */

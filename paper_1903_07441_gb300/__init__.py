@@ -33,7 +33,7 @@ WS_CONV_AUTO, WS_CONV_SIMT, WS_CONV_MMA = 0, 1, 2
 
 EXPORTS = (
     "tw_build_grid_workspace_size", "tw_build_grid", "tw_build_grids_workspace_size", "tw_build_grids",
-    "tw_ring_count", "tw_nearest_free",
+    "tw_ring_count", "tw_nearest_free", "hp_omega_update", "hp_omega_cap", "hp_omega_initial",
     "hp_relax_workspace_size", "hp_relax", "hp_relax_noalloc", "hp_relax_dirichlet", "hp_residual",
     "hp_relax_batched_workspace_size", "hp_relax_batched",
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
@@ -137,6 +137,12 @@ def load() -> ctypes.CDLL:
     lib.tw_build_grid_workspace_size.restype = Z
     lib.tw_build_grid.argtypes = [P, P, P, I, P, P, P, P, P, Z, P]
     lib.tw_build_grid.restype = I
+    lib.hp_omega_update.argtypes = [ctypes.c_double, ctypes.c_double, I, I]
+    lib.hp_omega_update.restype = ctypes.c_double
+    lib.hp_omega_cap.argtypes = [I, I]
+    lib.hp_omega_cap.restype = ctypes.c_double
+    lib.hp_omega_initial.argtypes = [I, I]
+    lib.hp_omega_initial.restype = ctypes.c_double
     lib.tw_build_grids_workspace_size.argtypes = [I, P]
     lib.tw_build_grids_workspace_size.restype = Z
     lib.tw_build_grids.argtypes = [I, P, P, Z, P]

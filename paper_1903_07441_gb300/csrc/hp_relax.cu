@@ -560,6 +560,17 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
 
 using namespace tw;
 
+extern "C" double hp_omega_update(double omega, double lambda, int nx, int ny) {
+    if (nx < 3 || ny < 3) return omega;
+    return sor_adapt(omega, lambda, sor_omega_cap(nx, ny));
+}
+
+extern "C" double hp_omega_cap(int nx, int ny) { return (nx < 3 || ny < 3) ? 0.0 : sor_omega_cap(nx, ny); }
+
+extern "C" double hp_omega_initial(int nx, int ny) {
+    return (nx < 3 || ny < 3) ? 0.0 : sor_initial_omega(nx, ny);
+}
+
 extern "C" size_t hp_relax_workspace_size(int nx, int ny, const hp_params *p) {
     if (nx < 3 || ny < 3) return 0;
     Carver cv;

@@ -211,3 +211,100 @@ def test_product_path_has_no_cpu_fallback():
     if not torch.cuda.is_available():
         with pytest.raises(RuntimeError):
             tw.hp_relax(tw.make_grid(8, 8, 0.1), torch.zeros((8, 8), dtype=torch.uint8), (3, 3))
+
+
+# ---------------------------------------------------------------------------
+# the adaptive SOR factor (host logic, pinned by brute-force linear algebra)
+# ---------------------------------------------------------------------------
+
+def _jacobi_and_sor(free):
+    """Dense Jacobi matrix of the free cells (1/4 of the free 4-neighbours; the
+    rest are Dirichlet cells) and the red-black SOR iteration matrix builder."""
+    idx = -np.ones(free.shape, int)
+    cells = np.argwhere(free)
+    idx[free] = np.arange(len(cells))
+    n = len(cells)
+    Jm = np.zeros((n, n))
+    for k, (y, x) in enumerate(cells):
+        for dy, dx in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+            j = idx[y + dy, x + dx]
+            if j >= 0:
+                Jm[k, j] = 0.25
+    red = ((cells[:, 0] + cells[:, 1]) % 2) == 0
+
+    def sor(omega):
+        # red half-sweep then black: u <- u + omega (J u - u) colour by colour
+        n_ = len(cells)
+        M = np.eye(n_)
+        for colour in (red, ~red):
+            S = np.eye(n_)
+            S[colour] = (1 - omega) * np.eye(n_)[colour] + omega * Jm[colour]
+            M = S @ M
+        return M
+    return Jm, sor
+
+
+def test_omega_cap_is_the_empty_box_optimum_and_bounds_every_occupancy(lib):
+    for nx, ny in ((9, 7), (12, 12), (5, 16)):
+        free = np.zeros((ny, nx), bool)
+        free[1:-1, 1:-1] = True
+        Jm, _ = _jacobi_and_sor(free)
+        mu = np.abs(np.linalg.eigvals(Jm)).max()
+        assert abs(lib.hp_omega_cap(nx, ny) - 2.0 / (1.0 + np.sqrt(1.0 - mu * mu))) < 1e-12
+        rng = np.random.default_rng(nx * ny)
+        for _ in range(5):   # obstacles only lower the Jacobi spectral radius (Perron-Frobenius)
+            f = free & (rng.random(free.shape) > 0.25)
+            if f.sum() < 2:
+                continue
+            Jf, _ = _jacobi_and_sor(f)
+            assert np.abs(np.linalg.eigvals(Jf)).max() <= mu + 1e-12
+    # the first factor of an adaptive solve never exceeds the cap
+    for n in (3, 5, 9, 64, 255, 256, 1023, 1024, 4096):
+        w0 = lib.hp_omega_initial(n, n)
+        assert 0.0 < w0 <= lib.hp_omega_cap(n, n) + 1e-15
+        assert w0 == min({True: 1.9, False: 1.85 if n >= 256 else 1.75}[n >= 1024], lib.hp_omega_cap(n, n))
+
+
+def test_omega_update_recovers_mu_through_youngs_relation(lib):
+    """On a red-black ordered box the spectral radius of the SOR matrix at
+    omega < omega_opt, computed by brute force, gives back the Jacobi spectral
+    radius: the update lands 10 % of the way from omega_opt to 2 (capped)."""
+    nx, ny = 14, 12
+    free = np.zeros((ny, nx), bool)
+    free[1:-1, 1:-1] = True
+    free[5:8, 4:9] = False   # an obstacle block keeps the matrix consistently ordered
+    Jm, sor = _jacobi_and_sor(free)
+    mu = np.abs(np.linalg.eigvals(Jm)).max()
+    w_opt = 2.0 / (1.0 + np.sqrt(1.0 - mu * mu))
+    cap = lib.hp_omega_cap(nx, ny)
+    adapted = 0
+    for omega in (1.0, 1.1, 1.2, 1.3, 0.5 * (1.0 + w_opt), w_opt - 0.01):
+        lam = np.abs(np.linalg.eigvals(sor(omega))).max()   # decay rate per full red + black sweep
+        got = lib.hp_omega_update(omega, lam, nx, ny)
+        if lam <= (omega - 1.0) ** 0.75:   # too close to omega - 1 to tell mu: omega is kept
+            assert got == omega
+            continue
+        want = min(cap, 2.0 - 0.9 * (2.0 - w_opt))
+        assert abs(got - max(omega, want)) < 1e-9, (omega, lam, got, want)
+        adapted += 1
+    assert adapted >= 3
+    # past the optimum every eigenvalue has modulus omega - 1: omega is kept
+    for omega in (w_opt + 0.01, w_opt + 0.05):
+        lam = np.abs(np.linalg.eigvals(sor(omega))).max()
+        assert abs(lam - (omega - 1.0)) < 1e-6
+        assert lib.hp_omega_update(omega, lam, nx, ny) == omega
+
+
+def test_omega_update_edge_cases(lib):
+    for lam in (0.0, -0.1, 1.0, 1.5, float("nan")):
+        assert lib.hp_omega_update(1.7, lam, 512, 512) == 1.7
+    # never below the current factor, never above the cap
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        n = int(rng.integers(3, 3000))
+        w = 1.0 + 0.99 * rng.random()
+        lam = rng.random()
+        got = lib.hp_omega_update(w, lam, n, n)
+        assert got >= w
+        assert got <= max(w, lib.hp_omega_cap(n, n)) + 1e-15
+    assert lib.hp_omega_update(1.5, 0.5, 2, 10) == 1.5   # not a grid
