@@ -208,6 +208,7 @@ typedef struct {
     int loop;          /* how the convergence loop ran: HP_LOOP_HOST or HP_LOOP_GRAPH */
     int polishes;      /* polish launches tried (HP_POLISH) */
     int polished;      /* 1: the output is the accepted polished copy */
+    double resid_check;/* the FP32 residual max of the loop's last check (0 if it made none) */
 } hp_stats;
 
 #define HP_LOOP_HOST 0     /* host-driven: HP_HOST_LOOP, HP_TIMING, HP_JACOBI, HP_MIXED, or a cap

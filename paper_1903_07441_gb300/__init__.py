@@ -91,7 +91,7 @@ class hp_stats(ctypes.Structure):
                 ("resid_l2", ctypes.c_double), ("omega", ctypes.c_double), ("checks", ctypes.c_int),
                 ("sweep_launches", ctypes.c_int), ("sweep_ms", ctypes.c_double), ("tblock", ctypes.c_int),
                 ("loop", ctypes.c_int), ("polishes", ctypes.c_int),
-                ("polished", ctypes.c_int)]
+                ("polished", ctypes.c_int), ("resid_check", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

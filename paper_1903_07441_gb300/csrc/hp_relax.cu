@@ -462,6 +462,7 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
     st->sweeps = c.sweeps + c.psweeps;
     st->polishes = c.polishes;
     st->polished = c.in_alt;
+    st->resid_check = c.checks ? c.r_last : 0.0;
     st->checks = c.checks;
     st->omega = c.omega;
     st->sweep_launches = launches;
@@ -542,6 +543,7 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
         local.sweeps = c.sweeps + c.psweeps;
         local.polishes = c.polishes;
         local.polished = c.in_alt;
+        local.resid_check = c.checks ? c.r_last : 0.0;
         local.checks = c.checks;
         local.omega = c.omega;
         local.sweep_launches = c.checks * KT + c.polishes;

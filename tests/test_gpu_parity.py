@@ -341,6 +341,32 @@ def test_deep_tiles_graph_matches_host_loop(dev):
     assert np.abs(e - a).max() <= 1e-4   # both within their a-posteriori bounds of the same solution
 
 
+@pytest.mark.parametrize("nx,ny,tb", [(2048, 1500, 7), (1800, 1403, 7), (600, 300, 4), (333, 97, 2)])
+def test_loop_check_residual_is_the_fields_residual(dev, nx, ny, tb):
+    """The residual the convergence loop stops on is the FP32 residual max of
+    the whole output field, exactly: the loop's last check equals the max over
+    the free cells of the FP32 residual of the returned field (neighbour sums
+    in FP32, then one rounding of 0.25 s - c), for ragged tiles and either loop."""
+    rng = np.random.default_rng(nx + ny)
+    occ = (rng.random((ny, nx)) < 0.25).astype(np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+    goal = (nx // 3, ny // 2)
+    occ[goal[1], goal[0]] = 0
+    fixed = oracle.dirichlet_from_occ(occ, goal)[1].astype(bool)
+    K = 28 if tb == 7 else 32
+    for flags in (0, tw.HP_HOST_LOOP):
+        for n_int in (1, 3):
+            u, st = _relax(occ, goal, dev, tw.Params(omega=1.93, tol=1e-30, max_sweeps=K * n_int, tblock=tb,
+                                                      flags=flags))
+            assert st["sweeps"] == K * n_int and st["checks"] == n_int and st["tblock"] == tb
+            u32 = u.astype(np.float32)
+            c = u32[1:-1, 1:-1]
+            s32 = (u32[1:-1, :-2] + u32[1:-1, 2:]) + (u32[:-2, 1:-1] + u32[2:, 1:-1])
+            t = (0.25 * s32.astype(np.float64) - c.astype(np.float64)).astype(np.float32)
+            r = float(np.abs(t)[~fixed[1:-1, 1:-1]].max())
+            assert st["resid_check"] == r, (st["resid_check"], r)
+
+
 def _polish_scenes():
     rng = np.random.default_rng(77)
     occ = (rng.random((1500, 2048)) < 0.25).astype(np.uint8)
