@@ -239,8 +239,52 @@ __global__ void __launch_bounds__(256) mx_inner_residual_kernel(RBLayout g, int 
 // half-sweep, so after the first one they hit L1).
 constexpr int kMxRows = 8, kMxWarps = 8;
 
+// One half-sweep of the correction equation for colour C (compile-time, so the
+// register arrays stay in registers): e <- e + omega ((1/4) sum nbr + q - e).
+template <int C, class S>
+__device__ __forceinline__ void mx_half(float4 (&v)[2][kMxRows], const uint32_t (&m)[2], float omega,
+                                        float4 (&s_top)[2][kMxWarps][32], float4 (&s_bot)[2][kMxWarps][32],
+                                        const S *__restrict__ Q, int y0, bool kin, int ny, int Sst, int k) {
+    constexpr int RB = kMxRows, WARPS = kMxWarps, O = 1 - C;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    s_top[C][warp][lane] = v[O][0];
+    s_bot[C][warp][lane] = v[O][RB - 1];
+    __syncthreads();
+    const float4 above = warp > 0 ? s_bot[C][warp - 1][lane] : z4;
+    const float4 below = warp < WARPS - 1 ? s_top[C][warp + 1][lane] : z4;
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+        const float4 mid = v[O][r];
+        const float4 up = r == 0 ? above : v[O][r - 1];
+        const float4 dn = r == RB - 1 ? below : v[O][r + 1];
+        float l0, l1, l2, l3, r0, r1, r2, r3;
+        if (((r + C) & 1) != 0) {   // rows start even
+            const float ex = __shfl_down_sync(0xffffffffu, mid.x, 1);
+            l0 = mid.x; l1 = mid.y; l2 = mid.z; l3 = mid.w; r0 = mid.y; r1 = mid.z; r2 = mid.w; r3 = ex;
+        } else {
+            const float ex = __shfl_up_sync(0xffffffffu, mid.w, 1);
+            l0 = ex; l1 = mid.x; l2 = mid.y; l3 = mid.z; r0 = mid.x; r1 = mid.y; r2 = mid.z; r3 = mid.w;
+        }
+        const int yq = y0 + r;
+        const bool qin = kin && yq >= 0 && yq < ny;
+        const float4 q = qin ? Store<S>::load4(Q + (size_t)yq * Sst + 4 + k) : z4;
+        float4 cv = v[C][r];
+        const uint32_t bits = (m[C] >> (4 * r)) & 0xFu;
+        const float n0 = fmaf(omega, fmaf(0.25f, (l0 + r0) + (up.x + dn.x), q.x - cv.x), cv.x);
+        const float n1 = fmaf(omega, fmaf(0.25f, (l1 + r1) + (up.y + dn.y), q.y - cv.y), cv.y);
+        const float n2 = fmaf(omega, fmaf(0.25f, (l2 + r2) + (up.z + dn.z), q.z - cv.z), cv.z);
+        const float n3 = fmaf(omega, fmaf(0.25f, (l3 + r3) + (up.w + dn.w), q.w - cv.w), cv.w);
+        cv.x = (bits & 1u) ? n0 : cv.x;
+        cv.y = (bits & 2u) ? n1 : cv.y;
+        cv.z = (bits & 4u) ? n2 : cv.z;
+        cv.w = (bits & 8u) ? n3 : cv.w;
+        v[C][r] = cv;
+    }
+}
+
 template <int T, class S>
-__global__ void __launch_bounds__(kMxWarps * 32)
+__global__ void __launch_bounds__(kMxWarps * 32, 2)
 mx_tb_kernel(const S *__restrict__ Rin, const S *__restrict__ Bin, S *__restrict__ Rout, S *__restrict__ Bout,
              const S *__restrict__ Qr, const S *__restrict__ Qb, const uint32_t *__restrict__ MR,
              const uint32_t *__restrict__ MB, int ny, int W4, int Sst, int MW, const float *__restrict__ omega_p) {
@@ -272,42 +316,9 @@ mx_tb_kernel(const S *__restrict__ Rin, const S *__restrict__ Bin, S *__restrict
         }
     }
 #pragma unroll 1
-    for (int p = 0; p < 2 * T; p++) {
-        const int c = p & 1, o = 1 - c, buf = p & 1;
-        s_top[buf][warp][lane] = v[o][0];
-        s_bot[buf][warp][lane] = v[o][RB - 1];
-        __syncthreads();
-        const float4 above = warp > 0 ? s_bot[buf][warp - 1][lane] : z4;
-        const float4 below = warp < WARPS - 1 ? s_top[buf][warp + 1][lane] : z4;
-#pragma unroll
-        for (int r = 0; r < RB; r++) {
-            const float4 mid = v[o][r];
-            const float4 up = r == 0 ? above : v[o][r - 1];
-            const float4 dn = r == RB - 1 ? below : v[o][r + 1];
-            const int s = (r + c) & 1;   // rows start even
-            float l0, l1, l2, l3, r0, r1, r2, r3;
-            if (s) {
-                const float ex = __shfl_down_sync(0xffffffffu, mid.x, 1);
-                l0 = mid.x; l1 = mid.y; l2 = mid.z; l3 = mid.w; r0 = mid.y; r1 = mid.z; r2 = mid.w; r3 = ex;
-            } else {
-                const float ex = __shfl_up_sync(0xffffffffu, mid.w, 1);
-                l0 = ex; l1 = mid.x; l2 = mid.y; l3 = mid.z; r0 = mid.x; r1 = mid.y; r2 = mid.z; r3 = mid.w;
-            }
-            const int yq = y0 + r;
-            const bool qin = kin && yq >= 0 && yq < ny;
-            const float4 q = qin ? Store<S>::load4((c ? Qb : Qr) + (size_t)yq * Sst + 4 + k) : z4;
-            float4 cv = v[c][r];
-            const uint32_t bits = ((c ? m[1] : m[0]) >> (4 * r)) & 0xFu;
-            const float n0 = fmaf(omega, fmaf(0.25f, (l0 + r0) + (up.x + dn.x), q.x - cv.x), cv.x);
-            const float n1 = fmaf(omega, fmaf(0.25f, (l1 + r1) + (up.y + dn.y), q.y - cv.y), cv.y);
-            const float n2 = fmaf(omega, fmaf(0.25f, (l2 + r2) + (up.z + dn.z), q.z - cv.z), cv.z);
-            const float n3 = fmaf(omega, fmaf(0.25f, (l3 + r3) + (up.w + dn.w), q.w - cv.w), cv.w);
-            cv.x = (bits & 1u) ? n0 : cv.x;
-            cv.y = (bits & 2u) ? n1 : cv.y;
-            cv.z = (bits & 4u) ? n2 : cv.z;
-            cv.w = (bits & 8u) ? n3 : cv.w;
-            v[c][r] = cv;
-        }
+    for (int p = 0; p < T; p++) {   // red then black, colour-indexed exchange buffers
+        mx_half<0, S>(v, m, omega, s_top, s_bot, Qr, y0, kin, ny, Sst, k);
+        mx_half<1, S>(v, m, omega, s_top, s_bot, Qb, y0, kin, ny, Sst, k);
     }
     const bool kint = lane >= HK4 && lane < 32 - HK4 && kin;
     if (kint) {
