@@ -58,7 +58,7 @@ extern "C" {
 
 /* ---- plain-data argument structs ----------------------------------------- */
 typedef struct {
-    int nx, ny;        /* cells; 3 <= nx, ny <= 65536 */
+    int nx, ny;        /* cells; 3 <= nx, ny <= 65535 (a launch dimension per row) */
     double cell;       /* cell side (m), > 0 */
     double ox, oy;     /* world position of the corner of cell (0, 0) (m) */
 } tw_grid;
@@ -277,7 +277,7 @@ int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, f
  * cap, or the first error (per-instance status in stats[i].status, e.g.
  * TW_EGOAL_BLOCKED).  Synchronises `stream`. */
 typedef struct {
-    int nx, ny;              /* grid of this instance (3..65536) */
+    int nx, ny;              /* grid of this instance (3..65535) */
     const uint8_t *occ_dev;  /* device uint8 [ny][nx] occupancy (nonzero = obstacle) */
     int gx, gy;              /* goal cell */
     float *field_dev;        /* device float [ny][nx]: the field (u unless HP_OUT_PHI) */

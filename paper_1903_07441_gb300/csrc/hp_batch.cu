@@ -451,7 +451,7 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
     size_t cells = 0;
     for (int i = 0; i < n; i++) {
         const hp_instance &q = inst[i];
-        if (q.nx < 3 || q.ny < 3 || q.nx > 65536 || q.ny > 65536 || !q.occ_dev || !q.field_dev) return TW_EINVAL;
+        if (q.nx < 3 || q.ny < 3 || q.nx > 65535 || q.ny > 65535 || !q.occ_dev || !q.field_dev) return TW_EINVAL;
         if (q.gx < 1 || q.gy < 1 || q.gx > q.nx - 2 || q.gy > q.ny - 2) return TW_EGOAL_BLOCKED;
         cells += (size_t)q.nx * q.ny;
     }

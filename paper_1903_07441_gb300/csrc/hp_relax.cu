@@ -582,7 +582,7 @@ extern "C" size_t hp_relax_workspace_size(int nx, int ny, const hp_params *p) {
 extern "C" int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *field_dev,
                         const hp_params *p, hp_stats *stats, void *workspace, size_t workspace_bytes,
                         void *stream) {
-    if (!g || g->nx < 3 || g->ny < 3 || g->nx > 65536 || g->ny > 65536 || !occ_dev || !field_dev ||
+    if (!g || g->nx < 3 || g->ny < 3 || g->nx > 65535 || g->ny > 65535 || !occ_dev || !field_dev ||
         !valid_params(p))
         return TW_EINVAL;
     int nx = g->nx, ny = g->ny;
@@ -600,7 +600,7 @@ extern "C" int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy
 extern "C" int hp_relax_dirichlet(int nx, int ny, const uint8_t *fixed_dev, float *u_dev,
                                   const hp_params *p, hp_stats *stats, void *workspace,
                                   size_t workspace_bytes, void *stream) {
-    if (nx < 3 || ny < 3 || nx > 65536 || ny > 65536 || !fixed_dev || !u_dev || !valid_params(p))
+    if (nx < 3 || ny < 3 || nx > 65535 || ny > 65535 || !fixed_dev || !u_dev || !valid_params(p))
         return TW_EINVAL;
     return relax_common(fixed_dev, nx, ny, -1, -1, u_dev, 1, p, stats, workspace, workspace_bytes,
                         (cudaStream_t)stream);

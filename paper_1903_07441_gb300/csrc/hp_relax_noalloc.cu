@@ -57,7 +57,7 @@ extern "C" int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx
                                 const hp_params *p, hp_stats *stats, void *stream) {
     if (!g || !p || (p->flags & HP_TIMING)) return TW_EINVAL;
     if (p->method != HP_RBSOR && p->method != HP_JACOBI) return TW_EINVAL;
-    if (g->nx < 3 || g->ny < 3 || g->nx > 65536 || g->ny > 65536) return TW_EINVAL;
+    if (g->nx < 3 || g->ny < 3 || g->nx > 65535 || g->ny > 65535) return TW_EINVAL;
     const size_t need = hp_relax_workspace_size(g->nx, g->ny, p);
     if (need == 0 || need > kNoAllocScratchBytes) return TW_EWORKSPACE;  // grid too large for the array
     void *ws = nullptr;

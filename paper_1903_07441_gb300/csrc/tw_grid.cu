@@ -351,7 +351,7 @@ tw_raster_batch_kernel(const Params *P, const RingTab *tabs, const Disk *disks, 
 static bool finite(double v) { return isfinite(v) != 0; }
 
 static bool valid_grid(const tw_grid *g) {
-    return g && g->nx >= 3 && g->ny >= 3 && g->nx <= 65536 && g->ny <= 65536 && finite(g->cell) &&
+    return g && g->nx >= 3 && g->ny >= 3 && g->nx <= 65535 && g->ny <= 65535 && finite(g->cell) &&
            g->cell > 0.0 && finite(g->ox) && finite(g->oy);
 }
 

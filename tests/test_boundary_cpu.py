@@ -183,6 +183,10 @@ def test_relax_rejects_bad_params_and_goal_on_host(lib):
     assert call(tw.Params(method=7)) == tw.TW_EINVAL
     assert call(tw.Params(), gx=0, gy=30) == tw.TW_EGOAL_BLOCKED     # on the border
     assert call(tw.Params(), gx=64, gy=30) == tw.TW_EGOAL_BLOCKED    # out of range
+    big = tw.make_grid(64, 65536, 0.05)   # one launch row per grid row: at most 65535 rows
+    cp = tw.Params().c()
+    assert lib.hp_relax(ctypes.byref(big), ctypes.c_void_p(256), 30, 30, ctypes.c_void_p(256), ctypes.byref(cp),
+                        ctypes.byref(st), ctypes.c_void_p(256), 1 << 30, None) == tw.TW_EINVAL
 
 
 def test_warm_start_entry_points_reject_bad_input_on_host(lib):
