@@ -134,7 +134,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
     }
     unsigned int *rmax = &scal->max32;
     RelaxCtl *ctl = &scal->ctl;
-    const dim3 rgrid(ceil_div(L.W4, 64), ceil_div(ny, 4)), rblock(64, 4);
+    const dim3 rgrid = rb_residual_grid(L, ny), rblock(64, 4);
     {   // residual of the current planes
         RBLayout Lc = L;
         Lc.R = R; Lc.B = B;

@@ -88,6 +88,7 @@ int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals,
 // squared residuals of every CTA in l2part[rb_residual_blocks(L, ny)].
 void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s);
 int rb_residual_blocks(const RBLayout &L, int ny);
+dim3 rb_residual_grid(const RBLayout &L, int ny);   // launch grid of rb_residual_kernel (64 x 4 threads)
 
 // Optional CUDA-event timing of the sweep kernels (HP_TIMING).
 struct SweepTimer {

@@ -338,13 +338,17 @@ static int relax_jacobi(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
 }
 
 // Red-black SOR driver on the split layout (pack -> sweeps -> unpack).
-int rb_residual_blocks(const RBLayout &L, int ny) { return (int)(ceil_div(L.W4, 64) * ceil_div(ny, 4)); }
+dim3 rb_residual_grid(const RBLayout &L, int ny) { return dim3(ceil_div(L.W4, 64), ceil_div(ny, 4 * kResidRows)); }
+
+int rb_residual_blocks(const RBLayout &L, int ny) {
+    const dim3 g = rb_residual_grid(L, ny);
+    return (int)(g.x * g.y);
+}
 
 void *rb_residual_kernel_ptr() { return (void *)rb_residual_kernel; }
 
 void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s) {
-    dim3 b(64, 4), gr(ceil_div(L.W4, 64), ceil_div(ny, 4));
-    TW_LAUNCH(rb_residual_kernel, gr, b, 0, s, L, ny, out, l2part);
+    TW_LAUNCH(rb_residual_kernel, rb_residual_grid(L, ny), dim3(64, 4), 0, s, L, ny, out, l2part);
 }
 
 // Red-black SOR driver on the split layout.  By default the check intervals

@@ -68,14 +68,17 @@ __device__ __forceinline__ float resid_row(const float4 c, const float4 mid, con
     return acc;
 }
 
-// One CTA (64 x 4 threads, one float4 of each colour per thread) of the FP32
-// residual check: atomicMax of the CTA's residual max into *out_max and, if
-// l2part is given, the CTA's sum of squared residuals, reduced in a fixed order,
-// into l2part[CTA index].
+// One CTA (64 x 4 threads; each thread one float4 of each colour in
+// kResidRows rows, strided by 4) of the FP32 residual check: atomicMax of the
+// CTA's residual max into *out_max and, if l2part is given, the CTA's sum of
+// squared residuals, reduced in a fixed order, into l2part[CTA index].
+constexpr int kResidRows = 4;
 __device__ __forceinline__ void rb_residual_cta(const RBLayout &L, int ny, unsigned int *out_max, float *l2part) {
     const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
     float r = 0.0f, q = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kResidRows; i++) {
+    const int y = (blockIdx.y * kResidRows + i) * blockDim.y + threadIdx.y + 1;
     if (k4 < L.W4 && y < ny - 1) {
         const int k = 4 * k4;
 #pragma unroll
@@ -98,6 +101,7 @@ __device__ __forceinline__ void rb_residual_cta(const RBLayout &L, int ny, unsig
             if (bits & 4u) { r = fmaxf(r, fabsf(t2)); q = fmaf(t2, t2, q); }
             if (bits & 8u) { r = fmaxf(r, fabsf(t3)); q = fmaf(t3, t3, q); }
         }
+    }
     }
     if (l2part) {   // fixed-order CTA sum: the same partials in every run
         __shared__ float sq[8];
