@@ -45,7 +45,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # DRAM traffic of the dominant kernel from one ncu capture, valid only while
 # the kernel source is unchanged (sha256 of the file that holds it).
-TRAFFIC = {"81fc0ee4ba36eaa4": 17463936 + 2176}   # rb_tb_kernel<7,14,12,1>, profiles/rb_tb_kernel_static2048.md
+TRAFFIC = {"43d78bc176f425ba": 17464832 + 2048}   # rb_tb_kernel<7,14,12,1>, profiles/rb_tb_kernel_static2048.md
 
 
 def _env_int(k, d):
