@@ -354,6 +354,18 @@ def run_twgrid(args, rank, world, dist):
                 "timing": f"CUDA events on the launching stream around the sweep launches of {n_roof} "
                           "further steps of the same workload run with the host-driven loop (HP_TIMING); "
                           "the timed steps above use the graph-driven loop"}
+    # the same launches against the FP32 ALU (the field pair is L2-resident at this size, so the fused
+    # sweeps are bound by instruction issue rather than HBM; reported beside the contract's HBM roofline)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_max = float((clocks or {}).get("sm_max_mhz") or 2070.0)
+    alu_peak = n_sm * 128 * 2 * f_max * 1e6 / 1e12
+    upd = cells * sweeps_per_launch / avg_launch_s
+    roofline["alu_view"] = {"flops_per_update": 7, "achieved_tflops": 7.0 * upd / 1e12, "peak_tflops": alu_peak,
+                            "frac": 7.0 * upd / 1e12 / alu_peak,
+                            "peak_derivation": f"{n_sm} SMs x 128 FP32 lanes x 2 (FMA) x {f_max:.0f} MHz",
+                            "note": "7 flops per useful cell-update (3 additions, then two fused multiply-adds: "
+                                    "0.25 s - c and c + omega t); the Dirichlet select, the halo recomputation "
+                                    "and the colour shuffles are not counted"}
 
     # ---- accuracy of the solved field against the stored FP64 reference of this scene
     accuracy = field_accuracy(u, occ, sc, timed_log[-1][0]) if rank == 0 else None
