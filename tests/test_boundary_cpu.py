@@ -312,3 +312,41 @@ def test_omega_update_edge_cases(lib):
         assert got >= w
         assert got <= max(w, lib.hp_omega_cap(n, n)) + 1e-15
     assert lib.hp_omega_update(1.5, 0.5, 2, 10) == 1.5   # not a grid
+
+
+# ---------------------------------------------------------------------------
+# temporal-blocking halo (host-side check of the tile geometry)
+# ---------------------------------------------------------------------------
+
+def _contaminated_after(T, rows, xcells):
+    """Grid-level red-black sweeps on a tile whose outside is unknown (NaN):
+    which cells of the tile depend on the outside after T full sweeps."""
+    u = np.zeros((rows + 2, xcells + 2))
+    u[0, :] = u[-1, :] = u[:, 0] = u[:, -1] = np.nan
+    yy, xx = np.mgrid[0:rows, 0:xcells]
+    red = ((xx + yy) & 1) == 0
+    for _ in range(T):
+        for colour in (red, ~red):
+            c = u[1:-1, 1:-1]
+            nb = 0.25 * (u[1:-1, :-2] + u[1:-1, 2:] + u[:-2, 1:-1] + u[2:, 1:-1])
+            c[colour] = nb[colour]
+    return np.isnan(u[1:-1, 1:-1])
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 4, 5, 6, 7])
+def test_tile_halo_is_enough_for_T_fused_sweeps(T):
+    """The fused sweep kernels keep a halo of 2T rows and ceil((T + 1) / 4)
+    float4 columns of each colour (8 cells of the row per float4 column) around
+    the tile interior they store; after T red-black sweeps no interior cell may
+    depend on values outside the tile.  Outside values reach exactly 2T rows and
+    2T cells of a row deep: the row halo is the least that works, the column
+    halo that rounded up to whole float4 columns."""
+    hy = 2 * T
+    hx = 8 * ((T + 1 + 3) // 4)
+    rows, xcells = 4 * hy + 16, 2 * hx + 64
+    bad = _contaminated_after(T, rows, xcells)
+    assert not bad[hy:rows - hy, hx:xcells - hx].any()
+    depth_rows = max(i for i in range(rows // 2) if bad[i, hx:xcells - hx].any()) + 1
+    depth_cols = max(j for j in range(xcells // 2) if bad[hy:rows - hy, j].any()) + 1
+    assert depth_rows == 2 * T == hy
+    assert depth_cols == 2 * T <= hx
