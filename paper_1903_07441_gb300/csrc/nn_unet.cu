@@ -1,8 +1,8 @@
 // Learned warm start: a small encoder-decoder network that predicts
 // log(u) (u = 1 - phi) from the occupancy and a goal-distance map, trained on
 // fields the relaxation itself produced.  The relaxation then finishes from
-// the prediction (hp_relax with HP_WARM_START), so it stays both the fallback
-// and the judge of the error.
+// the prediction (hp_relax with HP_WARM_START), so the method's own relaxation
+// still decides the final field and its residual.
 //
 // Network (fully convolutional, input H and W multiples of 8):
 //   enc0  conv3x3 2->32, conv 32->32            @ H     (ReLU after every conv but the head)
