@@ -174,6 +174,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sel), "source": self.mode}
 
 
+CLOCK_REJECT = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clocks_rejected(c) -> str:
+    """Why a timed region's clock record disqualifies it ('' if it does not):
+    a hardware or thermal slowdown, or SM clocks well below their maximum with
+    no reason given (a clock lock left by someone).  sw_power_cap is kept."""
+    bad = sorted(set(c.get("reasons") or []) & set(CLOCK_REJECT))
+    if bad:
+        return ",".join(bad)
+    sm, mx = c.get("sm_mhz"), c.get("sm_max_mhz")
+    if sm and mx and sm < 0.8 * mx and not c.get("reasons"):
+        return f"sm clock {sm:.0f} of {mx:.0f} MHz with no reason"
+    return ""
+
+
 def make_scene(rank: int):
     """Each rank solves its own scene (weak scaling, no data exchanged)."""
     return scenes.static2048(seed=scene_seed(rank))
@@ -287,31 +303,40 @@ def run_twgrid(args, rank, world, dist):
     # ---- device-resident timed region
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = tw.launch_count()
-    barrier()
-    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-    host_ms = []
-    clk.mark_start()
-    ev0.record(stream)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        if i:
-            flush.zero_()
-        h0 = time.perf_counter()
-        step_ev[i][0].record(stream)
-        step(static_d)
-        step_ev[i][1].record(stream)
-        host_ms.append((time.perf_counter() - h0) * 1e3)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    clk.mark_end()
-    clocks = clk.summary()
+
+    def timed_region():
+        stats_log.clear()
+        launches0 = tw.launch_count()
+        barrier()
+        step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+        host_ms = []
+        clk.mark_start()
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            if i:
+                flush.zero_()
+            h0 = time.perf_counter()
+            step_ev[i][0].record(stream)
+            step(static_d)
+            step_ev[i][1].record(stream)
+            host_ms.append((time.perf_counter() - h0) * 1e3)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clk.mark_end()
+        # library kernels only (not the L2-flush memsets)
+        return (clk.summary(), [a.elapsed_time(b) for a, b in step_ev], tw.launch_count() - launches0,
+                ev0.elapsed_time(ev1) / 1e3, wall, host_ms)
+
+    clocks, step_ms, launches, dev_s, wall, host_ms = timed_region()
+    why = clocks_rejected(clocks)
+    if why:   # a throttled (or clock-locked) run is measured once more
+        flush.zero_()
+        clocks, step_ms, launches, dev_s, wall, host_ms = timed_region()
+        clocks["remeasured_after"] = why
     clk.stop()
-    step_ms = [a.elapsed_time(b) for a, b in step_ev]
-    launches = tw.launch_count() - launches0   # library kernels only (not the L2-flush memsets)
-    dev_s = ev0.elapsed_time(ev1) / 1e3
     elapsed = max_over_ranks(max(dev_s, 1e-12), dist, dev)
     sweeps = [s["sweeps"] for s, _, _ in stats_log]
     resid = [s["resid_inf"] for s, _, _ in stats_log]
