@@ -350,3 +350,47 @@ def test_tile_halo_is_enough_for_T_fused_sweeps(T):
     depth_cols = max(j for j in range(xcells // 2) if bad[hy:rows - hy, j].any()) + 1
     assert depth_rows == 2 * T == hy
     assert depth_cols == 2 * T <= hx
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/twgrid.h is a C header: a C program that takes the address of
+    every declared function compiles with gcc (-std=c99, warnings as errors),
+    links against libtwgrid.so and calls the entry points that need no GPU."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    names = sorted(_declared_functions())
+    cuda_inc = "/usr/local/cuda/include"
+    src = ["#include <stdio.h>", "#include \"twgrid.h\"", "int main(void) {", "    void *f[] = {"]
+    src += [f"        (void *){n}," for n in names]
+    src += ["    };",
+            "    int n = 0;",
+            "    for (unsigned i = 0; i < sizeof f / sizeof f[0]; i++) n += f[i] != 0;",
+            "    tw_grid g = {64, 48, 0.05, 0.0, 0.0};",
+            "    tw_pose r = {1.0, 1.0, 1.0, 0.0, 0.75};",
+            "    tw_ring_law law = {TW_RING_CIRCULAR, TW_MARK_PER_CELL, 0.5, 1.3, 0, 1e-4, 2.0, 0.25, 0};",
+            "    printf(\"%d %s|%s|%d|%.6f\\n\", n, tw_version(), tw_status_string(TW_EINVAL),",
+            "           tw_ring_count(&g, &r, &law), hp_omega_cap(64, 48));",
+            "    return 0;", "}"]
+    c = tmp_path / "abi.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(tw.LIB_PATH)
+    cmd = ["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe),
+           "-L", libdir, "-ltwgrid", f"-Wl,-rpath,{libdir}"]
+    if os.path.isdir(cuda_inc):
+        cmd[4:4] = ["-I", cuda_inc]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    count, rest = out.stdout.split(" ", 1)
+    version, status, rings, cap = rest.strip().split("|")
+    assert int(count) == len(names)
+    assert version == lib.tw_version().decode()
+    assert status == tw.status_string(tw.TW_EINVAL)
+    assert int(rings) == lib.tw_ring_count(ctypes.byref(tw.make_grid(64, 48, 0.05)),
+                                           ctypes.byref(tw.make_pose([1.0, 1.0, 1.0, 0.0, 0.75])),
+                                           ctypes.byref(tw.make_law(scenes.RingLaw(q_accel=1e-4))))
+    assert abs(float(cap) - lib.hp_omega_cap(64, 48)) < 1e-6
