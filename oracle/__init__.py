@@ -36,10 +36,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "twgrid_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_twgrid.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_twgrid_omp.so")
 
 OK, NOT_CONVERGED, NO_PATH, EINVAL, EGOAL, ESTART = 0, 1, 2, -1, -2, -3
 
 _lib = None
+_libs = {}
 
 
 def build(force: bool = False) -> str:
@@ -52,11 +54,46 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_threads(force: bool = False):
+    """The same source built with OpenMP (the CPU baseline's multi-core timing); None if the
+    compiler has no OpenMP.  Threads share only order-independent work, so results are the
+    plain build's bit for bit."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        cmd = ["cc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-shared", "-fPIC", "-o", _LIB_OMP + ".tmp", _SRC, "-lm"]
+        try:
+            subprocess.check_call(cmd, stderr=subprocess.DEVNULL)
+        except (subprocess.CalledProcessError, OSError):
+            return None
+        os.replace(_LIB_OMP + ".tmp", _LIB_OMP)
+    return _LIB_OMP
+
+
+def use_threads(n: int) -> int:
+    """Run the following oracle calls on n threads (the OpenMP build) or, for n <= 1, on the
+    plain build.  Returns the thread count in use."""
+    global _lib
+    if n <= 1:
+        _lib = _open(build())
+        return 1
+    path = build_threads()
+    if path is None:
+        _lib = _open(build())
+        return 1
+    _lib = _open(path)
+    return int(_lib.or_set_threads(int(n)))
+
+
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        _lib = _open(build())
+    return _lib
+
+
+def _open(path):
+    if path not in _libs:
+        lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
         i32, f64 = ctypes.c_int, ctypes.c_double
         lib.or_ring_table.argtypes = [i32, f64, f64, i32, f64, i32, f64, f64, f64, P, P]
@@ -80,8 +117,10 @@ def _load():
         lib.or_kf_predict.argtypes = [P, P, f64, f64]
         lib.or_kf_update.argtypes = [P, P, P, f64]
         lib.or_kf_step.argtypes = [P, i32, P, f64, f64, f64]
-        _lib = lib
-    return _lib
+        lib.or_set_threads.argtypes = [i32]
+        lib.or_set_threads.restype = i32
+        _libs[path] = lib
+    return _libs[path]
 
 
 def _p(a: np.ndarray):

@@ -14,6 +14,12 @@
  * pre-stage must round on its own (no fused multiply-add) so that the integer
  * predicates are reproducible bit for bit.
  *
+ * Threads.  The same source is also built with -fopenmp, for timing the
+ * oracle on every host core (the benchmark's CPU baseline).  Threads share
+ * only work whose result does not depend on its order -- independent cells,
+ * maxima -- and every sum keeps its serial order, so both builds return the
+ * same bits; without -fopenmp the pragmas are ignored.
+ *
  * Conventions.  Grids are row-major [ny][nx]; cell (i, j) is column i, row j.
  * Fixed-point coordinates are in 1/256 of a cell relative to the grid origin;
  * the centre of cell (i, j) is (256 i + 128, 256 j + 128).
@@ -22,6 +28,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_NOT_CONVERGED 1
@@ -33,6 +42,19 @@
 #define OR_MAX_RINGS 64
 #define OR_COORD_CLAMP 1073741824LL  /* 2^30 */
 #define OR_RADIUS_CLAMP 536870912LL  /* 2^29 */
+
+/* Threads of the OpenMP build (n > 0 sets them); returns the count in use
+ * (1 in the plain build). */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------
  * a1. Ring table.
@@ -183,6 +205,7 @@ int or_build_grid(int nx, int ny, double cell, double ox, double oy,
         own[o] = ring_of(kind, exq - rxq, eyq - ryq, J, Rq, Aq, Cq, hxq, hyq);
     }
 
+#pragma omp parallel for schedule(dynamic, 8)
     for (int jy = 0; jy < ny; jy++) {
         for (int ix = 0; ix < nx; ix++) {
             size_t c = (size_t)jy * nx + ix;
@@ -245,6 +268,21 @@ void or_residual(const double *u, const uint8_t *fixed, int nx, int ny,
     *r_l2 = sqrt(s);
 }
 
+/* r_inf of or_residual alone (a maximum: the same whatever the order). */
+static double residual_max(const double *u, const uint8_t *fixed, int nx, int ny)
+{
+    double m = 0.0;
+#pragma omp parallel for reduction(max : m)
+    for (int j = 1; j < ny - 1; j++)
+        for (int i = 1; i < nx - 1; i++) {
+            size_t c = (size_t)j * nx + i;
+            if (fixed[c]) continue;
+            double r = fabs(nbr_avg(u, nx, c) - u[c]);
+            if (r > m) m = r;
+        }
+    return m;
+}
+
 /* Eq. 1: Jacobi sweeps until the residual of the current iterate <= tol. */
 int or_jacobi(double *u, const uint8_t *fixed, int nx, int ny, double tol,
               int max_sweeps, int *sweeps_out, double *res_out)
@@ -254,9 +292,9 @@ int or_jacobi(double *u, const uint8_t *fixed, int nx, int ny, double tol,
     double *v = (double *)malloc(N * sizeof(double));
     memcpy(v, u, N * sizeof(double));
     int k = 0;
-    double r, l2;
-    or_residual(u, fixed, nx, ny, &r, &l2);
+    double r = residual_max(u, fixed, nx, ny);
     while (r > tol && k < max_sweeps) {
+#pragma omp parallel for
         for (int j = 1; j < ny - 1; j++)
             for (int i = 1; i < nx - 1; i++) {
                 size_t c = (size_t)j * nx + i;
@@ -264,7 +302,7 @@ int or_jacobi(double *u, const uint8_t *fixed, int nx, int ny, double tol,
             }
         memcpy(u, v, N * sizeof(double));
         k++;
-        or_residual(u, fixed, nx, ny, &r, &l2);
+        r = residual_max(u, fixed, nx, ny);
     }
     free(v);
     *sweeps_out = k;
@@ -300,7 +338,8 @@ int or_gauss_seidel(double *u, const uint8_t *fixed, int nx, int ny, double tol,
 static void apply_A(const double *x, double *y, const uint8_t *fixed, int nx, int ny)
 {
     size_t N = (size_t)nx * ny;
-    for (size_t c = 0; c < N; c++) y[c] = 0.0;
+    memset(y, 0, N * sizeof(double));
+#pragma omp parallel for
     for (int j = 1; j < ny - 1; j++)
         for (int i = 1; i < nx - 1; i++) {
             size_t c = (size_t)j * nx + i;
@@ -314,11 +353,25 @@ static void apply_A(const double *x, double *y, const uint8_t *fixed, int nx, in
         }
 }
 
+/* Sum over free cells of a[c] b[c], in fixed chunks of OR_DOT_CHUNK cells:
+ * each chunk summed in index order, then the chunk sums in chunk order -- the
+ * same association whatever the thread count (chunks are independent). */
+#define OR_DOT_CHUNK 65536
 static double dot_free(const double *a, const double *b, const uint8_t *fixed, size_t N)
 {
+    size_t nc = (N + OR_DOT_CHUNK - 1) / OR_DOT_CHUNK;
+    double *part = (double *)malloc((nc ? nc : 1) * sizeof(double));
+#pragma omp parallel for
+    for (size_t k = 0; k < nc; k++) {
+        size_t lo = k * OR_DOT_CHUNK, hi = lo + OR_DOT_CHUNK < N ? lo + OR_DOT_CHUNK : N;
+        double s = 0.0;
+        for (size_t c = lo; c < hi; c++)
+            if (!fixed[c]) s += a[c] * b[c];
+        part[k] = s;
+    }
     double s = 0.0;
-    for (size_t c = 0; c < N; c++)
-        if (!fixed[c]) s += a[c] * b[c];
+    for (size_t k = 0; k < nc; k++) s += part[k];
+    free(part);
     return s;
 }
 
@@ -359,18 +412,21 @@ int or_cg(double *u, const uint8_t *fixed, int nx, int ny, double source, double
     while (rmax > tol && k < max_iters && rr > 0.0) {
         apply_A(p, Ap, fixed, nx, ny);
         double alpha = rr / dot_free(p, Ap, fixed, N);
+#pragma omp parallel for
         for (size_t c = 0; c < N; c++)
             if (!fixed[c]) { u[c] += alpha * p[c]; r[c] -= alpha * Ap[c]; }
         k++;
         /* every 50 iterations replace the recursive residual by the true one */
         if (k % 50 == 0) {
             apply_A(u, Ap, fixed, nx, ny);
+#pragma omp parallel for
             for (size_t c = 0; c < N; c++) r[c] = fixed[c] ? 0.0 : b[c] - Ap[c];
         }
         double rr_new = dot_free(r, r, fixed, N);
         double beta = rr_new / rr;
         rr = rr_new;
         rmax = 0.0;
+#pragma omp parallel for reduction(max : rmax)
         for (size_t c = 0; c < N; c++) {
             if (fixed[c]) continue;
             p[c] = r[c] + beta * p[c];

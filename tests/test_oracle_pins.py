@@ -389,6 +389,66 @@ def test_inflation_grows_with_covariance_and_time():
     assert r1q == round((0.2 + 2 * math.sqrt(0.05)) / 0.1 * 256)
 
 
+def _cv_prediction(x, P, t, q):
+    """Mean and covariance of the constant-velocity model (Eqs. 9-10) after t
+    seconds, built from the model's definition rather than from any closed-form
+    entry: the transition A(t) as a 4x4 matrix, the propagated covariance
+    A P A^T by matrix products, and the white-noise-acceleration term
+    Q(t) = q * integral_0^t A(s) L L^T A(s)^T ds (L maps the two accelerations
+    onto the velocities), integrated with Simpson's rule, which is exact here
+    because the integrand is a polynomial of degree 2 in s."""
+    def A(s):
+        a = np.eye(4)
+        a[0, 2] = a[1, 3] = s
+        return a
+    L = np.zeros((4, 2))
+    L[2, 0] = L[3, 1] = 1.0
+    f = lambda s: A(s) @ L @ L.T @ A(s).T
+    Q = q * (t / 6.0) * (f(0.0) + 4.0 * f(t / 2.0) + f(t))
+    return A(t) @ x, A(t) @ P @ A(t).T + Q
+
+
+def test_prediction_matches_the_constant_velocity_model_with_process_noise():
+    # a non-diagonal covariance (position-velocity cross terms of both axes, an x-y
+    # coupling that must not matter) and q > 0: every term of the prediction counts
+    rng = np.random.default_rng(11)
+    cell, ox, oy = 0.05, -1.3, 2.1
+    law = scenes.RingLaw(q_accel=0.02, kappa=2.0, d_safe=0.25)
+    G = rng.normal(size=(4, 4)) * np.array([0.15, 0.15, 0.3, 0.3])[:, None]
+    P = G @ G.T + np.diag([0.01, 0.02, 0.05, 0.04])
+    P[0, 2] = P[2, 0] = 0.03     # Pxv
+    P[1, 3] = P[3, 1] = -0.02    # Pyv
+    x = np.array([3.7, -0.4, 0.6, -0.9])
+    radius = 0.3
+    trk = _one_track(*x, radius, P)[0]
+    for t in (0.0, 0.4, 1.3, 3.0, 7.5):
+        mean, S = _cv_prediction(x, P, t, law.q_accel)
+        sigma = math.sqrt(0.5 * (S[0, 0] + S[1, 1]))
+        rho = radius + law.d_safe + law.kappa * sigma
+        pxq, pyq, rhoq = oracle.predict_disk(trk, t, law, cell, ox, oy)
+        # one quantum (cell / 256) of slack for the different rounding order
+        assert abs(pxq - round((mean[0] - ox) / cell * 256)) <= 1, t
+        assert abs(pyq - round((mean[1] - oy) / cell * 256)) <= 1, t
+        assert abs(rhoq - round(rho / cell * 256)) <= 1, (t, rhoq, rho / cell * 256)
+        if t < 1.0:
+            continue
+        # the pin separates the plausible misreadings of Eqs. 9-10 by many quanta
+        def q_rho(s2):
+            return round((radius + law.d_safe + law.kappa * math.sqrt(s2)) / cell * 256)
+        pxx, pyy = S[0, 0], S[1, 1]
+        q3 = law.q_accel * t ** 3 / 3.0
+        wrong = {
+            "no 1/3 on the process noise": 0.5 * (pxx + pyy) + 2.0 * q3,
+            "no process noise": 0.5 * (pxx + pyy) - q3,
+            "no position-velocity cross terms": 0.5 * (pxx + pyy) - 2.0 * t * (P[0, 2] + P[1, 3]) / 2.0,
+            "cross terms once, not twice": 0.5 * (pxx + pyy) - t * (P[0, 2] + P[1, 3]) / 2.0,
+            "velocity variance times t, not t^2": 0.5 * (pxx + pyy) - (t * t - t) * (P[2, 2] + P[3, 3]) / 2.0,
+            "x axis only": pxx,
+        }
+        for name, s2 in wrong.items():
+            assert abs(q_rho(s2) - rhoq) >= 5, (t, name)
+
+
 # ---------------------------------------------------------------------------
 # Kalman filter
 # ---------------------------------------------------------------------------
@@ -552,3 +612,25 @@ def test_stored_static2048_reference_matches_the_scene():
     cells = np.asarray(ref["cells"])
     assert np.all(occ[cells[:, 1], cells[:, 0]] == 0)
     assert 1.0 <= ref["tau_max"] < float(sc.nx) ** 2 and ref["reference_resid_inf"] <= 1e-12
+
+
+def test_threaded_oracle_build_returns_the_same_bits():
+    """The OpenMP build (the CPU baseline's multi-core timing) shares only order-independent work
+    among threads: raster, Jacobi and CG results equal the plain build's bit for bit."""
+    if oracle.build_threads() is None:
+        pytest.skip("no OpenMP in this compiler")
+    sc = scenes.dynamic(seed=1041, side=96, n_obs=16, frames=1, static_shapes=8)
+    try:
+        oracle.use_threads(1)
+        occ1, ring1, _ = oracle.build_grid(sc)
+        u0, fixed = oracle.dirichlet_from_occ(occ1, sc.goal)
+        j1 = oracle.jacobi(u0.copy(), fixed, tol=0.0, max_sweeps=200)[0]
+        c1 = oracle.cg(u0.copy(), fixed, tol=1e-12)[0]
+        assert oracle.use_threads(4) >= 1
+        occ4, ring4, _ = oracle.build_grid(sc)
+        j4 = oracle.jacobi(u0.copy(), fixed, tol=0.0, max_sweeps=200)[0]
+        c4 = oracle.cg(u0.copy(), fixed, tol=1e-12)[0]
+    finally:
+        oracle.use_threads(1)
+    assert np.array_equal(occ1, occ4) and np.array_equal(ring1, ring4)
+    assert np.array_equal(j1, j4) and np.array_equal(c1, c4)
