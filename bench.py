@@ -4,7 +4,8 @@
 One step = one pass of the planner's hot path on one synthetic 2048x2048
 static scene (2000 rectangles and disks at 30 % occupancy): time-warped raster
 (tw_build_grid), relaxation from the cold start u = 0.5 to the residual
-r_inf <= 1e-6 (hp_relax), and the Eq. 3 path with rubber band (plan_path).
+r_inf <= 1e-6 with the field's error estimate held to 1e-5 (hp_relax, etol),
+and the Eq. 3 path with rubber band (plan_path).
 
 Prints one JSON line (rank 0).  `value` is device-resident throughput (inputs
 already in HBM); `e2e` repeats the step through the same C ABI with host
@@ -38,7 +39,9 @@ METRIC = "converged-field solves/s at 2048^2, resid<=1e-6 (plus cell-updates/s v
 UNIT = "solves/s"
 WORKLOAD = ("static2048: 2048x2048 grid, 5 cm cells, 2000 rectangles+disks at 30% occupancy, "
             "goal (2027,2027), robot (20,20); step = raster + cold-start relaxation to r_inf<=1e-6 "
-            "+ Eq.3 path with 100 rubber-band sweeps")
+            "with the error estimate <= 1e-5 + Eq.3 path with 100 rubber-band sweeps from the robot "
+            "(which returns TW_NO_PATH at once: u*(20,20) ~ 1e-12, below the field's accuracy; "
+            "path_reachable times the path from a cell the field resolves)")
 STORAGE_BYTES = 4           # FP32 field
 MASK_BYTES = 1.0 / 8.0      # one Dirichlet bit per cell
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
@@ -261,11 +264,11 @@ def run_twgrid(args, rank, world, dist):
     u_h = torch.empty((sc.ny, sc.nx), dtype=torch.float32).pin_memory()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     method = {"rbsor": tw.HP_RBSOR, "jacobi": tw.HP_JACOBI, "mixed": tw.HP_MIXED}[args.method]
-    params = tw.Params(method=method, tol=args.tol, max_sweeps=args.max_sweeps,
+    params = tw.Params(method=method, tol=args.tol, max_sweeps=args.max_sweeps, etol=args.etol,
                        tblock=args.tblock, storage={"f16": 1, "bf16": 2, "f32": 0}[args.storage])
     # the same solve with the host-driven loop and CUDA events around every batch of sweep launches
     params_timed = tw.Params(method=method, tol=args.tol, max_sweeps=args.max_sweeps, flags=tw.HP_TIMING,
-                             tblock=args.tblock, storage=params.storage)
+                             tblock=args.tblock, storage=params.storage, etol=args.etol)
     max_len = 4 * (sc.nx + sc.ny) * 4
     stats_log = []
 
@@ -394,6 +397,35 @@ def run_twgrid(args, rank, world, dist):
 
     # ---- accuracy of the solved field against the stored FP64 reference of this scene
     accuracy = field_accuracy(u, occ, sc, timed_log[-1][0]) if rank == 0 else None
+    if accuracy is not None:
+        accuracy["err_est"] = timed_log[-1][0]["err_est"]
+
+    # ---- the path from a start the field resolves: the robot's cell (20, 20) has u* ~ 1e-12, below the
+    # accuracy of any field solved to r_inf <= 1e-6, so the step's descent returns TW_NO_PATH at once.
+    # Here the descent starts from the free cell nearest the robot among those with u >= 1e-3 on the
+    # step's own field (chosen outside the timed launches), and is timed with CUDA events.
+    path_reachable = None
+    if rank == 0:
+        pick = (u >= 1e-3) & (occ == 0)
+        yy, xx = torch.nonzero(pick, as_tuple=True)
+        if len(yy):
+            d2 = (xx - sc.start[0]) ** 2 + (yy - sc.start[1]) ** 2
+            j = int(torch.argmin(d2).item())
+            ps = (int(xx[j].item()), int(yy[j].item()))
+            tw.plan_path(grid, u, occ, ps, sc.goal, rubber_iters=100, max_len=max_len)   # warm
+            pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            pms = []
+            for _ in range(5):
+                pa.record(stream)
+                pst_, ppath = tw.plan_path(grid, u, occ, ps, sc.goal, rubber_iters=100, max_len=max_len)
+                pb.record(stream)
+                torch.cuda.synchronize()
+                pms.append(pa.elapsed_time(pb))
+            path_reachable = {"start": ps, "u_start": float(u[ps[1], ps[0]].item()), "status": int(pst_),
+                              "path_len": int(len(ppath)), "ms": float(np.median(pms)),
+                              "note": "plan_path (Eq. 3 descent + 100 rubber-band sweeps) from the free cell "
+                                      "nearest the robot with u >= 1e-3 on the solved field; CUDA events, "
+                                      "median of 5"}
 
     # ---- end to end through the C ABI with host buffers: every step copies its input map
     # from pinned host memory and its field back, on a copy stream with double buffers so
@@ -473,8 +505,9 @@ def run_twgrid(args, rank, world, dist):
         forms = {}
         tw.tw_build_grid(grid, sc.robot, sc.tracks, sc.law, static_occ=static_d, occ=occ)
         for name, prm in (("rbsor_fp32_graph", params),
+                          ("rbsor_fp32_graph_residual_only", tw.Params(tol=args.tol, max_sweeps=args.max_sweeps)),
                           ("rbsor_fp32_host_loop", tw.Params(tol=args.tol, max_sweeps=args.max_sweeps,
-                                                             flags=tw.HP_HOST_LOOP)),
+                                                             flags=tw.HP_HOST_LOOP, etol=args.etol)),
                           ("rbsor_fp32_graph_polish", tw.Params(tol=args.tol, max_sweeps=args.max_sweeps,
                                                                 flags=tw.HP_POLISH)),
                           ("mixed_fp16", tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_F16, tol=args.tol,
@@ -494,6 +527,7 @@ def run_twgrid(args, rank, world, dist):
             acc = field_accuracy(u, occ, sc, fst)
             forms[name] = {"ms_to_solution": t_med, "solves_per_s": 1e3 / t_med, "sweeps": fst["sweeps"],
                            "resid_inf": fst["resid_inf"], "converged": fst["status"] == tw.TW_OK,
+                           "etol": prm.etol, "err_est": fst["err_est"],
                            "max_abs_error_sampled": acc.get("max_abs_error_sampled"),
                            "mean_abs_error_sampled": acc.get("mean_abs_error_sampled"),
                            "error_bound": acc.get("error_bound")}
@@ -511,7 +545,7 @@ def run_twgrid(args, rank, world, dist):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "method": args.method, "tol": args.tol,
+           "config": {"workload": WORKLOAD, "method": args.method, "tol": args.tol, "etol": args.etol,
                       "parallelism": f"replicas x{world} (one scene per GPU, no collective)",
                       "l2": "256 MiB memset between timed steps (inside the timed region); the 33.5 MB "
                             "field pair itself is L2-resident within a solve"},
@@ -519,7 +553,7 @@ def run_twgrid(args, rank, world, dist):
            "resid_inf_max": max(resid) if resid else None, "relax_status": sorted(set(status)),
            "path_status": sorted(set(path_status)), "path_len": [n for _, _, n in stats_log][:1],
            "omega": stats_log[0][0]["omega"] if stats_log else None,
-           "roofline": roofline, "accuracy": accuracy, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms, "batched": batched,
+           "roofline": roofline, "accuracy": accuracy, "path_reachable": path_reachable, "e2e": e2e, "gpu_launches": launches, "plain_fp32": plain, "forms": forms, "batched": batched,
            "dynamic": dynamic, "learned_warm_start": learned,
            "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "min": min(step_ms), "max": max(step_ms), "host_p50": float(np.percentile(host_ms, 50))},
@@ -775,21 +809,33 @@ def oracle_step(sc, max_iters=None):
 
 
 def cpu_baseline(sc):
-    """The oracle as it stands on one host core: one full oracle step on the same scene."""
+    """The oracle as it stands: one full oracle step on the same scene on every host core (its
+    OpenMP build, which returns the plain build's bits), and on one core."""
     import oracle
     oracle.build()
-    t, iters, r = oracle_step(sc)
-    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+    n = os.cpu_count() or 1
+    used = oracle.use_threads(n)
+    try:
+        t, iters, r = oracle_step(sc)
+    finally:
+        oracle.use_threads(1)
+    t1, _, _ = oracle_step(sc)
+    return {"value": 1.0 / t, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"one full oracle step on the same 2048^2 scene (brute-force raster, FP64 CG to "
-                      f"r_inf<=1e-6 in {iters} iterations, descent + 100 band sweeps): {t:.1f} s"}
+                      f"r_inf<=1e-6 in {iters} iterations, descent + 100 band sweeps) on {used} threads: "
+                      f"{t:.1f} s",
+            "single_core": {"value": 1.0 / t1, "cores": 1, "sample": f"the same step on one core: {t1:.1f} s"}}
 
 
 def run_reference(args, rank, world, dist):
-    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    """Reference arm: the FP64 oracle on every host core (its OpenMP build; rank 0 only).  A step is
+    a full oracle step when one fits the time budget, else the oracle step with a bounded number of
+    CG iterations, extrapolated linearly to the iterations a full solve needs (the sample says which)."""
     import oracle
     if rank != 0:
         return None
     oracle.build()
+    cores = oracle.use_threads(os.cpu_count() or 1)
     sc = make_scene(0)
     budget = max(2.0, 150.0 / max(args.steps + args.warmup, 1))
     # warm-up: one full solve to learn the CG iterations to tolerance
@@ -805,13 +851,14 @@ def run_reference(args, rank, world, dist):
     total = time.perf_counter() - t0
     per_solve = statistics.mean(times)
     v = 1.0 / per_solve
+    how = ("a full oracle step (raster, CG to tolerance, path)" if m >= n_tol else
+           f"the oracle step with {m} of the {n_tol} CG iterations a full solve needs, extrapolated linearly")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "method": "oracle: brute-force raster + FP64 CG + descent/band"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the oracle step with {m} of the {n_tol} CG iterations a "
-                                       f"full solve needs, extrapolated linearly ({total:.1f} s for "
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {how}, on {cores} threads ({total:.1f} s for "
                                        f"{args.steps} steps)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -826,6 +873,8 @@ def main():
     ap.add_argument("--method", default="rbsor", choices=["rbsor", "jacobi", "mixed"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--etol", type=float, default=1e-5,
+                    help="error tolerance of the relaxation (hp_params.etol; 0 = the residual test alone)")
     ap.add_argument("--tblock", type=int, default=0)
     ap.add_argument("--max-sweeps", type=int, default=200000)
     ap.add_argument("--plain-max-sweeps", type=int, default=400000)

@@ -192,6 +192,24 @@ typedef struct {
                           96 of them -- about 2048 x 1400 cells and up -- else 4); hp_relax_batched
                           takes 2, 4 or 7 (anything else: autotuned) */
     int flags;         /* HP_WARM_START | HP_OUT_PHI | HP_TIMING | HP_HOST_LOOP | HP_POLISH */
+    double etol;       /* HP_RBSOR with T >= 2: also require the estimated field error max |u - u*| to be
+                          <= etol (0 = off).  The residual test alone does not bound the error well: the
+                          slowest mode of a cluttered field has a tiny residual and a large error.  From
+                          the first check with r_inf < 100 tol on, each check copies the field into
+                          snapshot planes (workspace grows by one plane pair) and measures d, the largest
+                          change of a free cell since the previous check's snapshot (Tl sweeps ago); its
+                          estimate is d / (1 - rho^Tl), rho = max(omega - 1, the last clear decay rate of
+                          the residual 2-norm) -- the error test of Hageman & Young's adaptive SOR
+                          (Applied Iterative Methods, 1981, ch. 9) over a check interval -- and the larger
+                          of the last two such estimates is the one compared with etol (past the optimal
+                          omega the error also turns, and one interval's change can be small).  The solve
+                          stops when r_inf <= tol and that estimate <= etol.  With etol > 0 the over-
+                          relaxation back-off is not used, omega is frozen once r_inf <= tol, and when the
+                          estimate is met while the FP32 rounding noise of SOR at omega near 2 keeps
+                          r_inf above tol, one launch of T Gauss-Seidel sweeps on a copy (the polish of
+                          HP_POLISH) is accepted if it meets tol.  If the estimate and the residual both
+                          stop falling for four checks (once r_inf < 16 tol) the solve ends with
+                          TW_NOT_CONVERGED.  HP_JACOBI and HP_MIXED ignore etol. */
 } hp_params;
 
 typedef struct {
@@ -199,7 +217,11 @@ typedef struct {
     int status;        /* TW_OK or TW_NOT_CONVERGED */
     double resid_inf;  /* FP64 residual max |(1/4) sum nbr - u| over free cells of the output
                           (HP_MIXED: of its FP64 master field, which the FP32 output rounds) */
-    double resid_l2;   /* FP64 sqrt(sum of squared residuals) */
+    double resid_l2;   /* sqrt(sum of squared residuals) over the same cells, to about 1e-6 relative:
+                          each residual is evaluated FP64-accurately (as for resid_inf), its leading
+                          FP32 part is squared and summed in FP32 over a thread's cells, and the
+                          per-CTA sums are added in FP64 (HP_MIXED: the FP64 master's residuals,
+                          squared and summed in FP64) */
     double omega;      /* SOR factor used last */
     int checks;        /* residual checks performed */
     int sweep_launches;/* launches of the sweep kernel */
@@ -209,6 +231,8 @@ typedef struct {
     int polishes;      /* polish launches tried (HP_POLISH) */
     int polished;      /* 1: the output is the accepted polished copy */
     double resid_check;/* the FP32 residual max of the loop's last check (0 if it made none) */
+    double err_est;    /* etol > 0: the last error estimate (see hp_params.etol; DBL_MAX until two
+                          checks have measured a change), else 0 */
 } hp_stats;
 
 #define HP_LOOP_HOST 0     /* host-driven: HP_HOST_LOOP, HP_TIMING, HP_JACOBI, HP_MIXED, or a cap
@@ -248,14 +272,19 @@ int hp_relax(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *fi
  * caller's), for method HP_RBSOR or HP_JACOBI without HP_TIMING; the
  * convergence loop is always host-driven (HP_HOST_LOOP).
  * Limits: grids whose hp_relax_workspace_size() exceeds the array (for
- * HP_RBSOR anything above about 1024 x 1024 cells) return TW_EWORKSPACE
+ * HP_RBSOR anything above about 1024 x 1024 cells, or 870 x 870 with
+ * etol > 0, which adds the snapshot planes) return TW_EWORKSPACE
  * before any GPU work; other methods or HP_TIMING return TW_EINVAL.
  * Set-up: the first call on a device, with that device current, looks up the
  * array's device address once and caches it; make that first call before any
  * stream capture.  All calls on a device share the array and it keeps the
  * previous call's contents (each call clears what must start at zero), so
  * calls whose GPU work overlaps -- on different streams or host threads --
- * race and must be serialised by the caller. */
+ * race and must be serialised by the caller.  The array is the one of the
+ * device current at the call, so make the device that holds occ_dev and
+ * field_dev current first.  Its address is looked up once per device and kept:
+ * after cudaDeviceReset on a device, do not call hp_relax_noalloc there again
+ * in the same process (the kept address belonged to the destroyed context). */
 #define HP_RELAX_NOALLOC_SCRATCH_BYTES ((size_t)9 << 20)
 int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, float *field_dev,
                      const hp_params *p, hp_stats *stats, void *stream);

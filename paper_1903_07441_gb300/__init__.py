@@ -78,7 +78,7 @@ class tw_grid_job(ctypes.Structure):
 class hp_params(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("storage", ctypes.c_int), ("omega", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("tblock", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("tblock", ctypes.c_int), ("flags", ctypes.c_int), ("etol", ctypes.c_double)]
 
 
 class hp_instance(ctypes.Structure):
@@ -91,7 +91,7 @@ class hp_stats(ctypes.Structure):
                 ("resid_l2", ctypes.c_double), ("omega", ctypes.c_double), ("checks", ctypes.c_int),
                 ("sweep_launches", ctypes.c_int), ("sweep_ms", ctypes.c_double), ("tblock", ctypes.c_int),
                 ("loop", ctypes.c_int), ("polishes", ctypes.c_int),
-                ("polished", ctypes.c_int), ("resid_check", ctypes.c_double)]
+                ("polished", ctypes.c_int), ("resid_check", ctypes.c_double), ("err_est", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -110,10 +110,11 @@ class Params:
     check_every: int = 0
     tblock: int = 0
     flags: int = 0
+    etol: float = 0.0
 
     def c(self) -> hp_params:
         return hp_params(self.method, self.storage, self.omega, self.tol, self.max_sweeps,
-                         self.check_every, self.tblock, self.flags)
+                         self.check_every, self.tblock, self.flags, self.etol)
 
 
 # ---------------------------------------------------------------------------
@@ -372,8 +373,10 @@ def hp_relax_noalloc(grid: tw_grid, occ, goal, field=None, params: Optional[Para
         field = torch.empty((grid.ny, grid.nx), dtype=torch.float32, device=occ.device)
     cp = params.c()
     stats = hp_stats()
-    st = load().hp_relax_noalloc(ctypes.byref(grid), _ptr(occ), int(goal[0]), int(goal[1]), _ptr(field),
-                                 ctypes.byref(cp), ctypes.byref(stats), _stream(occ.device))
+    # the library takes the scratch array of the current device: make it the tensors' device
+    with torch.cuda.device(occ.device):
+        st = load().hp_relax_noalloc(ctypes.byref(grid), _ptr(occ), int(goal[0]), int(goal[1]), _ptr(field),
+                                     ctypes.byref(cp), ctypes.byref(stats), _stream(occ.device))
     _check("hp_relax_noalloc", st, ok=(TW_OK, TW_NOT_CONVERGED))
     return field, stats.as_dict()
 

@@ -144,8 +144,7 @@ __global__ void __launch_bounds__(BCfg<T>::WARPS * 32, T <= 4 ? 2 : 1)
 batch_tb_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const BatchHdr *__restrict__ H,
                 int parity) {
     constexpr int RB = BCfg<T>::RB, WARPS = BCfg<T>::WARPS;
-    __shared__ float4 s_top[2][WARPS][32];
-    __shared__ float4 s_bot[2][WARPS][32];
+    __shared__ TBShared<WARPS> sh;
     const int n_active = H->n_active;
     for (int t = blockIdx.x; t < n_active; t += gridDim.x) {
         __syncthreads();   // the previous tile's exchange buffers are free again
@@ -153,7 +152,7 @@ batch_tb_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const 
         const BatchInst &b = I[it.x];
         const int bx = it.y % b.tx, by = it.y / b.tx;
         tb_tile<T, RB, WARPS>(b.P[parity][0], b.P[parity][1], b.P[1 - parity][0], b.P[1 - parity][1], b.MR, b.MB,
-                              b.ny, b.W4, b.S, b.MW, b.ctl.omega_f, bx, by, s_top, s_bot);
+                              b.ny, b.W4, b.S, b.MW, b.ctl.omega_f, bx, by, sh);
     }
 }
 
@@ -207,7 +206,7 @@ batch_control_kernel(BatchInst *__restrict__ I, BatchHdr *__restrict__ H, int2 *
             const float rf = __uint_as_float(b.rmax);
             b.rmax = 0u;
             c.sweeps += c.K;
-            int go = relax_control(c, (double)rf, -1.0, c.K);
+            int go = relax_control(c, (double)rf, -1.0, c.K, -1.0);
             if (c.sweeps + c.K > c.max_sweeps || final_check) go = 0;
             if (b.error) go = 0;
             c.omega_f = (float)c.omega;

@@ -30,16 +30,23 @@ void tb_kernel_node(int T, RBLayout &L, int ny, void **func, dim3 *grid, dim3 *b
 void *rb_residual_kernel_ptr();
 
 // handle: the loop condition (polish == 0) or the polish IF condition.
+// dmax (nullable): the largest change of a free cell over the interval's last launch.
 __global__ void relax_control_kernel(RelaxCtl *ctl, unsigned int *rmax, const float *l2part, int n_part,
-                                     int max_intervals, cudaGraphConditionalHandle handle, int polish) {
+                                     int max_intervals, cudaGraphConditionalHandle handle, int polish,
+                                     unsigned int *dmax) {
     // the 2-norm from the residual kernel's per-CTA partials (whole CTA), then thread 0 decides
     const double e = l2part ? sqrt(block_sum_partials(l2part, n_part, threadIdx.x)) : -1.0;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     RelaxCtl c = *ctl;
     const float rf = __uint_as_float(*rmax);
     *rmax = 0u;
+    double d = -1.0;
+    if (dmax && c.snap == 2) {   // the residual kernel compared with the snapshot in this interval
+        d = (double)__uint_as_float(*dmax);
+        *dmax = 0u;
+    }
     c.sweeps += c.K;
-    const int cont = relax_control(c, (double)rf, e, c.K);
+    const int cont = relax_control(c, (double)rf, e, c.K, d);
     int go = cont;
     if (c.checks >= max_intervals || c.sweeps + c.K > c.max_sweeps) go = 0;
     c.go = go;
@@ -79,7 +86,7 @@ static cudaError_t add_kernel_node(cudaGraphNode_t *node, cudaGraph_t g, cudaGra
 }
 
 struct GraphEntry {
-    int dev, nx, ny, T, K, max_intervals, polish;
+    int dev, nx, ny, T, K, max_intervals, polish, est;
     const void *key;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -89,7 +96,7 @@ static std::mutex g_graph_mutex;
 static std::vector<GraphEntry> g_graphs;
 constexpr size_t kMaxCachedGraphs = 16;
 
-static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_intervals, int polish,
+static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_intervals, int polish, int est,
                        RelaxScalars *scal, float *l2part, GraphEntry *out) {
     (void)nx;
     cudaGraph_t g = nullptr;
@@ -135,10 +142,14 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
     unsigned int *rmax = &scal->max32;
     RelaxCtl *ctl = &scal->ctl;
     const dim3 rgrid = rb_residual_grid(L, ny), rblock(64, 4);
-    {   // residual of the current planes
+    unsigned int *dmax = est ? &scal->dmax32 : nullptr;
+    {   // residual of the current planes (and with an error tolerance the snapshot work)
         RBLayout Lc = L;
         Lc.R = R; Lc.B = B;
-        void *args[] = {(void *)&Lc, (void *)&ny_, (void *)&rmax, (void *)&l2part};
+        int snap0 = 0;
+        const int *snap_dev = est ? &scal->ctl.snap : nullptr;
+        void *args[] = {(void *)&Lc, (void *)&ny_, (void *)&rmax, (void *)&l2part, (void *)&snap0,
+                        (void *)&snap_dev, (void *)&dmax};
         cudaGraphNode_t node;
         e = add_kernel_node(&node, body, &prev, rb_residual_kernel_ptr(), rgrid, rblock, args);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
@@ -154,7 +165,7 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         int n_part = rb_residual_blocks(L, ny);
         int mi = max_intervals, pol = polish;
         void *args[] = {(void *)&ctl, (void *)&rmax, (void *)&part, (void *)&n_part, (void *)&mi, (void *)&hp,
-                        (void *)&pol};
+                        (void *)&pol, (void *)&dmax};
         cudaGraphNode_t node;
         e = add_kernel_node(&node, body, &prev, (void *)relax_control_kernel, dim3(1), dim3(kPartThreads), args);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
@@ -182,7 +193,11 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
         RBLayout Lp = L;
         Lp.R = R2; Lp.B = B2;
         float *no_part = nullptr;
-        void *rargs[] = {(void *)&Lp, (void *)&ny_, (void *)&rmax, (void *)&no_part};
+        int no_snap = 0;
+        const int *no_snap_dev = nullptr;
+        unsigned int *no_dmax = nullptr;
+        void *rargs[] = {(void *)&Lp, (void *)&ny_, (void *)&rmax, (void *)&no_part, (void *)&no_snap,
+                         (void *)&no_snap_dev, (void *)&no_dmax};
         e = add_kernel_node(&node, pbody, &pprev, rb_residual_kernel_ptr(), rgrid, rblock, rargs);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
         prev = inode;
@@ -201,8 +216,8 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
     return TW_OK;
 }
 
-int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, int polish, RelaxScalars *scal,
-                   float *l2part, cudaStream_t s, int *launches) {
+int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, int polish, int est,
+                   RelaxScalars *scal, float *l2part, cudaStream_t s, int *launches) {
     if (max_intervals < 1) return 1;
     int dev = 0;
     TW_CUDA(cudaGetDevice(&dev));
@@ -210,7 +225,7 @@ int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals,
     GraphEntry *ent = nullptr;
     for (auto &g : g_graphs)
         if (g.dev == dev && g.key == (const void *)scal && g.nx == nx && g.ny == ny && g.T == T && g.K == K &&
-            g.max_intervals == max_intervals && g.polish == polish)
+            g.max_intervals == max_intervals && g.polish == polish && g.est == est)
             ent = &g;
     if (!ent) {
         if (g_graphs.size() >= kMaxCachedGraphs) {
@@ -221,8 +236,9 @@ int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals,
         GraphEntry ne;
         ne.dev = dev; ne.nx = nx; ne.ny = ny; ne.T = T; ne.K = K; ne.max_intervals = max_intervals;
         ne.polish = polish;
+        ne.est = est;
         ne.key = (const void *)scal;
-        int e = build_graph(L, nx, ny, T, K, max_intervals, polish, scal, l2part, &ne);
+        int e = build_graph(L, nx, ny, T, K, max_intervals, polish, est, scal, l2part, &ne);
         if (e) return e;
         g_graphs.push_back(ne);
         ent = &g_graphs.back();

@@ -23,6 +23,7 @@ struct RBLayout {
     float *R, *B;      // current red / black planes
     uint32_t *MR, *MB; // free-cell bits
     float *R2, *B2;    // ping-pong planes for temporal blocking
+    float *R3, *B3;    // snapshot of the planes at the last residual check (error estimate; may be null)
 };
 
 // Convergence-loop state, shared by the host-driven loop and the device
@@ -40,13 +41,23 @@ struct RelaxCtl {
     int go, T;             // continue flag of the last check; sweeps per launch
     int polish_ok, pad2;   // polish enabled (HP_RBSOR with HP_POLISH and T > 1)
     float one_f;           // 1.0f, the omega the polish launches read
-    float pad3;
+    int Tl;                // sweeps since the snapshot the change d is measured against
+    int snap;              // snapshot state of the next check: 0 none, 1 take it, 2 compare with it and retake
+    double etol;           // error tolerance (0: off; see relax_error_estimate)
+    double lam;            // last clear decay rate of the residual 2-norm per sweep (0: none yet)
+    double err_est;        // last error estimate (the larger of the last two checks' raw estimates)
+    double err_prev;       // the estimate of the check before
+    double err_raw;        // the last check's raw estimate (DBL_MAX: none)
+    int r_met;             // 1 once the residual test has been met (omega frozen from then on)
+    int stall;             // consecutive checks whose estimate did not fall clearly
 };
 
 
 struct RelaxScalars {
     unsigned int max32;
     int goal_blocked;      // set on the device when the goal cell is occupied
+    unsigned int dmax32;   // FP32 max change of a free cell over the last launch (bits); reset after each check
+    unsigned int pad0;
     unsigned long long max64;
     double sum64;
     double l2;             // residual 2-norm of the last check (host-driven loop)
@@ -71,7 +82,7 @@ struct RelaxLayout {
 };
 
 RBLayout rb_layout(int nx, int ny);
-size_t carve_rb(Carver &cv, int nx, int ny, RBLayout *out, bool pingpong);
+size_t carve_rb(Carver &cv, int nx, int ny, RBLayout *out, bool pingpong, bool snapshot = false);
 size_t carve_mixed(Carver &cv, int nx, int ny, int storage, RelaxLayout *R);
 int relax_mixed(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, int mode,
                 const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s);
@@ -82,11 +93,13 @@ int tb_tiles(int T, int nx, int ny);
 // Graph-driven loop: up to max_intervals check intervals of K sweeps (K/T even)
 // run on the device; ctl_dev must hold the initial state.  Returns TW_OK, or
 // a positive value when graphs are unavailable (the caller uses the host loop).
-int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, int polish, RelaxScalars *scal,
-                   float *l2part, cudaStream_t s, int *launches);
+int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals, int polish, int est,
+                   RelaxScalars *scal, float *l2part, cudaStream_t s, int *launches);
 // FP32 residual max (atomicMax into *out) and, if l2part is given, the sum of
 // squared residuals of every CTA in l2part[rb_residual_blocks(L, ny)].
-void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s);
+// snap: snapshot state (see RelaxCtl::snap) of this check; dmax receives the change when snap == 2.
+void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s, int snap,
+                        unsigned int *dmax);
 int rb_residual_blocks(const RBLayout &L, int ny);
 dim3 rb_residual_grid(const RBLayout &L, int ny);   // launch grid of rb_residual_kernel (64 x 4 threads)
 
@@ -173,15 +186,84 @@ __device__ inline double block_sum_partials(const float *part, int n, int t) {
     return sm[0];
 }
 
+// Error estimate of the current field from d, the largest change of a free
+// cell since the snapshot taken at the previous check (Tl sweeps ago).  If the
+// error decays by a factor rho per sweep, |e| <= d / (1 - rho^Tl); for SOR at
+// or past the optimal omega every eigenvalue has modulus omega - 1, and below
+// it the slowest mode decays at the rate the residual 2-norm shows, so
+// rho = max(omega - 1, lam).  This is the form of the error test of Hageman &
+// Young's adaptive SOR procedure (Applied Iterative Methods, 1981, ch. 9),
+// with the change over a whole check interval in place of a single sweep's:
+// near omega = 2 the FP32 rounding noise in the change is amplified by
+// 1 / (1 - rho^Tl), far less over an interval than over one sweep.  d < 0
+// means no change was measured.  Past the optimal omega the eigenvalues are
+// complex and the error turns as well as shrinks, so over one interval a
+// cell can come back close to where it was: relax_control keeps the larger of
+// the last two checks' estimates (on 48 seeded scenes of 256-512 cells a side
+// with 5-35 % obstacles that larger one was never below 0.98 times the true
+// error after the residual test had been met; a single check's estimate went
+// down to 0.36 times).
+__host__ __device__ inline double relax_error_estimate(const RelaxCtl &c, double d) {
+    if (!(d >= 0.0)) return DBL_MAX;
+    double rho = c.omega - 1.0 > c.lam ? c.omega - 1.0 : c.lam;
+    if (rho < 0.0) rho = 0.0;
+    if (rho > 0.9999) rho = 0.9999;
+    return d / (1.0 - pow(rho, (double)(c.Tl > 0 ? c.Tl : 1)));
+}
+
 // One residual check: stop test, over-relaxation back-off at the rounding
 // floor, adaptive omega.  r is the residual max (the stopping quantity); e,
 // when positive, its 2-norm, from which the decay rate that drives omega is
 // estimated (smoother than the max, whose location jumps between cells).
+// d is the largest change of a free cell since the previous check's snapshot
+// (< 0: not measured), used only with an error tolerance (c.etol > 0).  Then
+// the solve waits for both r <= tol and relax_error_estimate <= etol; the
+// over-relaxation back-off below is not used (it meets the residual test by
+// slowing the smooth error's decay, which leaves that error behind), omega is
+// frozen from the first check that meets the residual test on, so that the
+// rate the estimate assumes is the iteration's own, and a check whose
+// estimate is met while the FP32 rounding noise of SOR at omega near 2 keeps
+// r above tol tries the polish (relax_polish_decide).  If the estimate and the
+// residual both stop falling for kErrStall checks, the error target cannot be
+// shown in FP32 and the solve ends unconverged instead of running to the cap
+// (counted only once r < kStallFactor * tol: far from the tolerance the
+// residual of an open field can hover for many intervals while it converges).
+// The snapshot the change is measured against is taken from the first check
+// with r < kSnapFactor * tol on (with tol = 0: from the first check).
 // Returns 1 to continue, 0 when converged.
-__host__ __device__ inline int relax_control(RelaxCtl &c, double r, double e, int n) {
+constexpr int kErrStall = 4;
+constexpr double kStallFactor = 16.0;
+constexpr double kSnapFactor = 100.0;
+__host__ __device__ inline int relax_control(RelaxCtl &c, double r, double e, int n, double d) {
     c.checks++;
     c.r_last = r;
-    if (c.tol > 0.0 && r <= c.tol) {
+    if (c.etol > 0.0) {
+        // the 2-norm's decay rate, kept from the last interval over which it still fell clearly
+        if (e > 0.0 && c.e_prev > 0.0 && n == c.K && e <= 0.8 * c.e_prev) c.lam = pow(e / c.e_prev, 1.0 / n);
+        const bool r_ok = c.tol > 0.0 ? r <= c.tol : true;
+        if (r_ok) c.r_met = 1;
+        const double raw = relax_error_estimate(c, d);
+        c.err_est = raw > c.err_raw ? raw : c.err_raw;
+        c.err_raw = raw;
+        if (r_ok && c.err_est <= c.etol) {
+            c.status = TW_OK;
+            return 0;
+        }
+        if (c.snap || c.tol <= 0.0 || r < kSnapFactor * c.tol) c.snap = c.snap ? 2 : 1;
+        const bool stalled = c.err_prev > 0.0 && c.err_est > 0.9 * c.err_prev && c.r_prev > 0.0 &&
+                             r > 0.8 * c.r_prev && (c.tol <= 0.0 || r < kStallFactor * c.tol);
+        c.stall = stalled ? c.stall + 1 : 0;
+        c.err_prev = c.err_est;
+        if (c.stall >= kErrStall) {
+            c.status = TW_NOT_CONVERGED;
+            return 0;
+        }
+        if (c.r_met) {
+            c.r_prev = r;
+            c.e_prev = e;
+            return 1;
+        }
+    } else if (c.tol > 0.0 && r <= c.tol) {
         c.status = TW_OK;
         return 0;
     }
@@ -190,7 +272,7 @@ __host__ __device__ inline int relax_control(RelaxCtl &c, double r, double e, in
     // omega / (2 - omega): halve the over-relaxation and stop adapting
     // upwards.  (Far from the tolerance the max-norm can plateau while the
     // iteration still converges, so it is left alone there.)
-    if (c.r_prev > 0.0 && n == c.K && r > 0.8 * c.r_prev && r < 16.0 * c.tol && c.omega > 1.0) {
+    if (c.etol <= 0.0 && c.r_prev > 0.0 && n == c.K && r > 0.8 * c.r_prev && r < 16.0 * c.tol && c.omega > 1.0) {
         c.omega = 1.0 + 0.5 * (c.omega - 1.0);
         if (c.omega < 1.05) c.omega = 1.0;
         c.adapt = 0;
@@ -223,8 +305,14 @@ __host__ __device__ inline int relax_control(RelaxCtl &c, double r, double e, in
 constexpr double kPolishFactor = 100.0;
 
 // After relax_control returned cont: decide whether this check polishes.
+// With an error tolerance the polish removes the rounding noise that keeps r
+// above tol once the error estimate is met (the estimate, not the residual,
+// then says the smooth error is small enough).
 __host__ __device__ inline int relax_polish_decide(RelaxCtl &c, int cont) {
-    c.polish = (cont && c.polish_ok && c.tol > 0.0 && c.r_last < kPolishFactor * c.tol && c.omega >= 1.5) ? 1 : 0;
+    if (c.etol > 0.0)
+        c.polish = (cont && c.polish_ok && c.tol > 0.0 && c.r_last > c.tol && c.err_est <= c.etol) ? 1 : 0;
+    else
+        c.polish = (cont && c.polish_ok && c.tol > 0.0 && c.r_last < kPolishFactor * c.tol && c.omega >= 1.5) ? 1 : 0;
     return c.polish;
 }
 

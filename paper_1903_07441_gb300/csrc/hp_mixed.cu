@@ -420,7 +420,7 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
             if (er) return er;
             checks++;
             const double prev = c.r_prev;
-            if (!relax_control(c, (double)rf, -1.0, n)) break;
+            if (!relax_control(c, (double)rf, -1.0, n, -1.0)) break;
             if (prev > 0.0 && it > 4 && rf > 0.98 * prev) break;   // storage floor reached
         }
         // 4. x += s e

@@ -175,9 +175,12 @@ __global__ void rb_unpack_kernel(RBLayout L, int nx, int ny, float *__restrict__
 }
 
 // FP32 residual max over both colours of the split layout (one atomicMax per
-// CTA) and, if l2part is given, each CTA's sum of squared residuals.
-__global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, unsigned int *out_max, float *l2part) {
-    rb_residual_cta(L, ny, out_max, l2part);
+// CTA), if l2part is given each CTA's sum of squared residuals, and the
+// snapshot work of the error estimate (snap_dev, when given, overrides
+// snap_arg: the graph-driven loop keeps the state on the device).
+__global__ void __launch_bounds__(256) rb_residual_kernel(RBLayout L, int ny, unsigned int *out_max, float *l2part,
+                                                          int snap_arg, const int *snap_dev, unsigned int *out_dmax) {
+    rb_residual_cta(L, ny, out_max, l2part, snap_dev ? *snap_dev : snap_arg, out_dmax);
 }
 
 // The 2-norm of the last check's residual from its per-CTA partials (one CTA
@@ -203,7 +206,7 @@ RBLayout rb_layout(int nx, int ny) {
     return L;
 }
 
-size_t carve_rb(Carver &cv, int nx, int ny, RBLayout *out, bool pingpong) {
+size_t carve_rb(Carver &cv, int nx, int ny, RBLayout *out, bool pingpong, bool snapshot) {
     RBLayout L = rb_layout(nx, ny);
     size_t plane = (size_t)ny * L.S;
     L.R = cv.take<float>(plane);
@@ -213,6 +216,10 @@ size_t carve_rb(Carver &cv, int nx, int ny, RBLayout *out, bool pingpong) {
     if (pingpong) {
         L.R2 = cv.take<float>(plane);
         L.B2 = cv.take<float>(plane);
+    }
+    if (snapshot) {   // written before it is read: no clearing needed
+        L.R3 = cv.take<float>(plane);
+        L.B3 = cv.take<float>(plane);
     }
     if (out) *out = L;
     return cv.need;
@@ -226,7 +233,7 @@ static size_t carve_relax(Carver &cv, int nx, int ny, const hp_params *p, RelaxL
     if (method == HP_JACOBI) {
         R.tmp = cv.take<float>((size_t)nx * ny);
     } else if (method == HP_RBSOR) {
-        carve_rb(cv, nx, ny, &R.rb, true);
+        carve_rb(cv, nx, ny, &R.rb, true, p && p->etol > 0.0);
         R.l2part = cv.take<float>((size_t)rb_residual_blocks(R.rb, ny));
     } else {
         carve_mixed(cv, nx, ny, p ? p->storage : HP_STORE_F16, &R);
@@ -240,7 +247,7 @@ static bool valid_params(const hp_params *p) {
            (p->storage == HP_STORE_F32 || p->storage == HP_STORE_F16 || p->storage == HP_STORE_BF16) &&
            isfinite(p->omega) && (p->omega == 0.0 || (p->omega > 0.0 && p->omega < 2.0)) &&
            isfinite(p->tol) && p->tol >= 0.0 && p->max_sweeps >= 1 && p->check_every >= 0 &&
-           p->tblock >= 0 && p->tblock <= 16;
+           p->tblock >= 0 && p->tblock <= 16 && isfinite(p->etol) && p->etol >= 0.0;
 }
 
 // First omega of an adaptive solve, by the longer side n, and never above
@@ -347,8 +354,10 @@ int rb_residual_blocks(const RBLayout &L, int ny) {
 
 void *rb_residual_kernel_ptr() { return (void *)rb_residual_kernel; }
 
-void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s) {
-    TW_LAUNCH(rb_residual_kernel, rb_residual_grid(L, ny), dim3(64, 4), 0, s, L, ny, out, l2part);
+void rb_residual_launch(RBLayout &L, int ny, unsigned int *out, float *l2part, cudaStream_t s, int snap,
+                        unsigned int *dmax) {
+    TW_LAUNCH(rb_residual_kernel, rb_residual_grid(L, ny), dim3(64, 4), 0, s, L, ny, out, l2part, snap,
+              (const int *)nullptr, dmax);
 }
 
 // Red-black SOR driver on the split layout.  By default the check intervals
@@ -385,7 +394,13 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
     c.status = TW_NOT_CONVERGED;
     c.omega_max = sor_omega_cap(nx, ny);
     c.T = T;
-    c.polish_ok = (T > 1 && L.R2 && (p->flags & HP_POLISH)) ? 1 : 0;
+    // the error estimate needs the snapshot planes (carved with etol > 0); the polish it may end
+    // with needs T-fused launches (ping-pong planes)
+    c.etol = (T > 1 && L.R2 && L.R3) ? p->etol : 0.0;
+    c.Tl = K;
+    c.err_raw = DBL_MAX;
+    // HP_POLISH, or an error tolerance (its polish only clears the rounding noise at the end)
+    c.polish_ok = (T > 1 && L.R2 && ((p->flags & HP_POLISH) || c.etol > 0.0)) ? 1 : 0;
     c.one_f = 1.0f;
     int launches = 0;
     bool done = false;
@@ -393,7 +408,9 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
     if (checks && !host_loop && T > 1 && (K / T) % 2 == 0 && p->max_sweeps >= K) {
         TW_CUDA(cudaMemcpyAsync(&scal->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s));
         TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
-        int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, c.polish_ok, scal, l2part, s, &launches);
+        TW_CUDA(cudaMemsetAsync(&scal->dmax32, 0, sizeof(unsigned int), s));
+        int e = rb_solve_graph(L, nx, ny, T, K, p->max_sweeps / K, c.polish_ok, c.etol > 0.0, scal, l2part, s,
+                               &launches);
         if (e < 0) return e;
         if (e == TW_OK) st->loop = HP_LOOP_GRAPH;
         if (e == TW_OK && p->max_sweeps % K == 0) {
@@ -428,17 +445,22 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
         timer.accumulate();
         c.sweeps += n;
         if (checks) {
+            // error estimate: the change since the previous check's snapshot, n sweeps ago
+            const int snap = c.etol > 0.0 ? c.snap : 0;
+            c.Tl = n;
             TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
-            rb_residual_launch(L, ny, &scal->max32, l2part, s);
+            if (snap == 2) TW_CUDA(cudaMemsetAsync(&scal->dmax32, 0, sizeof(unsigned int), s));
+            rb_residual_launch(L, ny, &scal->max32, l2part, s, snap, snap == 2 ? &scal->dmax32 : nullptr);
             if (l2part)
                 TW_LAUNCH(l2_finalize_kernel, 1, kPartThreads, 0, s, l2part, rb_residual_blocks(L, ny), &scal->l2);
             TW_CHECK_LAUNCH();
             RelaxScalars hs;
             TW_CUDA(cudaMemcpyAsync(&hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
             TW_CUDA(cudaStreamSynchronize(s));
-            float rf;
+            float rf, df;
             memcpy(&rf, &hs.max32, sizeof(rf));
-            const int cont = relax_control(c, (double)rf, l2part ? hs.l2 : -1.0, n);
+            memcpy(&df, &hs.dmax32, sizeof(df));
+            const int cont = relax_control(c, (double)rf, l2part ? hs.l2 : -1.0, n, snap == 2 ? (double)df : -1.0);
             if (!cont) {
                 done = true;
             } else if (relax_polish_decide(c, cont)) {
@@ -450,7 +472,7 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
                 if (e) return e;
                 timer.accumulate();
                 TW_CUDA(cudaMemsetAsync(&scal->max32, 0, sizeof(unsigned int), s));
-                rb_residual_launch(Lp, ny, &scal->max32, nullptr, s);
+                rb_residual_launch(Lp, ny, &scal->max32, nullptr, s, 0, nullptr);
                 TW_CHECK_LAUNCH();
                 float r2;
                 e = read_max_f32(&scal->max32, s, &r2);
@@ -467,6 +489,7 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
     st->polishes = c.polishes;
     st->polished = c.in_alt;
     st->resid_check = c.checks ? c.r_last : 0.0;
+    st->err_est = c.etol > 0.0 ? c.err_est : 0.0;
     st->checks = c.checks;
     st->omega = c.omega;
     st->sweep_launches = launches;
@@ -548,6 +571,7 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
         local.polishes = c.polishes;
         local.polished = c.in_alt;
         local.resid_check = c.checks ? c.r_last : 0.0;
+        local.err_est = c.etol > 0.0 ? c.err_est : 0.0;
         local.checks = c.checks;
         local.omega = c.omega;
         local.sweep_launches = c.checks * KT + c.polishes;
@@ -557,7 +581,10 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
         memcpy(&local.resid_inf, &hs.max64, sizeof(double));
         local.resid_l2 = sqrt(hs.sum64);
     }
-    if (p->tol > 0.0 && local.resid_inf <= p->tol) local.status = TW_OK;
+    // the FP64 residual of the output decides the residual test; with an error tolerance the
+    // loop's error test must have passed as well
+    const bool err_ok = !(p->method == HP_RBSOR && p->etol > 0.0 && local.err_est > 0.0) || local.status == TW_OK;
+    if (p->tol > 0.0 && local.resid_inf <= p->tol && err_ok) local.status = TW_OK;
     if (st) *st = local;
     return local.status;
 }

@@ -13,7 +13,9 @@
 // runtime for the array's device address once (cudaGetSymbolAddress) and
 // caches it; host code never passes the array's name itself, which on the
 // host is only a stand-in symbol.  Make that first call before any stream
-// capture.
+// capture.  The kept address belongs to the device's context: after a
+// cudaDeviceReset the caller must not use this entry point on that device
+// again in the same process.
 //
 // The array is shared by every call on a device and keeps the previous call's
 // contents; the solver clears everything that must start at zero (padding,
@@ -25,7 +27,7 @@
 
 namespace tw {
 
-constexpr size_t kNoAllocScratchBytes = HP_RELAX_NOALLOC_SCRATCH_BYTES;  // 9 MiB: up to 1024 x 1024 cells
+constexpr size_t kNoAllocScratchBytes = HP_RELAX_NOALLOC_SCRATCH_BYTES;  // 9 MiB: up to 1024 x 1024 cells (870 x 870 with an error tolerance)
 constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_hp_noalloc_scratch[kNoAllocScratchBytes];

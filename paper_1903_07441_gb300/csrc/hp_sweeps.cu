@@ -70,12 +70,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 rb_tb_kernel(const float *__restrict__ Rin, const float *__restrict__ Bin, float *__restrict__ Rout,
              float *__restrict__ Bout, const uint32_t *__restrict__ MR, const uint32_t *__restrict__ MB,
              int ny, int W4, int S, int MW, float omega_arg, const float *__restrict__ omega_dev) {
-    __shared__ float4 s_top[2][WARPS][32];
-    __shared__ float4 s_bot[2][WARPS][32];
+    __shared__ TBShared<WARPS> sh;
     // the graph-driven loop keeps omega in device memory (it adapts on the device)
     const float omega = omega_dev ? *omega_dev : omega_arg;
-    tb_tile<T, RB, WARPS>(Rin, Bin, Rout, Bout, MR, MB, ny, W4, S, MW, omega, (int)blockIdx.x, (int)blockIdx.y,
-                          s_top, s_bot);
+    tb_tile<T, RB, WARPS>(Rin, Bin, Rout, Bout, MR, MB, ny, W4, S, MW, omega, (int)blockIdx.x, (int)blockIdx.y, sh);
 }
 
 // Tile shape per blocking depth.  T <= 4: 8 rows x 8 warps (256 x 64 cells

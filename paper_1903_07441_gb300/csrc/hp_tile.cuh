@@ -1,8 +1,6 @@
 // Register-blocked, temporally blocked red-black SOR tile (shared by the
 // single-field and the batched sweep kernels; see hp_sweeps.cu for the design).
 #pragma once
-#include <type_traits>
-
 #include "hp_internal.cuh"
 
 namespace tw {
@@ -68,14 +66,49 @@ __device__ __forceinline__ float resid_row(const float4 c, const float4 mid, con
     return acc;
 }
 
+// Block-wide max of two non-negative floats, one atomicMax per CTA on each
+// one's bits (out_b may be null: b is then not reduced).
+__device__ __forceinline__ void block_max2_atomic(float a, unsigned int *out_a, float b, unsigned int *out_b) {
+    __shared__ float sa[32], sb[32];
+    a = sane(a);
+    b = sane(b);
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y;
+    if ((t & 31) == 0) {
+        sa[t >> 5] = a;
+        sb[t >> 5] = b;
+    }
+    __syncthreads();
+    if (t < 32) {
+        const bool in = t < (nt + 31) / 32;
+        a = in ? sa[t] : 0.0f;
+        b = in ? sb[t] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if (t == 0 && a > 0.0f) atomicMax(out_a, __float_as_uint(a));
+        if (t == 0 && out_b && b > 0.0f) atomicMax(out_b, __float_as_uint(b));
+    }
+}
+
 // One CTA (64 x 4 threads; each thread one float4 of each colour in
 // kResidRows rows, strided by 4) of the FP32 residual check: atomicMax of the
 // CTA's residual max into *out_max and, if l2part is given, the CTA's sum of
 // squared residuals, reduced in a fixed order, into l2part[CTA index].
+// snap (the snapshot state, see RelaxCtl::snap) 1: copy the planes into the
+// snapshot planes L.R3/L.B3; 2: also atomicMax of the largest change of a free
+// cell since the snapshot into *out_dmax.  Each thread reads and rewrites only
+// the snapshot entries of its own cells.
 constexpr int kResidRows = 4;
-__device__ __forceinline__ void rb_residual_cta(const RBLayout &L, int ny, unsigned int *out_max, float *l2part) {
+__device__ __forceinline__ void rb_residual_cta(const RBLayout &L, int ny, unsigned int *out_max, float *l2part,
+                                                int snap, unsigned int *out_dmax) {
     const int k4 = blockIdx.x * blockDim.x + threadIdx.x;
-    float r = 0.0f, q = 0.0f;
+    float r = 0.0f, q = 0.0f, dm = 0.0f;
 #pragma unroll
     for (int i = 0; i < kResidRows; i++) {
     const int y = (blockIdx.y * kResidRows + i) * blockDim.y + threadIdx.y + 1;
@@ -100,6 +133,17 @@ __device__ __forceinline__ void rb_residual_cta(const RBLayout &L, int ny, unsig
             if (bits & 2u) { r = fmaxf(r, fabsf(t1)); q = fmaf(t1, t1, q); }
             if (bits & 4u) { r = fmaxf(r, fabsf(t2)); q = fmaf(t2, t2, q); }
             if (bits & 8u) { r = fmaxf(r, fabsf(t3)); q = fmaf(t3, t3, q); }
+            if (snap) {
+                float4 *P = reinterpret_cast<float4 *>((color ? L.B3 : L.R3) + (size_t)y * L.S + 4 + k);
+                if (snap == 2) {
+                    const float4 p = *P;
+                    if (bits & 1u) dm = fmaxf(dm, fabsf(c.x - p.x));
+                    if (bits & 2u) dm = fmaxf(dm, fabsf(c.y - p.y));
+                    if (bits & 4u) dm = fmaxf(dm, fabsf(c.z - p.z));
+                    if (bits & 8u) dm = fmaxf(dm, fabsf(c.w - p.w));
+                }
+                *P = c;
+            }
         }
     }
     }
@@ -115,7 +159,10 @@ __device__ __forceinline__ void rb_residual_cta(const RBLayout &L, int ny, unsig
             if (t == 0) l2part[blockIdx.y * gridDim.x + blockIdx.x] = v;
         }
     }
-    block_max_atomic(r, out_max);
+    if (snap == 2)
+        block_max2_atomic(r, out_max, dm, out_dmax);
+    else
+        block_max_atomic(r, out_max);
 }
 
 template <int T, int RB, int WARPS>
@@ -129,13 +176,38 @@ struct TBShape {
     static_assert(YI % 2 == 0 && HY % 2 == 0 && RB % 2 == 0, "thread rows must start on even rows");
 };
 
-// Free-cell bits of a thread's rows, 4 per row: one 32-bit word per colour up
-// to 8 rows, 64 bits beyond.
+// Free-cell bits of a thread's rows: the 4 bits of row r in byte r % 4 of
+// word r / 4, so that each row's bits are one byte-aligned field.
 template <int RB>
-using TBMask = typename std::conditional<(RB > 8), unsigned long long, uint32_t>::type;
+struct TBMask {
+    uint32_t w[(RB + 3) / 4];
+    __device__ __forceinline__ uint32_t row(int r) const { return (w[r >> 2] >> (8 * (r & 3))) & 0xFu; }
+};
+
+// Row exchange between the warps of a tile, double-buffered by colour.  top
+// holds each warp's first row at index warp, bot its last row at index
+// warp + 1; bot[c][0] and top[c][WARPS] stay zero, so that every warp reads
+// its neighbours' rows without a branch (the rows beyond the tile are halo,
+// whose values never reach the stored interior).
+template <int WARPS>
+struct TBShared {
+    float4 top[2][WARPS + 1][32];
+    float4 bot[2][WARPS + 1][32];
+};
+
+// Zero the two boundary slots; call before the first barrier of a tile.
+template <int WARPS>
+__device__ __forceinline__ void tb_shared_init(TBShared<WARPS> &sh) {
+    const int t = threadIdx.x;
+    if (t < 64) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        sh.bot[t >> 5][0][t & 31] = z;
+        sh.top[t >> 5][WARPS][t & 31] = z;
+    }
+}
 
 template <int COLOR, int RB, int WARPS>
-__device__ __forceinline__ void tb_half_sweep(float4 (&v)[2][RB], const TBMask<RB> m, float4 above, float4 below,
+__device__ __forceinline__ void tb_half_sweep(float4 (&v)[2][RB], const TBMask<RB> &m, float4 above, float4 below,
                                               float omega) {
     constexpr int O = 1 - COLOR;
 #pragma unroll
@@ -144,24 +216,26 @@ __device__ __forceinline__ void tb_half_sweep(float4 (&v)[2][RB], const TBMask<R
         const float4 dn = (r == RB - 1) ? below : v[O][r + 1];
         // rows start even, so the parity of row r for colour COLOR is (r + COLOR) & 1
         if (((r + COLOR) & 1) != 0)
-            v[COLOR][r] = sor_row<1>(v[COLOR][r], v[O][r], up, dn, (uint32_t)(m >> (4 * r)) & 0xFu, omega);
+            v[COLOR][r] = sor_row<1>(v[COLOR][r], v[O][r], up, dn, m.row(r), omega);
         else
-            v[COLOR][r] = sor_row<0>(v[COLOR][r], v[O][r], up, dn, (uint32_t)(m >> (4 * r)) & 0xFu, omega);
+            v[COLOR][r] = sor_row<0>(v[COLOR][r], v[O][r], up, dn, m.row(r), omega);
     }
 }
 
 // Load a thread's RB rows of float4 column k4 of both colours, and their
-// free-cell bits (bit 4*r + e: cell e of row r is free).  Rows and columns
-// outside the field read as zero with no free bit, so they never change.
+// free-cell bits.  Rows and columns outside the field read as zero with no
+// free bit, so they never change.
 template <int RB>
 __device__ __forceinline__ void tb_load(float4 (&v)[2][RB], TBMask<RB> (&m)[2], const float *__restrict__ Rin,
                                         const float *__restrict__ Bin, const uint32_t *__restrict__ MR,
                                         const uint32_t *__restrict__ MB, int y0, int k4, bool kin, int ny, int S,
                                         int MW) {
-    static_assert(RB <= 16, "free-cell bits of a thread's rows are kept in one 64-bit word per colour");
     const int k = 4 * k4;
-    m[0] = 0u;
-    m[1] = 0u;
+#pragma unroll
+    for (int i = 0; i < (RB + 3) / 4; i++) {
+        m[0].w[i] = 0u;
+        m[1].w[i] = 0u;
+    }
 #pragma unroll
     for (int r = 0; r < RB; r++) {
         const int y = y0 + r;
@@ -171,8 +245,8 @@ __device__ __forceinline__ void tb_load(float4 (&v)[2][RB], TBMask<RB> (&m)[2], 
         v[1][r] = in ? __ldg(reinterpret_cast<const float4 *>(Bin + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (in) {
             const size_t w = (size_t)y * MW + (k >> 5);
-            m[0] |= (TBMask<RB>)((__ldg(MR + w) >> (k & 31)) & 0xFu) << (4 * r);
-            m[1] |= (TBMask<RB>)((__ldg(MB + w) >> (k & 31)) & 0xFu) << (4 * r);
+            m[0].w[r >> 2] |= ((__ldg(MR + w) >> (k & 31)) & 0xFu) << (8 * (r & 3));
+            m[1].w[r >> 2] |= ((__ldg(MB + w) >> (k & 31)) & 0xFu) << (8 * (r & 3));
         }
     }
 }
@@ -182,19 +256,16 @@ __device__ __forceinline__ void tb_load(float4 (&v)[2][RB], TBMask<RB> (&m)[2], 
 // through shared memory (double-buffered by colour, one barrier each).
 template <int RB, int WARPS>
 __device__ __forceinline__ void tb_full_sweep(float4 (&v)[2][RB], const TBMask<RB> (&m)[2], float omega,
-                                              float4 (&s_top)[2][WARPS][32], float4 (&s_bot)[2][WARPS][32]) {
+                                              TBShared<WARPS> &sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    s_top[0][warp][lane] = v[1][0];
-    s_bot[0][warp][lane] = v[1][RB - 1];
+    sh.top[0][warp][lane] = v[1][0];
+    sh.bot[0][warp + 1][lane] = v[1][RB - 1];
     __syncthreads();
-    tb_half_sweep<0, RB, WARPS>(v, m[0], warp > 0 ? s_bot[0][warp - 1][lane] : zero,
-                                warp < WARPS - 1 ? s_top[0][warp + 1][lane] : zero, omega);
-    s_top[1][warp][lane] = v[0][0];
-    s_bot[1][warp][lane] = v[0][RB - 1];
+    tb_half_sweep<0, RB, WARPS>(v, m[0], sh.bot[0][warp][lane], sh.top[0][warp + 1][lane], omega);
+    sh.top[1][warp][lane] = v[0][0];
+    sh.bot[1][warp + 1][lane] = v[0][RB - 1];
     __syncthreads();
-    tb_half_sweep<1, RB, WARPS>(v, m[1], warp > 0 ? s_bot[1][warp - 1][lane] : zero,
-                                warp < WARPS - 1 ? s_top[1][warp + 1][lane] : zero, omega);
+    tb_half_sweep<1, RB, WARPS>(v, m[1], sh.bot[1][warp][lane], sh.top[1][warp + 1][lane], omega);
 }
 
 // Store the rows of the tile interior [y_tile, y_tile + YI) held by the thread.
@@ -220,8 +291,7 @@ template <int T, int RB, int WARPS>
 __device__ __forceinline__ void tb_tile(const float *__restrict__ Rin, const float *__restrict__ Bin,
                                         float *__restrict__ Rout, float *__restrict__ Bout,
                                         const uint32_t *__restrict__ MR, const uint32_t *__restrict__ MB, int ny,
-                                        int W4, int S, int MW, float omega, int bx, int by,
-                                        float4 (&s_top)[2][WARPS][32], float4 (&s_bot)[2][WARPS][32]) {
+                                        int W4, int S, int MW, float omega, int bx, int by, TBShared<WARPS> &sh) {
     using Sh = TBShape<T, RB, WARPS>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k4 = bx * Sh::KI4 - Sh::HK4 + lane;
@@ -231,9 +301,10 @@ __device__ __forceinline__ void tb_tile(const float *__restrict__ Rin, const flo
 
     float4 v[2][RB];
     TBMask<RB> m[2];
+    tb_shared_init<WARPS>(sh);
     tb_load<RB>(v, m, Rin, Bin, MR, MB, y0, k4, kin, ny, S, MW);
 #pragma unroll 1
-    for (int p = 0; p < T; p++) tb_full_sweep<RB, WARPS>(v, m, omega, s_top, s_bot);
+    for (int p = 0; p < T; p++) tb_full_sweep<RB, WARPS>(v, m, omega, sh);
     tb_store<RB>(v, Rout, Bout, y0, y_tile, Sh::YI, k4, kin && lane >= Sh::HK4 && lane < 32 - Sh::HK4, ny, S);
 }
 
