@@ -401,15 +401,29 @@ int ws_unet_train_step(float *params, float *grads, float *adam_m, float *adam_v
  * S: device BF16 [cout][H][W] added before the activation, or NULL; Y: device
  * BF16 [cout][H][W]; relu: 1 for ReLU, 0 for none.  impl: WS_CONV_AUTO (BF16
  * tensor cores where cin % 16 == 0 and cout % 32 == 0, else CUDA cores),
- * WS_CONV_SIMT (direct convolution on CUDA cores) or WS_CONV_MMA (tensor cores,
- * mma.sync m16n8k16, FP32 accumulation; TW_EINVAL when the channel counts do not
- * allow it).  Both accumulate every product in FP32; they differ only in the
- * order of the sums.  Enqueued on `stream`.  Errors: TW_EINVAL, TW_ECUDA. */
+ * WS_CONV_SIMT (direct convolution on CUDA cores), WS_CONV_MMA (tensor cores,
+ * mma.sync m16n8k16, FP32 accumulation) or WS_CONV_TC (5th-generation tensor
+ * cores: tcgen05.mma implicit GEMM with the accumulators in tensor memory, for
+ * cin % 16 == 0, cout in {32, 64, 128}, W % 128 == 0 and H even; it needs
+ * ws_conv3x3_workspace_size() bytes of 256-byte-aligned device workspace for
+ * the weights re-arranged in BF16, and is what WS_CONV_AUTO uses inside the
+ * network wherever those conditions hold).  Every form accumulates each
+ * product in FP32; they differ only in the order of the sums.  TW_EINVAL when
+ * the channel counts or sizes do not allow the form asked for; TW_EWORKSPACE
+ * for a missing or short workspace.  Enqueued on `stream`.  The implicit
+ * GEMM's waits on its own tensor-core work are bounded (one second): a wait
+ * that gives up sets a flag that ws_conv_check reads. */
 #define WS_CONV_AUTO 0
 #define WS_CONV_SIMT 1
 #define WS_CONV_MMA 2
+#define WS_CONV_TC 3
+size_t ws_conv3x3_workspace_size(int cin, int cout, int H, int W, int impl);
 int ws_conv3x3(const void *X, const float *Wt, const float *b, const void *S, void *Y, int cin, int cout, int H, int W,
-               int relu, int impl, void *stream);
+               int relu, int impl, void *workspace, size_t workspace_bytes, void *stream);
+/* ws_conv_check: *timed_out = 1 if a WS_CONV_TC convolution on the current
+ * device gave up a bounded wait since the last call (its output is then
+ * invalid), else 0; clears the flag.  Synchronises the device. */
+int ws_conv_check(int *timed_out);
 
 /* ---- Kalman filter (host) ----------------------------------------------------
  * kf_update: one step of the constant-velocity filter of Sec. 3.5 for n host

@@ -29,7 +29,7 @@ HP_JACOBI, HP_RBSOR, HP_MIXED = 0, 1, 2
 HP_STORE_F32, HP_STORE_F16, HP_STORE_BF16 = 0, 1, 2
 HP_WARM_START, HP_OUT_PHI, HP_TIMING, HP_HOST_LOOP, HP_POLISH = 1, 2, 4, 8, 16
 HP_LOOP_HOST, HP_LOOP_GRAPH = 0, 1
-WS_CONV_AUTO, WS_CONV_SIMT, WS_CONV_MMA = 0, 1, 2
+WS_CONV_AUTO, WS_CONV_SIMT, WS_CONV_MMA, WS_CONV_TC = 0, 1, 2, 3
 
 EXPORTS = (
     "tw_build_grid_workspace_size", "tw_build_grid", "tw_build_grids_workspace_size", "tw_build_grids",
@@ -39,7 +39,8 @@ EXPORTS = (
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
     "kf_update", "kf_init", "ws_unet_param_count", "ws_unet_workspace_size", "ws_unet_init", "ws_make_target",
     "ws_unet_forward", "ws_unet_train_step", "ws_unet_warm_start_workspace_size", "ws_unet_warm_start",
-    "ws_conv3x3", "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
+    "ws_conv3x3_workspace_size", "ws_conv3x3", "ws_conv_check",
+    "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
 )
 
 
@@ -191,8 +192,12 @@ def load() -> ctypes.CDLL:
     lib.ws_unet_warm_start_workspace_size.restype = Z
     lib.ws_unet_warm_start.argtypes = [P, P, I, I, I, I, I, P, P, Z, P]
     lib.ws_unet_warm_start.restype = I
-    lib.ws_conv3x3.argtypes = [P, P, P, P, P, I, I, I, I, I, I, P]
+    lib.ws_conv3x3.argtypes = [P, P, P, P, P, I, I, I, I, I, I, P, Z, P]
     lib.ws_conv3x3.restype = I
+    lib.ws_conv3x3_workspace_size.argtypes = [I, I, I, I, I]
+    lib.ws_conv3x3_workspace_size.restype = Z
+    lib.ws_conv_check.argtypes = [P]
+    lib.ws_conv_check.restype = I
     lib.tw_status_string.argtypes = [I]
     lib.tw_status_string.restype = ctypes.c_char_p
     lib.tw_last_cuda_error.restype = I
@@ -476,10 +481,22 @@ def ws_conv3x3(x, w, b=None, skip=None, relu=False, impl=WS_CONV_AUTO):
     cin, H, W = x.shape
     cout = w.shape[0]
     y = torch.empty((cout, H, W), dtype=torch.bfloat16, device=x.device)
-    _check("ws_conv3x3", load().ws_conv3x3(_ptr(x), _ptr(w), _ptr(b) if b is not None else None,
-                                           _ptr(skip) if skip is not None else None, _ptr(y), cin, cout, H, W,
-                                           1 if relu else 0, int(impl), _stream(x.device)))
+    lib = load()
+    nws = lib.ws_conv3x3_workspace_size(cin, cout, H, W, int(impl))
+    ws = workspace(nws, x.device, "conv") if nws else None
+    _check("ws_conv3x3", lib.ws_conv3x3(_ptr(x), _ptr(w), _ptr(b) if b is not None else None,
+                                        _ptr(skip) if skip is not None else None, _ptr(y), cin, cout, H, W,
+                                        1 if relu else 0, int(impl), _ptr(ws) if ws is not None else None,
+                                        ws.numel() if ws is not None else 0, _stream(x.device)))
     return y
+
+
+def ws_conv_check() -> bool:
+    """True if a WS_CONV_TC convolution on the current device gave up a bounded wait since the last
+    call (its output is then invalid); clears the flag."""
+    flag = ctypes.c_int()
+    _check("ws_conv_check", load().ws_conv_check(ctypes.byref(flag)))
+    return bool(flag.value)
 
 
 class WarmStartNet:

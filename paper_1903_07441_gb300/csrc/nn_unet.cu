@@ -516,6 +516,12 @@ static size_t carve_act(Carver &cv, int H, int W, Act *A) {
     return cv.need;
 }
 
+bool conv3x3_tc_ok(int cin, int cout, int H, int W);
+size_t conv3x3_tc_scratch_bytes(int cin, int cout);
+int conv3x3_tc(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
+               int W, int relu, void *scratch, cudaStream_t s);
+int conv3x3_tc_error(int *flag);
+
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256); }
 
 // Split-K factor of a tensor-core convolution: enough CTAs for two per SM of a
@@ -536,11 +542,17 @@ static int splitk_plan(int cin, int cout, int H, int W, size_t cap_floats) {
 
 // One 3x3 convolution: the tensor-core kernel where the channel counts allow
 // it (impl WS_CONV_AUTO), or the one asked for.  part (nullable): scratch for
-// split-K partial sums, part_floats long.
+// split-K partial sums, part_floats long, which also holds the re-arranged
+// weights of the tensor-memory kernel (WS_CONV_TC).
 static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
                    int W, int relu, int impl, cudaStream_t s, float *part = nullptr, size_t part_floats = 0) {
     const bool mma_ok = cin % 16 == 0 && cout % 32 == 0;
     if (impl == WS_CONV_MMA && !mma_ok) return TW_EINVAL;
+    if (impl == WS_CONV_TC) {
+        if (!conv3x3_tc_ok(cin, cout, H, W)) return TW_EINVAL;
+        if (!part || part_floats * sizeof(float) < conv3x3_tc_scratch_bytes(cin, cout)) return TW_EWORKSPACE;
+        return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, part, s);
+    }
     if (impl != WS_CONV_SIMT && mma_ok) {
         const int sp = part ? splitk_plan(cin, cout, H, W, part_floats) : 1;
         float *pp = sp > 1 ? part : nullptr;
@@ -834,15 +846,29 @@ extern "C" int ws_unet_train_step(float *params, float *grads, float *adam_m, fl
     return TW_OK;
 }
 
+extern "C" size_t ws_conv3x3_workspace_size(int cin, int cout, int H, int W, int impl) {
+    using namespace tw::nn;
+    if (impl != WS_CONV_TC || cin < 1 || cout < 1 || !conv3x3_tc_ok(cin, cout, H, W)) return 0;
+    return (conv3x3_tc_scratch_bytes(cin, cout) + 255) & ~(size_t)255;
+}
+
 extern "C" int ws_conv3x3(const void *X, const float *Wt, const float *b, const void *S, void *Y, int cin, int cout,
-                          int H, int W, int relu, int impl, void *stream) {
+                          int H, int W, int relu, int impl, void *workspace, size_t workspace_bytes, void *stream) {
     using namespace tw::nn;
     if (!X || !Wt || !Y || cin < 1 || cout < 1 || H < 1 || W < 1 || H > 65536 || W > 65536 ||
-        (impl != WS_CONV_AUTO && impl != WS_CONV_SIMT && impl != WS_CONV_MMA))
+        (impl != WS_CONV_AUTO && impl != WS_CONV_SIMT && impl != WS_CONV_MMA && impl != WS_CONV_TC))
         return TW_EINVAL;
+    if (impl == WS_CONV_TC && (!workspace || !ws_aligned(workspace))) return TW_EWORKSPACE;
     int e = conv3x3((const bf16 *)X, Wt, b, (const bf16 *)S, (bf16 *)Y, cin, cout, H, W, relu ? 1 : 0, impl,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, impl == WS_CONV_TC ? (float *)workspace : nullptr,
+                    impl == WS_CONV_TC ? workspace_bytes / sizeof(float) : 0);
     if (e) return e;
     TW_CHECK_LAUNCH();
     return TW_OK;
+}
+
+extern "C" int ws_conv_check(int *timed_out) {
+    using namespace tw::nn;
+    if (!timed_out) return TW_EINVAL;
+    return conv3x3_tc_error(timed_out);
 }

@@ -193,13 +193,21 @@ def test_warm_start_entry_points_reject_bad_input_on_host(lib):
     """The network's entry points validate sizes and choices before any GPU work."""
     P = ctypes.c_void_p(256)
     # ws_conv3x3: unknown implementation, non-positive sizes, missing pointers
-    assert lib.ws_conv3x3(P, P, None, None, P, 32, 32, 16, 16, 1, 7, None) == tw.TW_EINVAL
-    assert lib.ws_conv3x3(P, P, None, None, P, 0, 32, 16, 16, 1, tw.WS_CONV_AUTO, None) == tw.TW_EINVAL
-    assert lib.ws_conv3x3(P, P, None, None, P, 32, 32, 0, 16, 1, tw.WS_CONV_AUTO, None) == tw.TW_EINVAL
-    assert lib.ws_conv3x3(None, P, None, None, P, 32, 32, 16, 16, 1, tw.WS_CONV_AUTO, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 32, 32, 16, 16, 1, 7, None, 0, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 0, 32, 16, 16, 1, tw.WS_CONV_AUTO, None, 0, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 32, 32, 0, 16, 1, tw.WS_CONV_AUTO, None, 0, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(None, P, None, None, P, 32, 32, 16, 16, 1, tw.WS_CONV_AUTO, None, 0, None) == tw.TW_EINVAL
     # the tensor-core form needs cin % 16 == 0 and cout % 32 == 0
-    assert lib.ws_conv3x3(P, P, None, None, P, 8, 32, 16, 16, 1, tw.WS_CONV_MMA, None) == tw.TW_EINVAL
-    assert lib.ws_conv3x3(P, P, None, None, P, 32, 16, 16, 16, 1, tw.WS_CONV_MMA, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 8, 32, 16, 16, 1, tw.WS_CONV_MMA, None, 0, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 32, 16, 16, 16, 1, tw.WS_CONV_MMA, None, 0, None) == tw.TW_EINVAL
+    # the tensor-memory form: cin % 16 == 0, cout in {32, 64, 128}, W % 128 == 0, H even, and a workspace
+    assert lib.ws_conv3x3_workspace_size(64, 128, 16, 256, tw.WS_CONV_TC) >= 64 * 128 * 9 * 2
+    assert lib.ws_conv3x3_workspace_size(64, 128, 16, 256, tw.WS_CONV_MMA) == 0
+    for cin, cout, H, W in ((64, 96, 16, 256), (8, 64, 16, 256), (64, 64, 16, 200), (64, 64, 15, 256)):
+        assert lib.ws_conv3x3_workspace_size(cin, cout, H, W, tw.WS_CONV_TC) == 0
+        assert lib.ws_conv3x3(P, P, None, None, P, cin, cout, H, W, 1, tw.WS_CONV_TC, P, 1 << 20, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 64, 64, 16, 256, 1, tw.WS_CONV_TC, None, 0, None) == tw.TW_EWORKSPACE
+    assert lib.ws_conv3x3(P, P, None, None, P, 64, 64, 16, 256, 1, tw.WS_CONV_TC, P, 100, None) == tw.TW_EWORKSPACE
     # the network: H and W multiples of 8, goal inside, workspace present
     assert lib.ws_unet_workspace_size(64, 64) > lib.ws_unet_workspace_size(16, 16) > 0
     assert lib.ws_unet_forward(P, P, 60, 64, 1, 1, None, None, P, 1 << 30, None) == tw.TW_EINVAL

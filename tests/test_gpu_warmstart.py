@@ -63,6 +63,36 @@ def test_conv3x3_tensor_core_matches_cuda_core_and_fp64(dev, cin, cout, H, W):
     assert np.array_equal(outs[tw.WS_CONV_AUTO], outs[tw.WS_CONV_MMA])
 
 
+@pytest.mark.parametrize("cin,cout,H,W,with_skip", [(16, 32, 2, 128, False), (32, 32, 8, 256, True),
+                                                    (64, 64, 6, 128, True), (128, 128, 4, 384, True),
+                                                    (64, 128, 10, 128, False), (128, 64, 2, 256, True),
+                                                    (32, 128, 4, 128, True), (128, 32, 2, 128, False)])
+def test_conv3x3_tensor_memory_matches_cuda_core_and_fp64(dev, cin, cout, H, W, with_skip):
+    """The tcgen05 implicit GEMM (accumulators in tensor memory, operands staged channel-last in shared
+    memory) computes the same layer as the CUDA-core direct convolution: within BF16 output rounding of
+    the FP64 convolution of the same BF16 inputs and weights, at most one BF16 ulp from the CUDA-core
+    result, every edge pixel (zero padding) and every channel block included; its bounded waits never
+    gave up."""
+    g = torch.Generator(device="cpu").manual_seed(cin * 977 + cout * 13 + H * 7 + W)
+    x = (torch.randn((cin, H, W), generator=g)).to(torch.bfloat16).to(dev)
+    w = (torch.randn((cout, cin, 3, 3), generator=g) / (3.0 * cin ** 0.5)).to(dev)
+    b = (0.1 * torch.randn((cout,), generator=g)).to(dev)
+    skip = torch.randn((cout, H, W), generator=g).to(torch.bfloat16).to(dev) if with_skip else None
+    tc_out = tw.ws_conv3x3(x, w, b, skip, relu=with_skip, impl=tw.WS_CONV_TC).float().cpu().numpy()
+    simt = tw.ws_conv3x3(x, w, b, skip, relu=with_skip, impl=tw.WS_CONV_SIMT).float().cpu().numpy()
+    torch.cuda.synchronize()
+    assert not tw.ws_conv_check()
+    xr = x.float().cpu().numpy().astype(np.float64)
+    wr = w.to(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+    ref = nn.conv(xr, wr, b.cpu().numpy().astype(np.float64))
+    if with_skip:
+        ref = np.maximum(ref + skip.float().cpu().numpy(), 0.0)
+    scale = np.abs(ref) + 1e-2
+    assert np.all(np.abs(tc_out - ref) <= 2.0 ** -7 * scale), np.abs(tc_out - ref).max()
+    both = np.maximum(np.abs(tc_out), np.abs(simt))
+    assert np.all(np.abs(tc_out - simt) <= 2.0 ** -7 * (both + 1e-2))
+
+
 def test_conv3x3_rejects_tensor_core_shapes_it_cannot_take(dev):
     x = torch.zeros((8, 16, 16), dtype=torch.bfloat16, device=dev)
     w = torch.zeros((32, 8, 3, 3), dtype=torch.float32, device=dev)
