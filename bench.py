@@ -511,9 +511,12 @@ def run_twgrid(args, rank, world, dist):
                           ("rbsor_fp32_graph_polish", tw.Params(tol=args.tol, max_sweeps=args.max_sweeps,
                                                                 flags=tw.HP_POLISH)),
                           ("mixed_fp16", tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_F16, tol=args.tol,
-                                                   max_sweeps=args.max_sweeps)),
+                                                   max_sweeps=args.max_sweeps, etol=args.etol)),
                           ("mixed_bf16", tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_BF16, tol=args.tol,
-                                                   max_sweeps=args.max_sweeps))):
+                                                   max_sweeps=args.max_sweeps, etol=args.etol)),
+                          ("mixed_fp32_corrections", tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_F32,
+                                                               tol=args.tol, max_sweeps=args.max_sweeps,
+                                                               etol=args.etol))):
             tw.hp_relax(grid, occ, sc.goal, field=u, params=prm)   # warm
             times, fst = [], None
             for _ in range(5):
@@ -730,7 +733,7 @@ def run_learned(args, dev, tw):
         warm = {st: ([], [], []) for st in (1, 2, 4)}   # stride -> sweeps, total ms, network ms
         for sd in seeds:
             grid, occ, goal = scene(sd, sz)
-            prm = tw.Params(tol=args.tol)
+            prm = tw.Params(tol=args.tol, etol=args.etol)   # cold and warm solves to the same accuracy
             tw.hp_relax(grid, occ, goal, params=prm)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
@@ -748,7 +751,7 @@ def run_learned(args, dev, tw):
                 m_ = torch.cuda.Event(enable_timing=True)
                 m_.record()
                 _, s1 = tw.hp_relax(grid, occ, goal, field=u0,
-                                    params=tw.Params(tol=args.tol, flags=tw.HP_WARM_START))
+                                    params=tw.Params(tol=args.tol, etol=args.etol, flags=tw.HP_WARM_START))
                 b.record()
                 torch.cuda.synchronize()
                 warm[st][0].append(s1["sweeps"])

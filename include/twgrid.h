@@ -209,7 +209,10 @@ typedef struct {
                           r_inf above tol, one launch of T Gauss-Seidel sweeps on a copy (the polish of
                           HP_POLISH) is accepted if it meets tol.  If the estimate and the residual both
                           stop falling for four checks (once r_inf < 16 tol) the solve ends with
-                          TW_NOT_CONVERGED.  HP_JACOBI and HP_MIXED ignore etol. */
+                          TW_NOT_CONVERGED.  HP_MIXED: the outer loop also stops only once its
+                          estimate, the last FP64 update's size c times q / (1 - q) with q = its ratio
+                          to the update before (undefined while q >= 0.9), is <= etol.  HP_JACOBI
+                          ignores etol. */
 } hp_params;
 
 typedef struct {

@@ -173,17 +173,34 @@ __global__ void __launch_bounds__(256) mx_residual_kernel(RBLayout g, const doub
     if (pass == 0) block_max_sum_f64(rmax, out_max, reinterpret_cast<double *>(out_max + 1));
 }
 
-// x += s * e (FP64), e read from the colour-split planes.
+// x += s * e (FP64), e read from the colour-split planes; the largest |s e|
+// of the update goes to *dmax (bits of a non-negative double, atomicMax).
 template <class S>
-__global__ void mx_update_kernel(RBLayout g, double *__restrict__ x, int nx, int ny, const double *__restrict__ scale,
-                                 const S *__restrict__ er, const S *__restrict__ eb) {
+__global__ void __launch_bounds__(256) mx_update_kernel(RBLayout g, double *__restrict__ x, int nx, int ny,
+                                                        const double *__restrict__ scale, const S *__restrict__ er,
+                                                        const S *__restrict__ eb,
+                                                        unsigned long long *__restrict__ dmax) {
     const int xx = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (xx >= nx || y >= ny) return;
-    const int color = (xx + y) & 1, k = xx >> 1;
-    const S *e = color ? eb : er;
-    float4 q4 = Store<S>::load4(e + (size_t)y * g.S + 4 + (k & ~3));
-    const float ev = (&q4.x)[k & 3];
-    if (mx_free(g, xx, y)) x[(size_t)y * nx + xx] += *scale * (double)ev;
+    double d = 0.0;
+    if (xx < nx && y < ny) {
+        const int color = (xx + y) & 1, k = xx >> 1;
+        const S *e = color ? eb : er;
+        float4 q4 = Store<S>::load4(e + (size_t)y * g.S + 4 + (k & ~3));
+        const float ev = (&q4.x)[k & 3];
+        if (mx_free(g, xx, y)) {
+            d = *scale * (double)ev;
+            x[(size_t)y * nx + xx] += d;
+        }
+    }
+    d = fabs(d);
+    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    __shared__ double sm[8];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) d = fmax(d, sm[w]);
+        if (d > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(d));
+    }
 }
 
 __global__ void mx_output_kernel(const double *__restrict__ x, float *__restrict__ out, size_t n) {
@@ -362,7 +379,7 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
     c.omega = c.adapt ? sor_initial_omega(nx, ny) : p->omega;
     c.omega_max = sor_omega_cap(nx, ny);
     int sweeps = 0, launches = 0, checks = 0, outer = 0;
-    double r_inf = 0.0;
+    double r_inf = 0.0, corr = 0.0, corr_prev = 0.0;   // sizes of the last two outer updates (max |s e|)
     st->status = TW_NOT_CONVERGED;
     const dim3 rgrid(ceil_div(g.W4, 128), ny), rblock(128);
     const int KI4 = 32 - 2 * ((T + 4) / 4), YI = kMxWarps * kMxRows - 4 * T;
@@ -382,7 +399,20 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
         TW_CUDA(cudaStreamSynchronize(s));
         st->resid_l2 = sqrt(sum);
         checks++;
-        if ((p->tol > 0.0 && r_inf <= p->tol) || r_inf == 0.0) { st->status = TW_OK; break; }
+        // outer error estimate (etol > 0): the last update's size corr shrinks by q = corr / corr_prev
+        // per outer step, so the error left after it is about corr q / (1 - q) (q above 0.9, or no
+        // earlier update: not estimated yet)
+        double est = DBL_MAX;
+        if (corr_prev > 0.0 && corr > 0.0) {
+            const double q = corr / corr_prev;
+            if (q < 0.9) est = corr * q / (1.0 - q);
+        } else if (outer > 0 && corr == 0.0) {
+            est = 0.0;
+        }
+        if (p->etol > 0.0) st->err_est = est;
+        const bool r_ok = (p->tol > 0.0 && r_inf <= p->tol) || r_inf == 0.0;
+        if (r_ok && (p->etol <= 0.0 || est <= p->etol)) { st->status = TW_OK; break; }
+        if (p->etol > 0.0 && p->tol <= 0.0 && est <= p->etol) { st->status = TW_OK; break; }
         if (sweeps >= p->max_sweeps) break;
         // 2. q = r / s in storage precision (s kept on the device in pad1[0])
         double *scale = &sc->pad1[0];
@@ -423,10 +453,17 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
             if (!relax_control(c, (double)rf, -1.0, n, -1.0)) break;
             if (prev > 0.0 && it > 4 && rf > 0.98 * prev) break;   // storage floor reached
         }
-        // 4. x += s e
+        // 4. x += s e, and the update's size
+        unsigned long long *dmax = reinterpret_cast<unsigned long long *>(&sc->pad1[1]);
+        TW_CUDA(cudaMemsetAsync(dmax, 0, sizeof(*dmax), s));
         TW_LAUNCH((mx_update_kernel<S>), dim3(ceil_div(nx, 256), ny), 256, 0, s, g, x, nx, ny, (const double *)scale,
-                  e[cur][0], e[cur][1]);
+                  e[cur][0], e[cur][1], dmax);
         TW_CHECK_LAUNCH();
+        unsigned long long db = 0;
+        TW_CUDA(cudaMemcpyAsync(&db, dmax, sizeof(db), cudaMemcpyDeviceToHost, s));
+        TW_CUDA(cudaStreamSynchronize(s));
+        corr_prev = corr;
+        memcpy(&corr, &db, sizeof(double));
         outer++;
         if (outer > 64) break;
     }

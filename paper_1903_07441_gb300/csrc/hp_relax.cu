@@ -583,7 +583,7 @@ static int relax_common(const uint8_t *occ, int nx, int ny, int gx, int gy, floa
     }
     // the FP64 residual of the output decides the residual test; with an error tolerance the
     // loop's error test must have passed as well
-    const bool err_ok = !(p->method == HP_RBSOR && p->etol > 0.0 && local.err_est > 0.0) || local.status == TW_OK;
+    const bool err_ok = !(p->method != HP_JACOBI && p->etol > 0.0 && local.err_est > 0.0) || local.status == TW_OK;
     if (p->tol > 0.0 && local.resid_inf <= p->tol && err_ok) local.status = TW_OK;
     if (st) *st = local;
     return local.status;

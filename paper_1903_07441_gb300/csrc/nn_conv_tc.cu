@@ -18,7 +18,7 @@
 // K = 16, BF16 in, FP32 accumulate) and commits them to the stage's mbarrier;
 // meanwhile every thread stages the next chunk into the other stage
 // (double buffering).  The epilogue reads each accumulator row from TMEM
-// (warp w owns TMEM lanes 32w .. 32w + 31, i.e. pixels), adds bias and skip,
+// (warp w owns TMEM lanes 32 (w % 4) .. + 31, i.e. pixels), adds bias and skip,
 // applies ReLU and stores BF16 in the network's [cout][H][W] layout.
 //
 // Every wait is bounded (one second of %globaltimer); a timeout sets
@@ -72,6 +72,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     while (!mbar_try_wait(bar, parity))
         if (globaltimer() - t0 > 1000000000ull) return false;
     return true;
+}
+
+// One thread: expect tx bytes on *bar, then copy bytes (multiple of 16, both
+// addresses 16-byte aligned) from global to shared memory with the bulk-copy
+// engine; the barrier's phase completes when they have landed.
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // Generic-proxy shared-memory writes -> visible to the tensor core's (async proxy) reads.
@@ -179,14 +191,22 @@ struct TcShape {
 };
 
 // Y = act(conv3x3(X) + b + S) for W % 128 == 0, H % MT == 0, cin % 16 == 0,
-// cout == N; 128 threads; grid (W / 128, H / MT).
+// cout == N; kTcThreads threads; grid (W / 128, H / MT).  Per chunk i (stage i % 2):
+// once the MMAs of chunk i - 2 are done, thread 0 starts the bulk copy of the
+// chunk's weights into the stage, every thread writes the chunk's input tile
+// from the registers it loaded during the previous chunk and issues the loads
+// of the next chunk's tile (in flight while this chunk's MMAs run); after a
+// barrier thread 0 waits for the weights and issues the MMAs.
+constexpr int kTcThreads = 256;   // 8 warps: more tile loads in flight per SM
 template <int N, int MT>
-__global__ void __launch_bounds__(128) conv3x3_tc_kernel(const bf16 *__restrict__ X, const uint4 *__restrict__ Wb,
+__global__ void __launch_bounds__(kTcThreads, 2) conv3x3_tc_kernel(const bf16 *__restrict__ X, const uint4 *__restrict__ Wb,
                                                          const float *__restrict__ b, const bf16 *__restrict__ S,
                                                          bf16 *__restrict__ Y, int cin, int H, int W, int relu) {
     using Sh = TcShape<N, MT>;
+    constexpr int NITEMS = 2 * Sh::ROWS * Sh::PX;          // (half, row, pixel) items of a tile
+    constexpr int ITEMS = (NITEMS + kTcThreads - 1) / kTcThreads;   // per thread
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t bars[2];
+    __shared__ uint64_t mma_done[2], b_full[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -196,8 +216,10 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const bf16 *__restrict_
 
     if (warp == 0) tc::tmem_alloc(&tmem_base_sh, Sh::NCOL);
     if (tid == 0) {
-        tc::mbar_init(&bars[0], 1);
-        tc::mbar_init(&bars[1], 1);
+        for (int k = 0; k < 2; k++) {
+            tc::mbar_init(&mma_done[k], 1);
+            tc::mbar_init(&b_full[k], 1);
+        }
         tc::fence_mbar_init();
         abort_sh = 0;
     }
@@ -206,72 +228,103 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const bf16 *__restrict_
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base_sh;
     const uint32_t sbase = tc::smem_u32(smem);
-    int issued = 0;   // chunks whose MMAs were issued (thread 0's view; uniform through the barriers)
 
-    for (int i = 0; i < chunks; i++) {
-        const int st = i & 1;
-        // the stage's previous chunk (i - 2) must have been consumed by its MMAs
-        if (i >= 2 && !tc::mbar_wait(&bars[st], (uint32_t)(((i >> 1) - 1) & 1))) abort_sh = 1;
-        uint8_t *sA = smem + st * Sh::STAGE;
-        uint8_t *sB = sA + Sh::A_BYTES;
-        // A: channel-last copy of 16 channels x ROWS rows x 130 pixels (zero outside the image)
-        const int ci0 = 16 * i;
-        for (int it = tid; it < 2 * Sh::ROWS * Sh::PX; it += 128) {
+    // this thread's items: source offsets (or -1 outside the image / past the tile) and shared offsets
+    long long src_off[ITEMS];
+    uint32_t dst_off[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const int it = tid + kTcThreads * j;
+        src_off[j] = -1;
+        dst_off[j] = 0xFFFFFFFFu;
+        if (it < NITEMS) {
             const int h = it / (Sh::ROWS * Sh::PX), rem = it - h * (Sh::ROWS * Sh::PX);
             const int r = rem / Sh::PX, p = rem - r * Sh::PX;
             const int y = y0 - 1 + r, x = x0 - 1 + p;
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            if (y >= 0 && y < H && x >= 0 && x < W) {
-                const unsigned short *src =
-                    reinterpret_cast<const unsigned short *>(X) + (size_t)(ci0 + 8 * h) * plane + (size_t)y * W + x;
-#pragma unroll
-                for (int c = 0; c < 8; c += 2)
-                    w[c >> 1] = (uint32_t)__ldg(src + (size_t)c * plane) |
-                                ((uint32_t)__ldg(src + (size_t)(c + 1) * plane) << 16);
-            }
-            *reinterpret_cast<uint4 *>(sA + h * Sh::A_HALF + (r * Sh::PX + p) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+            dst_off[j] = h * Sh::A_HALF + (r * Sh::PX + p) * 16;
+            if (y >= 0 && y < H && x >= 0 && x < W) src_off[j] = (long long)(8 * h) * plane + (long long)y * W + x;
         }
-        // B: the chunk's pre-arranged weights, a contiguous copy
-        const uint4 *wsrc = Wb + (size_t)i * (Sh::B_BYTES / 16);
-        for (int it = tid; it < (int)(Sh::B_BYTES / 16); it += 128) reinterpret_cast<uint4 *>(sB)[it] = __ldg(wsrc + it);
+    }
+    const unsigned short *Xs = reinterpret_cast<const unsigned short *>(X);
+    uint32_t ra[ITEMS][4];   // the prefetched tile: 8 channels per item, packed in pairs
+    auto load_tile = [&](int chunk) {
+        const unsigned short *base = Xs + (size_t)(16 * chunk) * plane;
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+#pragma unroll
+            for (int c = 0; c < 8; c += 2) {
+                uint32_t lo = 0u, hi = 0u;
+                if (src_off[j] >= 0) {
+                    lo = __ldg(base + src_off[j] + (size_t)c * plane);
+                    hi = __ldg(base + src_off[j] + (size_t)(c + 1) * plane);
+                }
+                ra[j][c >> 1] = lo | (hi << 16);
+            }
+        }
+    };
+    load_tile(0);
+    int issued = 0;
+    for (int i = 0; i < chunks; i++) {
+        const int st = i & 1;
+        // the stage's previous chunk (i - 2) must have been consumed by its MMAs
+        if (i >= 2 && !tc::mbar_wait(&mma_done[st], (uint32_t)(((i >> 1) - 1) & 1))) abort_sh = 1;
+        uint8_t *sA = smem + st * Sh::STAGE;
+        if (tid == 0 && !abort_sh)
+            tc::bulk_load(sA + Sh::A_BYTES, Wb + (size_t)i * (Sh::B_BYTES / 16), Sh::B_BYTES, &b_full[st]);
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++)
+            if (dst_off[j] != 0xFFFFFFFFu)
+                *reinterpret_cast<uint4 *>(sA + dst_off[j]) = make_uint4(ra[j][0], ra[j][1], ra[j][2], ra[j][3]);
+        if (i + 1 < chunks) load_tile(i + 1);
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (abort_sh) break;
         if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t a0 = sbase + st * Sh::STAGE, b0 = a0 + Sh::A_BYTES;
+            if (!tc::mbar_wait(&b_full[st], (uint32_t)((i >> 1) & 1))) {
+                abort_sh = 1;
+            } else {
+                tc::fence_after_sync();
+                const uint32_t a0 = sbase + st * Sh::STAGE, b0 = a0 + Sh::A_BYTES;
 #pragma unroll 1
-            for (int t = 0; t < MT; t++) {
+                for (int t = 0; t < MT; t++) {
 #pragma unroll
-                for (int k = 0; k < 9; k++) {
-                    const int dy = k / 3, dx = k - 3 * (k / 3);
-                    const uint64_t ad = tc::smem_desc(a0 + ((t + dy) * Sh::PX + dx) * 16, Sh::A_HALF, 128);
-                    const uint64_t bd = tc::smem_desc(b0 + k * Sh::B_TAP, N * 16, 128);
-                    tc::mma_bf16(tmem + (uint32_t)(t * N), ad, bd, tc::IDesc<128, N>::value, (i > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < 9; k++) {
+                        const int dy = k / 3, dx = k - 3 * (k / 3);
+                        const uint64_t ad = tc::smem_desc(a0 + ((t + dy) * Sh::PX + dx) * 16, Sh::A_HALF, 128);
+                        const uint64_t bd = tc::smem_desc(b0 + k * Sh::B_TAP, N * 16, 128);
+                        tc::mma_bf16(tmem + (uint32_t)(t * N), ad, bd, tc::IDesc<128, N>::value,
+                                     (i > 0 || k > 0) ? 1u : 0u);
+                    }
                 }
+                tc::mma_commit(&mma_done[st]);
             }
-            tc::mma_commit(&bars[st]);
         }
         issued = i + 1;
     }
+    __syncthreads();   // thread 0's abort (a weight copy that never landed) is seen by all
     // the last issued chunk's commit covers every MMA issued before it
     bool done = true;
-    if (issued > 0) {
+    if (issued > 0 && !abort_sh) {
         const int last = issued - 1;
-        done = tc::mbar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1));
+        done = tc::mbar_wait(&mma_done[last & 1], (uint32_t)((last >> 1) & 1));
     }
     if (!done || abort_sh) {
         if (tid == 0) atomicExch(&g_conv_tc_error, 1);
+        // the MMAs already issued must finish before the tensor memory is released (bounded)
+        if (issued > 0) tc::mbar_wait(&mma_done[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1));
     } else {
         tc::fence_after_sync();
-        const int x = x0 + 32 * warp + lane;
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its pixels); warps 0-3 and 4-7 take alternate
+        // 16-column blocks of the MT accumulators
+        const int wl = warp & 3, wh = warp >> 2;
+        const int x = x0 + 32 * wl + lane;
 #pragma unroll 1
         for (int t = 0; t < MT; t++) {
             const int y = y0 + t;
 #pragma unroll 1
-            for (int c0 = 0; c0 < N; c0 += 16) {
+            for (int c0 = 16 * wh; c0 < N; c0 += 16 * (kTcThreads / 128)) {
                 float v[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * N + c0), v);
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * wl) << 16) + (uint32_t)(t * N + c0), v);
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int co = c0 + j;
@@ -303,7 +356,7 @@ static int launch_tc(const bf16 *X, const bf16 *Wb, const float *b, const bf16 *
         attr_set[dev] = true;
     }
     dim3 grid(W / 128, H / MT);
-    TW_LAUNCH((conv3x3_tc_kernel<N, MT>), grid, 128, Sh::SMEM, s, X, reinterpret_cast<const uint4 *>(Wb), b, S, Y,
+    TW_LAUNCH((conv3x3_tc_kernel<N, MT>), grid, kTcThreads, Sh::SMEM, s, X, reinterpret_cast<const uint4 *>(Wb), b, S, Y,
               cin, H, W, relu);
     return TW_OK;
 }

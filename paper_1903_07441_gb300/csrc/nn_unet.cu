@@ -260,11 +260,14 @@ __global__ void conv_transpose_weights_kernel(const float *__restrict__ Wt, floa
     }
 }
 
-// dW[co][ci][k] += sum_p dY[co][p] X[ci][p + k - (1,1)], db[co] += sum_p dY[co][p].
-// CTA: one output channel block (16) x one input channel block (8) x a chunk of rows.
+// Partial sums of dW[co][ci][k] = sum_p dY[co][p] X[ci][p + k - (1,1)] and
+// db[co] = sum_p dY[co][p] over one chunk of rows: CTA (co block of 16, ci
+// block of 8, row chunk z) writes its sums to part[z][co][ci][k] and (ci block
+// 0) part_b[z][co]; conv3x3_bwd_weight_sum_kernel adds the chunks in order, so
+// the gradients do not depend on the order CTAs finish in.
 __global__ void __launch_bounds__(256) conv3x3_bwd_weight_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ dY,
-                                                                 float *__restrict__ dW, float *__restrict__ db, int cin,
-                                                                 int cout, int H, int W, int rows_per_cta) {
+                                                                 float *__restrict__ part, float *__restrict__ part_b,
+                                                                 int cin, int cout, int H, int W, int rows_per_cta) {
     // thread t: weight index (co, c, k) = t for t < COB*CIB*9/...; accumulate over pixels
     const int co0 = blockIdx.x * COB, ci0 = blockIdx.y * CIB;
     const int ya = blockIdx.z * rows_per_cta, yb = min(H, ya + rows_per_cta);
@@ -303,14 +306,35 @@ __global__ void __launch_bounds__(256) conv3x3_bwd_weight_kernel(const bf16 *__r
                 for (int p = 0; p < TS * 4; p++) accb += sdy[threadIdx.x][p];
         }
     }
+    const size_t zo = (size_t)blockIdx.z * cout * cin * 9;
 #pragma unroll
     for (int j = 0; j < 5; j++) {
         const int t = threadIdx.x + 256 * j;
         if (t >= COB * CIB * 9) break;
         const int co = t / (CIB * 9), c = (t / 9) % CIB, k = t % 9;
-        if (co0 + co < cout && ci0 + c < cin) atomicAdd(&dW[((size_t)(co0 + co) * cin + ci0 + c) * 9 + k], acc[j]);
+        if (co0 + co < cout && ci0 + c < cin) part[zo + ((size_t)(co0 + co) * cin + ci0 + c) * 9 + k] = acc[j];
     }
-    if (blockIdx.y == 0 && threadIdx.x < COB && co0 + threadIdx.x < cout && db) atomicAdd(&db[co0 + threadIdx.x], accb);
+    if (blockIdx.y == 0 && threadIdx.x < COB && co0 + threadIdx.x < cout)
+        part_b[(size_t)blockIdx.z * cout + co0 + threadIdx.x] = accb;
+}
+
+// dW += sum over the row chunks of part, db += sum of part_b, chunks in order.
+__global__ void conv3x3_bwd_weight_sum_kernel(const float *__restrict__ part, const float *__restrict__ part_b,
+                                              int chunks, float *__restrict__ dW, float *__restrict__ db, int cin,
+                                              int cout) {
+    const size_t n = (size_t)cout * cin * 9;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + cout; i += (size_t)gridDim.x * blockDim.x) {
+        if (i < n) {
+            float v = 0.0f;
+            for (int z = 0; z < chunks; z++) v += part[(size_t)z * n + i];
+            dW[i] += v;
+        } else if (db) {
+            const size_t co = i - n;
+            float v = 0.0f;
+            for (int z = 0; z < chunks; z++) v += part_b[(size_t)z * cout + co];
+            db[co] += v;
+        }
+    }
 }
 
 // dA = dY * (A > 0) in place on dY (A: the post-ReLU activation)
@@ -385,8 +409,24 @@ __global__ void __launch_bounds__(256) mse_kernel(const bf16 *__restrict__ P, co
         s += d * d;
         dP[i] = __float2bfloat16(2.0f * d * inv_count);
     }
+    // the CTA's sum into part[blockIdx.x] (fixed-shape reduction); loss_sum_kernel adds the CTAs in order
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv_count);
+    __shared__ float sw[8];
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < 8; w++) t += sw[w];
+        loss[blockIdx.x] = t * inv_count;
+    }
+}
+
+// *loss = sum of the n per-CTA partials, in index order (one thread: n <= 4096).
+__global__ void loss_sum_kernel(const float *__restrict__ part, int n, float *__restrict__ loss) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float t = 0.0f;
+    for (int i = 0; i < n; i++) t += part[i];
+    *loss = t;
 }
 
 __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
@@ -553,6 +593,11 @@ static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S
         if (!part || part_floats * sizeof(float) < conv3x3_tc_scratch_bytes(cin, cout)) return TW_EWORKSPACE;
         return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, part, s);
     }
+    // the automatic choice: the tensor-memory kernel wherever its shape conditions hold and the
+    // scratch for its re-arranged weights is there (inside the network), else mma.sync or CUDA cores
+    if (impl == WS_CONV_AUTO && part && conv3x3_tc_ok(cin, cout, H, W) &&
+        part_floats * sizeof(float) >= conv3x3_tc_scratch_bytes(cin, cout))
+        return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, part, s);
     if (impl != WS_CONV_SIMT && mma_ok) {
         const int sp = part ? splitk_plan(cin, cout, H, W, part_floats) : 1;
         float *pp = sp > 1 ? part : nullptr;
@@ -623,9 +668,15 @@ static void conv_bwd(const bf16 *X, const float *P, float *G, int li, const bf16
     const float *Wt = P + param_offset(li);
     float *dW = G + param_offset(li);
     float *db = dW + (size_t)c.cout * c.cin * 9;
-    const int rows = H < 16 ? H : 16;
-    dim3 gw(ceil_div(c.cout, COB), ceil_div(c.cin, CIB), ceil_div(H, rows));
-    TW_LAUNCH(conv3x3_bwd_weight_kernel, gw, 256, 0, s, X, dY, dW, db, c.cin, c.cout, H, W, rows);
+    // row chunks of at least 16 rows, as many as the scratch holds partial sums for
+    const size_t per = (size_t)c.cout * c.cin * 9 + c.cout;
+    int rows = H < 16 ? H : 16;
+    while ((size_t)ceil_div(H, rows) * per > kSplitKCap) rows *= 2;
+    const int nz = ceil_div(H, rows);
+    float *part_b = kpart + (size_t)nz * c.cout * c.cin * 9;
+    dim3 gw(ceil_div(c.cout, COB), ceil_div(c.cin, CIB), nz);
+    TW_LAUNCH(conv3x3_bwd_weight_kernel, gw, 256, 0, s, X, dY, kpart, part_b, c.cin, c.cout, H, W, rows);
+    TW_LAUNCH(conv3x3_bwd_weight_sum_kernel, blocks_for(per), 256, 0, s, kpart, part_b, nz, dW, db, c.cin, c.cout);
     if (!dX) return;
     TW_LAUNCH(conv_transpose_weights_kernel, blocks_for((size_t)c.cin * c.cout * 9), 256, 0, s, Wt, wt, c.cin, c.cout);
     // dX = conv3x3(dY, W^T) with cin/cout swapped: a forward conv of the transposed layer
@@ -827,7 +878,8 @@ extern "C" int ws_unet_train_step(float *params, float *grads, float *adam_m, fl
     TW_CUDA(cudaStreamSynchronize(s));
     const float inv = cnt > 0.0f ? 1.0f / cnt : 0.0f;
     bf16 *d_out = A.g2;   // head-output gradient
-    TW_LAUNCH(mse_kernel, blocks_for(n), 256, 0, s, A.out, target, occ, gx, gy, W, n, inv, d_out, A.loss);
+    TW_LAUNCH(mse_kernel, blocks_for(n), 256, 0, s, A.out, target, occ, gx, gy, W, n, inv, d_out, A.kpart);
+    TW_LAUNCH(loss_sum_kernel, 1, 32, 0, s, A.kpart, (int)blocks_for(n), A.loss);
     TW_CUDA(cudaMemsetAsync(grads, 0, sizeof(float) * total_params(), s));
     // backward needs its own scratch: dcur, dnext, tmp (64 x H x W), and the skip gradients
     std::vector<bf16 *> scratch = {A.g0, A.g1, A.g2, A.sk[0], A.sk[1], A.sk[2]};

@@ -104,3 +104,26 @@ def test_mixed_reaches_1e6_at_2048(dev):
         bound = ref["tau_max"] * st["resid_inf"] * 1.001 + 1e-7   # + the FP32 rounding of the output
         assert u.min() >= -bound and u.max() <= 1.0 + bound
         assert np.abs(u[cells[:, 1], cells[:, 0]] - ustar).max() <= bound
+
+
+@pytest.mark.slow
+def test_mixed_with_error_tolerance_at_2048(dev):
+    """With the error tolerance (etol = 1e-5, r_inf <= 1e-6) at 2048^2, against the oracle's full
+    field: the FP16-storage form and the FP32-correction form (FP64 refinement) meet max |u - u*|
+    <= 1e-5 over every cell -- the FP32-correction form far below it, since its FP64 master goes
+    under the FP32 rounding floor -- and the BF16-storage form, whose 8-bit mantissa leaves each
+    correction solve too short to converge the field's slow mode, either meets the tolerance or
+    reports TW_NOT_CONVERGED (it never claims an accuracy it has not shown)."""
+    sc = scenes.static2048()
+    occ, _, _ = oracle.build_grid(sc)
+    ustar, fixed = oracle.solve_field(occ, sc.goal, tol=1e-13)
+    for storage, bound in ((tw.HP_STORE_F16, 1e-5), (tw.HP_STORE_F32, 1e-7)):
+        u, st = _solve(dev, occ, sc.goal, storage=storage, tol=1e-6, etol=1e-5)
+        err = np.abs(u - ustar).max()
+        assert st["status"] == tw.TW_OK and st["resid_inf"] <= 1e-6 and st["err_est"] <= 1e-5, st
+        assert err <= bound, (storage, err, st)
+    u, st = _solve(dev, occ, sc.goal, storage=tw.HP_STORE_BF16, tol=1e-6, etol=1e-5)
+    if st["status"] == tw.TW_OK:
+        assert np.abs(u - ustar).max() <= 1e-5, st
+    else:
+        assert st["status"] == tw.TW_NOT_CONVERGED and np.abs(u - ustar).max() > 1e-6

@@ -103,32 +103,42 @@ def test_conv3x3_rejects_tensor_core_shapes_it_cannot_take(dev):
     assert tw.ws_conv3x3(x, w, impl=tw.WS_CONV_AUTO).shape == (32, 16, 16)
 
 
-def test_forward_and_gradients_match_fp64_reference(dev):
+# Bounds from the BF16 storage of activations and gradients (relative precision 2^-9 per rounding,
+# about 30 roundings deep): measured on GB300 the forward differs by 1.8 % (32^2) and 3.5 % (128^2,
+# where the level-0 layers run on the tensor-memory kernel) of its range, the layer gradients by at
+# most 6.4 % and 11.3 % in norm, with cosine similarity 0.9994 and 0.9996.
+@pytest.mark.parametrize("side,seed,fwd_tol,layer_tol", [(32, 9100, 0.03, 0.08), (128, 9101, 0.05, 0.15)])
+def test_forward_and_gradients_match_fp64_reference(dev, side, seed, fwd_tol, layer_tol):
     net = tw.WarmStartNet(dev, seed=7)
-    sc, occ = _scene(9100, 32)
+    sc, occ = _scene(seed, side)
     occ_t = torch.from_numpy(occ).to(dev)
     p = net.params.cpu().numpy().astype(np.float64)
     rng = np.random.default_rng(1)
-    # perturb the biases so that every unit is active somewhere
     _, pred = net.forward(occ_t, sc.goal)
     ref, _ = nn.forward(p, occ, sc.goal)
     g = pred.cpu().numpy()
     scale = np.abs(ref).max()
     assert scale > 0
-    assert np.abs(g - ref).max() <= 0.05 * scale + 1e-3
+    assert np.abs(g - ref).max() <= fwd_tol * scale + 1e-3
     target = (rng.standard_normal(occ.shape) * 0.1 - 0.3).astype(np.float32)
-    loss, grads = net.gradients(occ_t, sc.goal, torch.from_numpy(target).to(dev))
+    tt = torch.from_numpy(target).to(dev)
+    loss, grads = net.gradients(occ_t, sc.goal, tt)
+    grads = grads.clone()   # the network keeps one gradient buffer
+    loss2, grads2 = net.gradients(occ_t, sc.goal, tt)
+    # fixed-order reductions everywhere (no floating-point atomics): the same bits twice
+    assert loss == loss2 and torch.equal(grads, grads2)
     loss_ref, g_ref = nn.loss_and_grads(p, occ, sc.goal, target.astype(np.float64))
-    assert abs(loss - loss_ref) <= 0.03 * loss_ref
+    assert abs(loss - loss_ref) <= 0.04 * loss_ref
     gg = grads.cpu().numpy().astype(np.float64)
     cos = gg @ g_ref / (np.linalg.norm(gg) * np.linalg.norm(g_ref))
-    assert cos >= 0.99, cos
+    assert cos >= 0.998, cos
     o = 0
     for ci, co in nn.LAYERS:
         k = co * ci * 9 + co
         a, b = gg[o:o + k], g_ref[o:o + k]
-        assert np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(b) + 1e-6, (ci, co)
+        assert np.linalg.norm(a - b) <= layer_tol * np.linalg.norm(b) + 1e-6, (ci, co)
         o += k
+    assert not tw.ws_conv_check()
 
 
 def _fields(dev, seeds, side):
