@@ -87,6 +87,11 @@ typedef struct {
     double kappa;      /* inflation in standard deviations, >= 0 */
     double d_safe;     /* safety distance added to the body radius (m), >= 0 */
     int time_outer;    /* 0: t_j = R_{j-1}/v (t_0 = 0); 1: t_j = R_j/v */
+    double p_mark;     /* in [0, 1); 0 = off.  Gaussian marking with a probability threshold: with the
+                          obstacle centre distributed N(p, sigma^2 I), the chance that it lies within
+                          rho0 = radius + d_safe of its predicted position is 1 - exp(-rho0^2 / (2 sigma^2));
+                          a prediction whose chance is below p_mark -- sigma > alpha rho0 with
+                          alpha = 1 / sqrt(-2 ln(1 - p_mark)) -- marks no cell (too uncertain to place). */
 } tw_ring_law;
 
 /* ---- time-warped grid ------------------------------------------------------
@@ -95,7 +100,8 @@ typedef struct {
  *  2. For every track and ring: constant-velocity prediction at t_j (Eqs. 9-10)
  *     p = x + t v, P(t) = A P A^T + Q(t); sigma^2 = (Pxx(t) + Pyy(t)) / 2;
  *     disk radius rho = (radius + d_safe) + kappa * sigma (the Gaussian marking
- *     of Sec. 3.4 made binary).  All of it in correctly rounded FP64, then
+ *     of Sec. 3.4 made binary; with law.p_mark > 0 no disk where
+ *     sigma^2 > (alpha (radius + d_safe))^2).  All of it in correctly rounded FP64, then
  *     quantised to 1/256 cell (round half to even).
  *  3. For every cell: its ring j (smallest ring whose closed boundary contains
  *     the cell centre; beyond the last ring: the last ring) and its code:
@@ -407,7 +413,8 @@ int ws_unet_train_step(float *params, float *grads, float *adam_m, float *adam_v
  * WS_CONV_SIMT (direct convolution on CUDA cores), WS_CONV_MMA (tensor cores,
  * mma.sync m16n8k16, FP32 accumulation) or WS_CONV_TC (5th-generation tensor
  * cores: tcgen05.mma implicit GEMM with the accumulators in tensor memory, for
- * cin % 16 == 0, cout in {32, 64, 128}, W % 128 == 0 and H even; it needs
+ * cin % 16 == 0, cout in {32, 64, 128}, W % 128 == 0 and H a multiple of 4 (of
+ * 2 for cout 128); it needs
  * ws_conv3x3_workspace_size() bytes of 256-byte-aligned device workspace for
  * the weights re-arranged in BF16, and is what WS_CONV_AUTO uses inside the
  * network wherever those conditions hold).  Every form accumulates each

@@ -28,6 +28,7 @@ cells, the energy never increases) but not by any value the paper fixes.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 
@@ -98,10 +99,10 @@ def _open(path):
         i32, f64 = ctypes.c_int, ctypes.c_double
         lib.or_ring_table.argtypes = [i32, f64, f64, i32, f64, i32, f64, f64, f64, P, P]
         lib.or_ring_table.restype = i32
-        lib.or_predict_one.argtypes = [P, f64, f64, f64, f64, f64, f64, f64, P, P, P]
+        lib.or_predict_one.argtypes = [P, f64, f64, f64, f64, f64, f64, f64, f64, P, P, P]
         lib.or_predict_one.restype = None
         lib.or_build_grid.argtypes = [i32, i32, f64, f64, f64, P, P, i32, i32, i32, f64, f64,
-                                      i32, f64, f64, f64, i32, P, P, P]
+                                      i32, f64, f64, f64, i32, f64, P, P, P]
         lib.or_build_grid.restype = i32
         lib.or_residual.argtypes = [P, P, i32, i32, P, P]
         lib.or_residual.restype = None
@@ -146,8 +147,10 @@ def predict_disk(track, t, law, cell, ox=0.0, oy=0.0):
     """Fixed-point predicted centre and inflated radius of one track at time t."""
     trk = np.ascontiguousarray(track, dtype=np.float64)
     out = [ctypes.c_int64() for _ in range(3)]
+    p_mark = float(getattr(law, "p_mark", 0.0))
+    alpha = 1.0 / math.sqrt(-2.0 * math.log(1.0 - p_mark)) if p_mark > 0.0 else 0.0   # as or_build_grid
     _load().or_predict_one(_p(trk), float(t), float(law.q_accel), float(law.kappa),
-                           float(law.d_safe), float(ox), float(oy), float(cell),
+                           float(law.d_safe), float(alpha), float(ox), float(oy), float(cell),
                            *[ctypes.byref(o) for o in out])
     return tuple(int(o.value) for o in out)
 
@@ -170,7 +173,7 @@ def build_grid(scene, law=None, robot=None, tracks=None, static_occ="scene"):
                               _p(tracks), tracks.shape[0], int(law.kind), int(law.mark),
                               float(law.r0), float(law.growth), int(law.n_rings),
                               float(law.q_accel), float(law.kappa), float(law.d_safe),
-                              int(law.time_outer), st_p, _p(occ), _p(ring))
+                              int(law.time_outer), float(getattr(law, "p_mark", 0.0)), st_p, _p(occ), _p(ring))
     if J <= 0:
         raise ValueError(f"or_build_grid failed: {J}")
     return occ, ring, J

@@ -118,7 +118,7 @@ static int64_t q_pos(double v, double origin, double cell)
  *   rho = (radius + d_safe) + kappa*sigma        (Sec. 3.4 Gaussian marking,
  *                                                  made binary at kappa sigma)
  * ---------------------------------------------------------------------- */
-void or_predict_one(const double *trk, double t, double q, double kappa, double d_safe,
+void or_predict_one(const double *trk, double t, double q, double kappa, double d_safe, double alpha,
                     double ox, double oy, double cell,
                     int64_t *pxq, int64_t *pyq, int64_t *rhoq)
 {
@@ -135,6 +135,13 @@ void or_predict_one(const double *trk, double t, double q, double kappa, double 
     *pxq = q_pos(px, ox, cell);
     *pyq = q_pos(py, oy, cell);
     *rhoq = q_clamp((rho / cell) * 256.0, 0, OR_RADIUS_CLAMP);
+    /* probability-threshold marking: a prediction whose centre is too uncertain to
+     * lie within radius + d_safe of its mean with the threshold probability marks
+     * nothing (radius -1) */
+    if (alpha > 0.0) {
+        double a = alpha * (radius + d_safe);
+        if (s2 > a * a) *rhoq = -1;
+    }
 }
 
 /* Ring of a fixed-point offset (dx, dy) from the robot: the smallest j whose
@@ -172,9 +179,12 @@ static int ring_of(int kind, int64_t dx, int64_t dy, int J, const int64_t *Rq,
 int or_build_grid(int nx, int ny, double cell, double ox, double oy,
                   const double *robot, const double *tracks, int n,
                   int kind, int mark, double r0, double growth, int n_rings,
-                  double q, double kappa, double d_safe, int time_outer,
+                  double q, double kappa, double d_safe, int time_outer, double p_mark,
                   const uint8_t *static_occ, uint8_t *occ, int16_t *ring)
 {
+    /* the probability that an N(p, sigma^2 I) centre lies within rho0 of p is
+     * 1 - exp(-rho0^2 / (2 sigma^2)); it reaches p_mark while sigma <= alpha rho0 */
+    double alpha = (p_mark > 0.0) ? 1.0 / sqrt(-2.0 * log(1.0 - p_mark)) : 0.0;
     double R[OR_MAX_RINGS], t[OR_MAX_RINGS];
     int64_t Rq[OR_MAX_RINGS], Aq[OR_MAX_RINGS], Cq[OR_MAX_RINGS];
     if (nx < 1 || ny < 1 || nx > 65536 || ny > 65536) return OR_EINVAL;
@@ -198,7 +208,7 @@ int or_build_grid(int nx, int ny, double cell, double ox, double oy,
     int *own = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
     for (int o = 0; o < n; o++) {
         for (int j = 0; j < J; j++)
-            or_predict_one(tracks + 21 * (size_t)o, t[j], q, kappa, d_safe, ox, oy, cell,
+            or_predict_one(tracks + 21 * (size_t)o, t[j], q, kappa, d_safe, alpha, ox, oy, cell,
                            &PX[(size_t)o * J + j], &PY[(size_t)o * J + j], &RH[(size_t)o * J + j]);
         int64_t exq = q_pos(tracks[21 * (size_t)o + 0], ox, cell);
         int64_t eyq = q_pos(tracks[21 * (size_t)o + 1], oy, cell);
@@ -221,7 +231,7 @@ int or_build_grid(int nx, int ny, double cell, double ox, double oy,
                     int jj = (mark == 0) ? jr : own[o];
                     size_t d = (size_t)o * J + jj;
                     int64_t dx = cx - PX[d], dy = cy - PY[d];
-                    if (dx * dx + dy * dy <= RH[d] * RH[d]) code = 2;
+                    if (RH[d] >= 0 && dx * dx + dy * dy <= RH[d] * RH[d]) code = 2;
                 }
             }
             occ[c] = code;

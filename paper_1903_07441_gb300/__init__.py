@@ -67,7 +67,8 @@ class tw_pose(ctypes.Structure):
 class tw_ring_law(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("mark", ctypes.c_int), ("r0", ctypes.c_double),
                 ("growth", ctypes.c_double), ("n_rings", ctypes.c_int), ("q_accel", ctypes.c_double),
-                ("kappa", ctypes.c_double), ("d_safe", ctypes.c_double), ("time_outer", ctypes.c_int)]
+                ("kappa", ctypes.c_double), ("d_safe", ctypes.c_double), ("time_outer", ctypes.c_int),
+                ("p_mark", ctypes.c_double)]
 
 
 class tw_grid_job(ctypes.Structure):
@@ -258,7 +259,8 @@ def make_pose(robot) -> tw_pose:
 
 def make_law(law) -> tw_ring_law:
     return tw_ring_law(int(law.kind), int(law.mark), float(law.r0), float(law.growth), int(law.n_rings),
-                       float(law.q_accel), float(law.kappa), float(law.d_safe), int(law.time_outer))
+                       float(law.q_accel), float(law.kappa), float(law.d_safe), int(law.time_outer),
+                       float(getattr(law, "p_mark", 0.0)))
 
 
 def _check(fn, st, ok=(TW_OK,)):

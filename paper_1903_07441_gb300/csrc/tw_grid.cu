@@ -46,6 +46,7 @@ struct Params {
     double cell, ox, oy;
     double rx, ry, hx, hy, speed;
     double r0, growth, q, kappa, d_safe;
+    double alpha;    // probability-threshold factor of the marking (0: every prediction is marked)
 };
 
 __device__ __forceinline__ long long qclamp(double v, long long lo, long long hi) {
@@ -143,6 +144,10 @@ __device__ Disk predict_disk(const tw_track &T, double t, const Params &p, int j
     d.j = j;
     d.pad = 0;
     d.r2 = rq * rq;
+    if (p.alpha > 0.0) {   // too uncertain to place: below the marking probability, no disk (r2 < 0)
+        const double a = __dmul_rn(p.alpha, __dadd_rn(T.radius, p.d_safe));
+        if (s2 > __dmul_rn(a, a)) d.r2 = -1;
+    }
     return d;
 }
 
@@ -361,7 +366,8 @@ static bool valid_law(const tw_ring_law *L) {
            L->r0 > 0.0 && finite(L->growth) && L->growth > 1.0 && L->n_rings >= 0 &&
            L->n_rings <= kMaxRings && finite(L->q_accel) && L->q_accel >= 0.0 &&
            finite(L->kappa) && L->kappa >= 0.0 && finite(L->d_safe) && L->d_safe >= 0.0 &&
-           (L->time_outer == 0 || L->time_outer == 1);
+           (L->time_outer == 0 || L->time_outer == 1) && finite(L->p_mark) && L->p_mark >= 0.0 &&
+           L->p_mark < 1.0;
 }
 
 static bool valid_pose(const tw_pose *r) {
@@ -413,6 +419,9 @@ static Params make_params(const tw_grid *g, const tw_pose *robot, const tw_ring_
     p.rx = robot->x; p.ry = robot->y; p.hx = robot->hx; p.hy = robot->hy; p.speed = robot->speed;
     p.r0 = law->r0; p.growth = law->growth; p.q = law->q_accel; p.kappa = law->kappa;
     p.d_safe = law->d_safe;
+    // P(|X - p| <= rho0) for X ~ N(p, sigma^2 I2) is 1 - exp(-rho0^2 / (2 sigma^2)) >= p_mark
+    // exactly when sigma <= alpha rho0
+    p.alpha = law->p_mark > 0.0 ? 1.0 / sqrt(-2.0 * log(1.0 - law->p_mark)) : 0.0;
     return p;
 }
 

@@ -45,6 +45,7 @@ class RingLaw:
     kappa: float = 2.0       # inflation in standard deviations
     d_safe: float = 0.25     # m, safety distance
     time_outer: int = 0      # 0: arrival time from inner ring radius; 1: outer
+    p_mark: float = 0.0      # probability threshold of the marking (0: every prediction marked)
 
 
 @dataclass

@@ -203,7 +203,8 @@ def test_warm_start_entry_points_reject_bad_input_on_host(lib):
     # the tensor-memory form: cin % 16 == 0, cout in {32, 64, 128}, W % 128 == 0, H even, and a workspace
     assert lib.ws_conv3x3_workspace_size(64, 128, 16, 256, tw.WS_CONV_TC) >= 64 * 128 * 9 * 2
     assert lib.ws_conv3x3_workspace_size(64, 128, 16, 256, tw.WS_CONV_MMA) == 0
-    for cin, cout, H, W in ((64, 96, 16, 256), (8, 64, 16, 256), (64, 64, 16, 200), (64, 64, 15, 256)):
+    for cin, cout, H, W in ((64, 96, 16, 256), (8, 64, 16, 256), (64, 64, 16, 200), (64, 64, 15, 256),
+                            (64, 64, 6, 256), (64, 128, 7, 256)):
         assert lib.ws_conv3x3_workspace_size(cin, cout, H, W, tw.WS_CONV_TC) == 0
         assert lib.ws_conv3x3(P, P, None, None, P, cin, cout, H, W, 1, tw.WS_CONV_TC, P, 1 << 20, None) == tw.TW_EINVAL
     assert lib.ws_conv3x3(P, P, None, None, P, 64, 64, 16, 256, 1, tw.WS_CONV_TC, None, 0, None) == tw.TW_EWORKSPACE

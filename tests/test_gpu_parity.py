@@ -76,6 +76,19 @@ def test_raster_law_variants(dev, kind, mark, outer):
     _assert_raster_equal(sc, dev, law=law)
 
 
+@pytest.mark.parametrize("frame,mark", [(0, scenes.MARK_PER_CELL), (50, scenes.MARK_PER_CELL),
+                                        (50, scenes.MARK_PER_OBSTACLE)])
+def test_raster_probability_threshold_marking(dev, frame, mark):
+    """The marking threshold (p_mark = 0.5: a prediction too uncertain to place the obstacle within
+    radius + d_safe of its mean with probability 1/2 marks nothing) on the 200-track scene: bit-exact
+    against the oracle, and fewer predicted cells than the plain marking."""
+    sc = scenes.dynamic(seed=1001, side=512, n_obs=200, frames=frame + 1, frame=frame)
+    law = scenes.RingLaw(mark=mark, p_mark=0.5)
+    o = _assert_raster_equal(sc, dev, law=law)
+    o0 = _assert_raster_equal(sc, dev, law=scenes.RingLaw(mark=mark))
+    assert 0 < (o == tw.TW_DYNAMIC).sum() < (o0 == tw.TW_DYNAMIC).sum()
+
+
 @pytest.mark.parametrize("nx,ny", [(3, 3), (3, 5), (5, 3), (17, 33), (33, 17), (1023, 3), (3, 1025),
                                    (65, 1025), (97, 31)])
 def test_raster_odd_sizes(dev, nx, ny):

@@ -634,3 +634,43 @@ def test_threaded_oracle_build_returns_the_same_bits():
         oracle.use_threads(1)
     assert np.array_equal(occ1, occ4) and np.array_equal(ring1, ring4)
     assert np.array_equal(j1, j4) and np.array_equal(c1, c4)
+
+
+def test_marking_threshold_is_the_coverage_probability():
+    """Probability-threshold marking (tw_ring_law.p_mark): a prediction marks cells only while the
+    chance that the obstacle centre, distributed N(p, sigma^2 I2), lies within rho0 = radius + d_safe
+    of p is at least p_mark.  That chance is the Rayleigh distribution function of |X - p| at rho0;
+    here it comes from scipy's Rayleigh law (and a Monte Carlo check), not from the oracle's formula,
+    and the oracle's disk appears exactly on the right side of the threshold."""
+    from scipy.stats import rayleigh
+    radius, d_safe, cell = 0.3, 0.25, 0.05
+    rho0 = radius + d_safe
+    for p_mark in (0.2, 0.5, 0.9):
+        law = scenes.RingLaw(q_accel=0.0, kappa=2.0, d_safe=d_safe, p_mark=p_mark)
+        # sigma at which the coverage probability equals p_mark, by bisection on scipy's CDF
+        lo, hi = 1e-3, 10.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if rayleigh.cdf(rho0, scale=mid) > p_mark else (lo, mid)
+        s_star = 0.5 * (lo + hi)
+        for f, marked in ((0.98, True), (1.02, False)):
+            s = f * s_star
+            P = np.diag([s * s, s * s, 0.0, 0.0])
+            _, _, rq = oracle.predict_disk(_one_track(1.0, 1.0, 0.0, 0.0, radius, P)[0], 0.0, law, cell)
+            assert (rq >= 0) == marked, (p_mark, f, rq)
+        # Monte Carlo: the coverage at 0.98 s* is above p_mark, at 1.02 s* below
+        rng = np.random.default_rng(int(p_mark * 100))
+        for f, above in ((0.95, True), (1.05, False)):
+            r = np.hypot(*rng.normal(0.0, f * s_star, (2, 400000)))
+            assert ((r <= rho0).mean() > p_mark) == above
+    # in the raster: one uncertain obstacle vanishes, a certain one stays
+    sc = scenes.Scene("hand", 0, 64, 64, cell, static_occ=np.zeros((64, 64), np.uint8))
+    sc.robot = np.array([0.5, 0.5, 1.0, 0.0, 1.0])
+    T = np.vstack([_one_track(1.6, 1.6, 0.0, 0.0, radius, np.diag([1e-4, 1e-4, 0.0, 0.0])),
+                   _one_track(2.4, 2.4, 0.0, 0.0, radius, np.diag([1.0, 1.0, 0.0, 0.0]))])
+    law = scenes.RingLaw(q_accel=0.0, kappa=2.0, d_safe=d_safe, p_mark=0.5)
+    occ, _, _ = oracle.build_grid(sc, law=law, tracks=T)
+    dyn = np.argwhere(occ == 2)
+    assert len(dyn) > 0 and np.all(np.hypot(dyn[:, 1] - 31.5, dyn[:, 0] - 31.5) <= 20)
+    occ0, _, _ = oracle.build_grid(sc, law=scenes.RingLaw(q_accel=0.0, kappa=2.0, d_safe=d_safe), tracks=T)
+    assert (occ0 == 2).sum() > (occ == 2).sum()
