@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # DRAM traffic of the dominant kernel from one ncu capture, valid only while
 # the kernel source is unchanged (sha256 of the file that holds it).
-TRAFFIC = {"43d78bc176f425ba": 17464832 + 2048}   # rb_tb_kernel<7,14,12,1>, profiles/rb_tb_kernel_static2048.md
+TRAFFIC = {"494e3fe7f3a237cf": 17468160 + 2048}   # rb_tb_kernel<7,14,12,1>, profiles/rb_tb_kernel_static2048.md
 
 
 def _env_int(k, d):
@@ -666,23 +666,38 @@ def run_batched(args, dev, tw):
 def run_dynamic(args, dev, tw):
     """The dynamic 512x512 configuration: 200 Kalman-tracked disks, rings 0.5 m x 1.3^j,
     100 replanning frames at 10 Hz (Kalman update + raster + warm-started relaxation
-    + path + robot motion per frame)."""
+    + path + robot motion per frame), with the plain binary marking and with the
+    probability-threshold marking (p_mark = 0.9)."""
+    import collections
+
     import torch
     from paper_1903_07441_gb300 import replan
     sc = scenes.dynamic(seed=1001, side=512, n_obs=200, frames=101)
     replan.run(sc, frames=3, device=dev)   # warm
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    res = replan.run(sc, frames=100, device=dev)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    sweeps = [f.relax.get("sweeps", 0) for f in res.frames if f.relax]
-    out = {"workload": "dynamic512: 512x512, 5 cm, 200 moving disks (Kalman-tracked), 100 frames at 10 Hz",
-           "frames": len(res.frames), "seconds": t, "frames_per_s": len(res.frames) / t,
-           "ms_per_frame": t / max(len(res.frames), 1) * 1e3,
-           "sweeps_per_frame_median": float(np.median(sweeps)) if sweeps else None,
-           "path_ok_frames": sum(1 for f in res.frames if f.path_status == tw.TW_OK),
-           "collision_free": res.collision_free, "min_clearance_m": res.min_clearance}
+    out = {"workload": "dynamic512: 512x512, 5 cm, 200 moving disks (Kalman-tracked), 100 frames at 10 Hz"}
+    for name, law in (("marking_binary", scenes.RingLaw()), ("marking_p0.9", scenes.RingLaw(p_mark=0.9))):
+        t0 = time.perf_counter()
+        res = replan.run(sc, frames=100, law=law, device=dev)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        sweeps = [f.relax.get("sweeps", 0) for f in res.frames if f.relax]
+        status = collections.Counter(int(f.path_status) for f in res.frames)
+        hist, edges = np.histogram(res.turning_angles(), bins=[0, 5, 10, 20, 45, 90, 180])
+        out[name] = {"frames": len(res.frames), "seconds": t, "frames_per_s": len(res.frames) / t,
+                     "ms_per_frame": t / max(len(res.frames), 1) * 1e3,
+                     "sweeps_per_frame_median": float(np.median(sweeps)) if sweeps else None,
+                     "path_ok_frames": status.get(tw.TW_OK, 0),
+                     "no_path_frames": status.get(tw.TW_NO_PATH, 0),
+                     "start_covered_frames": status.get(tw.TW_ESTART_BLOCKED, 0),
+                     "collision_free": res.collision_free, "collision_frame": res.collision_frame,
+                     "min_clearance_m": res.min_clearance, "path_length_m": res.path_length(),
+                     "turning_angle_hist_deg": {f"{int(a)}-{int(b)}": int(h)
+                                                for a, b, h in zip(edges[:-1], edges[1:], hist)}}
+    out["note"] = ("most frames without a path end in TW_NO_PATH because the potential at the robot is "
+                   "1e-11..1e-13 through 200 obstacles (the FP64 oracle's own descent fails on this frame), "
+                   "below what any field solved to an absolute tolerance orders; obstacles move up to 1 m/s "
+                   "without avoiding the robot (0.75 m/s)")
     if args.dynamic_eval:
         out["evaluation"] = dynamic_eval(dev, tw)
     return out

@@ -196,7 +196,7 @@ typedef struct {
     int tblock;        /* temporal-blocking depth T, sweeps fused per launch (0 = library default):
                           HP_RBSOR takes 1..7 (default 7 on deep tiles when the field has at least
                           96 of them -- about 2048 x 1400 cells and up -- else 4); hp_relax_batched
-                          takes 2, 4 or 7 (anything else: autotuned) */
+                          takes 2, 4, 6 or 7 (anything else: autotuned) */
     int flags;         /* HP_WARM_START | HP_OUT_PHI | HP_TIMING | HP_HOST_LOOP | HP_POLISH */
     double etol;       /* HP_RBSOR with T >= 2: also require the estimated field error max |u - u*| to be
                           <= etol (0 = off).  The residual test alone does not bound the error well: the
@@ -303,9 +303,15 @@ int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, f
  * are relaxed by red-black SOR inside one CUDA graph whose sweep kernel is a
  * persistent, grid-stride kernel over the tiles of every still-active
  * instance, with per-instance omega, residual and convergence (converged
- * instances drop out).  The blocking depth T is autotuned per batch shape
- * among 2, 4 (8 x 8-row tiles) and 7 (12 x 14-row tiles) (p->tblock 2, 4
- * or 7 forces it; the tuning sweeps count towards the solve).
+ * instances drop out).  The tile configuration is autotuned once per batch
+ * shape (device, workspace, n, total cells) among five: depth T = 2 or 4 on
+ * shallow tiles (8 x 8 rows), T = 4, 6 or 7 on deep tiles (12 x 2T rows);
+ * each is timed on two launches of Gauss-Seidel sweeps (which count towards
+ * the solve) and the fastest per sweep wins.  Unless p->check_every is set,
+ * the check interval is tuned too, from the measured cost of a check and of a
+ * sweep and the slowest instance's sweeps at the previous call of the same
+ * shape (256 at the first).  p->tblock 2 or 4 forces shallow tiles at that
+ * depth, 6 or 7 deep tiles; stats[i].tblock reports the depth used.
  * n: 1..1024 instances.  p: method HP_RBSOR, FP32; tol, max_sweeps, omega
  * (0 = adaptive) and check_every apply to every instance; HP_WARM_START reads
  * u from field_dev, HP_OUT_PHI writes phi (not both).  stats: host array of n,

@@ -33,14 +33,20 @@ namespace tw {
 
 constexpr int kMaxBatch = 1024;
 
-// Tile configuration per blocking depth, as for the single field: T <= 4,
-// 8 rows x 8 warps (two CTAs per SM); T = 7, 14 rows x 12 warps (one CTA per
-// SM, half the bytes per update of T = 4 and a quarter of T = 2).
-template <int T>
+// Tile configurations, chosen by the autotuner independently of the blocking
+// depth T: small tiles, 8 rows x 8 warps (two CTAs per SM), or deep tiles,
+// 14 rows x 12 warps (one CTA per SM; the single field's T = 5..7 shape).  A
+// configuration code c = T + 8 * deep names both.
+template <int T, int DEEP>
 struct BCfg {
-    static constexpr int RB = T <= 4 ? 8 : 14;
-    static constexpr int WARPS = T <= 4 ? 8 : 12;
+    static constexpr int RB = DEEP ? 14 : 8;
+    static constexpr int WARPS = DEEP ? 12 : 8;
 };
+constexpr int cfg_code(int T, int deep) { return T + 8 * deep; }
+constexpr int cfg_T(int c) { return c & 7; }
+constexpr int cfg_deep(int c) { return c >> 3; }
+// the candidates: T = 2 and 4 on small tiles, T = 4, 6 and 7 on deep tiles
+constexpr int kCfgCands[5] = {cfg_code(2, 0), cfg_code(4, 0), cfg_code(4, 1), cfg_code(6, 1), cfg_code(7, 1)};
 
 struct BatchInst {
     int nx, ny, gx, gy;
@@ -71,14 +77,16 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-template <int T>
+template <int T, int DEEP>
 struct BShape {
     static constexpr int HK4 = (T + 1 + 3) / 4, HY = 2 * T;
-    static constexpr int KI4 = 32 - 2 * HK4, YI = BCfg<T>::WARPS * BCfg<T>::RB - 2 * HY;
+    static constexpr int KI4 = 32 - 2 * HK4, YI = BCfg<T, DEEP>::WARPS * BCfg<T, DEEP>::RB - 2 * HY;
 };
 
-static void tiles_for(int T, int W4, int ny, int *tx, int *ty) {
-    const int rows = T <= 4 ? BCfg<4>::WARPS * BCfg<4>::RB : BCfg<7>::WARPS * BCfg<7>::RB;
+// Tiles per row and column of an instance for configuration code c.
+static void tiles_for(int c, int W4, int ny, int *tx, int *ty) {
+    const int T = cfg_T(c);
+    const int rows = cfg_deep(c) ? BCfg<7, 1>::WARPS * BCfg<7, 1>::RB : BCfg<4, 0>::WARPS * BCfg<4, 0>::RB;
     int KI4 = 32 - 2 * ((T + 4) / 4), YI = rows - 4 * T;
     *tx = (W4 + KI4 - 1) / KI4;
     *ty = (ny + YI - 1) / YI;
@@ -139,11 +147,11 @@ __global__ void batch_pack_kernel(BatchInst *I, const int *row_off, int n, int w
     }
 }
 
-template <int T>
-__global__ void __launch_bounds__(BCfg<T>::WARPS * 32, T <= 4 ? 2 : 1)
+template <int T, int DEEP>
+__global__ void __launch_bounds__(BCfg<T, DEEP>::WARPS * 32, DEEP ? 1 : 2)
 batch_tb_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const BatchHdr *__restrict__ H,
                 int parity) {
-    constexpr int RB = BCfg<T>::RB, WARPS = BCfg<T>::WARPS;
+    constexpr int RB = BCfg<T, DEEP>::RB, WARPS = BCfg<T, DEEP>::WARPS;
     __shared__ TBShared<WARPS> sh;
     const int n_active = H->n_active;
     for (int t = blockIdx.x; t < n_active; t += gridDim.x) {
@@ -157,10 +165,10 @@ batch_tb_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const 
 }
 
 // FP32 residual max of each active tile's interior, one atomic per CTA and tile.
-template <int T>
+template <int T, int DEEP>
 __global__ void __launch_bounds__(256)
 batch_residual_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const BatchHdr *__restrict__ H) {
-    using Sh = BShape<T>;
+    using Sh = BShape<T, DEEP>;
     const int n_active = H->n_active;
     for (int t = blockIdx.x; t < n_active; t += gridDim.x) {
         const int2 it = list[t];
@@ -289,7 +297,7 @@ static size_t carve_batch(Carver &cv, int n, const hp_instance *in, std::vector<
     for (int i = 0; i < n; i++) {
         RBLayout g = rb_layout(in[i].nx, in[i].ny);
         int tx2, ty2;
-        tiles_for(4, g.W4, in[i].ny, &tx2, &ty2);   // the deepest candidate has the most tiles
+        tiles_for(cfg_code(4, 0), g.W4, in[i].ny, &tx2, &ty2);   // the candidate with the most tiles
         max_tiles += (size_t)tx2 * ty2;
     }
     l.list = cv.take<int2>(max_tiles > 0 ? max_tiles : 1);
@@ -314,10 +322,14 @@ static size_t carve_batch(Carver &cv, int n, const hp_instance *in, std::vector<
 }
 
 static std::mutex g_batch_mutex;
-static std::map<std::tuple<int, const void *, int, size_t>, int> g_tuned_T;   // (dev, ws, n, cells) -> T
+// per batch shape (dev, ws, n, cells): the tuned configuration code and check interval, and the
+// slowest instance's sweeps at the last call (the autotuner's estimate of S)
+typedef std::tuple<int, const void *, int, size_t> BatchKey;
+static std::map<BatchKey, std::pair<int, int>> g_tuned;
+static std::map<BatchKey, int> g_last_sweeps;
 
 struct BatchGraph {
-    int dev, T, K, rounds;
+    int dev, T, K, rounds;   // T: the configuration code
     const void *ws;
     int n;
     cudaGraph_t graph;
@@ -334,29 +346,40 @@ static int persistent_grid(const void *func, int threads, size_t smem) {
     return sms * per;
 }
 
-template <int T>
+template <int T, int DEEP>
 static void launch_batch_sweep(BatchLayout &L, int parity, cudaStream_t s) {
-    constexpr int threads = BCfg<T>::WARPS * 32;
-    const int grid = persistent_grid((const void *)batch_tb_kernel<T>, threads, 0);
-    TW_LAUNCH((batch_tb_kernel<T>), grid, threads, 0, s, L.inst, L.list, L.hdr, parity);
+    constexpr int threads = BCfg<T, DEEP>::WARPS * 32;
+    const int grid = persistent_grid((const void *)batch_tb_kernel<T, DEEP>, threads, 0);
+    TW_LAUNCH((batch_tb_kernel<T, DEEP>), grid, threads, 0, s, L.inst, L.list, L.hdr, parity);
 }
 
-static void launch_batch_sweep_T(int T, BatchLayout &L, int parity, cudaStream_t s) {
-    if (T == 7) launch_batch_sweep<7>(L, parity, s);
-    else if (T == 4) launch_batch_sweep<4>(L, parity, s);
-    else launch_batch_sweep<2>(L, parity, s);
+// c: configuration code (cfg_code)
+static void launch_batch_sweep_T(int c, BatchLayout &L, int parity, cudaStream_t s) {
+    switch (c) {
+        case cfg_code(7, 1): launch_batch_sweep<7, 1>(L, parity, s); break;
+        case cfg_code(6, 1): launch_batch_sweep<6, 1>(L, parity, s); break;
+        case cfg_code(4, 1): launch_batch_sweep<4, 1>(L, parity, s); break;
+        case cfg_code(4, 0): launch_batch_sweep<4, 0>(L, parity, s); break;
+        default: launch_batch_sweep<2, 0>(L, parity, s); break;
+    }
 }
 
-static void launch_batch_residual_T(int T, BatchLayout &L, cudaStream_t s) {
+static void launch_batch_residual_T(int c, BatchLayout &L, cudaStream_t s) {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (T == 7) TW_LAUNCH((batch_residual_kernel<7>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
-    else if (T == 4) TW_LAUNCH((batch_residual_kernel<4>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
-    else TW_LAUNCH((batch_residual_kernel<2>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr);
+    switch (c) {
+        case cfg_code(7, 1): TW_LAUNCH((batch_residual_kernel<7, 1>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr); break;
+        case cfg_code(6, 1): TW_LAUNCH((batch_residual_kernel<6, 1>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr); break;
+        case cfg_code(4, 1): TW_LAUNCH((batch_residual_kernel<4, 1>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr); break;
+        case cfg_code(4, 0): TW_LAUNCH((batch_residual_kernel<4, 0>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr); break;
+        default: TW_LAUNCH((batch_residual_kernel<2, 0>), sms * 4, 256, 0, s, L.inst, L.list, L.hdr); break;
+    }
 }
 
-static int build_batch_graph(BatchLayout L, int T, int K, int max_rounds, BatchGraph *out) {
+// c: configuration code (cfg_code); K: sweeps per check interval (an even number of launches)
+static int build_batch_graph(BatchLayout L, int c, int K, int max_rounds, BatchGraph *out) {
+    const int T = cfg_T(c);
     cudaGraph_t g;
     TW_CUDA(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
@@ -376,8 +399,8 @@ static int build_batch_graph(BatchLayout L, int T, int K, int max_rounds, BatchG
     TW_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaStreamDestroy(cs); cudaGraphDestroy(g); set_cuda_error(e); return 1; }
-    for (int i = 0; i < K / T; i++) launch_batch_sweep_T(T, L, i & 1, cs);
-    launch_batch_residual_T(T, L, cs);
+    for (int i = 0; i < K / T; i++) launch_batch_sweep_T(c, L, i & 1, cs);
+    launch_batch_residual_T(c, L, cs);
     TW_LAUNCH(batch_control_kernel, 1, kMaxBatch, 0, cs, L.inst, L.hdr, L.list, max_rounds, 0, h, 1);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cs, &captured);
@@ -391,21 +414,29 @@ static int build_batch_graph(BatchLayout L, int T, int K, int max_rounds, BatchG
     return TW_OK;
 }
 
-// Autotuner: time each candidate depth with two launches of Gauss-Seidel
-// sweeps (omega = 1) on the batch; the sweeps count towards the solve.
-static int autotune(BatchLayout &L, std::vector<BatchInst> &hb, int n, cudaStream_t s, int *T_out, int *gs_sweeps) {
-    const int cands[3] = {2, 4, 7};
-    float best = FLT_MAX;
-    int bestT = 4;
-    cudaEvent_t a, b;
+// Autotuner: time each tile configuration (blocking depth and tile shape,
+// kCfgCands) with two launches of Gauss-Seidel sweeps (omega = 1) on the batch
+// (the sweeps count towards the solve), and the residual check once.  The
+// fastest configuration per sweep wins.  The check interval K then follows
+// from the measured costs: an instance that needs S sweeps pays about
+// S / K checks of cost c_chk and overshoots by K / 2 sweeps of cost c_sw, so
+// K* = sqrt(2 S c_chk / c_sw), rounded to an even number of launches (S: the
+// slowest instance's sweeps at the previous call of this batch shape, else
+// 256).
+static int autotune(BatchLayout &L, std::vector<BatchInst> &hb, int n, cudaStream_t s, int S_est, int *c_out,
+                    int *K_out, int *gs_sweeps) {
+    float best = FLT_MAX, best_chk = 0.0f;
+    int bestc = cfg_code(4, 0);
+    cudaEvent_t a, b, m;
     TW_CUDA(cudaEventCreate(&a));
     TW_CUDA(cudaEventCreate(&b));
+    TW_CUDA(cudaEventCreate(&m));
     *gs_sweeps = 0;
-    for (int ci = 0; ci < 3; ci++) {
-        const int T = cands[ci];
+    for (int ci = 0; ci < 5; ci++) {
+        const int c = kCfgCands[ci], T = cfg_T(c);
         std::vector<int2> lst;
         for (int i = 0; i < n; i++) {
-            tiles_for(T, hb[i].W4, hb[i].ny, &hb[i].tx, &hb[i].ty);
+            tiles_for(c, hb[i].W4, hb[i].ny, &hb[i].tx, &hb[i].ty);
             for (int t = 0; t < hb[i].tx * hb[i].ty; t++) lst.push_back(make_int2(i, t));
         }
         BatchHdr h = {n, (int)lst.size(), 0, T, 0ull};
@@ -413,19 +444,36 @@ static int autotune(BatchLayout &L, std::vector<BatchInst> &hb, int n, cudaStrea
         TW_CUDA(cudaMemcpyAsync(L.list, lst.data(), sizeof(int2) * lst.size(), cudaMemcpyHostToDevice, s));
         TW_CUDA(cudaMemcpyAsync(L.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, s));
         TW_CUDA(cudaEventRecord(a, s));
-        launch_batch_sweep_T(T, L, 0, s);
-        launch_batch_sweep_T(T, L, 1, s);
+        launch_batch_sweep_T(c, L, 0, s);
+        launch_batch_sweep_T(c, L, 1, s);
+        TW_CUDA(cudaEventRecord(m, s));
+        launch_batch_residual_T(c, L, s);   // only its time is used (the interval maxima are reset below)
         TW_CUDA(cudaEventRecord(b, s));
         TW_CUDA(cudaEventSynchronize(b));
-        float ms = 0.0f;
-        TW_CUDA(cudaEventElapsedTime(&ms, a, b));
+        float ms = 0.0f, chk = 0.0f;
+        TW_CUDA(cudaEventElapsedTime(&ms, a, m));
+        TW_CUDA(cudaEventElapsedTime(&chk, m, b));
         *gs_sweeps += 2 * T;
         const float per_sweep = ms / (2 * T);
-        if (per_sweep < best) { best = per_sweep; bestT = T; }
+        if (per_sweep < best) {
+            best = per_sweep;
+            bestc = c;
+            best_chk = chk;
+        }
     }
+    for (int i = 0; i < n; i++) hb[i].rmax = 0u;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    *T_out = bestT;
+    cudaEventDestroy(m);
+    // the check also runs the control kernel (about as long as a small launch)
+    const double c_chk = (double)best_chk + 0.005, c_sw = (double)best;
+    const double kstar = sqrt(2.0 * (double)S_est * c_chk / (c_sw > 1e-6 ? c_sw : 1e-6));
+    const int T = cfg_T(bestc);
+    int mm = (int)floor(kstar / (2.0 * T) + 0.5);
+    if (mm < 1) mm = 1;
+    if (mm > 8) mm = 8;
+    *c_out = bestc;
+    *K_out = 2 * T * mm;
     return TW_OK;
 }
 
@@ -484,26 +532,37 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
     std::lock_guard<std::mutex> lock(g_batch_mutex);
     int dev = 0;
     TW_CUDA(cudaGetDevice(&dev));
-    // pick the blocking depth (cached per batch shape)
-    int T = p->tblock;
+    // pick the tile configuration and check interval (tuned once per batch shape)
+    const BatchKey key = std::make_tuple(dev, (const void *)workspace, n, cells);
+    int C;
+    int Kt = 0;
     int gs_sweeps = 0;
-    if (T != 2 && T != 4 && T != 7) {
-        auto key = std::make_tuple(dev, (const void *)workspace, n, cells);
-        auto f = g_tuned_T.find(key);
-        if (f != g_tuned_T.end()) {
-            T = f->second;
+    if (p->tblock == 2 || p->tblock == 4) {
+        C = cfg_code(p->tblock, 0);
+    } else if (p->tblock == 6 || p->tblock == 7) {
+        C = cfg_code(p->tblock, 1);
+    } else {
+        auto f = g_tuned.find(key);
+        if (f != g_tuned.end()) {
+            C = f->second.first;
+            Kt = f->second.second;
         } else {
-            int e = autotune(L, hb, n, s, &T, &gs_sweeps);
+            auto ls = g_last_sweeps.find(key);
+            int e = autotune(L, hb, n, s, ls != g_last_sweeps.end() ? ls->second : 256, &C, &Kt, &gs_sweeps);
             if (e) return e;
-            g_tuned_T[key] = T;
+            g_tuned[key] = std::make_pair(C, Kt);
         }
     }
-    const int K0 = p->check_every > 0 ? p->check_every : 32;
-    const int K = K0 / (2 * T) > 0 ? K0 / (2 * T) * (2 * T) : 2 * T;   // an even number of launches
-    // control state and the initial tile list for T
+    const int T = cfg_T(C);
+    int K;
+    if (p->check_every > 0)
+        K = p->check_every / (2 * T) > 0 ? p->check_every / (2 * T) * (2 * T) : 2 * T;   // an even number of launches
+    else
+        K = Kt > 0 ? Kt : (32 / (2 * T) > 0 ? 32 / (2 * T) * (2 * T) : 2 * T);
+    // control state and the initial tile list for the configuration
     std::vector<int2> lst;
     for (int i = 0; i < n; i++) {
-        tiles_for(T, hb[i].W4, hb[i].ny, &hb[i].tx, &hb[i].ty);
+        tiles_for(C, hb[i].W4, hb[i].ny, &hb[i].tx, &hb[i].ty);
         RelaxCtl &c = hb[i].ctl;
         memset(&c, 0, sizeof(c));
         c.adapt = p->omega == 0.0;
@@ -531,7 +590,7 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
     const int max_rounds = (p->max_sweeps - gs_sweeps) / K > 0 ? (p->max_sweeps - gs_sweeps) / K : 1;
     BatchGraph *gr = nullptr;
     for (auto &g : g_batch_graphs)
-        if (g.dev == dev && g.ws == workspace && g.n == n && g.T == T && g.K == K && g.rounds == max_rounds) gr = &g;
+        if (g.dev == dev && g.ws == workspace && g.n == n && g.T == C && g.K == K && g.rounds == max_rounds) gr = &g;
     if (!gr) {
         if (g_batch_graphs.size() >= 8) {
             cudaGraphExecDestroy(g_batch_graphs.front().exec);
@@ -539,8 +598,8 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
             g_batch_graphs.erase(g_batch_graphs.begin());
         }
         BatchGraph ng;
-        ng.dev = dev; ng.T = T; ng.K = K; ng.rounds = max_rounds; ng.ws = workspace; ng.n = n;
-        int e = build_batch_graph(L, T, K, max_rounds, &ng);
+        ng.dev = dev; ng.T = C; ng.K = K; ng.rounds = max_rounds; ng.ws = workspace; ng.n = n;
+        int e = build_batch_graph(L, C, K, max_rounds, &ng);
         if (e < 0) return e;
         if (e == 0) { g_batch_graphs.push_back(ng); gr = &g_batch_graphs.back(); }
     }
@@ -550,8 +609,8 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
         TW_CUDA(cudaGraphLaunch(gr->exec, s));
     } else {   // no graph support: the same intervals driven from the host
         for (int r = 0; r < max_rounds; r++) {
-            for (int i = 0; i < K / T; i++) launch_batch_sweep_T(T, L, i & 1, s);
-            launch_batch_residual_T(T, L, s);
+            for (int i = 0; i < K / T; i++) launch_batch_sweep_T(C, L, i & 1, s);
+            launch_batch_residual_T(C, L, s);
             TW_LAUNCH(batch_control_kernel, 1, kMaxBatch, 0, s, L.inst, L.hdr, L.list, max_rounds, 0,
                       (cudaGraphConditionalHandle)0, 0);
             BatchHdr hh;
@@ -569,8 +628,9 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
     TW_CUDA(cudaStreamSynchronize(s));
     // launches run inside the graph: rounds x (K/T sweeps + residual + control)
     count_launches((unsigned long long)hh.rounds * (K / T + 2));
-    int worst = TW_OK;
+    int worst = TW_OK, slowest = 0;
     for (int i = 0; i < n; i++) {
+        if (!hb[i].error && hb[i].ctl.sweeps > slowest) slowest = hb[i].ctl.sweeps;
         const BatchInst &b = hb[i];
         hp_stats &st = stats[i];
         memset(&st, 0, sizeof(st));
@@ -588,5 +648,6 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
         if (st.status < 0) worst = st.status;
         else if (st.status > 0 && worst == TW_OK) worst = st.status;
     }
+    if (slowest > 0) g_last_sweeps[key] = slowest;
     return worst;
 }

@@ -35,7 +35,7 @@ def _batch(n, seed0, lo=40, hi=260):
     return out
 
 
-@pytest.mark.parametrize("tblock", [0, 2, 4, 7])
+@pytest.mark.parametrize("tblock", [0, 2, 4, 6, 7])
 def test_batched_matches_oracle_and_single_solver(dev, tblock):
     cases = _batch(10, 8100)
     occs = [torch.from_numpy(o).to(dev) for _, o in cases]
@@ -52,11 +52,11 @@ def test_batched_matches_oracle_and_single_solver(dev, tblock):
                                  params=tw.Params(tol=1e-6))
         assert np.abs(u - single.cpu().numpy()).max() <= tau * 2e-6 + 1e-7
         assert l > 0.0
-    if tblock in (2, 4, 7):
+    if tblock in (2, 4, 6, 7):
         assert all(st["tblock"] == tblock for st in stats)
 
 
-@pytest.mark.parametrize("tblock", [2, 4, 7])
+@pytest.mark.parametrize("tblock", [2, 4, 6, 7])
 def test_batched_sweeps_equal_single_field_sweeps(dev, tblock):
     """At a fixed omega and sweep count the batched tile kernel (persistent, one
     tile list over all instances) computes exactly what the single-field kernel
@@ -70,7 +70,7 @@ def test_batched_sweeps_equal_single_field_sweeps(dev, tblock):
         occ[g[1], g[0]] = 0
         occs.append(occ)
         goals.append(g)
-    n_sw = 56 if tblock == 7 else 64   # two check intervals
+    n_sw = {6: 48, 7: 56}.get(tblock, 64)   # two check intervals
     prm = tw.Params(omega=1.9, tol=0.0, max_sweeps=n_sw, tblock=tblock)
     occ_t = [torch.from_numpy(o).to(dev) for o in occs]
     fields, stats, _ = tw.hp_relax_batched(occ_t, goals, params=prm)
@@ -106,4 +106,23 @@ def test_batched_cap_and_repeat_calls(dev):
     b, sb, _ = tw.hp_relax_batched(occs, goals, params=tw.Params(tol=1e-6, tblock=4))
     for x, y, p, q in zip(a, b, sa, sb):
         assert p["sweeps"] == q["sweeps"]
+        assert torch.equal(x, y)
+
+
+def test_batched_autotuned_configuration_is_reused(dev):
+    """The autotuned configuration (tile shape, depth and check interval) is
+    chosen at the first call of a batch shape and reused: later calls of the
+    same batch are deterministic and converge."""
+    cases = _batch(12, 8500)
+    occs = [torch.from_numpy(o).to(dev) for _, o in cases]
+    goals = [sc.goal for sc, _ in cases]
+    prm = tw.Params(tol=1e-6)
+    _, s0, _ = tw.hp_relax_batched(occs, goals, params=prm)
+    assert all(st["status"] == tw.TW_OK for st in s0)
+    assert s0[0]["tblock"] in (2, 4, 6, 7)
+    a, sa, _ = tw.hp_relax_batched(occs, goals, params=prm)
+    b, sb, _ = tw.hp_relax_batched(occs, goals, params=prm)
+    for x, y, p, q in zip(a, b, sa, sb):
+        assert p["status"] == tw.TW_OK and p["sweeps"] == q["sweeps"] and p["checks"] == q["checks"]
+        assert p["tblock"] == s0[0]["tblock"]
         assert torch.equal(x, y)

@@ -77,3 +77,28 @@ def test_replan_paper_variants(dev, variant):
     ref, _, _ = oracle.build_grid(sc, law=law, robot=fr.robot, tracks=fr.tracks)
     assert np.array_equal(occ.cpu().numpy(), ref)
     assert _dist_to_goal(sc, res.trajectory[-1]) < _dist_to_goal(sc, res.trajectory[0])
+
+
+def test_dense_200_track_scene_limits(dev):
+    """The 512 x 512 scene with 200 Kalman-tracked disks (up to 1 m/s, not avoiding the robot).
+    With the probability-threshold marking (p_mark = 0.9) the loop finds paths on a good share of the
+    frames and moves the robot; the rasters stay bit-exact.  What keeps the rest of the frames without a
+    path is fixed by the problem, not by the solver: the FP64 oracle's potential at the robot's cell is
+    below 1e-10 (the harmonic field decays exponentially through the clutter), under the absolute
+    accuracy of any relaxation to a residual tolerance."""
+    sc = scenes.dynamic(seed=1011, side=512, n_obs=200, frames=61)
+    law = scenes.RingLaw(p_mark=0.9)
+    res = replan.run(sc, frames=60, law=law, device=dev)
+    ok = sum(1 for fr in res.frames if fr.path_status == tw.TW_OK)
+    assert ok >= 0.2 * len(res.frames), ok
+    assert math.hypot(*(np.array(res.trajectory[-1]) - np.array(res.trajectory[0]))) > 0.5
+    for fr in (res.frames[0], res.frames[len(res.frames) // 2]):
+        grid = tw.make_grid(sc.nx, sc.ny, sc.cell)
+        occ, _ = tw.tw_build_grid(grid, fr.robot, fr.tracks, law)
+        ref, _, _ = oracle.build_grid(sc, law=law, robot=fr.robot, tracks=fr.tracks)
+        assert np.array_equal(occ.cpu().numpy(), ref), fr.frame
+    sc0 = scenes.dynamic(seed=1001, side=512, n_obs=200, frames=1)
+    occ0, _, _ = oracle.build_grid(sc0, law=law)
+    assert occ0[sc0.goal[1], sc0.goal[0]] == 0
+    ustar, _ = oracle.solve_field(occ0, sc0.goal, tol=1e-14)
+    assert ustar[sc0.start[1], sc0.start[0]] < 1e-10
