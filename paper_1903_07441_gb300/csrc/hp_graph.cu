@@ -85,6 +85,21 @@ static cudaError_t add_kernel_node(cudaGraphNode_t *node, cudaGraph_t g, cudaGra
     return cudaGraphAddKernelNode(node, g, *prev ? prev : nullptr, *prev ? 1 : 0, &kp);
 }
 
+// A kernel node that depends on *prev through a programmatic edge: it may be
+// scheduled once every CTA of *prev has triggered (griddepcontrol.launch_
+// dependents) and waits for *prev's completion itself (griddepcontrol.wait).
+static cudaError_t add_kernel_node_pdl(cudaGraphNode_t *node, cudaGraph_t g, cudaGraphNode_t *prev, void *func,
+                                       dim3 grid, dim3 block, void **args) {
+    cudaGraphNode_t none = nullptr;
+    cudaError_t e = add_kernel_node(node, g, &none, func, grid, block, args);
+    if (e != cudaSuccess || !*prev) return e;
+    cudaGraphEdgeData ed;
+    memset(&ed, 0, sizeof(ed));
+    ed.type = cudaGraphDependencyTypeProgrammatic;
+    ed.from_port = cudaGraphKernelNodePortProgrammatic;
+    return cudaGraphAddDependencies(g, prev, node, &ed, 1);
+}
+
 struct GraphEntry {
     int dev, nx, ny, T, K, max_intervals, polish, est;
     const void *key;
@@ -97,7 +112,7 @@ static std::vector<GraphEntry> g_graphs;
 constexpr size_t kMaxCachedGraphs = 16;
 
 static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_intervals, int polish, int est,
-                       RelaxScalars *scal, float *l2part, GraphEntry *out) {
+                       RelaxScalars *scal, float *l2part, bool pdl, GraphEntry *out) {
     (void)nx;
     cudaGraph_t g = nullptr;
     TW_CUDA(cudaGraphCreate(&g, 0));
@@ -133,7 +148,8 @@ static int build_graph(RBLayout L, int nx, int ny, int T, int K, int max_interva
                         (void *)&ny_, (void *)&w4, (void *)&S, (void *)&mw, (void *)&omega_unused,
                         (void *)&omega_dev};
         cudaGraphNode_t node;
-        e = add_kernel_node(&node, body, &prev, func, grid, block, args);
+        e = pdl ? add_kernel_node_pdl(&node, body, &prev, func, grid, block, args)
+                : add_kernel_node(&node, body, &prev, func, grid, block, args);
         if (e != cudaSuccess) { cudaGraphDestroy(g); set_cuda_error(e); return TW_ECUDA; }
         prev = node;
         float *t = R; R = R2; R2 = t;
@@ -238,7 +254,14 @@ int rb_solve_graph(RBLayout &L, int nx, int ny, int T, int K, int max_intervals,
         ne.polish = polish;
         ne.est = est;
         ne.key = (const void *)scal;
-        int e = build_graph(L, nx, ny, T, K, max_intervals, polish, est, scal, l2part, &ne);
+        // sweep launches chained by programmatic edges where the driver takes them, else plain edges
+        static bool pdl_ok = true;
+        int e = build_graph(L, nx, ny, T, K, max_intervals, polish, est, scal, l2part, pdl_ok, &ne);
+        if (e && pdl_ok) {
+            pdl_ok = false;
+            cudaGetLastError();
+            e = build_graph(L, nx, ny, T, K, max_intervals, polish, est, scal, l2part, false, &ne);
+        }
         if (e) return e;
         g_graphs.push_back(ne);
         ent = &g_graphs.back();

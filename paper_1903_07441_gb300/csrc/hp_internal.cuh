@@ -104,6 +104,8 @@ int rb_residual_blocks(const RBLayout &L, int ny);
 dim3 rb_residual_grid(const RBLayout &L, int ny);   // launch grid of rb_residual_kernel (64 x 4 threads)
 
 // Optional CUDA-event timing of the sweep kernels (HP_TIMING).
+// Keep `s` busy for about 30 us (one thread polling %globaltimer, bounded).
+void timing_gate(cudaStream_t s);
 struct SweepTimer {
     cudaEvent_t a = nullptr, b = nullptr;
     bool on = false;
@@ -114,7 +116,14 @@ struct SweepTimer {
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return TW_ECUDA;
         return TW_OK;
     }
-    void start(cudaStream_t s) { if (on) cudaEventRecord(a, s); }
+    // the start event follows a short device-side delay (timing_gate), so that
+    // it is stamped after the host has queued the launches it brackets: the
+    // measured time is the launches' run on the device, not their submission
+    void start(cudaStream_t s) {
+        if (!on) return;
+        timing_gate(s);
+        cudaEventRecord(a, s);
+    }
     void stop(cudaStream_t s) { if (on) cudaEventRecord(b, s); }
     // after the stream has passed the stop event
     void accumulate() {

@@ -71,6 +71,12 @@ rb_tb_kernel(const float *__restrict__ Rin, const float *__restrict__ Bin, float
              float *__restrict__ Bout, const uint32_t *__restrict__ MR, const uint32_t *__restrict__ MB,
              int ny, int W4, int S, int MW, float omega_arg, const float *__restrict__ omega_dev) {
     __shared__ TBShared<WARPS> sh;
+    // Programmatic dependent launch: consecutive sweep launches are chained so
+    // that the next launch is scheduled while this one runs; each waits here for
+    // the grid it depends on to complete (and its writes to be visible) before
+    // touching memory.  Without such a dependency both instructions are no-ops.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // the graph-driven loop keeps omega in device memory (it adapts on the device)
     const float omega = omega_dev ? *omega_dev : omega_arg;
     tb_tile<T, RB, WARPS>(Rin, Bin, Rout, Bout, MR, MB, ny, W4, S, MW, omega, (int)blockIdx.x, (int)blockIdx.y, sh);
@@ -89,12 +95,26 @@ struct TBCfg {
     using Sh = TBShape<T, RB, WARPS>;
 };
 
+// Launched with programmatic stream serialisation: back-to-back sweep launches
+// overlap the next launch's scheduling with the current one's run (the kernel
+// waits for its predecessor before its first memory access).
 template <int T>
 static void launch_tb(RBLayout &L, int ny, float omega, cudaStream_t s) {
     using C = TBCfg<T>;
-    dim3 grid(ceil_div(L.W4, C::Sh::KI4), ceil_div(ny, C::Sh::YI));
-    TW_LAUNCH((rb_tb_kernel<T, C::RB, C::WARPS, 1>), grid, C::WARPS * 32, 0, s, L.R, L.B, L.R2, L.B2, L.MR, L.MB,
-              ny, L.W4, L.S, L.MW, omega, (const float *)nullptr);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ceil_div(L.W4, C::Sh::KI4), ceil_div(ny, C::Sh::YI));
+    cfg.blockDim = dim3(C::WARPS * 32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, rb_tb_kernel<T, C::RB, C::WARPS, 1>, (const float *)L.R, (const float *)L.B, L.R2, L.B2,
+                       (const uint32_t *)L.MR, (const uint32_t *)L.MB, ny, L.W4, L.S, L.MW, omega,
+                       (const float *)nullptr);
+    count_launches(1);
     float *t = L.R; L.R = L.R2; L.R2 = t;
     t = L.B; L.B = L.B2; L.B2 = t;
 }
