@@ -7,7 +7,11 @@ namespace tw {
 static std::atomic<int> g_last_cuda_error{0};
 static std::atomic<unsigned long long> g_launches{0};
 void set_cuda_error(cudaError_t e) { g_last_cuda_error.store((int)e); }
-void count_launches(unsigned long long n) { g_launches.fetch_add(n); }
+static thread_local int g_count_paused = 0;
+void count_launches(unsigned long long n) {
+    if (!g_count_paused) g_launches.fetch_add(n);
+}
+void pause_launch_count(bool on) { g_count_paused += on ? 1 : -1; }
 }  // namespace tw
 
 extern "C" const char *tw_status_string(int status) {

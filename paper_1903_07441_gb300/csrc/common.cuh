@@ -12,6 +12,9 @@ namespace tw {
 void set_cuda_error(cudaError_t e);
 // host-side count of kernel launches (read by tw_launch_count)
 void count_launches(unsigned long long n);
+// while paused (per host thread, nestable), launches are not counted: stream
+// capture records kernels that run later, when their graph is launched
+void pause_launch_count(bool on);
 
 #define TW_CUDA(call)                                   \
     do {                                                \

@@ -87,7 +87,14 @@ size_t carve_mixed(Carver &cv, int nx, int ny, int storage, RelaxLayout *R);
 int relax_mixed(const uint8_t *occ, int nx, int ny, int gx, int gy, float *u, int mode,
                 const hp_params *p, hp_stats *st, RelaxLayout &R, cudaStream_t s);
 // n full red-black SOR sweeps, T fused per launch; *launches += launches made
-int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream_t s, int *launches);
+// omega_dev (optional): the sweep kernels read omega there instead of `omega`
+int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream_t s, int *launches,
+              const float *omega_dev = nullptr);
+// The same n sweeps as one captured CUDA graph (cached per planes, n and T; the
+// kernels read omega from omega_dev), launched on s: the sweep launches run
+// back to back as in the graph-driven loop (HP_TIMING times them this way).
+int rb_sweeps_graph(RBLayout &L, int nx, int ny, int n, int T, const float *omega_dev, cudaStream_t s,
+                    int *launches);
 // Number of tiles (CTAs) of one T-fused launch over an nx x ny field.
 int tb_tiles(int T, int nx, int ny);
 // Graph-driven loop: up to max_intervals check intervals of K sweeps (K/T even)

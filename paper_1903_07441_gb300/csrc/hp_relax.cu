@@ -450,9 +450,20 @@ int rb_solve(RBLayout &L, int nx, int ny, const hp_params *p, RelaxScalars *scal
     if (timer.open((p->flags & HP_TIMING) != 0)) return TW_ECUDA;
     while (!done && c.sweeps < p->max_sweeps) {
         int n = p->max_sweeps - c.sweeps < K ? p->max_sweeps - c.sweeps : K;
-        timer.start(s);
-        int e = rb_sweeps(L, nx, ny, n, T, (float)c.omega, s, &launches);
-        timer.stop(s);
+        int e;
+        if (timer.on && T > 1) {
+            // timed as the graph-driven loop runs them: one graph of the interval's launches
+            const float om = (float)c.omega;
+            TW_CUDA(cudaMemcpyAsync(&scal->ctl.omega_f, &om, sizeof(om), cudaMemcpyHostToDevice, s));
+            TW_CUDA(cudaStreamSynchronize(s));
+            timer.start(s);
+            e = rb_sweeps_graph(L, nx, ny, n, T, &scal->ctl.omega_f, s, &launches);
+            timer.stop(s);
+        } else {
+            timer.start(s);
+            e = rb_sweeps(L, nx, ny, n, T, (float)c.omega, s, &launches);
+            timer.stop(s);
+        }
         if (e) return e;
         timer.accumulate();
         c.sweeps += n;

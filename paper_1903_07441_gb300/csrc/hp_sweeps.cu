@@ -24,6 +24,11 @@
 // the 1-bit mask, for T sweeps.  Halo cells are recomputed redundantly
 // (garbage from the tile edge advances one cell per half-sweep and never
 // reaches the interior that is stored).
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "hp_internal.cuh"
 #include "hp_tile.cuh"
@@ -92,6 +97,7 @@ template <int T>
 struct TBCfg {
     static constexpr int RB = T <= 4 ? 8 : 14;
     static constexpr int WARPS = T <= 4 ? 8 : 12;
+    static constexpr int MINB = T <= 4 ? 2 : 1;   // CTAs per SM the register budget must allow
     using Sh = TBShape<T, RB, WARPS>;
 };
 
@@ -99,7 +105,7 @@ struct TBCfg {
 // overlap the next launch's scheduling with the current one's run (the kernel
 // waits for its predecessor before its first memory access).
 template <int T>
-static void launch_tb(RBLayout &L, int ny, float omega, cudaStream_t s) {
+static void launch_tb(RBLayout &L, int ny, float omega, const float *omega_dev, cudaStream_t s) {
     using C = TBCfg<T>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ceil_div(L.W4, C::Sh::KI4), ceil_div(ny, C::Sh::YI));
@@ -111,15 +117,16 @@ static void launch_tb(RBLayout &L, int ny, float omega, cudaStream_t s) {
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, rb_tb_kernel<T, C::RB, C::WARPS, 1>, (const float *)L.R, (const float *)L.B, L.R2, L.B2,
-                       (const uint32_t *)L.MR, (const uint32_t *)L.MB, ny, L.W4, L.S, L.MW, omega,
-                       (const float *)nullptr);
+    cudaLaunchKernelEx(&cfg, rb_tb_kernel<T, C::RB, C::WARPS, C::MINB>, (const float *)L.R, (const float *)L.B,
+                       L.R2, L.B2, (const uint32_t *)L.MR, (const uint32_t *)L.MB, ny, L.W4, L.S, L.MW, omega,
+                       omega_dev);
     count_launches(1);
     float *t = L.R; L.R = L.R2; L.R2 = t;
     t = L.B; L.B = L.B2; L.B2 = t;
 }
 
-int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream_t s, int *launches) {
+int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream_t s, int *launches,
+              const float *omega_dev) {
     (void)nx;
     if (T <= 1 || !L.R2) return rb_sweeps_simple(L, ny, n, omega, s, launches);
     if (T > kMaxTBlock) T = kMaxTBlock;
@@ -127,18 +134,80 @@ int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream
     while (left > 0) {
         int t = left >= T ? T : left;
         switch (t) {
-            case 7: launch_tb<7>(L, ny, omega, s); break;
-            case 6: launch_tb<6>(L, ny, omega, s); break;
-            case 5: launch_tb<5>(L, ny, omega, s); break;
-            case 4: launch_tb<4>(L, ny, omega, s); break;
-            case 3: launch_tb<3>(L, ny, omega, s); break;
-            case 2: launch_tb<2>(L, ny, omega, s); break;
-            default: launch_tb<1>(L, ny, omega, s); break;
+            case 7: launch_tb<7>(L, ny, omega, omega_dev, s); break;
+            case 6: launch_tb<6>(L, ny, omega, omega_dev, s); break;
+            case 5: launch_tb<5>(L, ny, omega, omega_dev, s); break;
+            case 4: launch_tb<4>(L, ny, omega, omega_dev, s); break;
+            case 3: launch_tb<3>(L, ny, omega, omega_dev, s); break;
+            case 2: launch_tb<2>(L, ny, omega, omega_dev, s); break;
+            default: launch_tb<1>(L, ny, omega, omega_dev, s); break;
         }
         left -= t;
         (*launches)++;
     }
     TW_CHECK_LAUNCH();
+    return TW_OK;
+}
+
+struct SweepGraph {
+    int dev, ny, n, T;
+    const void *key[5];
+    cudaGraphExec_t exec;
+    int launches;
+    bool swap;
+};
+static std::mutex g_sweep_graph_mutex;
+static std::vector<SweepGraph> g_sweep_graphs;
+
+int rb_sweeps_graph(RBLayout &L, int nx, int ny, int n, int T, const float *omega_dev, cudaStream_t s,
+                    int *launches) {
+    int dev = 0;
+    TW_CUDA(cudaGetDevice(&dev));
+    const void *key[5] = {L.R, L.B, L.R2, L.B2, omega_dev};
+    std::lock_guard<std::mutex> lock(g_sweep_graph_mutex);
+    SweepGraph *ent = nullptr;
+    for (auto &g : g_sweep_graphs)
+        if (g.dev == dev && g.ny == ny && g.n == n && g.T == T && !memcmp(g.key, key, sizeof(key))) ent = &g;
+    if (!ent) {
+        if (g_sweep_graphs.size() >= 8) {
+            cudaGraphExecDestroy(g_sweep_graphs.front().exec);
+            g_sweep_graphs.erase(g_sweep_graphs.begin());
+        }
+        cudaStream_t cs;
+        TW_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { cudaStreamDestroy(cs); set_cuda_error(e); return TW_ECUDA; }
+        RBLayout Lc = L;
+        int nl = 0;
+        pause_launch_count(true);
+        const int err = rb_sweeps(Lc, nx, ny, n, T, 1.0f, cs, &nl, omega_dev);
+        pause_launch_count(false);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (err || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) set_cuda_error(e);
+            return err ? err : TW_ECUDA;
+        }
+        SweepGraph ne;
+        ne.dev = dev; ne.ny = ny; ne.n = n; ne.T = T;
+        memcpy(ne.key, key, sizeof(key));
+        e = cudaGraphInstantiate(&ne.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { set_cuda_error(e); return TW_ECUDA; }
+        ne.launches = nl;
+        ne.swap = Lc.R != L.R;
+        g_sweep_graphs.push_back(ne);
+        ent = &g_sweep_graphs.back();
+    }
+    TW_CUDA(cudaGraphLaunch(ent->exec, s));
+    *launches += ent->launches;
+    count_launches((unsigned long long)ent->launches);
+    if (ent->swap) {
+        float *t = L.R; L.R = L.R2; L.R2 = t;
+        t = L.B; L.B = L.B2; L.B2 = t;
+    }
     return TW_OK;
 }
 
@@ -159,7 +228,7 @@ int tb_tiles(int T, int nx, int ny) {
 template <int T>
 static void node_of(RBLayout &L, int ny, void **func, dim3 *grid, dim3 *block) {
     using C = TBCfg<T>;
-    *func = (void *)rb_tb_kernel<T, C::RB, C::WARPS, 1>;
+    *func = (void *)rb_tb_kernel<T, C::RB, C::WARPS, C::MINB>;
     *grid = dim3(ceil_div(L.W4, C::Sh::KI4), ceil_div(ny, C::Sh::YI));
     *block = dim3(C::WARPS * 32);
 }

@@ -231,10 +231,16 @@ __device__ __forceinline__ void tb_load(float4 (&v)[2][RB], TBMask<RB> (&m)[2], 
                                         const uint32_t *__restrict__ MB, int y0, int k4, bool kin, int ny, int S,
                                         int MW) {
     const int k = 4 * k4;
+    // the mask words first: they are small and gate the first half-sweep, so
+    // they should not queue behind the tile's field rows
+    uint32_t mr[RB], mb[RB];
 #pragma unroll
-    for (int i = 0; i < (RB + 3) / 4; i++) {
-        m[0].w[i] = 0u;
-        m[1].w[i] = 0u;
+    for (int r = 0; r < RB; r++) {
+        const int y = y0 + r;
+        const bool in = kin && y >= 0 && y < ny;
+        const size_t w = (size_t)(in ? y : 0) * MW + (in ? (k >> 5) : 0);
+        mr[r] = in ? __ldg(MR + w) : 0u;
+        mb[r] = in ? __ldg(MB + w) : 0u;
     }
 #pragma unroll
     for (int r = 0; r < RB; r++) {
@@ -243,29 +249,52 @@ __device__ __forceinline__ void tb_load(float4 (&v)[2][RB], TBMask<RB> (&m)[2], 
         const size_t off = (size_t)(in ? y : 0) * S + 4 + (in ? k : 0);
         v[0][r] = in ? __ldg(reinterpret_cast<const float4 *>(Rin + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
         v[1][r] = in ? __ldg(reinterpret_cast<const float4 *>(Bin + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (in) {
-            const size_t w = (size_t)y * MW + (k >> 5);
-            m[0].w[r >> 2] |= ((__ldg(MR + w) >> (k & 31)) & 0xFu) << (8 * (r & 3));
-            m[1].w[r >> 2] |= ((__ldg(MB + w) >> (k & 31)) & 0xFu) << (8 * (r & 3));
-        }
+    }
+#pragma unroll
+    for (int i = 0; i < (RB + 3) / 4; i++) {
+        m[0].w[i] = 0u;
+        m[1].w[i] = 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+        m[0].w[r >> 2] |= ((mr[r] >> (k & 31)) & 0xFu) << (8 * (r & 3));
+        m[1].w[r >> 2] |= ((mb[r] >> (k & 31)) & 0xFu) << (8 * (r & 3));
     }
 }
 
-// One full red-black sweep of the CTA's registers: each half-sweep first
-// exchanges the other colour's first/last rows with the warps above/below
-// through shared memory (double-buffered by colour, one barrier each).
+// Half-sweep of colour COLOR of the CTA's registers: first the other colour's
+// first/last rows are exchanged with the warps above/below through shared
+// memory (double-buffered by colour, one barrier).
+template <int COLOR, int RB, int WARPS>
+__device__ __forceinline__ void tb_exchange_half_sweep(float4 (&v)[2][RB], const TBMask<RB> &m, float omega,
+                                                       TBShared<WARPS> &sh) {
+    constexpr int O = 1 - COLOR;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    sh.top[COLOR][warp][lane] = v[O][0];
+    sh.bot[COLOR][warp + 1][lane] = v[O][RB - 1];
+    __syncthreads();
+    tb_half_sweep<COLOR, RB, WARPS>(v, m, sh.bot[COLOR][warp][lane], sh.top[COLOR][warp + 1][lane], omega);
+}
+
+// One full red-black sweep of the CTA's registers.
 template <int RB, int WARPS>
 __device__ __forceinline__ void tb_full_sweep(float4 (&v)[2][RB], const TBMask<RB> (&m)[2], float omega,
                                               TBShared<WARPS> &sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    sh.top[0][warp][lane] = v[1][0];
-    sh.bot[0][warp + 1][lane] = v[1][RB - 1];
-    __syncthreads();
-    tb_half_sweep<0, RB, WARPS>(v, m[0], sh.bot[0][warp][lane], sh.top[0][warp + 1][lane], omega);
-    sh.top[1][warp][lane] = v[0][0];
-    sh.bot[1][warp + 1][lane] = v[0][RB - 1];
-    __syncthreads();
-    tb_half_sweep<1, RB, WARPS>(v, m[1], sh.bot[1][warp][lane], sh.top[1][warp + 1][lane], omega);
+    tb_exchange_half_sweep<0, RB, WARPS>(v, m[0], omega, sh);
+    tb_exchange_half_sweep<1, RB, WARPS>(v, m[1], omega, sh);
+}
+
+// Store colour C's rows of the tile interior [y_tile, y_tile + YI) held by the thread.
+template <int C, int RB>
+__device__ __forceinline__ void tb_store_colour(const float4 (&v)[2][RB], float *__restrict__ P, int y0, int y_tile,
+                                                int YI, int k4, bool lane_int, int ny, int S) {
+    if (!lane_int) return;
+#pragma unroll
+    for (int r = 0; r < RB; r++) {
+        const int y = y0 + r;
+        if (y >= y_tile && y < y_tile + YI && y < ny)
+            *reinterpret_cast<float4 *>(P + (size_t)y * S + 4 + 4 * k4) = v[C][r];
+    }
 }
 
 // Store the rows of the tile interior [y_tile, y_tile + YI) held by the thread.
@@ -273,16 +302,8 @@ template <int RB>
 __device__ __forceinline__ void tb_store(const float4 (&v)[2][RB], float *__restrict__ Rout,
                                          float *__restrict__ Bout, int y0, int y_tile, int YI, int k4,
                                          bool lane_int, int ny, int S) {
-    if (!lane_int) return;
-#pragma unroll
-    for (int r = 0; r < RB; r++) {
-        const int y = y0 + r;
-        if (y >= y_tile && y < y_tile + YI && y < ny) {
-            const size_t off = (size_t)y * S + 4 + 4 * k4;
-            *reinterpret_cast<float4 *>(Rout + off) = v[0][r];
-            *reinterpret_cast<float4 *>(Bout + off) = v[1][r];
-        }
-    }
+    tb_store_colour<0, RB>(v, Rout, y0, y_tile, YI, k4, lane_int, ny, S);
+    tb_store_colour<1, RB>(v, Bout, y0, y_tile, YI, k4, lane_int, ny, S);
 }
 
 // One tile of the T-fused sweep: tile (bx, by) of a colour-split field.

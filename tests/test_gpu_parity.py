@@ -351,6 +351,11 @@ def test_deep_tiles_graph_matches_host_loop(dev):
     c, sc_ = _relax(occ, goal, dev, tw.Params(tol=1e-12, max_sweeps=100))
     d, sd = _relax(occ, goal, dev, tw.Params(tol=1e-12, max_sweeps=100, flags=tw.HP_HOST_LOOP))
     assert sc_["sweeps"] == sd["sweeps"] == 100 and np.array_equal(c, d)
+    # HP_TIMING runs each interval's launches as one captured graph (omega read from device memory)
+    t, st_ = _relax(occ, goal, dev, tw.Params(tol=1e-6, flags=tw.HP_TIMING))
+    assert st_["loop"] == tw.HP_LOOP_HOST and st_["sweeps"] == sb["sweeps"] and st_["sweep_ms"] > 0.0
+    assert st_["sweep_launches"] == sb["sweep_launches"]
+    assert np.array_equal(t, b)
     e, se = _relax(occ, goal, dev, tw.Params(tol=1e-6, tblock=4))
     assert se["tblock"] == 4 and se["status"] == tw.TW_OK
     assert np.abs(e - a).max() <= 1e-4   # both within their a-posteriori bounds of the same solution
