@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # DRAM traffic of the dominant kernel from one ncu capture, valid only while
 # the kernel source is unchanged (sha256 of the file that holds it).
-TRAFFIC = {"494e3fe7f3a237cf": 17468160 + 2048}   # rb_tb_kernel<7,14,12,1>, profiles/rb_tb_kernel_static2048.md
+TRAFFIC = {"64bfdbdb9e655bd5": 17464576 + 2304}   # rb_tb_kernel<7,14,12,1>, profiles/rb_tb_kernel_static2048.md
 
 
 def _env_int(k, d):
@@ -222,10 +222,34 @@ def field_accuracy(u, occ, sc, st):
     ustar = np.asarray([float(v) for v in ref["u_star"]])
     got = u[cells[:, 1], cells[:, 0]].double().cpu().numpy()
     err = np.abs(got - ustar)
-    return {"reference": ref["reference"], "tau_max": ref["tau_max"], "resid_inf": st["resid_inf"],
-            "error_bound": ref["tau_max"] * st["resid_inf"], "sampled_cells": int(len(cells)),
-            "max_abs_error_sampled": float(err.max()), "mean_abs_error_sampled": float(err.mean()),
-            "u_start": float(got[0]), "u_star_start": float(ustar[0])}
+    out = {"reference": ref["reference"], "tau_max": ref["tau_max"], "resid_inf": st["resid_inf"],
+           "error_bound": ref["tau_max"] * st["resid_inf"], "sampled_cells": int(len(cells)),
+           "max_abs_error_sampled": float(err.max()), "mean_abs_error_sampled": float(err.mean()),
+           "u_start": float(got[0]), "u_star_start": float(ustar[0])}
+    if "descent" in ref:
+        out["descent_agreement"] = descent_agreement(u, ref["descent"])
+    return out
+
+
+def descent_agreement(u, d):
+    """Eq. 3 direction agreement where phi* > 0.99: the fraction of the stored
+    sample cells (free, u* < 0.01, the reference's top two neighbours further
+    apart than twice its own error bound) at which the largest of the four
+    neighbours of the solved field is the reference's; overall and by u*."""
+    c = np.asarray(d["cells"], dtype=np.int64)
+    x, y = c[:, 0], c[:, 1]
+    nb = np.stack([u[y, x + 1].cpu().numpy(), u[y, x - 1].cpu().numpy(), u[y + 1, x].cpu().numpy(),
+                   u[y - 1, x].cpu().numpy()], axis=1)
+    hit = np.argmax(nb, axis=1) == np.asarray(d["index"])
+    us = np.asarray([float(v) for v in d["u_star"]])
+    bins = {}
+    for lo, hi in ((1e-3, 1e-2), (1e-4, 1e-3), (1e-5, 1e-4), (1e-6, 1e-5), (0.0, 1e-6)):
+        sel = (us >= lo) & (us < hi)
+        if sel.any():
+            bins[f"u*[{lo:g},{hi:g})"] = {"cells": int(sel.sum()), "agree": float(hit[sel].mean())}
+    return {"cells": int(len(hit)), "agree": float(hit.mean()), "by_u_star": bins,
+            "free_cells_phi_above_0.99": d["free_cells_phi_above_0.99"],
+            "near_ties_excluded": d["near_ties_excluded"], "reference_error_bound": d["oracle_error_bound"]}
 
 
 def max_over_ranks(x: float, dist, device=None) -> float:
@@ -533,7 +557,8 @@ def run_twgrid(args, rank, world, dist):
                            "etol": prm.etol, "err_est": fst["err_est"],
                            "max_abs_error_sampled": acc.get("max_abs_error_sampled"),
                            "mean_abs_error_sampled": acc.get("mean_abs_error_sampled"),
-                           "error_bound": acc.get("error_bound")}
+                           "error_bound": acc.get("error_bound"),
+                           "descent_agreement": (acc.get("descent_agreement") or {}).get("agree")}
             if prm.flags & tw.HP_POLISH:
                 forms[name]["polishes"] = fst["polishes"]
                 forms[name]["polished"] = fst["polished"]
