@@ -244,10 +244,12 @@ typedef struct {
                           checks have measured a change), else 0 */
 } hp_stats;
 
-#define HP_LOOP_HOST 0     /* host-driven: HP_HOST_LOOP, HP_TIMING, HP_JACOBI, HP_MIXED, or a cap
-                              below one check interval */
+#define HP_LOOP_HOST 0     /* host-driven: HP_HOST_LOOP, HP_TIMING, HP_JACOBI, or a cap below one
+                              check interval */
 #define HP_LOOP_GRAPH 1    /* CUDA graph whose conditional while-node runs the check intervals
-                              (the host finishes a cap that is not a whole number of intervals) */
+                              (the host finishes a cap that is not a whole number of intervals;
+                              HP_MIXED: each correction solve is one such graph launch, the outer
+                              FP64 steps are driven by the host) */
 
 /* hp_relax: the harmonic field of the occupancy grid (Sec. 3.1).  Cells with
  * occ != 0 and the border are Dirichlet cells at phi = 1, the goal cell is

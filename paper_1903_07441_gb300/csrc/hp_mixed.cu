@@ -20,7 +20,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "hp_internal.cuh"
@@ -351,6 +353,118 @@ mx_tb_kernel(const S *__restrict__ Rin, const S *__restrict__ Bin, S *__restrict
     }
 }
 
+// ---- graph-driven inner solve --------------------------------------------------------
+// One correction solve as a CUDA graph: a conditional while-node whose body is
+// K/T sweep launches, the inner residual and this control kernel, which takes
+// the host loop's decision on the device (relax_control, then the storage-floor
+// stop: after five intervals a residual that fell by less than 2 % ends the
+// solve) and sets the loop condition.  ctl->pad counts the intervals.
+__global__ void mx_inner_control_kernel(RelaxCtl *ctl, unsigned int *rmax, cudaGraphConditionalHandle h) {
+    RelaxCtl c = *ctl;
+    const float rf = __uint_as_float(*rmax);
+    *rmax = 0u;
+    const double prev = c.r_prev;
+    const int it = c.pad;
+    c.sweeps += c.K;
+    int go = relax_control(c, (double)rf, -1.0, c.K, -1.0);
+    if (go && prev > 0.0 && it > 4 && rf > 0.98 * prev) go = 0;   // storage floor reached
+    if (c.sweeps + c.K > c.max_sweeps) go = 0;
+    c.pad = it + 1;
+    c.go = go;
+    *ctl = c;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+struct MxGraph {
+    int dev, ny, W4, ssize;
+    const void *key[5];
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+static std::mutex g_mx_graph_mutex;
+static std::vector<MxGraph> g_mx_graphs;
+
+template <int T, class S>
+static int mx_build_inner_graph(RBLayout g, S *const (&e)[2][2], S *const (&q)[2], RelaxScalars *sc, int ny, int K,
+                                MxGraph *out) {
+    cudaGraph_t G = nullptr;
+    TW_CUDA(cudaGraphCreate(&G, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t err = cudaGraphConditionalHandleCreate(&h, G, 1u, cudaGraphCondAssignDefault);
+    if (err != cudaSuccess) { cudaGraphDestroy(G); set_cuda_error(err); return TW_ECUDA; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    err = cudaGraphAddNode(&cnode, G, nullptr, nullptr, 0, &cp);
+    if (err != cudaSuccess) { cudaGraphDestroy(G); set_cuda_error(err); return TW_ECUDA; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (err != cudaSuccess) { cudaGraphDestroy(G); set_cuda_error(err); return TW_ECUDA; }
+    err = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) { cudaStreamDestroy(cs); cudaGraphDestroy(G); set_cuda_error(err); return TW_ECUDA; }
+    const int KI4 = 32 - 2 * ((T + 4) / 4), YI = kMxWarps * kMxRows - 4 * T;
+    const dim3 tgrid(ceil_div(g.W4, KI4), ceil_div(ny, YI));
+    const float *omega_dev = &sc->ctl.omega_f;
+    pause_launch_count(true);
+    int cur = 0;
+    for (int i = 0; i < K / T; i++) {
+        TW_LAUNCH((mx_tb_kernel<T, S>), tgrid, kMxWarps * 32, 0, cs, e[cur][0], e[cur][1], e[1 - cur][0],
+                  e[1 - cur][1], q[0], q[1], g.MR, g.MB, ny, g.W4, g.S, g.MW, omega_dev);
+        cur = 1 - cur;
+    }
+    TW_LAUNCH((mx_inner_residual_kernel<S>), dim3(ceil_div(g.W4, 64), ceil_div(ny, 4)), dim3(64, 4), 0, cs, g, ny,
+              e[cur][0], e[cur][1], q[0], q[1], &sc->max32);
+    TW_LAUNCH(mx_inner_control_kernel, 1, 1, 0, cs, &sc->ctl, &sc->max32, h);
+    pause_launch_count(false);
+    cudaGraph_t captured = nullptr;
+    err = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (err != cudaSuccess) { cudaGraphDestroy(G); set_cuda_error(err); return TW_ECUDA; }
+    cudaGraphExec_t exec;
+    err = cudaGraphInstantiate(&exec, G, 0);
+    if (err != cudaSuccess) { cudaGraphDestroy(G); set_cuda_error(err); return TW_ECUDA; }
+    out->graph = G;
+    out->exec = exec;
+    return TW_OK;
+}
+
+// Run one correction solve through the cached graph of this layout; the
+// control record sc->ctl must hold the solve's starting state.
+template <int T, class S>
+static int mx_inner_graph(RBLayout &g, S *const (&e)[2][2], S *const (&q)[2], RelaxScalars *sc, int ny, int K,
+                          cudaStream_t s) {
+    int dev = 0;
+    TW_CUDA(cudaGetDevice(&dev));
+    const void *key[5] = {sc, e[0][0], e[1][0], q[0], g.MR};
+    std::lock_guard<std::mutex> lock(g_mx_graph_mutex);
+    const int ssize = (int)(sizeof(S) + 8 * std::is_same<S, __half>::value);   // the storage type
+    MxGraph *ent = nullptr;
+    for (auto &m : g_mx_graphs)
+        if (m.dev == dev && m.ny == ny && m.W4 == g.W4 && m.ssize == ssize && !memcmp(m.key, key, sizeof(key)))
+            ent = &m;
+    if (!ent) {
+        if (g_mx_graphs.size() >= 8) {
+            cudaGraphExecDestroy(g_mx_graphs.front().exec);
+            cudaGraphDestroy(g_mx_graphs.front().graph);
+            g_mx_graphs.erase(g_mx_graphs.begin());
+        }
+        MxGraph ne;
+        ne.dev = dev; ne.ny = ny; ne.W4 = g.W4;
+        ne.ssize = ssize;
+        memcpy(ne.key, key, sizeof(key));
+        const int er = mx_build_inner_graph<T, S>(g, e, q, sc, ny, K, &ne);
+        if (er) return er;
+        g_mx_graphs.push_back(ne);
+        ent = &g_mx_graphs.back();
+    }
+    TW_CUDA(cudaGraphLaunch(ent->exec, s));
+    return TW_OK;
+}
+
 // ---- driver ----------------------------------------------------------------------
 
 template <class S>
@@ -379,6 +493,7 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
     c.omega = c.adapt ? sor_initial_omega(nx, ny) : p->omega;
     c.omega_max = sor_omega_cap(nx, ny);
     int sweeps = 0, launches = 0, checks = 0, outer = 0;
+    bool graph_used = false;
     double r_inf = 0.0, corr = 0.0, corr_prev = 0.0;   // sizes of the last two outer updates (max |s e|)
     st->status = TW_NOT_CONVERGED;
     const dim3 rgrid(ceil_div(g.W4, 128), ny), rblock(128);
@@ -430,7 +545,28 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
         c.status = TW_NOT_CONVERGED;
         c.omega_f = (float)c.omega;
         float *omega_dev = &sc->ctl.omega_f;
-        for (int it = 0; sweeps < p->max_sweeps; it++) {
+        // whole check intervals run in the inner graph (no host round trip per interval); a cap
+        // closer than one interval, or HP_HOST_LOOP, keeps the host-driven loop below
+        const bool graph = !(p->flags & HP_HOST_LOOP) && p->max_sweeps - sweeps >= K;
+        if (graph) {
+            c.sweeps = 0;
+            c.checks = 0;
+            c.pad = 0;
+            c.max_sweeps = p->max_sweeps - sweeps;
+            c.go = 1;
+            TW_CUDA(cudaMemcpyAsync(&sc->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s));
+            TW_CUDA(cudaMemsetAsync(&sc->max32, 0, sizeof(unsigned int), s));
+            const int er = mx_inner_graph<T, S>(g, e, q, sc, ny, K, s);
+            if (er) return er;
+            TW_CUDA(cudaMemcpyAsync(&c, &sc->ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
+            TW_CUDA(cudaStreamSynchronize(s));
+            sweeps += c.sweeps;
+            checks += c.checks;
+            launches += c.checks * (K / T);
+            count_launches((unsigned long long)c.checks * (K / T + 2));
+            graph_used = true;
+        }
+        for (int it = 0; !graph && sweeps < p->max_sweeps; it++) {
             TW_CUDA(cudaMemcpyAsync(omega_dev, &c.omega_f, sizeof(float), cudaMemcpyHostToDevice, s));
             int n = p->max_sweeps - sweeps < K ? p->max_sweeps - sweeps : K;
             for (int done = 0; done < n; done += T) {
@@ -475,6 +611,7 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
     st->omega = c.omega;
     st->sweep_launches = launches;
     st->tblock = T;
+    st->loop = graph_used ? HP_LOOP_GRAPH : HP_LOOP_HOST;
     st->resid_inf = r_inf;   // the FP64 master's residual (the FP32 output rounds it)
     return TW_OK;
 }

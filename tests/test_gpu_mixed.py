@@ -127,3 +127,24 @@ def test_mixed_with_error_tolerance_at_2048(dev):
         assert np.abs(u - ustar).max() <= 1e-5, st
     else:
         assert st["status"] == tw.TW_NOT_CONVERGED and np.abs(u - ustar).max() > 1e-6
+
+
+@pytest.mark.parametrize("storage", STORES)
+def test_mixed_inner_graph_matches_host_loop(dev, storage):
+    """The correction solves run as CUDA graphs (conditional while-node, control on
+    the device) by default and from the host with HP_HOST_LOOP: the same decisions,
+    so both converge to the same field (omega is adapted by the device's or the
+    host's libm, which may differ in the last bit, so the fields are compared
+    within the a-posteriori bound rather than bit for bit)."""
+    sc = scenes.static128()
+    occ, _, _ = oracle.build_grid(sc)
+    _, fixed = oracle.solve_field(occ, sc.goal, tol=1e-12)
+    tau_max = oracle.exit_time(fixed).max()
+    tol = 1e-9
+    a, sa = _solve(dev, occ, sc.goal, storage=storage, tol=tol)
+    b, sb = _solve(dev, occ, sc.goal, storage=storage, tol=tol, flags=tw.HP_HOST_LOOP)
+    assert sa["loop"] == tw.HP_LOOP_GRAPH and sb["loop"] == tw.HP_LOOP_HOST
+    assert sa["status"] == sb["status"] == tw.TW_OK
+    assert sa["resid_inf"] <= tol and sb["resid_inf"] <= tol
+    assert np.abs(a - b).max() <= 2.0 * tau_max * tol + 1e-7
+    assert abs(sa["sweeps"] - sb["sweeps"]) <= 0.1 * sb["sweeps"] + 64
