@@ -254,16 +254,18 @@ __global__ void __launch_bounds__(256) mx_inner_residual_kernel(RBLayout g, int 
 // T-fused SOR sweeps of the correction equation, storage S, FP32 arithmetic.
 // Same register blocking as the FP32 kernel (8 rows x float4 of both colours
 // per thread, 8 warps, halo 2T rows / ceil((T+1)/4) float4 columns); the
-// right-hand side is read through the L1 cache (the tile's rows repeat every
-// half-sweep, so after the first one they hit L1).
+// right-hand side of the thread's rows is converted to FP32 once, at the start,
+// into the thread's own slots of shared memory (re-read from global memory or
+// L1 for every row of every half-sweep, half of those reads missed L1).
 constexpr int kMxRows = 8, kMxWarps = 8;
+constexpr size_t kMxQBytes = sizeof(float4) * 2 * kMxRows * kMxWarps * 32;   // dynamic shared memory (64 KB)
 
 // One half-sweep of the correction equation for colour C (compile-time, so the
 // register arrays stay in registers): e <- e + omega ((1/4) sum nbr + q - e).
 template <int C, class S>
 __device__ __forceinline__ void mx_half(float4 (&v)[2][kMxRows], const uint32_t (&m)[2], float omega,
                                         float4 (&s_top)[2][kMxWarps][32], float4 (&s_bot)[2][kMxWarps][32],
-                                        const S *__restrict__ Q, int y0, bool kin, int ny, int Sst, int k) {
+                                        const float4 *__restrict__ sq) {
     constexpr int RB = kMxRows, WARPS = kMxWarps, O = 1 - C;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -285,9 +287,7 @@ __device__ __forceinline__ void mx_half(float4 (&v)[2][kMxRows], const uint32_t 
             const float ex = __shfl_up_sync(0xffffffffu, mid.w, 1);
             l0 = ex; l1 = mid.x; l2 = mid.y; l3 = mid.z; r0 = mid.x; r1 = mid.y; r2 = mid.z; r3 = mid.w;
         }
-        const int yq = y0 + r;
-        const bool qin = kin && yq >= 0 && yq < ny;
-        const float4 q = qin ? Store<S>::load4(Q + (size_t)yq * Sst + 4 + k) : z4;
+        const float4 q = sq[(C * RB + r) * (WARPS * 32) + threadIdx.x];
         float4 cv = v[C][r];
         const uint32_t bits = (m[C] >> (4 * r)) & 0xFu;
         const float n0 = fmaf(omega, fmaf(0.25f, (l0 + r0) + (up.x + dn.x), q.x - cv.x), cv.x);
@@ -317,6 +317,7 @@ mx_tb_kernel(const S *__restrict__ Rin, const S *__restrict__ Bin, S *__restrict
     const int y0 = y_tile - HY + warp * RB;
     const bool kin = (k4 >= 0) && (k4 < W4);
     const int k = 4 * k4;
+    extern __shared__ float4 sq[];   // [colour][row][thread]: the right-hand side of the thread's rows
     const float omega = *omega_p;
     float4 v[2][RB];
     uint32_t m[2] = {0u, 0u};
@@ -328,6 +329,8 @@ mx_tb_kernel(const S *__restrict__ Rin, const S *__restrict__ Bin, S *__restrict
         const size_t off = (size_t)(in ? y : 0) * Sst + 4 + (in ? k : 0);
         v[0][r] = in ? Store<S>::load4(Rin + off) : z4;
         v[1][r] = in ? Store<S>::load4(Bin + off) : z4;
+        sq[r * (WARPS * 32) + threadIdx.x] = in ? Store<S>::load4(Qr + off) : z4;
+        sq[(RB + r) * (WARPS * 32) + threadIdx.x] = in ? Store<S>::load4(Qb + off) : z4;
         if (in) {
             const size_t w = (size_t)y * MW + (k >> 5);
             m[0] |= ((MR[w] >> (k & 31)) & 0xFu) << (4 * r);
@@ -336,8 +339,8 @@ mx_tb_kernel(const S *__restrict__ Rin, const S *__restrict__ Bin, S *__restrict
     }
 #pragma unroll 1
     for (int p = 0; p < T; p++) {   // red then black, colour-indexed exchange buffers
-        mx_half<0, S>(v, m, omega, s_top, s_bot, Qr, y0, kin, ny, Sst, k);
-        mx_half<1, S>(v, m, omega, s_top, s_bot, Qb, y0, kin, ny, Sst, k);
+        mx_half<0, S>(v, m, omega, s_top, s_bot, sq);
+        mx_half<1, S>(v, m, omega, s_top, s_bot, sq);
     }
     const bool kint = lane >= HK4 && lane < 32 - HK4 && kin;
     if (kint) {
@@ -412,7 +415,7 @@ static int mx_build_inner_graph(RBLayout g, S *const (&e)[2][2], S *const (&q)[2
     pause_launch_count(true);
     int cur = 0;
     for (int i = 0; i < K / T; i++) {
-        TW_LAUNCH((mx_tb_kernel<T, S>), tgrid, kMxWarps * 32, 0, cs, e[cur][0], e[cur][1], e[1 - cur][0],
+        TW_LAUNCH((mx_tb_kernel<T, S>), tgrid, kMxWarps * 32, kMxQBytes, cs, e[cur][0], e[cur][1], e[1 - cur][0],
                   e[1 - cur][1], q[0], q[1], g.MR, g.MB, ny, g.W4, g.S, g.MW, omega_dev);
         cur = 1 - cur;
     }
@@ -485,6 +488,7 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
               (p->flags & HP_WARM_START) ? 1 : 0, g, x);
     TW_CHECK_LAUNCH();
     const int T = 4, K = 32;
+    TW_CUDA(cudaFuncSetAttribute(mx_tb_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMxQBytes));
     // inner solves relax the correction residual by this factor (bounded by the storage precision)
     const double inner_drop = (sizeof(S) == 4) ? 1e-4 : (std::is_same<S, __half>::value ? 2e-3 : 1e-2);
     RelaxCtl c;   // omega state carried across the inner solves
@@ -571,7 +575,7 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
             int n = p->max_sweeps - sweeps < K ? p->max_sweeps - sweeps : K;
             for (int done = 0; done < n; done += T) {
                 // a partial last launch is rounded up to T sweeps (the cap may be exceeded by < T)
-                TW_LAUNCH((mx_tb_kernel<T, S>), tgrid, kMxWarps * 32, 0, s, e[cur][0], e[cur][1], e[1 - cur][0],
+                TW_LAUNCH((mx_tb_kernel<T, S>), tgrid, kMxWarps * 32, kMxQBytes, s, e[cur][0], e[cur][1], e[1 - cur][0],
                           e[1 - cur][1], q[0], q[1], g.MR, g.MB, ny, g.W4, g.S, g.MW, (const float *)omega_dev);
                 cur = 1 - cur;
                 launches++;
