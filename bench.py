@@ -906,6 +906,49 @@ def run_reference(args, rank, world, dist):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_case(case):
+    """One small case of a kernel other than the headline's, for an ncu capture of that kernel
+    (profiles/ names the command): conv128 = a 128 -> 128 tensor-memory convolution on 512 x 512,
+    conv32 = 32 -> 32 on 1024 x 1024 (3 warm-up calls, then 10 timed); mixed_fp16 = one HP_MIXED FP16
+    solve of a seeded 2048 x 2048 field (20 % blocked) through the host-driven loop, whose correction
+    sweeps are separate launches (ncu does not profile kernel nodes of graphs with conditional nodes)."""
+    import torch
+    import paper_1903_07441_gb300 as tw
+    dev = torch.device("cuda:0")
+    if case.startswith("conv"):
+        cin, cout, H, W = (128, 128, 512, 512) if case == "conv128" else (32, 32, 1024, 1024)
+        g = torch.Generator(device=dev).manual_seed(0)
+        x = (torch.randn(cin, H, W, device=dev, generator=g) * 0.5).to(torch.bfloat16)
+        w = torch.randn(cout, cin, 3, 3, device=dev, generator=g) * (1.0 / (9 * cin) ** 0.5)
+        b = torch.randn(cout, device=dev, generator=g) * 0.1
+        for _ in range(3):
+            tw.ws_conv3x3(x, w, b, relu=True, impl=tw.WS_CONV_TC)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            tw.ws_conv3x3(x, w, b, relu=True, impl=tw.WS_CONV_TC)
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / 10
+        if tw.ws_conv_check():
+            raise RuntimeError("a tensor-memory convolution gave up a bounded wait")
+        return {"case": case, "ms_per_call": ms, "tflops": 2 * 9 * cin * cout * H * W / ms / 1e9,
+                "note": "per call: the weight re-arrangement kernel and the convolution"}
+    rng = np.random.default_rng(3)
+    n = 2048
+    occ = (rng.random((n, n)) < 0.2).astype(np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 3
+    goal = (1500, 700)
+    occ[goal[1], goal[0]] = 0
+    grid = tw.make_grid(n, n, 0.05)
+    u, st = tw.hp_relax(grid, torch.from_numpy(occ).to(dev), goal,
+                        params=tw.Params(method=tw.HP_MIXED, storage=tw.HP_STORE_F16, tol=1e-6, max_sweeps=2000,
+                                         flags=tw.HP_HOST_LOOP))
+    torch.cuda.synchronize()
+    return {"case": case, "sweeps": st["sweeps"], "status": st["status"], "sweep_launches": st["sweep_launches"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -933,8 +976,13 @@ def main():
                     help="also run the success / collision-free evaluation over 1-16 moving obstacles")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--profile-case", choices=["conv128", "conv32", "mixed_fp16"], default=None,
+                    help="run one small kernel case (for an ncu capture) and print its timing, instead of the bench")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_case:
+        print(json.dumps(profile_case(args.profile_case)), flush=True)
+        return
 
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
