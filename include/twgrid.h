@@ -216,7 +216,7 @@ typedef struct {
                           HP_POLISH) is accepted if it meets tol.  If the estimate and the residual both
                           stop falling for four checks (once r_inf < 16 tol) the solve ends with
                           TW_NOT_CONVERGED.  HP_MIXED: the outer loop also stops only once its
-                          estimate, the last FP64 update's size c times q / (1 - q) with q = its ratio
+                          estimate, the last FP64 update's size c divided by 1 - q with q = its ratio
                           to the update before (undefined while q >= 0.9), is <= etol.  HP_JACOBI
                           ignores etol. */
 } hp_params;

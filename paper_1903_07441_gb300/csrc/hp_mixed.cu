@@ -519,12 +519,14 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
         st->resid_l2 = sqrt(sum);
         checks++;
         // outer error estimate (etol > 0): the last update's size corr shrinks by q = corr / corr_prev
-        // per outer step, so the error left after it is about corr q / (1 - q) (q above 0.9, or no
-        // earlier update: not estimated yet)
+        // per outer step; the error left is taken as corr / (1 - q), the whole geometric tail including
+        // a step of the last update's own size -- that update comes from an inexact, low-precision
+        // correction solve, and the tail alone (corr q / (1 - q)) was measured below the true error
+        // (q above 0.9, or no earlier update: not estimated yet)
         double est = DBL_MAX;
         if (corr_prev > 0.0 && corr > 0.0) {
             const double q = corr / corr_prev;
-            if (q < 0.9) est = corr * q / (1.0 - q);
+            if (q < 0.9) est = corr / (1.0 - q);
         } else if (outer > 0 && corr == 0.0) {
             est = 0.0;
         }
