@@ -70,11 +70,12 @@ descent_kernel(const float *__restrict__ u, const uint8_t *__restrict__ occ, int
     if (tid == 0) { out->len = s_len; out->status = s_status; }
 }
 
-__device__ __forceinline__ double band_energy(const float *u, int nx, int qx, int qy, const int *path, int i,
-                                              double w, double k) {
-    double uq = (double)u[(size_t)qy * nx + qx];
-    double ax = qx - path[2 * (i - 1)], ay = qy - path[2 * (i - 1) + 1];
-    double bx = qx - path[2 * (i + 1)], by = qy - path[2 * (i + 1) + 1];
+// Energy of node position q between its neighbours a and b (u_q = u at q).
+__device__ __forceinline__ double band_energy_q(float u_q, int qx, int qy, int pax, int pay, int pbx, int pby,
+                                                double w, double k) {
+    double uq = (double)u_q;
+    double ax = qx - pax, ay = qy - pay;
+    double bx = qx - pbx, by = qy - pby;
     return __dadd_rn(__ddiv_rn(w, uq),
                      __dmul_rn(__dmul_rn(0.5, k),
                                __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)),
@@ -100,20 +101,48 @@ band_kernel(const float *__restrict__ u, const uint8_t *__restrict__ occ, int nx
                 int px = path[2 * i], py = path[2 * i + 1];
                 int ax = path[2 * (i - 1)], ay = path[2 * (i - 1) + 1];
                 int bx_ = path[2 * (i + 1)], by_ = path[2 * (i + 1) + 1];
-                double best = band_energy(u, nx, px, py, path, i, w, k);
+                // the 3 x 3 neighbourhood's u and occupancy, loaded together (one round trip
+                // instead of one per candidate); outside the grid reads as occupied
+                float uq[9];
+                uint8_t oq[9];
+#pragma unroll
+                for (int t = 0; t < 9; t++) {
+                    const int qx = px + t % 3 - 1, qy = py + t / 3 - 1;
+                    const bool in = qx >= 0 && qy >= 0 && qx < nx && qy < ny;
+                    const size_t c = in ? (size_t)qy * nx + qx : 0;
+                    uq[t] = in ? u[c] : 0.0f;
+                    oq[t] = in ? occ[c] : (uint8_t)1;
+                }
+                // FP32 screen: a candidate whose FP32 energy exceeds the smallest by more than a
+                // relative 1e-5 cannot be the FP64 minimum (the FP32 values carry a relative error
+                // below 1e-6 and every energy is positive), so only the near-minimal candidates
+                // take the FP64 energies the decision is made with
+                float e32[9];   // NaN: not a candidate; +inf (FP32 overflow): always checked in FP64
+                float m32 = INFINITY;
+                const float w32 = (float)w, hk32 = 0.5f * (float)k;
+#pragma unroll
+                for (int t = 0; t < 9; t++) {
+                    e32[t] = __int_as_float(0x7fc00000);
+                    if (t == 4) continue;
+                    const int qx = px + t % 3 - 1, qy = py + t / 3 - 1;
+                    if (oq[t] != 0) continue;
+                    if (!(uq[t] > 0.0f)) continue;
+                    if (abs(qx - ax) > 1 || abs(qy - ay) > 1 || abs(qx - bx_) > 1 || abs(qy - by_) > 1) continue;
+                    const int d2 = (qx - ax) * (qx - ax) + (qy - ay) * (qy - ay) + (qx - bx_) * (qx - bx_) +
+                                   (qy - by_) * (qy - by_);
+                    e32[t] = w32 / uq[t] + hk32 * (float)d2;
+                    m32 = fminf(m32, e32[t]);
+                }
+                double best = band_energy_q(uq[4], px, py, ax, ay, bx_, by_, w, k);
                 int nxp = px, nyp = py;
-                for (int dy = -1; dy <= 1; dy++)
-                    for (int dx = -1; dx <= 1; dx++) {
-                        if (dx == 0 && dy == 0) continue;
-                        int qx = px + dx, qy = py + dy;
-                        if (qx < 0 || qy < 0 || qx >= nx || qy >= ny) continue;
-                        size_t c = (size_t)qy * nx + qx;
-                        if (occ[c] != 0) continue;
-                        if (!(u[c] > 0.0f)) continue;
-                        if (abs(qx - ax) > 1 || abs(qy - ay) > 1 || abs(qx - bx_) > 1 || abs(qy - by_) > 1) continue;
-                        double e = band_energy(u, nx, qx, qy, path, i, w, k);
-                        if (e < best) { best = e; nxp = qx; nyp = qy; }
-                    }
+                const float lim = m32 * (1.0f + 1e-5f);
+#pragma unroll
+                for (int t = 0; t < 9; t++) {   // dy outer, dx inner, as listed
+                    if (t == 4 || e32[t] != e32[t] || (e32[t] > lim && e32[t] != INFINITY)) continue;
+                    const int qx = px + t % 3 - 1, qy = py + t / 3 - 1;
+                    double e = band_energy_q(uq[t], qx, qy, ax, ay, bx_, by_, w, k);
+                    if (e < best) { best = e; nxp = qx; nyp = qy; }
+                }
                 if (nxp != px || nyp != py) {
                     path[2 * i] = nxp; path[2 * i + 1] = nyp;
                     s_moved = 1;

@@ -651,3 +651,31 @@ def test_end_to_end_planner_frame(dev):
     if status == tw.TW_OK:
         assert (occ_ref[path[:, 1], path[:, 0]] == 0).all()
         assert _hausdorff(path, opath) <= 2.0
+
+
+@pytest.mark.parametrize("seed,rubber", [(1041, 50), (1042, 100), (1046, 7)])
+def test_path_equals_oracle_on_the_same_field(dev, seed, rubber):
+    """Given the GPU's own field, the GPU descent (Eq. 3, tie order +x, -x, +y, -y) and rubber band
+    (odd-then-even node sweeps, candidates in dy-then-dx order, FP64 energies) return exactly the
+    oracle's path, node for node -- not just within the Hausdorff tolerance that separate fields
+    need.  Starts: the scene's start, and the free cell farthest from the goal where u >= 1e-5."""
+    sc = scenes.dynamic(seed=seed, side=256, n_obs=16, frames=1, static_shapes=12)
+    occ, _, _ = oracle.build_grid(sc)
+    goal = sc.goal
+    assert occ[goal[1], goal[0]] == 0
+    occ_t = torch.from_numpy(occ).to(dev)
+    grid = tw.make_grid(sc.nx, sc.ny, sc.cell)
+    u, _ = tw.hp_relax(grid, occ_t, goal, params=tw.Params(omega=1.0, tol=0.0, max_sweeps=40000))
+    u64 = u.cpu().numpy().astype(np.float64)
+    _, fixed = oracle.dirichlet_from_occ(occ, goal)
+    cand = np.argwhere((occ == 0) & (u64 >= 1e-5))
+    far = cand[np.argmax(np.abs(cand[:, 1] - goal[0]) + np.abs(cand[:, 0] - goal[1]))]
+    long_paths = 0
+    for start in (sc.start, (int(far[1]), int(far[0]))):
+        status, path = tw.plan_path(grid, u, occ_t, start, goal, rubber_iters=rubber)
+        ost, opath = oracle.plan_path(u64, fixed, start, goal, rubber_iters=rubber)
+        assert status == ost
+        if status == tw.TW_OK:
+            assert np.array_equal(path, opath)
+            long_paths += len(path) > 50
+    assert long_paths >= 1
