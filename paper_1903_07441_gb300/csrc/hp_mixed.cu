@@ -496,6 +496,12 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
     c.adapt = p->omega == 0.0;
     c.omega = c.adapt ? sor_initial_omega(nx, ny) : p->omega;
     c.omega_max = sor_omega_cap(nx, ny);
+    // Each correction solve starts from the over-relaxation the earlier ones adapted to, not from
+    // where the last one ended: a correction solve ends at its storage floor, where the controller
+    // takes the stagnation for the FP32 rounding floor and backs omega off for good; carried into
+    // the next solve, that left every later one at omega ~1.5 (FP16 on static2048: 44 outer steps).
+    const int adapt0 = c.adapt;
+    double omega_keep = c.omega;
     int sweeps = 0, launches = 0, checks = 0, outer = 0;
     bool graph_used = false;
     double r_inf = 0.0, corr = 0.0, corr_prev = 0.0;   // sizes of the last two outer updates (max |s e|)
@@ -544,6 +550,8 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
         TW_CUDA(cudaMemsetAsync(e[0][0], 0, plane, s));
         TW_CUDA(cudaMemsetAsync(e[0][1], 0, plane, s));
         int cur = 0;
+        c.omega = omega_keep;
+        c.adapt = adapt0;
         c.r_prev = -1.0;
         c.same_iv = 0;
         c.K = K;
@@ -595,6 +603,7 @@ static int mixed_solve(const uint8_t *occ, int nx, int ny, int gx, int gy, float
             if (!relax_control(c, (double)rf, -1.0, n, -1.0)) break;
             if (prev > 0.0 && it > 4 && rf > 0.98 * prev) break;   // storage floor reached
         }
+        if (c.adapt && c.omega > omega_keep) omega_keep = c.omega;   // adapted upwards, not backed off
         // 4. x += s e, and the update's size
         unsigned long long *dmax = reinterpret_cast<unsigned long long *>(&sc->pad1[1]);
         TW_CUDA(cudaMemsetAsync(dmax, 0, sizeof(*dmax), s));

@@ -110,10 +110,10 @@ def test_mixed_reaches_1e6_at_2048(dev):
 def test_mixed_with_error_tolerance_at_2048(dev):
     """With the error tolerance (etol = 1e-5, r_inf <= 1e-6) at 2048^2, against the oracle's full
     field: the FP16-storage form and the FP32-correction form (FP64 refinement) meet max |u - u*|
-    <= 1e-5 over every cell -- the FP32-correction form far below it, since its FP64 master goes
-    under the FP32 rounding floor -- and the BF16-storage form, whose 8-bit mantissa leaves each
-    correction solve too short to converge the field's slow mode, either meets the tolerance or
-    reports TW_NOT_CONVERGED (it never claims an accuracy it has not shown)."""
+    <= 1e-5 over every cell -- far below it, since the FP64 master goes under the FP32 rounding
+    floor -- and the BF16-storage form, whose 8-bit mantissa makes each correction solve short,
+    either meets the tolerance or reports TW_NOT_CONVERGED (it never claims an accuracy it has not
+    shown)."""
     sc = scenes.static2048()
     occ, _, _ = oracle.build_grid(sc)
     ustar, fixed = oracle.solve_field(occ, sc.goal, tol=1e-13)
