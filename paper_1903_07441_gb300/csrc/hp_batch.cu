@@ -14,9 +14,10 @@
 //     retires converged (or capped) instances with their completion time
 //     (%globaltimer, for the per-instance latency), compacts the tile list of
 //     the remaining ones and sets the loop condition.
-// The blocking depth T is chosen per batch shape by a small autotuner that
-// times the candidates on the batch itself (Gauss-Seidel sweeps that count
-// towards the solve) and caches the choice.
+// The tile configuration (blocking depth T and tile shape) and the check
+// interval K are chosen per batch shape by a small autotuner that times the
+// candidates on the batch itself (Gauss-Seidel sweeps that count towards the
+// solve) and caches the choice.
 #include <float.h>
 #include <string.h>
 
