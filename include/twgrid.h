@@ -198,7 +198,8 @@ typedef struct {
                           96 of them -- about 2048 x 1400 cells and up -- else 4); hp_relax_batched
                           takes 2, 4, 6 or 7 (anything else: autotuned) */
     int flags;         /* HP_WARM_START | HP_OUT_PHI | HP_TIMING | HP_HOST_LOOP | HP_POLISH */
-    double etol;       /* HP_RBSOR with T >= 2: also require the estimated field error max |u - u*| to be
+    double etol;       /* HP_RBSOR with T >= 2 (and hp_relax_batched): also require the estimated field
+                          error max |u - u*| to be
                           <= etol (0 = off).  The residual test alone does not bound the error well: the
                           slowest mode of a cluttered field has a tiny residual and a large error.  From
                           the first check with r_inf < 100 tol on, each check copies the field into
@@ -315,8 +316,13 @@ int hp_relax_noalloc(const tw_grid *g, const uint8_t *occ_dev, int gx, int gy, f
  * shape (256 at the first).  p->tblock 2 or 4 forces shallow tiles at that
  * depth, 6 or 7 deep tiles; stats[i].tblock reports the depth used.
  * n: 1..1024 instances.  p: method HP_RBSOR, FP32; tol, max_sweeps, omega
- * (0 = adaptive) and check_every apply to every instance; HP_WARM_START reads
- * u from field_dev, HP_OUT_PHI writes phi (not both).  stats: host array of n,
+ * (0 = adaptive), check_every and etol apply to every instance (with etol > 0
+ * each instance gets the error estimate of hp_relax -- snapshot planes, which
+ * the workspace size includes, and the residual 2-norm from per-tile sums
+ * added in tile order -- while omega keeps adapting on the residual max; an
+ * instance is TW_OK once r_inf <= tol and its estimate <= etol, reported in
+ * stats[i].err_est); HP_WARM_START reads u from field_dev, HP_OUT_PHI writes
+ * phi (not both).  stats: host array of n,
  * latency_ms: host array of n or NULL -- the time from the start of the
  * relaxation to each instance's convergence, measured on the device
  * (%globaltimer).  Returns TW_OK, TW_NOT_CONVERGED if any instance hit the

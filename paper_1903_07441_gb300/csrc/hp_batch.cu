@@ -57,10 +57,12 @@ struct BatchInst {
     uint32_t *MR, *MB;
     const uint8_t *occ;
     float *field;
+    float *P3[2];                     // snapshot planes [colour] (error tolerance only, else null)
+    float *l2p;                       // per-tile sums of squared residuals of this instance (etol only)
     unsigned int rmax;                // FP32 residual max (bits) of the current interval
+    unsigned int dmax;                // FP32 max change of a free cell since the snapshot (bits)
     int active;                       // 1 while the instance is being relaxed
     int error;                        // TW_EGOAL_BLOCKED if the goal cell is occupied
-    int pad2;
     unsigned long long t_done;        // %globaltimer at retirement
     unsigned long long max64;         // final FP64 residual max (bits) and sum of squares
     double sum64;
@@ -166,16 +168,23 @@ batch_tb_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const 
 }
 
 // FP32 residual max of each active tile's interior, one atomic per CTA and tile.
+// With an error tolerance (the instance has snapshot planes) also the tile's
+// sum of squared residuals, into its own slot (added in tile order by the
+// control kernel: deterministic), and the snapshot work of the single-field
+// residual pass (snap 1: copy the planes; 2: also the largest change of a
+// free cell since the copy, atomicMax into dmax).
 template <int T, int DEEP>
 __global__ void __launch_bounds__(256)
 batch_residual_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, const BatchHdr *__restrict__ H) {
     using Sh = BShape<T, DEEP>;
+    __shared__ float s_q[8];
     const int n_active = H->n_active;
     for (int t = blockIdx.x; t < n_active; t += gridDim.x) {
         const int2 it = list[t];
         BatchInst &b = I[it.x];
         const int bx = it.y % b.tx, by = it.y / b.tx;
-        float r = 0.0f;
+        const int snap = b.P3[0] ? b.ctl.snap : 0;
+        float r = 0.0f, q = 0.0f, dm = 0.0f;
         for (int idx = threadIdx.x; idx < Sh::KI4 * Sh::YI; idx += blockDim.x) {
             const int k4 = bx * Sh::KI4 + idx % Sh::KI4;
             const int y = by * Sh::YI + idx / Sh::KI4;
@@ -189,13 +198,38 @@ batch_residual_kernel(BatchInst *__restrict__ I, const int2 *__restrict__ list, 
                 float4 nb[4];
                 rb_load_neighbours(V, b.S, y, k, (y + color) & 1, nb);
                 const float4 c = *reinterpret_cast<const float4 *>(U + (size_t)y * b.S + 4 + k);
-                if (bits & 1u) r = fmaxf(r, fabsf(rb_step(c.x, nb[0].x, nb[1].x, nb[2].x, nb[3].x)));
-                if (bits & 2u) r = fmaxf(r, fabsf(rb_step(c.y, nb[0].y, nb[1].y, nb[2].y, nb[3].y)));
-                if (bits & 4u) r = fmaxf(r, fabsf(rb_step(c.z, nb[0].z, nb[1].z, nb[2].z, nb[3].z)));
-                if (bits & 8u) r = fmaxf(r, fabsf(rb_step(c.w, nb[0].w, nb[1].w, nb[2].w, nb[3].w)));
+                const float t0 = rb_step(c.x, nb[0].x, nb[1].x, nb[2].x, nb[3].x);
+                const float t1 = rb_step(c.y, nb[0].y, nb[1].y, nb[2].y, nb[3].y);
+                const float t2 = rb_step(c.z, nb[0].z, nb[1].z, nb[2].z, nb[3].z);
+                const float t3 = rb_step(c.w, nb[0].w, nb[1].w, nb[2].w, nb[3].w);
+                if (bits & 1u) { r = fmaxf(r, fabsf(t0)); q = fmaf(t0, t0, q); }
+                if (bits & 2u) { r = fmaxf(r, fabsf(t1)); q = fmaf(t1, t1, q); }
+                if (bits & 4u) { r = fmaxf(r, fabsf(t2)); q = fmaf(t2, t2, q); }
+                if (bits & 8u) { r = fmaxf(r, fabsf(t3)); q = fmaf(t3, t3, q); }
+                if (snap) {
+                    float4 *Pp = reinterpret_cast<float4 *>(b.P3[color] + (size_t)y * b.S + 4 + k);
+                    if (snap == 2) {
+                        const float4 o = *Pp;
+                        if (bits & 1u) dm = fmaxf(dm, fabsf(c.x - o.x));
+                        if (bits & 2u) dm = fmaxf(dm, fabsf(c.y - o.y));
+                        if (bits & 4u) dm = fmaxf(dm, fabsf(c.z - o.z));
+                        if (bits & 8u) dm = fmaxf(dm, fabsf(c.w - o.w));
+                    }
+                    *Pp = c;
+                }
             }
         }
-        block_max_atomic(r, &b.rmax);
+        if (b.l2p) {   // the tile's sum of squares, reduced in a fixed order
+            for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+            if ((threadIdx.x & 31) == 0) s_q[threadIdx.x >> 5] = q;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float v = 0.0f;
+                for (int w = 0; w < 8; w++) v += s_q[w];
+                b.l2p[it.y] = v;
+            }
+        }
+        block_max2_atomic(r, &b.rmax, dm, snap == 2 ? &b.dmax : nullptr);
         __syncthreads();
     }
 }
@@ -214,8 +248,16 @@ batch_control_kernel(BatchInst *__restrict__ I, BatchHdr *__restrict__ H, int2 *
             RelaxCtl c = b.ctl;
             const float rf = __uint_as_float(b.rmax);
             b.rmax = 0u;
+            double e = -1.0, d = -1.0;
+            if (b.l2p) {   // error tolerance: the 2-norm (tile order) and the change since the snapshot
+                double sum = 0.0;
+                for (int t = 0; t < b.tx * b.ty; t++) sum += (double)b.l2p[t];
+                e = sqrt(sum);
+                if (c.snap == 2) d = (double)__uint_as_float(b.dmax);
+                b.dmax = 0u;
+            }
             c.sweeps += c.K;
-            int go = relax_control(c, (double)rf, -1.0, c.K, -1.0);
+            int go = relax_control(c, (double)rf, e, c.K, d);
             if (c.sweeps + c.K > c.max_sweeps || final_check) go = 0;
             if (b.error) go = 0;
             c.omega_f = (float)c.omega;
@@ -285,11 +327,13 @@ struct BatchLayout {
     BatchInst *inst;
     int *row_off;     // prefix sums of the instances' ny (n + 1 entries)
     int2 *list;
+    float *l2p;       // per-tile sums of squares (error tolerance only), max_tiles entries
     size_t max_tiles;
 };
 
+// est: carve the error estimate's snapshot planes and per-tile partial sums
 static size_t carve_batch(Carver &cv, int n, const hp_instance *in, std::vector<BatchInst> *host,
-                          BatchLayout *L) {
+                          BatchLayout *L, bool est) {
     BatchLayout l;
     l.hdr = cv.take<BatchHdr>(1);
     l.inst = cv.take<BatchInst>(n > 0 ? n : 1);
@@ -302,6 +346,7 @@ static size_t carve_batch(Carver &cv, int n, const hp_instance *in, std::vector<
         max_tiles += (size_t)tx2 * ty2;
     }
     l.list = cv.take<int2>(max_tiles > 0 ? max_tiles : 1);
+    l.l2p = est ? cv.take<float>(max_tiles > 0 ? max_tiles : 1) : nullptr;
     l.max_tiles = max_tiles;
     for (int i = 0; i < n; i++) {
         RBLayout g = rb_layout(in[i].nx, in[i].ny);
@@ -314,6 +359,10 @@ static size_t carve_batch(Carver &cv, int n, const hp_instance *in, std::vector<
         b.P[1][0] = cv.take<float>(plane); b.P[1][1] = cv.take<float>(plane);
         b.MR = cv.take<uint32_t>((size_t)in[i].ny * g.MW);
         b.MB = cv.take<uint32_t>((size_t)in[i].ny * g.MW);
+        if (est) {   // written before they are read (the first check takes the snapshot)
+            b.P3[0] = cv.take<float>(plane);
+            b.P3[1] = cv.take<float>(plane);
+        }
         b.occ = in[i].occ_dev;
         b.field = in[i].field_dev;
         if (host) host->push_back(b);
@@ -483,10 +532,9 @@ static int autotune(BatchLayout &L, std::vector<BatchInst> &hb, int n, cudaStrea
 using namespace tw;
 
 extern "C" size_t hp_relax_batched_workspace_size(int n, const hp_instance *inst, const hp_params *p) {
-    (void)p;
     if (n < 1 || n > kMaxBatch || !inst) return 0;
     Carver cv;
-    return carve_batch(cv, n, inst, nullptr, nullptr);
+    return carve_batch(cv, n, inst, nullptr, nullptr, p && p->etol > 0.0);
 }
 
 extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params *p, hp_stats *stats,
@@ -494,8 +542,9 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
     if (n < 1 || n > kMaxBatch || !inst || !p || !stats) return TW_EINVAL;
     if (p->method != HP_RBSOR || !(p->tol >= 0.0) || p->max_sweeps < 1 ||
         ((p->flags & HP_WARM_START) && (p->flags & HP_OUT_PHI)) ||
-        !(p->omega == 0.0 || (p->omega > 0.0 && p->omega < 2.0)))
+        !(p->omega == 0.0 || (p->omega > 0.0 && p->omega < 2.0)) || !isfinite(p->etol) || p->etol < 0.0)
         return TW_EINVAL;
+    const bool est = p->etol > 0.0;
     size_t cells = 0;
     for (int i = 0; i < n; i++) {
         const hp_instance &q = inst[i];
@@ -507,7 +556,7 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
     Carver cv(workspace, workspace_bytes);
     std::vector<BatchInst> hb;
     BatchLayout L;
-    carve_batch(cv, n, inst, &hb, &L);
+    carve_batch(cv, n, inst, &hb, &L, est);
     if (!cv.ok()) return TW_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     for (int i = 0; i < n; i++) {
@@ -562,6 +611,7 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
         K = Kt > 0 ? Kt : (32 / (2 * T) > 0 ? 32 / (2 * T) * (2 * T) : 2 * T);
     // control state and the initial tile list for the configuration
     std::vector<int2> lst;
+    size_t l2off = 0;
     for (int i = 0; i < n; i++) {
         tiles_for(C, hb[i].W4, hb[i].ny, &hb[i].tx, &hb[i].ty);
         RelaxCtl &c = hb[i].ctl;
@@ -576,6 +626,14 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
         c.max_sweeps = p->max_sweeps;
         c.sweeps = gs_sweeps;
         c.status = TW_NOT_CONVERGED;
+        if (est) {   // the error estimate of the single-field solve; omega still adapts on the max norm
+            c.etol = p->etol;
+            c.Tl = K;
+            c.err_raw = DBL_MAX;
+            c.maxnorm_adapt = 1;
+            hb[i].l2p = L.l2p + l2off;
+            l2off += (size_t)hb[i].tx * hb[i].ty;
+        }
         hb[i].active = hb[i].error ? 0 : 1;
         hb[i].rmax = 0;
         if (hb[i].active)
@@ -644,7 +702,10 @@ extern "C" int hp_relax_batched(int n, const hp_instance *inst, const hp_params 
         st.omega = b.ctl.omega;
         st.tblock = T;
         st.loop = HP_LOOP_GRAPH;
-        st.status = b.error ? b.error : ((p->tol > 0.0 && rinf <= p->tol) ? TW_OK : TW_NOT_CONVERGED);
+        // with an error tolerance also the estimate (the control's own verdict, TW_OK only once both met)
+        const bool err_ok = !est || b.ctl.status == TW_OK;
+        st.status = b.error ? b.error : ((p->tol > 0.0 && rinf <= p->tol && err_ok) ? TW_OK : TW_NOT_CONVERGED);
+        st.err_est = est ? b.ctl.err_est : 0.0;
         if (latency_ms) latency_ms[i] = b.t_done > hh.t_start ? (double)(b.t_done - hh.t_start) * 1e-6 : 0.0;
         if (st.status < 0) worst = st.status;
         else if (st.status > 0 && worst == TW_OK) worst = st.status;

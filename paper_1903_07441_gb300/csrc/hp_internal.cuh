@@ -39,7 +39,9 @@ struct RelaxCtl {
     int in_alt;            // 1: the solution is the polished copy in the other ping-pong planes
     int polishes, psweeps; // polish launches tried, and their sweeps
     int go, T;             // continue flag of the last check; sweeps per launch
-    int polish_ok, pad2;   // polish enabled (HP_RBSOR with HP_POLISH and T > 1)
+    int polish_ok;         // polish enabled (HP_RBSOR with HP_POLISH and T > 1)
+    int maxnorm_adapt;     // 1: adapt omega on the residual max even when the 2-norm is given (the
+                           // 2-norm then only serves the error estimate's decay rate)
     float one_f;           // 1.0f, the omega the polish launches read
     int Tl;                // sweeps since the snapshot the change d is measured against
     int snap;              // snapshot state of the next check: 0 none, 1 take it, 2 compare with it and retake
@@ -295,7 +297,7 @@ __host__ __device__ inline int relax_control(RelaxCtl &c, double r, double e, in
         c.same_iv = 0;
     } else if (c.adapt) {
         if (c.r_prev > 0.0 && c.same_iv >= 1 && n == c.K) {
-            const bool l2 = e > 0.0 && c.e_prev > 0.0;
+            const bool l2 = !c.maxnorm_adapt && e > 0.0 && c.e_prev > 0.0;
             double lambda = pow(l2 ? e / c.e_prev : r / c.r_prev, 1.0 / n);
             double w = sor_adapt(c.omega, lambda, c.omega_max);
             if (w > c.omega + 1e-4) { c.omega = w; c.same_iv = -1; }
