@@ -150,8 +150,8 @@ int rb_sweeps(RBLayout &L, int nx, int ny, int n, int T, float omega, cudaStream
 }
 
 struct SweepGraph {
-    int dev, ny, n, T;
-    const void *key[5];
+    int dev, ny, n, T, W4, S, MW;
+    const void *key[7];
     cudaGraphExec_t exec;
     int launches;
     bool swap;
@@ -163,11 +163,13 @@ int rb_sweeps_graph(RBLayout &L, int nx, int ny, int n, int T, const float *omeg
                     int *launches) {
     int dev = 0;
     TW_CUDA(cudaGetDevice(&dev));
-    const void *key[5] = {L.R, L.B, L.R2, L.B2, omega_dev};
+    const void *key[7] = {L.R, L.B, L.R2, L.B2, L.MR, L.MB, omega_dev};   // with the row geometry below
     std::lock_guard<std::mutex> lock(g_sweep_graph_mutex);
     SweepGraph *ent = nullptr;
     for (auto &g : g_sweep_graphs)
-        if (g.dev == dev && g.ny == ny && g.n == n && g.T == T && !memcmp(g.key, key, sizeof(key))) ent = &g;
+        if (g.dev == dev && g.ny == ny && g.n == n && g.T == T && g.W4 == L.W4 && g.S == L.S && g.MW == L.MW &&
+            !memcmp(g.key, key, sizeof(key)))
+            ent = &g;
     if (!ent) {
         if (g_sweep_graphs.size() >= 8) {
             cudaGraphExecDestroy(g_sweep_graphs.front().exec);
@@ -192,6 +194,7 @@ int rb_sweeps_graph(RBLayout &L, int nx, int ny, int n, int T, const float *omeg
         }
         SweepGraph ne;
         ne.dev = dev; ne.ny = ny; ne.n = n; ne.T = T;
+        ne.W4 = L.W4; ne.S = L.S; ne.MW = L.MW;
         memcpy(ne.key, key, sizeof(key));
         e = cudaGraphInstantiate(&ne.exec, g, 0);
         cudaGraphDestroy(g);
