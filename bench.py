@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # DRAM traffic of the dominant kernel from one ncu capture, valid only while
 # the kernel source is unchanged (sha256 of the file that holds it).
-TRAFFIC = {"64bfdbdb9e655bd5": 17464576 + 2304}   # rb_tb_kernel<7,14,12,1>, profiles/rb_tb_kernel_static2048.md
+TRAFFIC = {"ba6d59fceb4f12d5": 17464576 + 2304}   # rb_tb_kernel<7,14,12,1>, profiles/rb_tb_kernel_static2048.md
 
 
 def _env_int(k, d):
@@ -203,6 +203,20 @@ def scene_seed(rank: int) -> int:
 
 
 GOLDEN_FIELD = os.path.join(ROOT, "tests", "golden", "static2048_field.json")
+
+
+def sweep_kernel_hash() -> str:
+    """Hash of the source text that defines the measured sweep kernel: the tile code (hp_tile.cuh)
+    and, in hp_sweeps.cu, the kernel and its tile configuration (not the host code around them),
+    so that a stored ncu traffic figure is used only for the kernel it was taken on."""
+    csrc = os.path.join(ROOT, "paper_1903_07441_gb300", "csrc")
+    sweeps = open(os.path.join(csrc, "hp_sweeps.cu")).read()
+    i = sweeps.index("template <int T, int RB, int WARPS, int MINB>")
+    j = sweeps.index("};", sweeps.index("struct TBCfg", i)) + 2
+    h_ = hashlib.sha256()
+    h_.update(open(os.path.join(csrc, "hp_tile.cuh"), "rb").read())
+    h_.update(sweeps[i:j].encode())
+    return h_.hexdigest()[:16]
 
 
 def field_accuracy(u, occ, sc, st):
@@ -393,10 +407,7 @@ def run_twgrid(args, rank, world, dist):
     sweeps_per_launch = roof_sweeps / max(sweep_launches, 1)
     bytes_per_launch = cells * (2 * STORAGE_BYTES + MASK_BYTES) * min(1.0, sweeps_per_launch)
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    h_ = hashlib.sha256()
-    for name in ("hp_sweeps.cu", "hp_tile.cuh"):   # the files that define the sweep kernel
-        h_.update(open(os.path.join(ROOT, "paper_1903_07441_gb300", "csrc", name), "rb").read())
-    src_hash = h_.hexdigest()[:16]
+    src_hash = sweep_kernel_hash()
     traffic = TRAFFIC.get(src_hash)
     roofline = {"bound": "hbm", "kernel": "red-black SOR sweep (hp_sweeps.cu)", "achieved": achieved,
                 "peak": hbm, "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": achieved / hbm,
