@@ -148,3 +148,23 @@ def test_mixed_inner_graph_matches_host_loop(dev, storage):
     assert sa["resid_inf"] <= tol and sb["resid_inf"] <= tol
     assert np.abs(a - b).max() <= 2.0 * tau_max * tol + 1e-7
     assert abs(sa["sweeps"] - sb["sweeps"]) <= 0.1 * sb["sweeps"] + 64
+
+
+@pytest.mark.parametrize("storage", STORES)
+def test_mixed_error_tolerance_on_several_scenes(dev, storage):
+    """The mixed form's outer error estimate (the last FP64 update's size over 1 - q) holds the
+    field within etol = 1e-5 of the FP64 oracle over the whole field on scenes of different sizes
+    and occupancies, for every storage (BF16 may instead report TW_NOT_CONVERGED, never a field
+    outside the tolerance with TW_OK)."""
+    cases = [scenes.dynamic512(), scenes.static_occupancy(31, 640, 300, 0.30),
+             scenes.static_occupancy(32, 768, 150, 0.15)]
+    for sc in cases:
+        occ, _, _ = oracle.build_grid(sc)
+        goal = _nearest_free(occ, sc.goal)
+        ustar, _ = oracle.solve_field(occ, goal, tol=1e-13)
+        u, st = _solve(dev, occ, goal, storage=storage, tol=1e-6, etol=1e-5)
+        err = np.abs(u - ustar).max()
+        if st["status"] == tw.TW_OK:
+            assert st["err_est"] <= 1e-5 and err <= 1e-5, (sc.nx, sc.ny, err, st)
+        else:
+            assert storage == tw.HP_STORE_BF16 and st["status"] == tw.TW_NOT_CONVERGED, st
