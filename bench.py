@@ -938,7 +938,8 @@ def profile_case(case):
     (profiles/ names the command): conv128 = a 128 -> 128 tensor-memory convolution on 512 x 512,
     conv32 = 32 -> 32 on 1024 x 1024 (3 warm-up calls, then 10 timed); mixed_fp16 = one HP_MIXED FP16
     solve of a seeded 2048 x 2048 field (20 % blocked) through the host-driven loop, whose correction
-    sweeps are separate launches (ncu does not profile kernel nodes of graphs with conditional nodes)."""
+    sweeps are separate launches (ncu does not profile kernel nodes of graphs with conditional nodes);
+    train256 = warm-start network training steps on one 256 x 256 field (3 warm-up, 20 timed)."""
     import torch
     import paper_1903_07441_gb300 as tw
     dev = torch.device("cuda:0")
@@ -962,6 +963,24 @@ def profile_case(case):
             raise RuntimeError("a tensor-memory convolution gave up a bounded wait")
         return {"case": case, "ms_per_call": ms, "tflops": 2 * 9 * cin * cout * H * W / ms / 1e9,
                 "note": "per call: the weight re-arrangement kernel and the convolution"}
+    if case == "train256":   # warm-start network training steps on one 256 x 256 field
+        sc = scenes.dynamic(seed=20000, side=256, n_obs=12, frames=1, static_shapes=10)
+        grid = tw.make_grid(256, 256, sc.cell)
+        occ, _ = tw.tw_build_grid(grid, sc.robot, sc.tracks, sc.law, static_occ=torch.from_numpy(sc.static_occ).to(dev))
+        goal = sc.goal if occ[sc.goal[1], sc.goal[0]].item() == 0 else tw.tw_nearest_free(grid, occ, *sc.goal)
+        u, _ = tw.hp_relax(grid, occ, goal, params=tw.Params(omega=1.0, tol=0.0, max_sweeps=2000))
+        net = tw.WarmStartNet(dev, seed=11)
+        t = net.target(u)
+        for _ in range(3):
+            net.train_step(occ, goal, t)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(20):
+            net.train_step(occ, goal, t)
+        e.record()
+        torch.cuda.synchronize()
+        return {"case": case, "ms_per_step": a.elapsed_time(e) / 20}
     rng = np.random.default_rng(3)
     n = 2048
     occ = (rng.random((n, n)) < 0.2).astype(np.uint8)
@@ -1003,7 +1022,7 @@ def main():
                     help="also run the success / collision-free evaluation over 1-16 moving obstacles")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-reps", type=int, default=3)
-    ap.add_argument("--profile-case", choices=["conv128", "conv32", "mixed_fp16"], default=None,
+    ap.add_argument("--profile-case", choices=["conv128", "conv32", "mixed_fp16", "train256"], default=None,
                     help="run one small kernel case (for an ncu capture) and print its timing, instead of the bench")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
