@@ -939,7 +939,9 @@ def profile_case(case):
     conv32 = 32 -> 32 on 1024 x 1024 (3 warm-up calls, then 10 timed); mixed_fp16 = one HP_MIXED FP16
     solve of a seeded 2048 x 2048 field (20 % blocked) through the host-driven loop, whose correction
     sweeps are separate launches (ncu does not profile kernel nodes of graphs with conditional nodes);
-    train256 = warm-start network training steps on one 256 x 256 field (3 warm-up, 20 timed)."""
+    train256 = warm-start network training steps on one 256 x 256 field (3 warm-up, 20 timed);
+    wgrad128 / wgrad32 = the tensor-memory weight gradient of the conv128 / conv32 layer (3 warm-up
+    calls, then 10 timed; each call adds the chunks' partial sums in a second, small kernel)."""
     import torch
     import paper_1903_07441_gb300 as tw
     dev = torch.device("cuda:0")
@@ -963,6 +965,25 @@ def profile_case(case):
             raise RuntimeError("a tensor-memory convolution gave up a bounded wait")
         return {"case": case, "ms_per_call": ms, "tflops": 2 * 9 * cin * cout * H * W / ms / 1e9,
                 "note": "per call: the weight re-arrangement kernel and the convolution"}
+    if case.startswith("wgrad"):
+        cin, cout, H, W = (128, 128, 512, 512) if case == "wgrad128" else (32, 32, 1024, 1024)
+        g = torch.Generator(device=dev).manual_seed(0)
+        x = (torch.randn(cin, H, W, device=dev, generator=g) * 0.5).to(torch.bfloat16)
+        dy = (torch.randn(cout, H, W, device=dev, generator=g) * 0.5).to(torch.bfloat16)
+        for _ in range(3):
+            tw.ws_conv3x3_wgrad(x, dy, impl=tw.WS_CONV_TC)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            tw.ws_conv3x3_wgrad(x, dy, impl=tw.WS_CONV_TC)
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / 10
+        if tw.ws_conv_check():
+            raise RuntimeError("a tensor-memory weight gradient gave up a bounded wait")
+        return {"case": case, "ms_per_call": ms, "tflops": 2 * 9 * cin * cout * H * W / ms / 1e9,
+                "note": "per call: two zeroed outputs, the weight-gradient kernel and the chunk sum"}
     if case == "train256":   # warm-start network training steps on one 256 x 256 field
         sc = scenes.dynamic(seed=20000, side=256, n_obs=12, frames=1, static_shapes=10)
         grid = tw.make_grid(256, 256, sc.cell)
@@ -1022,7 +1043,7 @@ def main():
                     help="also run the success / collision-free evaluation over 1-16 moving obstacles")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-reps", type=int, default=3)
-    ap.add_argument("--profile-case", choices=["conv128", "conv32", "mixed_fp16", "train256"], default=None,
+    ap.add_argument("--profile-case", choices=["conv128", "conv32", "mixed_fp16", "train256", "wgrad128", "wgrad32"], default=None,
                     help="run one small kernel case (for an ncu capture) and print its timing, instead of the bench")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -444,6 +444,24 @@ int ws_unet_train_step(float *params, float *grads, float *adam_m, float *adam_v
 size_t ws_conv3x3_workspace_size(int cin, int cout, int H, int W, int impl);
 int ws_conv3x3(const void *X, const float *Wt, const float *b, const void *S, void *Y, int cin, int cout, int H, int W,
                int relu, int impl, void *workspace, size_t workspace_bytes, void *stream);
+/* ws_conv3x3_wgrad: the parameter gradients of one such layer (the backward pass
+ * of Sec. 3.4's network): dW[co][ci][ky][kx] += sum_p dY[co][p] X[ci][p + (ky-1,
+ * kx-1)] (zero padding) and db[co] += sum_p dY[co][p], accumulated into what dW
+ * and db hold.  X: device BF16 [cin][H][W] (the layer's input); dY: device BF16
+ * [cout][H][W] (the gradient of its pre-activation output); dW: device FP32
+ * [cout][cin][3][3]; db: device FP32 [cout] or NULL.  impl: WS_CONV_TC (5th-
+ * generation tensor cores: per tap a GEMM over the pixels issued with
+ * tcgen05.mma, accumulators in tensor memory; cin and cout in {32, 64, 128},
+ * W % 16 == 0, X and dY 16-byte aligned), WS_CONV_SIMT (CUDA cores) or
+ * WS_CONV_AUTO (WS_CONV_TC where it applies, else CUDA cores); WS_CONV_MMA is
+ * TW_EINVAL.  Both forms add BF16 x BF16 products exactly in FP32 and the
+ * partial sums of their pixel chunks in a fixed order, so repeated calls give
+ * identical results; they differ from each other only in the order of the sums.
+ * workspace: ws_conv3x3_wgrad_workspace_size() bytes (256-byte aligned), else
+ * TW_EWORKSPACE.  Enqueued on `stream`; bounded waits as for ws_conv3x3. */
+size_t ws_conv3x3_wgrad_workspace_size(int cin, int cout, int H, int W, int impl);
+int ws_conv3x3_wgrad(const void *X, const void *dY, float *dW, float *db, int cin, int cout, int H, int W, int impl,
+                     void *workspace, size_t workspace_bytes, void *stream);
 /* ws_conv_check: *timed_out = 1 if a WS_CONV_TC convolution on the current
  * device gave up a bounded wait since the last call (its output is then
  * invalid), else 0; clears the flag.  Synchronises the device. */

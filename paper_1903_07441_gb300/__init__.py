@@ -39,7 +39,8 @@ EXPORTS = (
     "plan_path_workspace_size", "plan_path", "plan_path_ex",
     "kf_update", "kf_init", "ws_unet_param_count", "ws_unet_workspace_size", "ws_unet_init", "ws_make_target",
     "ws_unet_forward", "ws_unet_train_step", "ws_unet_warm_start_workspace_size", "ws_unet_warm_start",
-    "ws_conv3x3_workspace_size", "ws_conv3x3", "ws_conv_check",
+    "ws_conv3x3_workspace_size", "ws_conv3x3", "ws_conv3x3_wgrad_workspace_size", "ws_conv3x3_wgrad",
+    "ws_conv_check",
     "tw_status_string", "tw_last_cuda_error", "tw_launch_count", "tw_version",
 )
 
@@ -197,6 +198,10 @@ def load() -> ctypes.CDLL:
     lib.ws_conv3x3.restype = I
     lib.ws_conv3x3_workspace_size.argtypes = [I, I, I, I, I]
     lib.ws_conv3x3_workspace_size.restype = Z
+    lib.ws_conv3x3_wgrad.argtypes = [P, P, P, P, I, I, I, I, I, P, Z, P]
+    lib.ws_conv3x3_wgrad.restype = I
+    lib.ws_conv3x3_wgrad_workspace_size.argtypes = [I, I, I, I, I]
+    lib.ws_conv3x3_wgrad_workspace_size.restype = Z
     lib.ws_conv_check.argtypes = [P]
     lib.ws_conv_check.restype = I
     lib.tw_status_string.argtypes = [I]
@@ -491,6 +496,23 @@ def ws_conv3x3(x, w, b=None, skip=None, relu=False, impl=WS_CONV_AUTO):
                                         1 if relu else 0, int(impl), _ptr(ws) if ws is not None else None,
                                         ws.numel() if ws is not None else 0, _stream(x.device)))
     return y
+
+
+def ws_conv3x3_wgrad(x, dy, impl=WS_CONV_AUTO):
+    """Parameter gradients of one convolution layer from its input x bf16 [cin, H, W] and output
+    gradient dy bf16 [cout, H, W] (device).  Returns (dW fp32 [cout, cin, 3, 3], db fp32 [cout])."""
+    torch = _torch()
+    cin, H, W = x.shape
+    cout = dy.shape[0]
+    dw = torch.zeros((cout, cin, 3, 3), dtype=torch.float32, device=x.device)
+    db = torch.zeros((cout,), dtype=torch.float32, device=x.device)
+    lib = load()
+    nws = lib.ws_conv3x3_wgrad_workspace_size(cin, cout, H, W, int(impl))
+    ws = workspace(nws, x.device, "wgrad") if nws else None
+    _check("ws_conv3x3_wgrad", lib.ws_conv3x3_wgrad(_ptr(x), _ptr(dy), _ptr(dw), _ptr(db), cin, cout, H, W, int(impl),
+                                                    _ptr(ws) if ws is not None else None,
+                                                    ws.numel() if ws is not None else 0, _stream(x.device)))
+    return dw, db
 
 
 def ws_conv_check() -> bool:

@@ -402,5 +402,295 @@ int conv3x3_tc_error(int *flag) {
     return TW_OK;
 }
 
+
+// ---- weight gradient on the tensor cores ---------------------------------------
+//
+// dW[co][ci][ky][kx] = sum_p dY[co][p] X[ci][p + (ky - 1, kx - 1)] (zero outside
+// the image) and db[co] = sum_p dY[co][p]: for each tap a GEMM whose K runs over
+// the pixels.  CTA (ky, z) owns the three taps (ky, 0..2) and the pixel chunk z
+// (consecutive pixels in row-major order), 64 pixels per stage.  The operands are
+// staged K-major without swizzle: 8 consecutive pixels of one channel (16 bytes,
+// one aligned vector load from the network's [c][H][W] layout) form one row of a
+// core matrix, channel group g and pixel group j sit at g * 1024 + j * 128
+// bytes.  X is staged three times, shifted by kx - 1 pixels (two-byte funnel of
+// the loaded vector with its neighbours), so that every tap's operand starts on
+// a 16-byte boundary.  M = 128 is the side with 128 channels (dY where cout is
+// 128, else X where cin is 128, else dY with its rows beyond cout unused), N the
+// other side's channel count; the three taps' accumulators lie side by side in
+// tensor memory.  Each CTA writes its chunk's sums to part[z][k][m][n] (m the M
+// row, n the N column), the bias sums (CTAs with ky = 0) to part_b[z][co];
+// conv_wgrad_tc_sum_kernel adds the chunks in order, so the result does not
+// depend on the order the CTAs finish in.
+constexpr int kWgPx = 64;          // pixels per stage
+constexpr int kWgThreads = 256;
+
+template <bool XA, int N>
+struct WgShape {
+    static constexpr uint32_t ROWB = kWgPx * 2;                 // one channel's pixels of a stage
+    static constexpr uint32_t D_BYTES = (XA ? N : 128) * ROWB;  // dY operand (128 rows on the M side)
+    static constexpr uint32_t X_PLANE = (XA ? 128 : N) * ROWB;  // one shifted copy of X
+    static constexpr uint32_t STAGE = D_BYTES + 3 * X_PLANE;
+    static constexpr uint32_t SMEM = 2 * STAGE;
+    static constexpr uint32_t NCOL = 3 * N <= 128 ? 128 : (3 * N <= 256 ? 256 : 512);
+    static_assert(3 * N <= 512, "accumulators exceed the tensor memory");
+    static_assert(STAGE % 1024 == 0, "stage alignment");
+};
+
+template <bool XA, int N>
+__global__ void __launch_bounds__(kWgThreads, 1)
+    conv3x3_wgrad_tc_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ dY, float *__restrict__ part,
+                            float *__restrict__ part_b, int cin, int cout, int H, int W, int chunk_px) {
+    using Sh = WgShape<XA, N>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t mma_done[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    __shared__ float bias_sh[4][4][8];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ky = blockIdx.x, z = blockIdx.y;
+    const size_t plane = (size_t)H * W;
+    const long pa = (long)z * chunk_px;
+    const long pb = pa + chunk_px < (long)plane ? pa + chunk_px : (long)plane;
+    const int nst = (int)((pb - pa + kWgPx - 1) / kWgPx);
+    const int ma = XA ? cin : cout;   // rows of the M side that hold data
+
+    if (warp == 0) tc::tmem_alloc(&tmem_base_sh, Sh::NCOL);
+    if (tid == 0) {
+        tc::mbar_init(&mma_done[0], 1);
+        tc::mbar_init(&mma_done[1], 1);
+        tc::fence_mbar_init();
+        abort_sh = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t sbase = tc::smem_u32(smem);
+
+    // thread t stages pixel group j = (t / 8) % 8 of every stage, for channels (t / 64 + 4 q) * 8 + t % 8
+    const int jg = (tid >> 3) & 7;
+    const int cb = (tid >> 6) * 8 + (tid & 7);
+    const int nqd = cout / 32, nqx = cin / 32;
+    uint4 rd[4], rx[4];
+    uint32_t ra[4], rb[4];
+    float bsum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const bool with_bias = ky == 0;
+    auto load_stage = [&](int i) {
+        const long p = pa + (long)i * kWgPx + 8 * jg;   // this thread's 8 pixels (one row: W % 16 == 0)
+        const bool in = p < pb;
+        const int y = in ? (int)(p / W) : 0, x = in ? (int)(p - (long)y * W) : 0;
+        const int yy = y + ky - 1;
+        const bool xin = in && yy >= 0 && yy < H;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int c = cb + 32 * q;
+            rd[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (q < nqd && in) rd[q] = __ldg(reinterpret_cast<const uint4 *>(dY + (size_t)c * plane + p));
+            rx[q] = make_uint4(0u, 0u, 0u, 0u);
+            ra[q] = rb[q] = 0u;
+            if (q < nqx && xin) {
+                const unsigned short *xs =
+                    reinterpret_cast<const unsigned short *>(X) + (size_t)c * plane + (size_t)yy * W + x;
+                rx[q] = __ldg(reinterpret_cast<const uint4 *>(xs));
+                if (x > 0) ra[q] = __ldg(xs - 1);
+                if (x + 8 < W) rb[q] = __ldg(xs + 8);
+            }
+        }
+    };
+    load_stage(0);
+    int issued = 0;
+    for (int i = 0; i < nst; i++) {
+        const int st = i & 1;
+        if (i >= 2 && !tc::mbar_wait(&mma_done[st], (uint32_t)(((i >> 1) - 1) & 1))) abort_sh = 1;
+        uint8_t *sD = smem + st * Sh::STAGE;
+        uint8_t *sX = sD + Sh::D_BYTES;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            // unit (channel c, group jg) sits at ((c / 8) * 8 + jg) * 128 + (c % 8) * 16 = (tid + 256 q) * 16
+            const uint32_t off = (uint32_t)(tid + 256 * q) * 16u;
+            if (q < nqd) {
+                *reinterpret_cast<uint4 *>(sD + off) = rd[q];
+                if (with_bias) {
+                    const uint32_t w[4] = {rd[q].x, rd[q].y, rd[q].z, rd[q].w};
+                    float t = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < 4; e++)
+                        t += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xFFFF0000u);
+                    bsum[q] += t;
+                }
+            }
+            if (q < nqx) {
+                const uint4 v = rx[q];
+                // kx = 0: pixels x - 1 .. x + 6; kx = 1: x .. x + 7; kx = 2: x + 1 .. x + 8
+                *reinterpret_cast<uint4 *>(sX + off) =
+                    make_uint4(__byte_perm(ra[q], v.x, 0x5410), __byte_perm(v.x, v.y, 0x5432),
+                               __byte_perm(v.y, v.z, 0x5432), __byte_perm(v.z, v.w, 0x5432));
+                *reinterpret_cast<uint4 *>(sX + Sh::X_PLANE + off) = v;
+                *reinterpret_cast<uint4 *>(sX + 2 * Sh::X_PLANE + off) =
+                    make_uint4(__byte_perm(v.x, v.y, 0x5432), __byte_perm(v.y, v.z, 0x5432),
+                               __byte_perm(v.z, v.w, 0x5432), __byte_perm(v.w, rb[q], 0x5432));
+            }
+        }
+        if (i + 1 < nst) load_stage(i + 1);
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (abort_sh) break;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const long left = pb - (pa + (long)i * kWgPx);
+            const int ks = (int)((left < kWgPx ? left : kWgPx) / 16);   // K steps of 16 pixels
+            const uint32_t d0 = sbase + st * Sh::STAGE, x0 = d0 + Sh::D_BYTES;
+            for (int s = 0; s < ks; s++) {
+#pragma unroll
+                for (int kx = 0; kx < 3; kx++) {
+                    const uint64_t dd = tc::smem_desc(d0 + 256 * s, 128, 1024);
+                    const uint64_t xd = tc::smem_desc(x0 + kx * Sh::X_PLANE + 256 * s, 128, 1024);
+                    tc::mma_bf16(tmem + (uint32_t)(kx * N), XA ? xd : dd, XA ? dd : xd, tc::IDesc<128, N>::value,
+                                 (i > 0 || s > 0) ? 1u : 0u);
+                }
+            }
+            tc::mma_commit(&mma_done[st]);
+        }
+        issued = i + 1;
+    }
+    __syncthreads();
+    bool done = true;
+    if (issued > 0 && !abort_sh) {
+        const int last = issued - 1;
+        done = tc::mbar_wait(&mma_done[last & 1], (uint32_t)((last >> 1) & 1));
+    }
+    if (!done) abort_sh = 1;
+    __syncthreads();   // one outcome for the whole CTA (the epilogue below synchronises)
+    if (abort_sh) {
+        if (tid == 0) atomicExch(&g_conv_tc_error, 1);
+        if (issued > 0) tc::mbar_wait(&mma_done[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1));
+    } else {
+        tc::fence_after_sync();
+        const int wl = warp & 3, wh = warp >> 2;
+        const int m = 32 * wl + lane;
+        const size_t tap = (size_t)ma * N;
+#pragma unroll 1
+        for (int c0 = 16 * wh; c0 < 3 * N; c0 += 32) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * wl) << 16) + (uint32_t)c0, v);
+            if (m < ma) {
+                const int k = 3 * ky + c0 / N, n0 = c0 % N;
+                float4 *o = reinterpret_cast<float4 *>(part + ((size_t)z * 9 + k) * tap + (size_t)m * N + n0);
+#pragma unroll
+                for (int e = 0; e < 4; e++) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+            }
+        }
+        if (with_bias) {
+            // threads with the same channels differ in the pixel group: lane bits 3-4 and the warp's parity
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                float t = bsum[q];
+                t += __shfl_xor_sync(0xffffffffu, t, 8);
+                t += __shfl_xor_sync(0xffffffffu, t, 16);
+                if ((warp & 1) && lane < 8) bias_sh[warp >> 1][q][lane] = t;
+                bsum[q] = t;
+            }
+            __syncthreads();
+            if (!(warp & 1) && lane < 8)
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int c = cb + 32 * q;
+                    if (q < nqd) part_b[(size_t)z * cout + c] = bsum[q] + bias_sh[warp >> 1][q][lane];
+                }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, Sh::NCOL);
+}
+
+// dW += sum over the chunks of part (layout [z][k][m][n]), db += sum of part_b, chunks in order.
+__global__ void conv_wgrad_tc_sum_kernel(const float *__restrict__ part, const float *__restrict__ part_b, int chunks,
+                                         float *__restrict__ dW, float *__restrict__ db, int cin, int cout, int xa) {
+    const int ma = xa ? cin : cout, nb = xa ? cout : cin;
+    const size_t n = (size_t)cout * cin * 9, tap = (size_t)ma * nb;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + cout; i += (size_t)gridDim.x * blockDim.x) {
+        if (i < n) {
+            float v = 0.0f;
+            for (int z = 0; z < chunks; z++) v += part[(size_t)z * n + i];
+            const int k = (int)(i / tap), m = (int)((i / nb) % ma), c = (int)(i % nb);
+            const int co = xa ? c : m, ci = xa ? m : c;
+            dW[((size_t)co * cin + ci) * 9 + k] += v;
+        } else if (db) {
+            const size_t co = i - n;
+            float v = 0.0f;
+            for (int z = 0; z < chunks; z++) v += part_b[(size_t)z * cout + co];
+            db[co] += v;
+        }
+    }
+}
+
+// Shape conditions of the tensor-memory weight gradient.
+bool conv3x3_wgrad_tc_ok(int cin, int cout, int H, int W) {
+    return (cin == 32 || cin == 64 || cin == 128) && (cout == 32 || cout == 64 || cout == 128) && W % 16 == 0 &&
+           W >= 16 && H >= 1 && (size_t)H * W <= ((size_t)1 << 31);
+}
+
+// Pixel chunks of the weight gradient: about 50 chunks (three CTAs each, one per
+// kernel row: 150 CTAs on a 152-SM GPU), at least one stage each, and at most
+// cap_floats of FP32 partial sums.  Returns the number of chunks, *chunk_px their size.
+int conv3x3_wgrad_tc_plan(int cin, int cout, int H, int W, size_t cap_floats, int *chunk_px) {
+    const long px = (long)H * W;
+    const size_t per = (size_t)9 * cin * cout + cout;
+    long zc = (px + kWgPx - 1) / kWgPx;
+    if (zc > 50) zc = 50;
+    if ((size_t)zc > cap_floats / per) zc = (long)(cap_floats / per);
+    if (zc < 1) return 0;
+    long ch = (px + zc - 1) / zc;
+    ch = (ch + kWgPx - 1) / kWgPx * kWgPx;
+    *chunk_px = (int)ch;
+    return (int)((px + ch - 1) / ch);
+}
+
+template <bool XA, int N>
+static int launch_wgrad_tc(const bf16 *X, const bf16 *dY, float *part, float *part_b, int cin, int cout, int H, int W,
+                           int nz, int chunk_px, cudaStream_t s) {
+    using Sh = WgShape<XA, N>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    TW_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        TW_CUDA(cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel<XA, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Sh::SMEM));
+        attr_set[dev] = true;
+    }
+    TW_LAUNCH((conv3x3_wgrad_tc_kernel<XA, N>), dim3(3, nz), kWgThreads, Sh::SMEM, s, X, dY, part, part_b, cin, cout,
+              H, W, chunk_px);
+    return TW_OK;
+}
+
+// dW += dL/dW, db += dL/db (db nullable) of a 3x3 convolution from its input X
+// (BF16 [cin][H][W]) and output gradient dY (BF16 [cout][H][W]) on the tensor
+// cores; part: part_floats floats of scratch (16-byte aligned) for the chunks'
+// partial sums.
+int conv3x3_wgrad_tc(const bf16 *X, const bf16 *dY, float *dW, float *db, int cin, int cout, int H, int W,
+                     float *part, size_t part_floats, cudaStream_t s) {
+    if (!conv3x3_wgrad_tc_ok(cin, cout, H, W) || (((uintptr_t)X | (uintptr_t)dY) & 15)) return TW_EINVAL;
+    int chunk = 0;
+    const int nz = conv3x3_wgrad_tc_plan(cin, cout, H, W, part_floats, &chunk);
+    if (!part || ((uintptr_t)part & 15) || nz < 1) return TW_EWORKSPACE;
+    float *part_b = part + (size_t)nz * 9 * cin * cout;
+    int e;
+    const bool xa = cout != 128 && cin == 128;
+    if (xa) {
+        e = cout == 32 ? launch_wgrad_tc<true, 32>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
+                       : launch_wgrad_tc<true, 64>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s);
+    } else {
+        e = cin == 32   ? launch_wgrad_tc<false, 32>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
+            : cin == 64 ? launch_wgrad_tc<false, 64>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
+                        : launch_wgrad_tc<false, 128>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s);
+    }
+    if (e) return e;
+    const size_t n = (size_t)cout * cin * 9 + cout;
+    TW_LAUNCH(conv_wgrad_tc_sum_kernel, (unsigned)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256), 256, 0, s, part,
+              part_b, nz, dW, db, cin, cout, xa ? 1 : 0);
+    return TW_OK;
+}
+
 }  // namespace nn
 }  // namespace tw

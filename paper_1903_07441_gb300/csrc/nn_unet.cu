@@ -561,6 +561,10 @@ size_t conv3x3_tc_scratch_bytes(int cin, int cout);
 int conv3x3_tc(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
                int W, int relu, void *scratch, cudaStream_t s);
 int conv3x3_tc_error(int *flag);
+bool conv3x3_wgrad_tc_ok(int cin, int cout, int H, int W);
+int conv3x3_wgrad_tc_plan(int cin, int cout, int H, int W, size_t cap_floats, int *chunk_px);
+int conv3x3_wgrad_tc(const bf16 *X, const bf16 *dY, float *dW, float *db, int cin, int cout, int H, int W,
+                     float *part, size_t part_floats, cudaStream_t s);
 
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256); }
 
@@ -626,6 +630,50 @@ static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S
     return TW_OK;
 }
 
+// Row chunks of the CUDA-core weight gradient: at least 16 rows each, as many as
+// cap_floats of partial sums allow; 0 if even one chunk does not fit.
+static int wgrad_simt_rows(int cin, int cout, int H, size_t cap_floats) {
+    const size_t per = (size_t)cout * cin * 9 + cout;
+    if (per > cap_floats) return 0;
+    int rows = H < 16 ? H : 16;
+    while ((size_t)ceil_div(H, rows) * per > cap_floats) rows *= 2;
+    return rows;
+}
+
+// dW += dL/dW, db += dL/db (db nullable) of one 3x3 convolution from its input X
+// and output gradient dY: on the tensor cores (tcgen05, accumulators in tensor
+// memory) where the channel counts and the width allow it and impl is
+// WS_CONV_AUTO or WS_CONV_TC, else on CUDA cores (WS_CONV_SIMT, or AUTO
+// elsewhere).  part: part_floats floats of scratch for the partial sums of the
+// pixel chunks.  Either form adds the chunks in a fixed order: the result is
+// the same on every run.
+static int conv3x3_wgrad(const bf16 *X, const bf16 *dY, float *dW, float *db, int cin, int cout, int H, int W,
+                         int impl, float *part, size_t part_floats, cudaStream_t s) {
+    if (impl == WS_CONV_MMA) return TW_EINVAL;
+    const bool tc_ok = conv3x3_wgrad_tc_ok(cin, cout, H, W);
+    if (impl == WS_CONV_TC && !tc_ok) return TW_EINVAL;
+    if (impl != WS_CONV_SIMT && tc_ok) return conv3x3_wgrad_tc(X, dY, dW, db, cin, cout, H, W, part, part_floats, s);
+    const int rows = wgrad_simt_rows(cin, cout, H, part_floats);
+    if (!part || rows < 1) return TW_EWORKSPACE;
+    const size_t per = (size_t)cout * cin * 9 + cout;
+    const int nz = ceil_div(H, rows);
+    float *part_b = part + (size_t)nz * cout * cin * 9;
+    dim3 gw(ceil_div(cout, COB), ceil_div(cin, CIB), nz);
+    TW_LAUNCH(conv3x3_bwd_weight_kernel, gw, 256, 0, s, X, dY, part, part_b, cin, cout, H, W, rows);
+    TW_LAUNCH(conv3x3_bwd_weight_sum_kernel, blocks_for(per), 256, 0, s, part, part_b, nz, dW, db, cin, cout);
+    return TW_OK;
+}
+
+// Floats of scratch conv3x3_wgrad needs for the form impl selects.
+static size_t conv3x3_wgrad_floats(int cin, int cout, int H, int W, int impl) {
+    const size_t per = (size_t)cout * cin * 9 + cout;
+    if (impl != WS_CONV_SIMT && conv3x3_wgrad_tc_ok(cin, cout, H, W)) {
+        int chunk = 0;
+        return (size_t)conv3x3_wgrad_tc_plan(cin, cout, H, W, (size_t)-1, &chunk) * per;
+    }
+    return (size_t)ceil_div(H, H < 16 ? H : 16) * per;
+}
+
 static void conv_fwd(const bf16 *X, const float *params, int li, const bf16 *S, bf16 *Y, int H, int W, int relu,
                      float *kpart, cudaStream_t s, bool bias = true) {
     const ConvSpec &c = kConvs[li];
@@ -668,15 +716,7 @@ static void conv_bwd(const bf16 *X, const float *P, float *G, int li, const bf16
     const float *Wt = P + param_offset(li);
     float *dW = G + param_offset(li);
     float *db = dW + (size_t)c.cout * c.cin * 9;
-    // row chunks of at least 16 rows, as many as the scratch holds partial sums for
-    const size_t per = (size_t)c.cout * c.cin * 9 + c.cout;
-    int rows = H < 16 ? H : 16;
-    while ((size_t)ceil_div(H, rows) * per > kSplitKCap) rows *= 2;
-    const int nz = ceil_div(H, rows);
-    float *part_b = kpart + (size_t)nz * c.cout * c.cin * 9;
-    dim3 gw(ceil_div(c.cout, COB), ceil_div(c.cin, CIB), nz);
-    TW_LAUNCH(conv3x3_bwd_weight_kernel, gw, 256, 0, s, X, dY, kpart, part_b, c.cin, c.cout, H, W, rows);
-    TW_LAUNCH(conv3x3_bwd_weight_sum_kernel, blocks_for(per), 256, 0, s, kpart, part_b, nz, dW, db, c.cin, c.cout);
+    conv3x3_wgrad(X, dY, dW, db, c.cin, c.cout, H, W, WS_CONV_AUTO, kpart, kSplitKCap, s);
     if (!dX) return;
     TW_LAUNCH(conv_transpose_weights_kernel, blocks_for((size_t)c.cin * c.cout * 9), 256, 0, s, Wt, wt, c.cin, c.cout);
     // dX = conv3x3(dY, W^T) with cin/cout swapped: a forward conv of the transposed layer
@@ -914,6 +954,32 @@ extern "C" int ws_conv3x3(const void *X, const float *Wt, const float *b, const 
     int e = conv3x3((const bf16 *)X, Wt, b, (const bf16 *)S, (bf16 *)Y, cin, cout, H, W, relu ? 1 : 0, impl,
                     (cudaStream_t)stream, impl == WS_CONV_TC ? (float *)workspace : nullptr,
                     impl == WS_CONV_TC ? workspace_bytes / sizeof(float) : 0);
+    if (e) return e;
+    TW_CHECK_LAUNCH();
+    return TW_OK;
+}
+
+extern "C" size_t ws_conv3x3_wgrad_workspace_size(int cin, int cout, int H, int W, int impl) {
+    using namespace tw::nn;
+    if (cin < 1 || cout < 1 || H < 1 || W < 1 || H > 65536 || W > 65536 ||
+        (impl != WS_CONV_AUTO && impl != WS_CONV_SIMT && impl != WS_CONV_TC) ||
+        (impl == WS_CONV_TC && !conv3x3_wgrad_tc_ok(cin, cout, H, W)))
+        return 0;
+    return (conv3x3_wgrad_floats(cin, cout, H, W, impl) * sizeof(float) + 255) & ~(size_t)255;
+}
+
+extern "C" int ws_conv3x3_wgrad(const void *X, const void *dY, float *dW, float *db, int cin, int cout, int H, int W,
+                                int impl, void *workspace, size_t workspace_bytes, void *stream) {
+    using namespace tw::nn;
+    if (!X || !dY || !dW || cin < 1 || cout < 1 || H < 1 || W < 1 || H > 65536 || W > 65536 ||
+        (impl != WS_CONV_AUTO && impl != WS_CONV_SIMT && impl != WS_CONV_TC) ||
+        (impl == WS_CONV_TC && !conv3x3_wgrad_tc_ok(cin, cout, H, W)))
+        return TW_EINVAL;
+    if (!workspace || !ws_aligned(workspace) ||
+        workspace_bytes < conv3x3_wgrad_floats(cin, cout, H, W, impl) * sizeof(float))
+        return TW_EWORKSPACE;
+    int e = conv3x3_wgrad((const bf16 *)X, (const bf16 *)dY, dW, db, cin, cout, H, W, impl, (float *)workspace,
+                          workspace_bytes / sizeof(float), (cudaStream_t)stream);
     if (e) return e;
     TW_CHECK_LAUNCH();
     return TW_OK;

@@ -93,6 +93,60 @@ def test_conv3x3_tensor_memory_matches_cuda_core_and_fp64(dev, cin, cout, H, W, 
     assert np.all(np.abs(tc_out - simt) <= 2.0 ** -7 * (both + 1e-2))
 
 
+@pytest.mark.parametrize("cin,cout,H,W", [(32, 32, 8, 256), (32, 64, 10, 128), (64, 64, 12, 48), (64, 128, 6, 64),
+                                          (128, 128, 9, 128), (128, 64, 5, 80), (64, 32, 16, 256), (128, 32, 7, 32),
+                                          (32, 128, 4, 16), (128, 128, 64, 64)])
+def test_conv3x3_weight_gradient_tensor_memory_matches_fp64(dev, cin, cout, H, W):
+    """The tcgen05 weight gradient (per tap a GEMM over the pixels, X staged three times shifted by one
+    pixel, accumulators in tensor memory, pixel chunks summed in a fixed order) and the CUDA-core one
+    against the FP64 gradient of the same BF16 inputs: every weight and bias within 2^-12 of the sum of
+    the absolute products it adds (FP32 accumulation; one pixel more or less moves a weight by about
+    1 / (H W) of that sum, so a dropped, repeated or misplaced pixel, tap or channel fails), ragged
+    chunks, image rows shorter than a stage, and every edge (zero padding) included.  Repeated calls
+    give identical bits, the automatic choice is the tensor-memory form, and no bounded wait gave up."""
+    g = torch.Generator(device="cpu").manual_seed(cin * 31 + cout * 7 + H * 5 + W)
+    x = torch.randn((cin, H, W), generator=g).to(torch.bfloat16).to(dev)
+    dy = torch.randn((cout, H, W), generator=g).to(torch.bfloat16).to(dev)
+    tc = tw.ws_conv3x3_wgrad(x, dy, impl=tw.WS_CONV_TC)
+    tc2 = tw.ws_conv3x3_wgrad(x, dy, impl=tw.WS_CONV_TC)
+    auto = tw.ws_conv3x3_wgrad(x, dy, impl=tw.WS_CONV_AUTO)
+    simt = tw.ws_conv3x3_wgrad(x, dy, impl=tw.WS_CONV_SIMT)
+    torch.cuda.synchronize()
+    assert not tw.ws_conv_check()
+    xr = x.float().cpu().numpy().astype(np.float64)
+    dyr = dy.float().cpu().numpy().astype(np.float64)
+    w0 = np.zeros((cout, cin, 3, 3))
+    _, ref_w, ref_b = nn.conv_bwd(xr, w0, dyr)
+    _, abs_w, abs_b = nn.conv_bwd(np.abs(xr), w0, np.abs(dyr))
+    for name, (dw, db) in (("tc", tc), ("simt", simt)):
+        dw = dw.cpu().numpy()
+        db = db.cpu().numpy()
+        assert np.all(np.abs(dw - ref_w) <= 2.0 ** -12 * abs_w + 1e-30), (name, np.abs(dw - ref_w).max())
+        assert np.all(np.abs(db - ref_b) <= 2.0 ** -12 * abs_b + 1e-30), (name, np.abs(db - ref_b).max())
+    for a, b in zip(tc, tc2):
+        assert torch.equal(a, b)
+    for a, b in zip(tc, auto):
+        assert torch.equal(a, b)
+
+
+def test_conv3x3_weight_gradient_adds_to_what_it_is_given(dev):
+    """dW and db are accumulated into, as the network's backward pass needs for a sum of layers."""
+    g = torch.Generator(device="cpu").manual_seed(77)
+    x = torch.randn((64, 8, 64), generator=g).to(torch.bfloat16).to(dev)
+    dy = torch.randn((32, 8, 64), generator=g).to(torch.bfloat16).to(dev)
+    dw, db = tw.ws_conv3x3_wgrad(x, dy, impl=tw.WS_CONV_TC)
+    lib = tw.load()
+    dw2 = torch.full_like(dw, 0.5)
+    db2 = torch.full_like(db, -0.25)
+    nws = lib.ws_conv3x3_wgrad_workspace_size(64, 32, 8, 64, tw.WS_CONV_TC)
+    ws = torch.empty(nws, dtype=torch.uint8, device=dev)
+    assert lib.ws_conv3x3_wgrad(x.data_ptr(), dy.data_ptr(), dw2.data_ptr(), db2.data_ptr(), 64, 32, 8, 64,
+                                tw.WS_CONV_TC, ws.data_ptr(), nws, None) == tw.TW_OK
+    torch.cuda.synchronize()
+    assert torch.allclose(dw2, dw + 0.5, rtol=0, atol=1e-6 * float(dw.abs().max()) + 1e-6)
+    assert torch.allclose(db2, db - 0.25, rtol=0, atol=1e-6 * float(db.abs().max()) + 1e-6)
+
+
 def test_conv3x3_rejects_tensor_core_shapes_it_cannot_take(dev):
     x = torch.zeros((8, 16, 16), dtype=torch.bfloat16, device=dev)
     w = torch.zeros((32, 8, 3, 3), dtype=torch.float32, device=dev)
