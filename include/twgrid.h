@@ -451,8 +451,9 @@ int ws_conv3x3(const void *X, const float *Wt, const float *b, const void *S, vo
  * [cout][H][W] (the gradient of its pre-activation output); dW: device FP32
  * [cout][cin][3][3]; db: device FP32 [cout] or NULL.  impl: WS_CONV_TC (5th-
  * generation tensor cores: per tap a GEMM over the pixels issued with
- * tcgen05.mma, accumulators in tensor memory; cin and cout in {32, 64, 128},
- * W % 16 == 0, X and dY 16-byte aligned), WS_CONV_SIMT (CUDA cores) or
+ * tcgen05.mma, accumulators in tensor memory; cin and cout at most 128 (other
+ * counts than 32, 64 and 128 padded), W % 16 == 0, X and dY 16-byte aligned),
+ * WS_CONV_SIMT (CUDA cores) or
  * WS_CONV_AUTO (WS_CONV_TC where it applies, else CUDA cores); WS_CONV_MMA is
  * TW_EINVAL.  Both forms add BF16 x BF16 products exactly in FP32 and the
  * partial sums of their pixel chunks in a fixed order, so repeated calls give

@@ -410,31 +410,58 @@ int conv3x3_tc_error(int *flag) {
 // the pixels.  CTA (ky, z) owns the three taps (ky, 0..2) and the pixel chunk z
 // (consecutive pixels in row-major order), 64 pixels per stage.  The operands are
 // staged K-major without swizzle: 8 consecutive pixels of one channel (16 bytes,
-// one aligned vector load from the network's [c][H][W] layout) form one row of a
-// core matrix, channel group g and pixel group j sit at g * 1024 + j * 128
-// bytes.  X is staged three times, shifted by kx - 1 pixels (two-byte funnel of
-// the loaded vector with its neighbours), so that every tap's operand starts on
-// a 16-byte boundary.  M = 128 is the side with 128 channels (dY where cout is
-// 128, else X where cin is 128, else dY with its rows beyond cout unused), N the
-// other side's channel count; the three taps' accumulators lie side by side in
-// tensor memory.  Each CTA writes its chunk's sums to part[z][k][m][n] (m the M
-// row, n the N column), the bias sums (CTAs with ky = 0) to part_b[z][co];
-// conv_wgrad_tc_sum_kernel adds the chunks in order, so the result does not
-// depend on the order the CTAs finish in.
+// one aligned copy from the network's [c][H][W] layout) form one row of a core
+// matrix; channel group g and pixel group j sit at g * SBO + j * 128 bytes.
+// Every thread copies its share of a stage with cp.async (16 bytes, zero-filled
+// outside the tensor) into a ring of four stages, two stages ahead of the one
+// the tensor cores consume: dY, and X at the row of tap ky with one extra pixel
+// group on each side (groups -1 .. 8).  Once a stage has landed, the threads
+// build the two copies of X shifted by one pixel (taps kx = 0 and 2) from the
+// landed groups and their neighbours (zero across the image's left and right
+// edges), so that every tap's operand starts on a 16-byte boundary; the
+// unshifted tap reads the landed X directly.  M = 128 is the side with 128
+// channels (dY where cout is 128, else X where cin is 128, else dY with its rows
+// beyond cout unused), N the other side's channel count; the three taps'
+// accumulators lie side by side in tensor memory.  Each CTA writes its chunk's
+// sums to part[z][k][m][n] (m the M row, n the N column), the bias sums (CTAs
+// with ky = 0) to part_b[z][co]; conv_wgrad_tc_sum_kernel adds the chunks in
+// order, so the result does not depend on the order the CTAs finish in.
 constexpr int kWgPx = 64;          // pixels per stage
 constexpr int kWgThreads = 256;
+constexpr int kWgRing = 4;         // stages of copies in flight or landed
+constexpr int kWgAhead = 2;        // stages copied ahead of the one consumed
 
 template <bool XA, int N>
 struct WgShape {
-    static constexpr uint32_t ROWB = kWgPx * 2;                 // one channel's pixels of a stage
-    static constexpr uint32_t D_BYTES = (XA ? N : 128) * ROWB;  // dY operand (128 rows on the M side)
-    static constexpr uint32_t X_PLANE = (XA ? 128 : N) * ROWB;  // one shifted copy of X
-    static constexpr uint32_t STAGE = D_BYTES + 3 * X_PLANE;
-    static constexpr uint32_t SMEM = 2 * STAGE;
+    static constexpr int DROWS = XA ? N : 128;                   // dY rows (128 on the M side)
+    static constexpr int XROWS = XA ? 128 : N;                   // X rows
+    static constexpr uint32_t D_BYTES = DROWS * 128;             // 8 groups of 8 pixels per channel
+    static constexpr uint32_t X1_SBO = 10 * 128;                 // 10 groups (-1 .. 8) per channel group
+    static constexpr uint32_t X1_BYTES = XROWS * 160;
+    static constexpr uint32_t SLOT = D_BYTES + X1_BYTES;         // one ring stage
+    static constexpr uint32_t XS_PLANE = XROWS * 128;            // one shifted copy
+    static constexpr uint32_t XS_BUF = 2 * XS_PLANE;             // kx = 0 and 2
+    static constexpr uint32_t SMEM = kWgRing * SLOT + 2 * XS_BUF;
     static constexpr uint32_t NCOL = 3 * N <= 128 ? 128 : (3 * N <= 256 ? 256 : 512);
+    static constexpr int QD = DROWS * 8 / kWgThreads;            // dY groups per thread (at most)
+    static constexpr int QX1 = (XROWS * 10 + kWgThreads - 1) / kWgThreads;   // X groups per thread (at most)
+    // CTAs one SM holds (233472 bytes of shared memory, 512 tensor-memory columns)
+    static constexpr int RES = (233472 / (SMEM + 2048)) < (512 / NCOL) ? (233472 / (SMEM + 2048)) : (512 / NCOL);
     static_assert(3 * N <= 512, "accumulators exceed the tensor memory");
-    static_assert(STAGE % 1024 == 0, "stage alignment");
+    static_assert(SLOT % 1024 == 0 && XS_PLANE % 1024 == 0, "stage alignment");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
+
+namespace tc {
+// 16-byte global -> shared copy; src_bytes = 0 fills zeros without reading.
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst_smem)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory"); }
+}  // namespace tc
 
 template <bool XA, int N>
 __global__ void __launch_bounds__(kWgThreads, 1)
@@ -448,11 +475,12 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     __shared__ float bias_sh[4][4][8];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ky = blockIdx.x, z = blockIdx.y;
-    const size_t plane = (size_t)H * W;
+    const long plane = (long)H * W;
     const long pa = (long)z * chunk_px;
-    const long pb = pa + chunk_px < (long)plane ? pa + chunk_px : (long)plane;
+    const long pb = pa + chunk_px < plane ? pa + chunk_px : plane;
     const int nst = (int)((pb - pa + kWgPx - 1) / kWgPx);
     const int ma = XA ? cin : cout;   // rows of the M side that hold data
+    const long xoff = (long)(ky - 1) * W;   // X pixel of dY pixel p: p + xoff (+ kx - 1)
 
     if (warp == 0) tc::tmem_alloc(&tmem_base_sh, Sh::NCOL);
     if (tid == 0) {
@@ -466,72 +494,90 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base_sh;
     const uint32_t sbase = tc::smem_u32(smem);
+    uint8_t *const xs_buf = smem + kWgRing * Sh::SLOT;
 
-    // thread t stages pixel group j = (t / 8) % 8 of every stage, for channels (t / 64 + 4 q) * 8 + t % 8
-    const int jg = (tid >> 3) & 7;
-    const int cb = (tid >> 6) * 8 + (tid & 7);
-    const int nqd = cout / 32, nqx = cin / 32;
-    uint4 rd[4], rx[4];
-    uint32_t ra[4], rb[4];
-    float bsum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const bool with_bias = ky == 0;
-    auto load_stage = [&](int i) {
-        const long p = pa + (long)i * kWgPx + 8 * jg;   // this thread's 8 pixels (one row: W % 16 == 0)
-        const bool in = p < pb;
-        const int y = in ? (int)(p / W) : 0, x = in ? (int)(p - (long)y * W) : 0;
-        const int yy = y + ky - 1;
-        const bool xin = in && yy >= 0 && yy < H;
+    // copies of stage i into ring slot i % kWgRing: dY group (c, j) at ((c / 8) * 8 + j) * 128 + (c % 8) * 16,
+    // X group (c, j), j = -1 .. 8, at ((c / 8) * 10 + j + 1) * 128 + (c % 8) * 16
+    auto issue_stage = [&](int i) {
+        uint8_t *sD = smem + (i % kWgRing) * Sh::SLOT;
+        uint8_t *sX = sD + Sh::D_BYTES;
+        const long p0 = pa + (long)i * kWgPx;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int c = cb + 32 * q;
-            rd[q] = make_uint4(0u, 0u, 0u, 0u);
-            if (q < nqd && in) rd[q] = __ldg(reinterpret_cast<const uint4 *>(dY + (size_t)c * plane + p));
-            rx[q] = make_uint4(0u, 0u, 0u, 0u);
-            ra[q] = rb[q] = 0u;
-            if (q < nqx && xin) {
-                const unsigned short *xs =
-                    reinterpret_cast<const unsigned short *>(X) + (size_t)c * plane + (size_t)yy * W + x;
-                rx[q] = __ldg(reinterpret_cast<const uint4 *>(xs));
-                if (x > 0) ra[q] = __ldg(xs - 1);
-                if (x + 8 < W) rb[q] = __ldg(xs + 8);
+        for (int q = 0; q < Sh::QD; q++) {
+            const int u = tid + kWgThreads * q;
+            const int c = (u >> 6) * 8 + (u & 7), j = (u >> 3) & 7;
+            if (c < cout) {
+                const long p = p0 + 8 * j;
+                const bool in = p < pb;
+                tc::cp_async16(sD + u * 16, in ? (const void *)(dY + (size_t)c * plane + p) : (const void *)dY,
+                               in ? 16u : 0u);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Sh::QX1; q++) {
+            const int v = tid + kWgThreads * q;
+            const int c = (v / 80) * 8 + (v & 7), jj = (v >> 3) % 10;
+            if (c < cin) {
+                const long px = p0 + 8 * (jj - 1) + xoff;
+                const bool in = px >= 0 && px < plane;
+                tc::cp_async16(sX + v * 16, in ? (const void *)(X + (size_t)c * plane + px) : (const void *)X,
+                               in ? 16u : 0u);
             }
         }
     };
-    load_stage(0);
+
+    // this thread's groups when building the shifted copies: pixel group jg, channels cb + 32 q
+    const int jg = (tid >> 3) & 7;
+    const int cb = (tid >> 6) * 8 + (tid & 7);
+    const int nqd = (cout + 31) / 32, nqx = (cin + 31) / 32;
+    float bsum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const bool with_bias = ky == 0;
+
+#pragma unroll 1
+    for (int i = 0; i < kWgAhead; i++) {
+        if (i < nst) issue_stage(i);
+        tc::cp_async_commit();
+    }
     int issued = 0;
     for (int i = 0; i < nst; i++) {
         const int st = i & 1;
+        // MMAs of stage i - 2 read ring slot (i + 2) % 4 and shifted buffer st
         if (i >= 2 && !tc::mbar_wait(&mma_done[st], (uint32_t)(((i >> 1) - 1) & 1))) abort_sh = 1;
-        uint8_t *sD = smem + st * Sh::STAGE;
-        uint8_t *sX = sD + Sh::D_BYTES;
+        if (i + kWgAhead < nst) issue_stage(i + kWgAhead);
+        tc::cp_async_commit();
+        tc::cp_async_wait<kWgAhead>();   // stage i has landed (this thread's copies)
+        __syncthreads();                 // ... and every other thread's
+        const uint8_t *sD = smem + (i % kWgRing) * Sh::SLOT;
+        const uint8_t *sX = sD + Sh::D_BYTES;
+        uint8_t *sS = xs_buf + st * Sh::XS_BUF;
+        const long p = pa + (long)i * kWgPx + 8 * jg;
+        const int x = (int)(p % W);
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            // unit (channel c, group jg) sits at ((c / 8) * 8 + jg) * 128 + (c % 8) * 16 = (tid + 256 q) * 16
-            const uint32_t off = (uint32_t)(tid + 256 * q) * 16u;
-            if (q < nqd) {
-                *reinterpret_cast<uint4 *>(sD + off) = rd[q];
-                if (with_bias) {
-                    const uint32_t w[4] = {rd[q].x, rd[q].y, rd[q].z, rd[q].w};
-                    float t = 0.0f;
-#pragma unroll
-                    for (int e = 0; e < 4; e++)
-                        t += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xFFFF0000u);
-                    bsum[q] += t;
-                }
-            }
-            if (q < nqx) {
-                const uint4 v = rx[q];
-                // kx = 0: pixels x - 1 .. x + 6; kx = 1: x .. x + 7; kx = 2: x + 1 .. x + 8
-                *reinterpret_cast<uint4 *>(sX + off) =
-                    make_uint4(__byte_perm(ra[q], v.x, 0x5410), __byte_perm(v.x, v.y, 0x5432),
+            const int c = cb + 32 * q;
+            if (q < nqx && c < cin) {
+                const uint8_t *g = sX + (((c >> 3) * 10 + jg + 1) * 128 + (c & 7) * 16);
+                const uint4 v = *reinterpret_cast<const uint4 *>(g);
+                const uint32_t a = x > 0 ? *reinterpret_cast<const unsigned short *>(g - 128 + 14) : 0u;
+                const uint32_t b = x + 8 < W ? *reinterpret_cast<const unsigned short *>(g + 128) : 0u;
+                const uint32_t off = (uint32_t)(tid + 256 * q) * 16u;
+                // kx = 0: pixels x - 1 .. x + 6; kx = 2: x + 1 .. x + 8
+                *reinterpret_cast<uint4 *>(sS + off) =
+                    make_uint4(__byte_perm(a, v.x, 0x5410), __byte_perm(v.x, v.y, 0x5432),
                                __byte_perm(v.y, v.z, 0x5432), __byte_perm(v.z, v.w, 0x5432));
-                *reinterpret_cast<uint4 *>(sX + Sh::X_PLANE + off) = v;
-                *reinterpret_cast<uint4 *>(sX + 2 * Sh::X_PLANE + off) =
+                *reinterpret_cast<uint4 *>(sS + Sh::XS_PLANE + off) =
                     make_uint4(__byte_perm(v.x, v.y, 0x5432), __byte_perm(v.y, v.z, 0x5432),
-                               __byte_perm(v.z, v.w, 0x5432), __byte_perm(v.w, rb[q], 0x5432));
+                               __byte_perm(v.z, v.w, 0x5432), __byte_perm(v.w, b, 0x5432));
+            }
+            if (with_bias && q < nqd && c < cout) {
+                const uint4 d = *reinterpret_cast<const uint4 *>(sD + (uint32_t)(tid + 256 * q) * 16u);
+                const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+                float t = 0.0f;
+#pragma unroll
+                for (int e = 0; e < 4; e++) t += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xFFFF0000u);
+                bsum[q] += t;
             }
         }
-        if (i + 1 < nst) load_stage(i + 1);
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (abort_sh) break;
@@ -539,12 +585,14 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             tc::fence_after_sync();
             const long left = pb - (pa + (long)i * kWgPx);
             const int ks = (int)((left < kWgPx ? left : kWgPx) / 16);   // K steps of 16 pixels
-            const uint32_t d0 = sbase + st * Sh::STAGE, x0 = d0 + Sh::D_BYTES;
+            const uint32_t d0 = sbase + (uint32_t)((i % kWgRing) * Sh::SLOT), x1 = d0 + Sh::D_BYTES + 128;
+            const uint32_t s0 = sbase + kWgRing * Sh::SLOT + st * Sh::XS_BUF;
             for (int s = 0; s < ks; s++) {
+                const uint64_t dd = tc::smem_desc(d0 + 256 * s, 128, 1024);
 #pragma unroll
                 for (int kx = 0; kx < 3; kx++) {
-                    const uint64_t dd = tc::smem_desc(d0 + 256 * s, 128, 1024);
-                    const uint64_t xd = tc::smem_desc(x0 + kx * Sh::X_PLANE + 256 * s, 128, 1024);
+                    const uint64_t xd = kx == 1 ? tc::smem_desc(x1 + 256 * s, 128, Sh::X1_SBO)
+                                                : tc::smem_desc(s0 + (kx >> 1) * Sh::XS_PLANE + 256 * s, 128, 1024);
                     tc::mma_bf16(tmem + (uint32_t)(kx * N), XA ? xd : dd, XA ? dd : xd, tc::IDesc<128, N>::value,
                                  (i > 0 || s > 0) ? 1u : 0u);
                 }
@@ -553,6 +601,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         }
         issued = i + 1;
     }
+    tc::cp_async_wait<0>();
     __syncthreads();
     bool done = true;
     if (issued > 0 && !abort_sh) {
@@ -568,16 +617,24 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         tc::fence_after_sync();
         const int wl = warp & 3, wh = warp >> 2;
         const int m = 32 * wl + lane;
-        const size_t tap = (size_t)ma * N;
+        const int nb = XA ? cout : cin;   // columns of a tap that hold data
+        const size_t tap = (size_t)ma * nb;
 #pragma unroll 1
         for (int c0 = 16 * wh; c0 < 3 * N; c0 += 32) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(32 * wl) << 16) + (uint32_t)c0, v);
-            if (m < ma) {
-                const int k = 3 * ky + c0 / N, n0 = c0 % N;
-                float4 *o = reinterpret_cast<float4 *>(part + ((size_t)z * 9 + k) * tap + (size_t)m * N + n0);
+            const int k = 3 * ky + c0 / N, n0 = c0 % N;
+            if (m < ma && n0 < nb) {
+                float *o = part + ((size_t)z * 9 + k) * tap + (size_t)m * nb + n0;
+                if (nb == N) {
 #pragma unroll
-                for (int e = 0; e < 4; e++) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                    for (int e = 0; e < 4; e++)
+                        reinterpret_cast<float4 *>(o)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; e++)
+                        if (n0 + e < nb) o[e] = v[e];
+                }
             }
         }
         if (with_bias) {
@@ -595,7 +652,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int c = cb + 32 * q;
-                    if (q < nqd) part_b[(size_t)z * cout + c] = bsum[q] + bias_sh[warp >> 1][q][lane];
+                    if (q < nqd && c < cout) part_b[(size_t)z * cout + c] = bsum[q] + bias_sh[warp >> 1][q][lane];
                 }
         }
     }
@@ -604,41 +661,71 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     if (warp == 0) tc::tmem_dealloc(tmem, Sh::NCOL);
 }
 
-// dW += sum over the chunks of part (layout [z][k][m][n]), db += sum of part_b, chunks in order.
-__global__ void conv_wgrad_tc_sum_kernel(const float *__restrict__ part, const float *__restrict__ part_b, int chunks,
-                                         float *__restrict__ dW, float *__restrict__ db, int cin, int cout, int xa) {
+// dW += sum over the chunks of part (layout [z][k][m][n]), db += sum of part_b.
+// A block takes 32 consecutive sums; its warp w adds chunks w, w + 8, ... in
+// order, and lane i of warp 0 adds the eight warps' results in order: a fixed
+// order, whatever the timing.
+__global__ void __launch_bounds__(256) conv_wgrad_tc_sum_kernel(const float *__restrict__ part,
+                                                                const float *__restrict__ part_b, int chunks,
+                                                                float *__restrict__ dW, float *__restrict__ db, int cin,
+                                                                int cout, int xa) {
+    __shared__ float acc[8][32];
     const int ma = xa ? cin : cout, nb = xa ? cout : cin;
     const size_t n = (size_t)cout * cin * 9, tap = (size_t)ma * nb;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + cout; i += (size_t)gridDim.x * blockDim.x) {
-        if (i < n) {
-            float v = 0.0f;
-            for (int z = 0; z < chunks; z++) v += part[(size_t)z * n + i];
-            const int k = (int)(i / tap), m = (int)((i / nb) % ma), c = (int)(i % nb);
-            const int co = xa ? c : m, ci = xa ? m : c;
-            dW[((size_t)co * cin + ci) * 9 + k] += v;
-        } else if (db) {
-            const size_t co = i - n;
-            float v = 0.0f;
-            for (int z = 0; z < chunks; z++) v += part_b[(size_t)z * cout + co];
-            db[co] += v;
-        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t i = (size_t)blockIdx.x * 32 + lane;
+    float v = 0.0f;
+    if (i < n) {
+        for (int z = w; z < chunks; z += 8) v += part[(size_t)z * n + i];
+    } else if (i < n + cout) {
+        for (int z = w; z < chunks; z += 8) v += part_b[(size_t)z * cout + (i - n)];
+    }
+    acc[w][lane] = v;
+    __syncthreads();
+    if (w != 0 || i >= n + cout) return;
+    float t = acc[0][lane];
+#pragma unroll
+    for (int j = 1; j < 8; j++) t += acc[j][lane];
+    if (i < n) {
+        const int k = (int)(i / tap), m = (int)((i / nb) % ma), c = (int)(i % nb);
+        const int co = xa ? c : m, ci = xa ? m : c;
+        dW[((size_t)co * cin + ci) * 9 + k] += t;
+    } else if (db) {
+        db[i - n] += t;
     }
 }
 
 // Shape conditions of the tensor-memory weight gradient.
+// Channel counts up to 128 on either side: the M side (128 rows) and the N
+// side (32, 64 or 128 columns) are padded, and what the padding rows and
+// columns accumulate is never stored.
 bool conv3x3_wgrad_tc_ok(int cin, int cout, int H, int W) {
-    return (cin == 32 || cin == 64 || cin == 128) && (cout == 32 || cout == 64 || cout == 128) && W % 16 == 0 &&
-           W >= 16 && H >= 1 && (size_t)H * W <= ((size_t)1 << 31);
+    return cin >= 1 && cin <= 128 && cout >= 1 && cout <= 128 && W % 16 == 0 && W >= 16 && H >= 1 &&
+           (size_t)H * W <= ((size_t)1 << 31);
 }
 
-// Pixel chunks of the weight gradient: about 50 chunks (three CTAs each, one per
-// kernel row: 150 CTAs on a 152-SM GPU), at least one stage each, and at most
-// cap_floats of FP32 partial sums.  Returns the number of chunks, *chunk_px their size.
+// Which side is M: X where it has all 128 rows and dY fits N = 64 (half the MMA
+// work of padding dY to 128), else dY.
+static bool wgrad_tc_xa(int cin, int cout) { return cin == 128 && cout <= 64; }
+static int wgrad_tc_n(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : 128; }
+
+// CTAs per SM of the weight-gradient form a cin -> cout layer uses.
+static int wgrad_tc_res(int cin, int cout) {
+    if (wgrad_tc_xa(cin, cout)) return wgrad_tc_n(cout) == 32 ? WgShape<true, 32>::RES : WgShape<true, 64>::RES;
+    const int n = wgrad_tc_n(cin);
+    return n == 32 ? WgShape<false, 32>::RES : n == 64 ? WgShape<false, 64>::RES : WgShape<false, 128>::RES;
+}
+
+// Pixel chunks of the weight gradient: about 50 chunks per CTA an SM holds
+// (three CTAs each, one per kernel row: 150 per wave on a 152-SM GPU), at least
+// one stage each, and at most cap_floats of FP32 partial sums.  Returns the
+// number of chunks, *chunk_px their size.
 int conv3x3_wgrad_tc_plan(int cin, int cout, int H, int W, size_t cap_floats, int *chunk_px) {
     const long px = (long)H * W;
     const size_t per = (size_t)9 * cin * cout + cout;
     long zc = (px + kWgPx - 1) / kWgPx;
-    if (zc > 50) zc = 50;
+    const long target = 50L * wgrad_tc_res(cin, cout);
+    if (zc > target) zc = target;
     if ((size_t)zc > cap_floats / per) zc = (long)(cap_floats / per);
     if (zc < 1) return 0;
     long ch = (px + zc - 1) / zc;
@@ -676,19 +763,20 @@ int conv3x3_wgrad_tc(const bf16 *X, const bf16 *dY, float *dW, float *db, int ci
     if (!part || ((uintptr_t)part & 15) || nz < 1) return TW_EWORKSPACE;
     float *part_b = part + (size_t)nz * 9 * cin * cout;
     int e;
-    const bool xa = cout != 128 && cin == 128;
+    const bool xa = wgrad_tc_xa(cin, cout);
     if (xa) {
-        e = cout == 32 ? launch_wgrad_tc<true, 32>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
-                       : launch_wgrad_tc<true, 64>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s);
+        e = wgrad_tc_n(cout) == 32 ? launch_wgrad_tc<true, 32>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
+                                   : launch_wgrad_tc<true, 64>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s);
     } else {
-        e = cin == 32   ? launch_wgrad_tc<false, 32>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
-            : cin == 64 ? launch_wgrad_tc<false, 64>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
-                        : launch_wgrad_tc<false, 128>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s);
+        const int n = wgrad_tc_n(cin);
+        e = n == 32   ? launch_wgrad_tc<false, 32>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
+            : n == 64 ? launch_wgrad_tc<false, 64>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s)
+                      : launch_wgrad_tc<false, 128>(X, dY, part, part_b, cin, cout, H, W, nz, chunk, s);
     }
     if (e) return e;
     const size_t n = (size_t)cout * cin * 9 + cout;
-    TW_LAUNCH(conv_wgrad_tc_sum_kernel, (unsigned)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256), 256, 0, s, part,
-              part_b, nz, dW, db, cin, cout, xa ? 1 : 0);
+    TW_LAUNCH(conv_wgrad_tc_sum_kernel, (unsigned)((n + 31) / 32), 256, 0, s, part, part_b, nz, dW, db, cin, cout,
+              xa ? 1 : 0);
     return TW_OK;
 }
 

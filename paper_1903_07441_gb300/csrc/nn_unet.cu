@@ -630,12 +630,17 @@ static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S
     return TW_OK;
 }
 
-// Row chunks of the CUDA-core weight gradient: at least 16 rows each, as many as
-// cap_floats of partial sums allow; 0 if even one chunk does not fit.
+// Row chunks of the CUDA-core weight gradient: enough chunks for about four
+// CTAs per SM of a 152-SM GPU (the layers it serves have few channels, so few
+// channel blocks), as many as cap_floats of partial sums allow; 0 if even one
+// chunk does not fit.
 static int wgrad_simt_rows(int cin, int cout, int H, size_t cap_floats) {
     const size_t per = (size_t)cout * cin * 9 + cout;
     if (per > cap_floats) return 0;
-    int rows = H < 16 ? H : 16;
+    const long blocks = (long)ceil_div(cout, COB) * ceil_div(cin, CIB);
+    long nz = (608 + blocks - 1) / blocks;
+    if (nz > H) nz = H;
+    int rows = ceil_div(H, (int)nz);
     while ((size_t)ceil_div(H, rows) * per > cap_floats) rows *= 2;
     return rows;
 }
@@ -671,7 +676,7 @@ static size_t conv3x3_wgrad_floats(int cin, int cout, int H, int W, int impl) {
         int chunk = 0;
         return (size_t)conv3x3_wgrad_tc_plan(cin, cout, H, W, (size_t)-1, &chunk) * per;
     }
-    return (size_t)ceil_div(H, H < 16 ? H : 16) * per;
+    return (size_t)ceil_div(H, wgrad_simt_rows(cin, cout, H, (size_t)-1)) * per;
 }
 
 static void conv_fwd(const bf16 *X, const float *params, int li, const bf16 *S, bf16 *Y, int H, int W, int relu,

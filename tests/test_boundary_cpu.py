@@ -209,15 +209,17 @@ def test_warm_start_entry_points_reject_bad_input_on_host(lib):
         assert lib.ws_conv3x3(P, P, None, None, P, cin, cout, H, W, 1, tw.WS_CONV_TC, P, 1 << 20, None) == tw.TW_EINVAL
     assert lib.ws_conv3x3(P, P, None, None, P, 64, 64, 16, 256, 1, tw.WS_CONV_TC, None, 0, None) == tw.TW_EWORKSPACE
     assert lib.ws_conv3x3(P, P, None, None, P, 64, 64, 16, 256, 1, tw.WS_CONV_TC, P, 100, None) == tw.TW_EWORKSPACE
-    # ws_conv3x3_wgrad: the tensor-memory form needs cin, cout in {32, 64, 128} and W % 16 == 0; no
-    # mma.sync form; the workspace holds the partial sums of the pixel chunks
+    # ws_conv3x3_wgrad: the tensor-memory form needs cin, cout <= 128 and W % 16 == 0; no mma.sync
+    # form; the workspace holds the partial sums of the pixel chunks
     per = 9 * 64 * 128 + 128
     # 4096 pixels: about 50 chunks, rounded up to whole 64-pixel stages of 128 pixels -> 32 chunks
     assert lib.ws_conv3x3_wgrad_workspace_size(64, 128, 16, 256, tw.WS_CONV_TC) >= 32 * per * 4
     assert lib.ws_conv3x3_wgrad_workspace_size(64, 128, 1, 16, tw.WS_CONV_TC) >= per * 4
     assert lib.ws_conv3x3_wgrad_workspace_size(2, 32, 16, 16, tw.WS_CONV_AUTO) >= (9 * 2 * 32 + 32) * 4
     assert lib.ws_conv3x3_wgrad_workspace_size(64, 64, 16, 256, tw.WS_CONV_MMA) == 0
-    for cin, cout, H, W in ((64, 96, 16, 256), (16, 64, 16, 256), (64, 64, 16, 200), (64, 64, 16, 8)):
+    assert lib.ws_conv3x3_wgrad_workspace_size(2, 32, 16, 256, tw.WS_CONV_TC) > 0
+    assert lib.ws_conv3x3_wgrad_workspace_size(32, 1, 16, 256, tw.WS_CONV_TC) > 0
+    for cin, cout, H, W in ((256, 64, 16, 256), (64, 160, 16, 256), (64, 64, 16, 200), (64, 64, 16, 8)):
         assert lib.ws_conv3x3_wgrad_workspace_size(cin, cout, H, W, tw.WS_CONV_TC) == 0
         assert lib.ws_conv3x3_wgrad(P, P, P, None, cin, cout, H, W, tw.WS_CONV_TC, P, 1 << 30, None) == tw.TW_EINVAL
     assert lib.ws_conv3x3_wgrad(P, P, P, None, 64, 64, 16, 256, tw.WS_CONV_MMA, P, 1 << 30, None) == tw.TW_EINVAL

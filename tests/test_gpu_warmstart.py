@@ -95,10 +95,12 @@ def test_conv3x3_tensor_memory_matches_cuda_core_and_fp64(dev, cin, cout, H, W, 
 
 @pytest.mark.parametrize("cin,cout,H,W", [(32, 32, 8, 256), (32, 64, 10, 128), (64, 64, 12, 48), (64, 128, 6, 64),
                                           (128, 128, 9, 128), (128, 64, 5, 80), (64, 32, 16, 256), (128, 32, 7, 32),
-                                          (32, 128, 4, 16), (128, 128, 64, 64)])
+                                          (32, 128, 4, 16), (128, 128, 64, 64), (2, 32, 16, 256),
+                                          (32, 1, 16, 256), (16, 96, 6, 48), (128, 48, 5, 32)])
 def test_conv3x3_weight_gradient_tensor_memory_matches_fp64(dev, cin, cout, H, W):
     """The tcgen05 weight gradient (per tap a GEMM over the pixels, X staged three times shifted by one
-    pixel, accumulators in tensor memory, pixel chunks summed in a fixed order) and the CUDA-core one
+    pixel, accumulators in tensor memory, channel counts other than 32, 64 and 128 padded, pixel chunks
+    summed in a fixed order) and the CUDA-core one
     against the FP64 gradient of the same BF16 inputs: every weight and bias within 2^-12 of the sum of
     the absolute products it adds (FP32 accumulation; one pixel more or less moves a weight by about
     1 / (H W) of that sum, so a dropped, repeated or misplaced pixel, tap or channel fails), ragged
