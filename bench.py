@@ -936,7 +936,8 @@ def run_reference(args, rank, world, dist):
 def profile_case(case):
     """One small case of a kernel other than the headline's, for an ncu capture of that kernel
     (profiles/ names the command): conv128 = a 128 -> 128 tensor-memory convolution on 512 x 512,
-    conv32 = 32 -> 32 on 1024 x 1024 (3 warm-up calls, then 10 timed); mixed_fp16 = one HP_MIXED FP16
+    conv32 = 32 -> 32 on 1024 x 1024, conv128n / conv128s = 128 -> 128 on 4096 x 64 / 64 x 64 pixels (the
+    narrow form) (3 warm-up calls, then 10 timed); mixed_fp16 = one HP_MIXED FP16
     solve of a seeded 2048 x 2048 field (20 % blocked) through the host-driven loop, whose correction
     sweeps are separate launches (ncu does not profile kernel nodes of graphs with conditional nodes);
     train256 = warm-start network training steps on one 256 x 256 field (3 warm-up, 20 timed);
@@ -946,7 +947,8 @@ def profile_case(case):
     import paper_1903_07441_gb300 as tw
     dev = torch.device("cuda:0")
     if case.startswith("conv"):
-        cin, cout, H, W = (128, 128, 512, 512) if case == "conv128" else (32, 32, 1024, 1024)
+        cin, cout, H, W = {"conv128": (128, 128, 512, 512), "conv32": (32, 32, 1024, 1024),
+                           "conv128n": (128, 128, 4096, 64), "conv128s": (128, 128, 64, 64)}[case]
         g = torch.Generator(device=dev).manual_seed(0)
         x = (torch.randn(cin, H, W, device=dev, generator=g) * 0.5).to(torch.bfloat16)
         w = torch.randn(cout, cin, 3, 3, device=dev, generator=g) * (1.0 / (9 * cin) ** 0.5)
@@ -1043,7 +1045,8 @@ def main():
                     help="also run the success / collision-free evaluation over 1-16 moving obstacles")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-reps", type=int, default=3)
-    ap.add_argument("--profile-case", choices=["conv128", "conv32", "mixed_fp16", "train256", "wgrad128", "wgrad32"], default=None,
+    ap.add_argument("--profile-case", choices=["conv128", "conv32", "conv128n", "conv128s", "mixed_fp16", "train256", "wgrad128",
+                                                        "wgrad32"], default=None,
                     help="run one small kernel case (for an ncu capture) and print its timing, instead of the bench")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -427,11 +427,13 @@ int ws_unet_train_step(float *params, float *grads, float *adam_m, float *adam_v
  * WS_CONV_SIMT (direct convolution on CUDA cores), WS_CONV_MMA (tensor cores,
  * mma.sync m16n8k16, FP32 accumulation) or WS_CONV_TC (5th-generation tensor
  * cores: tcgen05.mma implicit GEMM with the accumulators in tensor memory, for
- * cin % 16 == 0, cout in {32, 64, 128}, W % 128 == 0 and H a multiple of 4 (of
- * 2 for cout 128); it needs
+ * cin % 16 == 0, cout in {32, 64, 128}, and either W % 128 == 0 and H a
+ * multiple of 4 (of 2 for cout 128), or W in {16, 32, 64} and H a multiple of
+ * 256 / W (the narrow form: 128-pixel blocks spanning 128 / W rows, split K over
+ * the 16-channel chunks with the partial sums added in split order); it needs
  * ws_conv3x3_workspace_size() bytes of 256-byte-aligned device workspace for
- * the weights re-arranged in BF16, and is what WS_CONV_AUTO uses inside the
- * network wherever those conditions hold).  Every form accumulates each
+ * the weights re-arranged in BF16 (and the narrow form's partial sums), and is
+ * what WS_CONV_AUTO uses inside the network wherever those conditions hold).  Every form accumulates each
  * product in FP32; they differ only in the order of the sums.  TW_EINVAL when
  * the channel counts or sizes do not allow the form asked for; TW_EWORKSPACE
  * for a missing or short workspace.  Enqueued on `stream`.  The implicit

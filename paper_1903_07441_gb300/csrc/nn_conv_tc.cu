@@ -390,6 +390,256 @@ int conv3x3_tc(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf
     }
 }
 
+// ---- the same convolution for images narrower than 128 pixels ------------------
+//
+// W in {16, 32, 64}: one M block of 128 pixels spans R = 128 / W image rows, and
+// a CTA computes NMB such blocks (NMB * R rows).  The tap shift in x cannot be a
+// whole-row offset of one haloed tile here (the halo columns would sit between
+// the rows of an M block), so per 16-channel chunk the input rows are written
+// channel-last three times, shifted by dx - 1 pixels with zeros at the row ends:
+// copy dx holds X[y][x + dx - 1], rows contiguous with pitch W, so the operand of
+// tap (dy, dx) for block t is copy dx started (t * R + dy) * W pixels in.  The
+// weights are the wide kernel's per-chunk layout, brought by the bulk-copy
+// engine.  Split K: CTA (block, split) takes its share of the chunks; with more
+// than one split it writes FP32 partial sums part[split][cout][H][W] (added in
+// split order by the caller's finalisation, which also applies bias, skip and
+// activation), else the finished BF16 output.
+constexpr int kNarrowMB = 2;   // M blocks (of 128 pixels) per CTA
+
+template <int N>
+struct TcNarrowShape {
+    static constexpr int PXMAX = kNarrowMB * 128 + 2 * 64;          // tile pixels at W = 64 (the widest)
+    static constexpr uint32_t A_BYTES = 3 * 2 * PXMAX * 16;         // 3 shifted copies x 2 halves
+    static constexpr uint32_t B_TAP = 2 * N * 16;
+    static constexpr uint32_t B_BYTES = 9 * B_TAP;
+    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    static constexpr uint32_t SMEM = 2 * STAGE;
+    static constexpr uint32_t NCOL = kNarrowMB * N <= 64 ? 64 : (kNarrowMB * N <= 128 ? 128 : 256);
+    static constexpr int ITEMS = (2 * PXMAX + kTcThreads - 1) / kTcThreads;
+    static_assert(STAGE % 16 == 0 && A_BYTES % 16 == 0, "16-byte operand alignment");
+};
+
+template <int N>
+__global__ void __launch_bounds__(kTcThreads, N == 128 ? 1 : 2)
+    conv3x3_tc_narrow_kernel(const bf16 *__restrict__ X, const uint4 *__restrict__ Wb, const float *__restrict__ b,
+                             const bf16 *__restrict__ S, bf16 *__restrict__ Y, float *__restrict__ part, int cin,
+                             int H, int W, int relu, int splits) {
+    using Sh = TcNarrowShape<N>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t mma_done[2], b_full[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = 128 / W;                       // image rows per M block
+    const int rows = kNarrowMB * R + 2;          // staged rows (one halo row above and below)
+    const int y0 = blockIdx.x * kNarrowMB * R;
+    const int chunks = cin / 16, per = (chunks + splits - 1) / splits;
+    const int cb = blockIdx.y * per, ce = min(chunks, cb + per);
+    const uint32_t half = (uint32_t)(rows * W) * 16u;   // bytes of one 8-channel half of one copy
+    const size_t plane = (size_t)H * W;
+
+    if (warp == 0) tc::tmem_alloc(&tmem_base_sh, Sh::NCOL);
+    if (tid == 0) {
+        for (int k = 0; k < 2; k++) {
+            tc::mbar_init(&mma_done[k], 1);
+            tc::mbar_init(&b_full[k], 1);
+        }
+        tc::fence_mbar_init();
+        abort_sh = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t sbase = tc::smem_u32(smem);
+
+    // this thread's items (half, row, x): source offsets (-1 outside the image) and positions
+    const int nitems = 2 * rows * W;
+    long long src_off[Sh::ITEMS];
+    int pos[Sh::ITEMS];   // h * rows * W + r * W + x, or -1 past the tile
+#pragma unroll
+    for (int j = 0; j < Sh::ITEMS; j++) {
+        const int it = tid + kTcThreads * j;
+        src_off[j] = -1;
+        pos[j] = -1;
+        if (it < nitems) {
+            const int h = it / (rows * W), rem = it - h * (rows * W);
+            const int r = rem / W, x = rem - r * W;
+            const int y = y0 - 1 + r;
+            pos[j] = it;
+            if (y >= 0 && y < H) src_off[j] = (long long)(8 * h) * plane + (long long)y * W + x;
+        }
+    }
+    const unsigned short *Xs = reinterpret_cast<const unsigned short *>(X);
+    uint32_t ra[Sh::ITEMS][4];
+    auto load_tile = [&](int chunk) {
+        const unsigned short *base = Xs + (size_t)(16 * chunk) * plane;
+#pragma unroll
+        for (int j = 0; j < Sh::ITEMS; j++) {
+#pragma unroll
+            for (int c = 0; c < 8; c += 2) {
+                uint32_t lo = 0u, hi = 0u;
+                if (src_off[j] >= 0) {
+                    lo = __ldg(base + src_off[j] + (size_t)c * plane);
+                    hi = __ldg(base + src_off[j] + (size_t)(c + 1) * plane);
+                }
+                ra[j][c >> 1] = lo | (hi << 16);
+            }
+        }
+    };
+    if (cb < ce) load_tile(cb);
+    int issued = 0;
+    for (int i = cb; i < ce; i++) {
+        const int li = i - cb, st = li & 1;
+        if (li >= 2 && !tc::mbar_wait(&mma_done[st], (uint32_t)(((li >> 1) - 1) & 1))) abort_sh = 1;
+        uint8_t *sA = smem + st * Sh::STAGE;
+        if (tid == 0 && !abort_sh)
+            tc::bulk_load(sA + Sh::A_BYTES, Wb + (size_t)i * (Sh::B_BYTES / 16), Sh::B_BYTES, &b_full[st]);
+#pragma unroll
+        for (int j = 0; j < Sh::ITEMS; j++) {
+            if (pos[j] < 0) continue;
+            const int h = pos[j] / (rows * W), rem = pos[j] - h * (rows * W);
+            const int x = rem % W;
+            const uint4 v = make_uint4(ra[j][0], ra[j][1], ra[j][2], ra[j][3]);
+            const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+            uint8_t *p = sA + h * half + (uint32_t)rem * 16u;   // copy 0, this pixel's slot
+            // copy dx holds X[x + dx - 1]: this pixel is copy 1 at x, copy 0 at x + 1, copy 2 at x - 1
+            *reinterpret_cast<uint4 *>(p + 2 * half) = v;
+            if (x + 1 < W) *reinterpret_cast<uint4 *>(p + 16) = v;
+            if (x == 0) *reinterpret_cast<uint4 *>(p) = zero;
+            if (x >= 1) *reinterpret_cast<uint4 *>(p + 4 * half - 16) = v;
+            if (x == W - 1) *reinterpret_cast<uint4 *>(p + 4 * half) = zero;
+        }
+        if (i + 1 < ce) load_tile(i + 1);
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (abort_sh) break;
+        if (tid == 0) {
+            if (!tc::mbar_wait(&b_full[st], (uint32_t)((li >> 1) & 1))) {
+                abort_sh = 1;
+            } else {
+                tc::fence_after_sync();
+                const uint32_t a0 = sbase + st * Sh::STAGE, b0 = a0 + Sh::A_BYTES;
+#pragma unroll 1
+                for (int t = 0; t < kNarrowMB; t++) {
+#pragma unroll
+                    for (int k = 0; k < 9; k++) {
+                        const int dy = k / 3, dx = k - 3 * (k / 3);
+                        const uint64_t ad =
+                            tc::smem_desc(a0 + dx * 2 * half + (uint32_t)((t * R + dy) * W) * 16u, half, 128);
+                        const uint64_t bd = tc::smem_desc(b0 + k * Sh::B_TAP, N * 16, 128);
+                        tc::mma_bf16(tmem + (uint32_t)(t * N), ad, bd, tc::IDesc<128, N>::value,
+                                     (li > 0 || k > 0) ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(&mma_done[st]);
+            }
+        }
+        issued = li + 1;
+    }
+    __syncthreads();
+    bool done = true;
+    if (issued > 0 && !abort_sh) {
+        const int last = issued - 1;
+        done = tc::mbar_wait(&mma_done[last & 1], (uint32_t)((last >> 1) & 1));
+    }
+    if (!done) abort_sh = 1;
+    __syncthreads();
+    if (abort_sh) {
+        if (tid == 0) atomicExch(&g_conv_tc_error, 1);
+        if (issued > 0) tc::mbar_wait(&mma_done[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1));
+    } else {
+        tc::fence_after_sync();
+        const int wl = warp & 3, wh = warp >> 2;
+        const int pix = 32 * wl + lane;   // TMEM lane = pixel of the M block
+#pragma unroll 1
+        for (int t = 0; t < kNarrowMB; t++) {
+            const int y = y0 + t * R + pix / W, x = pix % W;
+#pragma unroll 1
+            for (int c0 = 16 * wh; c0 < N; c0 += 16 * (kTcThreads / 128)) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * wl) << 16) + (uint32_t)(t * N + c0), v);
+                if (issued == 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; j++) v[j] = 0.0f;   // a split without chunks adds nothing
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int co = c0 + j;
+                    const size_t o = (size_t)co * plane + (size_t)y * W + x;
+                    if (splits > 1) {
+                        part[(size_t)blockIdx.y * N * plane + o] = v[j];
+                    } else {
+                        float val = v[j] + (b ? b[co] : 0.0f);
+                        if (S) val += __bfloat162float(S[o]);
+                        if (relu) val = fmaxf(val, 0.0f);
+                        Y[o] = __float2bfloat16(val);
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, Sh::NCOL);
+}
+
+// Shape conditions of the narrow tensor-memory convolution.
+bool conv3x3_tc_narrow_ok(int cin, int cout, int H, int W) {
+    return cin % 16 == 0 && cin >= 16 && (cout == 32 || cout == 64 || cout == 128) &&
+           (W == 16 || W == 32 || W == 64) && H % (kNarrowMB * 128 / W) == 0;
+}
+
+// Splits of the narrow form: enough CTAs for two per SM of a 152-SM GPU, at most
+// one per 16-channel chunk, no empty split, and partial sums within part_floats.
+int conv3x3_tc_narrow_splits(int cin, int cout, int H, int W, size_t part_floats) {
+    const int base = H / (kNarrowMB * 128 / W);
+    const int chunks = cin / 16;
+    int sp = (304 + base - 1) / base;
+    if (sp > chunks) sp = chunks;
+    while (sp > 1 && (size_t)sp * cout * H * W > part_floats) sp--;
+    if (sp < 1) sp = 1;
+    const int per = (chunks + sp - 1) / sp;
+    return (chunks + per - 1) / per;
+}
+
+template <int N>
+static int launch_tc_narrow(const bf16 *X, const bf16 *Wb, const float *b, const bf16 *S, bf16 *Y, float *part,
+                            int cin, int H, int W, int relu, int splits, cudaStream_t s) {
+    using Sh = TcNarrowShape<N>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    TW_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        TW_CUDA(cudaFuncSetAttribute(conv3x3_tc_narrow_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Sh::SMEM));
+        attr_set[dev] = true;
+    }
+    dim3 grid(H / (kNarrowMB * 128 / W), splits);
+    TW_LAUNCH((conv3x3_tc_narrow_kernel<N>), grid, kTcThreads, Sh::SMEM, s, X, reinterpret_cast<const uint4 *>(Wb), b,
+              S, Y, part, cin, H, W, relu, splits);
+    return TW_OK;
+}
+
+// The narrow form: wscratch holds conv3x3_tc_scratch_bytes(cin, cout) bytes for the
+// re-arranged weights (16-byte aligned); with splits > 1 the kernel writes FP32
+// partial sums to part[split][cout][H][W] and the caller finalises them.
+int conv3x3_tc_narrow(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
+                      int W, int relu, int splits, void *wscratch, float *part, cudaStream_t s) {
+    if (!conv3x3_tc_narrow_ok(cin, cout, H, W) || !wscratch || ((uintptr_t)wscratch & 15) || splits < 1 ||
+        (splits > 1 && !part))
+        return TW_EINVAL;
+    bf16 *Wb = (bf16 *)wscratch;
+    const size_t n = (size_t)cin * cout * 9;
+    TW_LAUNCH(conv_tc_weights_kernel, (unsigned)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256), 256, 0, s, Wt, Wb,
+              cin, cout);
+    switch (cout) {
+        case 32: return launch_tc_narrow<32>(X, Wb, b, S, Y, part, cin, H, W, relu, splits, s);
+        case 64: return launch_tc_narrow<64>(X, Wb, b, S, Y, part, cin, H, W, relu, splits, s);
+        default: return launch_tc_narrow<128>(X, Wb, b, S, Y, part, cin, H, W, relu, splits, s);
+    }
+}
+
 // Reads and clears the timeout flag of the current device (1 if a bounded wait gave up).
 int conv3x3_tc_error(int *flag) {
     int h = 0;

@@ -53,7 +53,7 @@ static size_t total_params() { return param_offset(kNumConvs); }
 // ---- kernels ----------------------------------------------------------------------
 
 constexpr int TS = 16;   // pixel tile side
-constexpr size_t kSplitKCap = (size_t)1 << 21;   // floats of split-K partial sums (8 MB of workspace)
+constexpr size_t kSplitKCap = (size_t)1 << 23;   // floats of split-K partial sums (32 MB of workspace)
 constexpr int COB = 16;  // output channels per CTA (CUDA-core kernels)
 constexpr int CIB = 8;   // input channels per staged chunk
 
@@ -561,6 +561,10 @@ size_t conv3x3_tc_scratch_bytes(int cin, int cout);
 int conv3x3_tc(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
                int W, int relu, void *scratch, cudaStream_t s);
 int conv3x3_tc_error(int *flag);
+bool conv3x3_tc_narrow_ok(int cin, int cout, int H, int W);
+int conv3x3_tc_narrow_splits(int cin, int cout, int H, int W, size_t part_floats);
+int conv3x3_tc_narrow(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
+                      int W, int relu, int splits, void *wscratch, float *part, cudaStream_t s);
 bool conv3x3_wgrad_tc_ok(int cin, int cout, int H, int W);
 int conv3x3_wgrad_tc_plan(int cin, int cout, int H, int W, size_t cap_floats, int *chunk_px);
 int conv3x3_wgrad_tc(const bf16 *X, const bf16 *dY, float *dW, float *db, int cin, int cout, int H, int W,
@@ -584,24 +588,49 @@ static int splitk_plan(int cin, int cout, int H, int W, size_t cap_floats) {
     return (chunks + per - 1) / per;
 }
 
+// Floats of part the narrow tensor-memory form takes ahead of its partial sums
+// (the re-arranged BF16 weights, rounded up to 256 bytes).
+static size_t narrow_weight_floats(int cin, int cout) {
+    return ((conv3x3_tc_scratch_bytes(cin, cout) + 255) & ~(size_t)255) / sizeof(float);
+}
+
+// The narrow tensor-memory form (W < 128) with its split-K finalisation: the
+// weights at the start of part, the partial sums after them.
+static int conv3x3_narrow(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout,
+                          int H, int W, int relu, cudaStream_t s, float *part, size_t part_floats) {
+    const size_t wf = narrow_weight_floats(cin, cout);
+    if (!part || part_floats < wf) return TW_EWORKSPACE;
+    const int sp = conv3x3_tc_narrow_splits(cin, cout, H, W, part_floats - wf);
+    float *pp = part + wf;
+    const int e = conv3x3_tc_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, sp, part, sp > 1 ? pp : nullptr, s);
+    if (e || sp == 1) return e;
+    TW_LAUNCH(splitk_finalize_kernel, dim3(ceil_div(W, 256), H, cout), 256, 0, s, pp, sp, b, S, Y, cout, H, W, relu);
+    return TW_OK;
+}
+
 // One 3x3 convolution: the tensor-core kernel where the channel counts allow
 // it (impl WS_CONV_AUTO), or the one asked for.  part (nullable): scratch for
 // split-K partial sums, part_floats long, which also holds the re-arranged
-// weights of the tensor-memory kernel (WS_CONV_TC).
+// weights of the tensor-memory kernels (WS_CONV_TC).
 static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
                    int W, int relu, int impl, cudaStream_t s, float *part = nullptr, size_t part_floats = 0) {
     const bool mma_ok = cin % 16 == 0 && cout % 32 == 0;
     if (impl == WS_CONV_MMA && !mma_ok) return TW_EINVAL;
     if (impl == WS_CONV_TC) {
+        if (conv3x3_tc_narrow_ok(cin, cout, H, W))
+            return conv3x3_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, s, part, part_floats);
         if (!conv3x3_tc_ok(cin, cout, H, W)) return TW_EINVAL;
         if (!part || part_floats * sizeof(float) < conv3x3_tc_scratch_bytes(cin, cout)) return TW_EWORKSPACE;
         return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, part, s);
     }
-    // the automatic choice: the tensor-memory kernel wherever its shape conditions hold and the
+    // the automatic choice: a tensor-memory kernel wherever its shape conditions hold and the
     // scratch for its re-arranged weights is there (inside the network), else mma.sync or CUDA cores
     if (impl == WS_CONV_AUTO && part && conv3x3_tc_ok(cin, cout, H, W) &&
         part_floats * sizeof(float) >= conv3x3_tc_scratch_bytes(cin, cout))
         return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, part, s);
+    if (impl == WS_CONV_AUTO && part && conv3x3_tc_narrow_ok(cin, cout, H, W) &&
+        part_floats >= narrow_weight_floats(cin, cout))
+        return conv3x3_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, s, part, part_floats);
     if (impl != WS_CONV_SIMT && mma_ok) {
         const int sp = part ? splitk_plan(cin, cout, H, W, part_floats) : 1;
         float *pp = sp > 1 ? part : nullptr;
@@ -945,7 +974,12 @@ extern "C" int ws_unet_train_step(float *params, float *grads, float *adam_m, fl
 
 extern "C" size_t ws_conv3x3_workspace_size(int cin, int cout, int H, int W, int impl) {
     using namespace tw::nn;
-    if (impl != WS_CONV_TC || cin < 1 || cout < 1 || !conv3x3_tc_ok(cin, cout, H, W)) return 0;
+    if (impl != WS_CONV_TC || cin < 1 || cout < 1 || H < 1 || W < 1) return 0;
+    if (conv3x3_tc_narrow_ok(cin, cout, H, W)) {
+        const int sp = conv3x3_tc_narrow_splits(cin, cout, H, W, (size_t)-1);
+        return narrow_weight_floats(cin, cout) * sizeof(float) + (sp > 1 ? (size_t)sp * cout * H * W * sizeof(float) : 0);
+    }
+    if (!conv3x3_tc_ok(cin, cout, H, W)) return 0;
     return (conv3x3_tc_scratch_bytes(cin, cout) + 255) & ~(size_t)255;
 }
 

@@ -207,6 +207,13 @@ def test_warm_start_entry_points_reject_bad_input_on_host(lib):
                             (64, 64, 6, 256), (64, 128, 7, 256)):
         assert lib.ws_conv3x3_workspace_size(cin, cout, H, W, tw.WS_CONV_TC) == 0
         assert lib.ws_conv3x3(P, P, None, None, P, cin, cout, H, W, 1, tw.WS_CONV_TC, P, 1 << 20, None) == tw.TW_EINVAL
+    # the narrow form: W in {16, 32, 64}, H a multiple of 256 / W; its workspace adds split-K partial sums
+    assert lib.ws_conv3x3_workspace_size(128, 128, 64, 64, tw.WS_CONV_TC) > 128 * 128 * 9 * 2 + 128 * 64 * 64 * 4
+    assert lib.ws_conv3x3_workspace_size(16, 32, 16, 16, tw.WS_CONV_TC) >= 16 * 32 * 9 * 2
+    for cin, cout, H, W in ((64, 64, 6, 64), (64, 64, 12, 32), (64, 64, 8, 48), (8, 64, 16, 64)):
+        assert lib.ws_conv3x3_workspace_size(cin, cout, H, W, tw.WS_CONV_TC) == 0
+        assert lib.ws_conv3x3(P, P, None, None, P, cin, cout, H, W, 1, tw.WS_CONV_TC, P, 1 << 20, None) == tw.TW_EINVAL
+    assert lib.ws_conv3x3(P, P, None, None, P, 64, 64, 16, 64, 1, tw.WS_CONV_TC, P, 100, None) == tw.TW_EWORKSPACE
     assert lib.ws_conv3x3(P, P, None, None, P, 64, 64, 16, 256, 1, tw.WS_CONV_TC, None, 0, None) == tw.TW_EWORKSPACE
     assert lib.ws_conv3x3(P, P, None, None, P, 64, 64, 16, 256, 1, tw.WS_CONV_TC, P, 100, None) == tw.TW_EWORKSPACE
     # ws_conv3x3_wgrad: the tensor-memory form needs cin, cout <= 128 and W % 16 == 0; no mma.sync

@@ -66,13 +66,18 @@ def test_conv3x3_tensor_core_matches_cuda_core_and_fp64(dev, cin, cout, H, W):
 @pytest.mark.parametrize("cin,cout,H,W,with_skip", [(16, 32, 4, 128, False), (32, 32, 8, 256, True),
                                                     (64, 64, 12, 128, True), (128, 128, 4, 384, True),
                                                     (64, 128, 10, 128, False), (128, 64, 4, 256, True),
-                                                    (32, 128, 6, 128, True), (128, 32, 8, 128, False)])
+                                                    (32, 128, 6, 128, True), (128, 32, 8, 128, False),
+                                                    (64, 128, 8, 64, True), (128, 128, 16, 32, True),
+                                                    (128, 64, 16, 16, False), (32, 32, 12, 64, True),
+                                                    (64, 32, 8, 32, True), (16, 128, 4, 64, False),
+                                                    (128, 128, 64, 64, True)])
 def test_conv3x3_tensor_memory_matches_cuda_core_and_fp64(dev, cin, cout, H, W, with_skip):
     """The tcgen05 implicit GEMM (accumulators in tensor memory, operands staged channel-last in shared
     memory) computes the same layer as the CUDA-core direct convolution: within BF16 output rounding of
     the FP64 convolution of the same BF16 inputs and weights, at most one BF16 ulp from the CUDA-core
     result, every edge pixel (zero padding) and every channel block included; its bounded waits never
-    gave up."""
+    gave up.  Widths below 128 take the narrow form (M blocks spanning 128 / W rows, x taps as shifted
+    copies, split K over the channel chunks with a fixed-order finalisation)."""
     g = torch.Generator(device="cpu").manual_seed(cin * 977 + cout * 13 + H * 7 + W)
     x = (torch.randn((cin, H, W), generator=g)).to(torch.bfloat16).to(dev)
     w = (torch.randn((cout, cin, 3, 3), generator=g) / (3.0 * cin ** 0.5)).to(dev)
