@@ -28,11 +28,10 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "nn_tc.cuh"
 
 namespace tw {
 namespace nn {
-
-typedef __nv_bfloat16 bf16;
 
 __device__ int g_conv_tc_error;   // 1 after a bounded wait timed out
 
@@ -173,6 +172,46 @@ __global__ void conv_tc_weights_kernel(const float *__restrict__ Wt, bf16 *__res
         const int ci = 16 * chunk + 8 * h + e;
         Wb[i] = __float2bfloat16(Wt[((size_t)co * cin + ci) * 9 + k]);
     }
+}
+
+__global__ void conv_tc_weights_all_kernel(const float *__restrict__ P, bf16 *__restrict__ wf, bf16 *__restrict__ wb,
+                                           TcPrepTable t) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < t.total;
+         g += (long long)gridDim.x * blockDim.x) {
+        long long i = g;
+        int l = 0;
+        for (; l < t.n; l++) {
+            const long long n2 = 2LL * t.cin[l] * t.cout[l] * 9;
+            if (i < n2) break;
+            i -= n2;
+        }
+        if (l >= t.n) continue;
+        const long long n = (long long)t.cin[l] * t.cout[l] * 9;
+        const bool bwd = i >= n;
+        if (bwd) i -= n;
+        const long long off = bwd ? t.boff[l] : t.foff[l];
+        if (off < 0) continue;
+        // the arranged layer: cin_a -> cout_a
+        const int cin_a = bwd ? t.cout[l] : t.cin[l], cout_a = bwd ? t.cin[l] : t.cout[l];
+        const int e = (int)(i % 8);
+        long long r = i / 8;
+        const int co = (int)(r % cout_a);
+        r /= cout_a;
+        const int h = (int)(r % 2);
+        r /= 2;
+        const int k = (int)(r % 9);
+        const int chunk = (int)(r / 9);
+        const int ci = 16 * chunk + 8 * h + e;
+        const float *W = P + t.poff[l];
+        const float v = bwd ? W[((size_t)ci * t.cin[l] + co) * 9 + (8 - k)] : W[((size_t)co * t.cin[l] + ci) * 9 + k];
+        (bwd ? wb : wf)[off + i] = __float2bfloat16(v);
+    }
+}
+
+int conv_tc_prepare_weights(const float *P, const TcPrepTable &t, bf16 *wf, bf16 *wb, cudaStream_t s) {
+    TW_LAUNCH(conv_tc_weights_all_kernel, (unsigned)((t.total + 255) / 256 > 2048 ? 2048 : (t.total + 255) / 256), 256,
+              0, s, P, wf, wb, t);
+    return TW_OK;
 }
 
 template <int N, int MT>
@@ -375,14 +414,16 @@ bool conv3x3_tc_ok(int cin, int cout, int H, int W) {
 size_t conv3x3_tc_scratch_bytes(int cin, int cout) { return (size_t)cin * cout * 9 * sizeof(bf16); }
 
 // Y = act(conv3x3(X, Wt) + b + S) on the tensor cores; scratch holds
-// conv3x3_tc_scratch_bytes(cin, cout) bytes (16-byte aligned).
+// conv3x3_tc_scratch_bytes(cin, cout) bytes (16-byte aligned), where the
+// weights are re-arranged, or (prearranged) already holds them in that layout.
 int conv3x3_tc(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
-               int W, int relu, void *scratch, cudaStream_t s) {
+               int W, int relu, void *scratch, cudaStream_t s, bool prearranged) {
     if (!conv3x3_tc_ok(cin, cout, H, W) || !scratch || ((uintptr_t)scratch & 15)) return TW_EINVAL;
     bf16 *Wb = (bf16 *)scratch;
     const size_t n = (size_t)cin * cout * 9;
-    TW_LAUNCH(conv_tc_weights_kernel, (unsigned)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256), 256, 0, s, Wt, Wb,
-              cin, cout);
+    if (!prearranged)
+        TW_LAUNCH(conv_tc_weights_kernel, (unsigned)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256), 256, 0, s, Wt,
+                  Wb, cin, cout);
     switch (cout) {
         case 32: return launch_tc<32>(X, Wb, b, S, Y, cin, H, W, relu, s);
         case 64: return launch_tc<64>(X, Wb, b, S, Y, cin, H, W, relu, s);
@@ -622,17 +663,19 @@ static int launch_tc_narrow(const bf16 *X, const bf16 *Wb, const float *b, const
 }
 
 // The narrow form: wscratch holds conv3x3_tc_scratch_bytes(cin, cout) bytes for the
-// re-arranged weights (16-byte aligned); with splits > 1 the kernel writes FP32
-// partial sums to part[split][cout][H][W] and the caller finalises them.
+// re-arranged weights (16-byte aligned; already arranged if prearranged); with
+// splits > 1 the kernel writes FP32 partial sums to part[split][cout][H][W] and
+// the caller finalises them.
 int conv3x3_tc_narrow(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
-                      int W, int relu, int splits, void *wscratch, float *part, cudaStream_t s) {
+                      int W, int relu, int splits, void *wscratch, float *part, cudaStream_t s, bool prearranged) {
     if (!conv3x3_tc_narrow_ok(cin, cout, H, W) || !wscratch || ((uintptr_t)wscratch & 15) || splits < 1 ||
         (splits > 1 && !part))
         return TW_EINVAL;
     bf16 *Wb = (bf16 *)wscratch;
     const size_t n = (size_t)cin * cout * 9;
-    TW_LAUNCH(conv_tc_weights_kernel, (unsigned)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256), 256, 0, s, Wt, Wb,
-              cin, cout);
+    if (!prearranged)
+        TW_LAUNCH(conv_tc_weights_kernel, (unsigned)((n + 255) / 256 > 1024 ? 1024 : (n + 255) / 256), 256, 0, s, Wt,
+                  Wb, cin, cout);
     switch (cout) {
         case 32: return launch_tc_narrow<32>(X, Wb, b, S, Y, part, cin, H, W, relu, splits, s);
         case 64: return launch_tc_narrow<64>(X, Wb, b, S, Y, part, cin, H, W, relu, splits, s);

@@ -18,9 +18,16 @@
 // Storage: activations and their gradients in BF16, weights in FP32 (rounded
 // to BF16 when loaded), every product accumulated in FP32.
 //
-// Kernels are direct convolutions on CUDA cores: each CTA computes a 16x16
-// pixel tile for 16 output channels, staging an 18x18 input tile per chunk of
-// 8 input channels and the matching weights in shared memory.
+// Kernels: every convolution with 16k input channels and 32, 64 or 128 output
+// channels, its data gradient included, runs on the 5th-generation tensor
+// cores with tensor-memory accumulators (nn_conv_tc.cu: the wide form for
+// W % 128 == 0, the narrow form for W = 16, 32, 64), and so does every weight
+// gradient; all layers' BF16 tensor-core weights are arranged once per step.
+// Here: the mma.sync implicit GEMM for other shapes, direct convolutions on
+// CUDA cores (16x16 pixel tiles for 16 output channels, 18x18 input tiles per
+// chunk of 8 input channels) for the 2-channel input layer and the 1-channel
+// head, the CUDA-core weight gradient where W % 16 != 0, pooling, upsampling,
+// loss and Adam.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -28,6 +35,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "nn_tc.cuh"
 
 namespace tw {
 namespace nn {
@@ -517,11 +525,28 @@ struct Act {   // activation buffers per level (bf16 [C][h][w])
     bf16 *sk[3];                       // gradients into the skip sources e[2][1], e[1][1], e[0][1]
     float *target;                     // [H][W] training target (log u / 30)
     float *wt;                         // transposed weights scratch
+    bf16 *wtf, *wtb;                   // every layer's tensor-core weights: forward, transposed
     float *kpart;                      // split-K partial sums (kSplitKCap floats)
     float *loss;
 };
 
 static size_t lvl_px(int H, int W, int l) { return (size_t)(H >> l) * (W >> l); }
+
+// Offset of layer li's tensor-core weights (BF16, 128-byte aligned slots) in Act::wtf / Act::wtb.
+static size_t tc_w_off(int li) {
+    size_t o = 0;
+    for (int k = 0; k < li; k++) o += ((size_t)kConvs[k].cin * kConvs[k].cout * 9 + 63) & ~(size_t)63;
+    return o;
+}
+// Channel counts the tensor-memory kernels take: the layer itself, and its transpose (the data gradient).
+static bool tc_fwd_ok(int li) {
+    const ConvSpec &c = kConvs[li];
+    return c.cin % 16 == 0 && (c.cout == 32 || c.cout == 64 || c.cout == 128);
+}
+static bool tc_bwd_ok(int li) {
+    const ConvSpec &c = kConvs[li];
+    return c.cout % 16 == 0 && (c.cin == 32 || c.cin == 64 || c.cin == 128);
+}
 
 static size_t carve_act(Carver &cv, int H, int W, Act *A) {
     Act a;
@@ -550,25 +575,13 @@ static size_t carve_act(Carver &cv, int H, int W, Act *A) {
     a.sk[2] = cv.take<bf16>(32 * lvl_px(H, W, 0));
     a.target = cv.take<float>(lvl_px(H, W, 0));
     a.wt = cv.take<float>(128 * 128 * 9);
+    a.wtf = cv.take<bf16>(tc_w_off(kNumConvs));
+    a.wtb = cv.take<bf16>(tc_w_off(kNumConvs));
     a.kpart = cv.take<float>(kSplitKCap);
     a.loss = cv.take<float>(64);
     if (A) *A = a;
     return cv.need;
 }
-
-bool conv3x3_tc_ok(int cin, int cout, int H, int W);
-size_t conv3x3_tc_scratch_bytes(int cin, int cout);
-int conv3x3_tc(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
-               int W, int relu, void *scratch, cudaStream_t s);
-int conv3x3_tc_error(int *flag);
-bool conv3x3_tc_narrow_ok(int cin, int cout, int H, int W);
-int conv3x3_tc_narrow_splits(int cin, int cout, int H, int W, size_t part_floats);
-int conv3x3_tc_narrow(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
-                      int W, int relu, int splits, void *wscratch, float *part, cudaStream_t s);
-bool conv3x3_wgrad_tc_ok(int cin, int cout, int H, int W);
-int conv3x3_wgrad_tc_plan(int cin, int cout, int H, int W, size_t cap_floats, int *chunk_px);
-int conv3x3_wgrad_tc(const bf16 *X, const bf16 *dY, float *dW, float *db, int cin, int cout, int H, int W,
-                     float *part, size_t part_floats, cudaStream_t s);
 
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256); }
 
@@ -597,12 +610,15 @@ static size_t narrow_weight_floats(int cin, int cout) {
 // The narrow tensor-memory form (W < 128) with its split-K finalisation: the
 // weights at the start of part, the partial sums after them.
 static int conv3x3_narrow(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout,
-                          int H, int W, int relu, cudaStream_t s, float *part, size_t part_floats) {
-    const size_t wf = narrow_weight_floats(cin, cout);
+                          int H, int W, int relu, cudaStream_t s, float *part, size_t part_floats,
+                          const bf16 *wpre) {
+    const size_t wf = wpre ? 0 : narrow_weight_floats(cin, cout);
     if (!part || part_floats < wf) return TW_EWORKSPACE;
     const int sp = conv3x3_tc_narrow_splits(cin, cout, H, W, part_floats - wf);
     float *pp = part + wf;
-    const int e = conv3x3_tc_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, sp, part, sp > 1 ? pp : nullptr, s);
+    void *wsc = wpre ? (void *)wpre : (void *)part;
+    const int e = conv3x3_tc_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, sp, wsc, sp > 1 ? pp : nullptr, s,
+                                    wpre != nullptr);
     if (e || sp == 1) return e;
     TW_LAUNCH(splitk_finalize_kernel, dim3(ceil_div(W, 256), H, cout), 256, 0, s, pp, sp, b, S, Y, cout, H, W, relu);
     return TW_OK;
@@ -611,26 +627,29 @@ static int conv3x3_narrow(const bf16 *X, const float *Wt, const float *b, const 
 // One 3x3 convolution: the tensor-core kernel where the channel counts allow
 // it (impl WS_CONV_AUTO), or the one asked for.  part (nullable): scratch for
 // split-K partial sums, part_floats long, which also holds the re-arranged
-// weights of the tensor-memory kernels (WS_CONV_TC).
+// weights of the tensor-memory kernels (WS_CONV_TC) unless wpre (nullable)
+// holds them already arranged.
 static int conv3x3(const bf16 *X, const float *Wt, const float *b, const bf16 *S, bf16 *Y, int cin, int cout, int H,
-                   int W, int relu, int impl, cudaStream_t s, float *part = nullptr, size_t part_floats = 0) {
+                   int W, int relu, int impl, cudaStream_t s, float *part = nullptr, size_t part_floats = 0,
+                   const bf16 *wpre = nullptr) {
     const bool mma_ok = cin % 16 == 0 && cout % 32 == 0;
     if (impl == WS_CONV_MMA && !mma_ok) return TW_EINVAL;
+    const bool room = part && part_floats * sizeof(float) >= conv3x3_tc_scratch_bytes(cin, cout);
+    void *wsc = wpre ? (void *)wpre : (void *)part;
     if (impl == WS_CONV_TC) {
         if (conv3x3_tc_narrow_ok(cin, cout, H, W))
-            return conv3x3_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, s, part, part_floats);
+            return conv3x3_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, s, part, part_floats, wpre);
         if (!conv3x3_tc_ok(cin, cout, H, W)) return TW_EINVAL;
-        if (!part || part_floats * sizeof(float) < conv3x3_tc_scratch_bytes(cin, cout)) return TW_EWORKSPACE;
-        return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, part, s);
+        if (!wpre && !room) return TW_EWORKSPACE;
+        return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, wsc, s, wpre != nullptr);
     }
     // the automatic choice: a tensor-memory kernel wherever its shape conditions hold and the
     // scratch for its re-arranged weights is there (inside the network), else mma.sync or CUDA cores
-    if (impl == WS_CONV_AUTO && part && conv3x3_tc_ok(cin, cout, H, W) &&
-        part_floats * sizeof(float) >= conv3x3_tc_scratch_bytes(cin, cout))
-        return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, part, s);
+    if (impl == WS_CONV_AUTO && part && conv3x3_tc_ok(cin, cout, H, W) && (wpre || room))
+        return conv3x3_tc(X, Wt, b, S, Y, cin, cout, H, W, relu, wsc, s, wpre != nullptr);
     if (impl == WS_CONV_AUTO && part && conv3x3_tc_narrow_ok(cin, cout, H, W) &&
-        part_floats >= narrow_weight_floats(cin, cout))
-        return conv3x3_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, s, part, part_floats);
+        (wpre || part_floats >= narrow_weight_floats(cin, cout)))
+        return conv3x3_narrow(X, Wt, b, S, Y, cin, cout, H, W, relu, s, part, part_floats, wpre);
     if (impl != WS_CONV_SIMT && mma_ok) {
         const int sp = part ? splitk_plan(cin, cout, H, W, part_floats) : 1;
         float *pp = sp > 1 ? part : nullptr;
@@ -708,26 +727,44 @@ static size_t conv3x3_wgrad_floats(int cin, int cout, int H, int W, int impl) {
     return (size_t)ceil_div(H, wgrad_simt_rows(cin, cout, H, (size_t)-1)) * per;
 }
 
+// Every layer's tensor-core weights (forward and, with bwd, transposed) in one launch;
+// the convolutions of the step then read them from wtf / wtb.
+static void prepare_tc_weights(const float *P, Act &A, bool bwd, cudaStream_t s) {
+    TcPrepTable t;
+    memset(&t, 0, sizeof(t));
+    t.n = kNumConvs;
+    for (int li = 0; li < kNumConvs; li++) {
+        t.poff[li] = (long long)param_offset(li);
+        t.cin[li] = kConvs[li].cin;
+        t.cout[li] = kConvs[li].cout;
+        t.foff[li] = tc_fwd_ok(li) ? (long long)tc_w_off(li) : -1;
+        t.boff[li] = bwd && tc_bwd_ok(li) ? (long long)tc_w_off(li) : -1;
+        t.total += 2LL * kConvs[li].cin * kConvs[li].cout * 9;
+    }
+    conv_tc_prepare_weights(P, t, A.wtf, A.wtb, s);
+}
+
 static void conv_fwd(const bf16 *X, const float *params, int li, const bf16 *S, bf16 *Y, int H, int W, int relu,
-                     float *kpart, cudaStream_t s, bool bias = true) {
+                     float *kpart, const bf16 *wtf, cudaStream_t s, bool bias = true) {
     const ConvSpec &c = kConvs[li];
     const float *Wt = params + param_offset(li);
     const float *b = bias ? Wt + (size_t)c.cout * c.cin * 9 : nullptr;
-    conv3x3(X, Wt, b, S, Y, c.cin, c.cout, H, W, relu, WS_CONV_AUTO, s, kpart, kSplitKCap);
+    conv3x3(X, Wt, b, S, Y, c.cin, c.cout, H, W, relu, WS_CONV_AUTO, s, kpart, kSplitKCap,
+            tc_fwd_ok(li) ? wtf + tc_w_off(li) : nullptr);
 }
 
 // The forward pass; every intermediate is kept for the backward pass.
 static void forward(const float *P, Act &A, int H, int W, cudaStream_t s) {
     const int ch[4] = {32, 64, 128, 128};
     // encoder
-    conv_fwd(A.in, P, 0, nullptr, A.e[0][0], H, W, 1, A.kpart, s);
-    conv_fwd(A.e[0][0], P, 1, nullptr, A.e[0][1], H, W, 1, A.kpart, s);
+    conv_fwd(A.in, P, 0, nullptr, A.e[0][0], H, W, 1, A.kpart, A.wtf, s);
+    conv_fwd(A.e[0][0], P, 1, nullptr, A.e[0][1], H, W, 1, A.kpart, A.wtf, s);
     for (int l = 1; l < 4; l++) {
         const int h = H >> l, w = W >> l;
         TW_LAUNCH(pool2_fwd_kernel, dim3(ceil_div(w, 256), h, ch[l - 1]), 256, 0, s, A.e[l - 1][1], A.p[l - 1],
                   ch[l - 1], H >> (l - 1), W >> (l - 1));
-        conv_fwd(A.p[l - 1], P, 2 * l, nullptr, A.e[l][0], h, w, 1, A.kpart, s);
-        conv_fwd(A.e[l][0], P, 2 * l + 1, nullptr, A.e[l][1], h, w, 1, A.kpart, s);
+        conv_fwd(A.p[l - 1], P, 2 * l, nullptr, A.e[l][0], h, w, 1, A.kpart, A.wtf, s);
+        conv_fwd(A.e[l][0], P, 2 * l + 1, nullptr, A.e[l][1], h, w, 1, A.kpart, A.wtf, s);
     }
     // decoder: level 2, 1, 0
     const bf16 *prev = A.e[3][1];
@@ -735,27 +772,33 @@ static void forward(const float *P, Act &A, int H, int W, cudaStream_t s) {
     for (int j = 0; j < 3; j++) {
         const int l = 2 - j, h = H >> l, w = W >> l;
         TW_LAUNCH(up2_fwd_kernel, dim3(ceil_div(w, 256), h, pc[j]), 256, 0, s, prev, A.u[j], pc[j], h, w);
-        conv_fwd(A.u[j], P, 8 + 2 * j, A.e[l][1], A.d[j][0], h, w, 1, A.kpart, s);
-        conv_fwd(A.d[j][0], P, 9 + 2 * j, nullptr, A.d[j][1], h, w, 1, A.kpart, s);
+        conv_fwd(A.u[j], P, 8 + 2 * j, A.e[l][1], A.d[j][0], h, w, 1, A.kpart, A.wtf, s);
+        conv_fwd(A.d[j][0], P, 9 + 2 * j, nullptr, A.d[j][1], h, w, 1, A.kpart, A.wtf, s);
         prev = A.d[j][1];
     }
-    conv_fwd(A.d[2][1], P, 14, nullptr, A.out, H, W, 0, A.kpart, s);
+    conv_fwd(A.d[2][1], P, 14, nullptr, A.out, H, W, 0, A.kpart, A.wtf, s);
 }
 
 // Gradient through one conv layer: dY (its output gradient, ReLU already applied)
 // -> dX (overwritten, or accumulated when accumulate != 0) and dW/db (accumulated).
 static void conv_bwd(const bf16 *X, const float *P, float *G, int li, const bf16 *dY, bf16 *dX, bf16 *tmp, int H,
-                     int W, float *wt, float *kpart, int accumulate, cudaStream_t s) {
+                     int W, float *wt, float *kpart, const bf16 *wtb, int accumulate, cudaStream_t s) {
     const ConvSpec &c = kConvs[li];
     const float *Wt = P + param_offset(li);
     float *dW = G + param_offset(li);
     float *db = dW + (size_t)c.cout * c.cin * 9;
     conv3x3_wgrad(X, dY, dW, db, c.cin, c.cout, H, W, WS_CONV_AUTO, kpart, kSplitKCap, s);
     if (!dX) return;
-    TW_LAUNCH(conv_transpose_weights_kernel, blocks_for((size_t)c.cin * c.cout * 9), 256, 0, s, Wt, wt, c.cin, c.cout);
-    // dX = conv3x3(dY, W^T) with cin/cout swapped: a forward conv of the transposed layer
+    // dX = conv3x3(dY, W^T) with cin/cout swapped: a forward conv of the transposed layer, whose
+    // tensor-core weights the step prepared; the FP32 transpose only for the other kernels
+    const bool tcx = wtb && tc_bwd_ok(li) &&
+                     (conv3x3_tc_ok(c.cout, c.cin, H, W) || conv3x3_tc_narrow_ok(c.cout, c.cin, H, W));
+    if (!tcx)
+        TW_LAUNCH(conv_transpose_weights_kernel, blocks_for((size_t)c.cin * c.cout * 9), 256, 0, s, Wt, wt, c.cin,
+                  c.cout);
     bf16 *dst = accumulate ? tmp : dX;
-    conv3x3(dY, wt, nullptr, nullptr, dst, c.cout, c.cin, H, W, 0, WS_CONV_AUTO, s, kpart, kSplitKCap);
+    conv3x3(dY, wt, nullptr, nullptr, dst, c.cout, c.cin, H, W, 0, WS_CONV_AUTO, s, kpart, kSplitKCap,
+            tcx ? wtb + tc_w_off(li) : nullptr);
     if (accumulate)
         TW_LAUNCH(add_inplace_kernel, blocks_for((size_t)c.cin * H * W), 256, 0, s, dX, tmp, (size_t)c.cin * H * W);
 }
@@ -767,19 +810,19 @@ static void backward(const float *P, float *G, Act &A, int H, int W, cudaStream_
     bf16 *dcur = scratch[0], *dnext = scratch[1], *tmp = scratch[2];
     bf16 *dskip[3] = {scratch[3], scratch[4], scratch[5]};   // gradients into e[2][1], e[1][1], e[0][1]
     // head (linear): dOut -> d(d[2][1])
-    conv_bwd(A.d[2][1], P, G, 14, d_out, dcur, tmp, H, W, A.wt, A.kpart, 0, s);
+    conv_bwd(A.d[2][1], P, G, 14, d_out, dcur, tmp, H, W, A.wt, A.kpart, A.wtb, 0, s);
     const int dc[3] = {128, 64, 32}, pc[3] = {128, 128, 64};
     for (int j = 2; j >= 0; j--) {
         const int l = 2 - j, h = H >> l, w = W >> l;
         // dcur: gradient of d[j][1] (post-ReLU output of conv 9 + 2j)
         TW_LAUNCH(relu_bwd_kernel, blocks_for(dc[j] * lvl_px(H, W, l)), 256, 0, s, A.d[j][1], dcur,
                   (size_t)dc[j] * lvl_px(H, W, l));
-        conv_bwd(A.d[j][0], P, G, 9 + 2 * j, dcur, dnext, tmp, h, w, A.wt, A.kpart, 0, s);   // -> grad of d[j][0]
+        conv_bwd(A.d[j][0], P, G, 9 + 2 * j, dcur, dnext, tmp, h, w, A.wt, A.kpart, A.wtb, 0, s);   // -> grad of d[j][0]
         TW_LAUNCH(relu_bwd_kernel, blocks_for(dc[j] * lvl_px(H, W, l)), 256, 0, s, A.d[j][0], dnext,
                   (size_t)dc[j] * lvl_px(H, W, l));
         // d[j][0] = relu(conv(u[j]) + e[l][1]): the skip receives the same gradient
         cudaMemcpyAsync(dskip[j], dnext, sizeof(bf16) * dc[j] * lvl_px(H, W, l), cudaMemcpyDeviceToDevice, s);
-        conv_bwd(A.u[j], P, G, 8 + 2 * j, dnext, dcur, tmp, h, w, A.wt, A.kpart, 0, s);      // -> grad of u[j]
+        conv_bwd(A.u[j], P, G, 8 + 2 * j, dnext, dcur, tmp, h, w, A.wt, A.kpart, A.wtb, 0, s);      // -> grad of u[j]
         // u[j] = up2(prev): gradient to prev (level l + 1)
         TW_LAUNCH(up2_bwd_kernel, dim3(ceil_div(w / 2, 256), h / 2, pc[j]), 256, 0, s, dcur, dnext, pc[j], h, w);
         bf16 *t = dcur; dcur = dnext; dnext = t;   // dcur: gradient of the previous decoder output
@@ -793,14 +836,14 @@ static void backward(const float *P, float *G, Act &A, int H, int W, cudaStream_
                       (size_t)ch[l] * lvl_px(H, W, l));
         TW_LAUNCH(relu_bwd_kernel, blocks_for(ch[l] * lvl_px(H, W, l)), 256, 0, s, A.e[l][1], dcur,
                   (size_t)ch[l] * lvl_px(H, W, l));
-        conv_bwd(A.e[l][0], P, G, 2 * l + 1, dcur, dnext, tmp, h, w, A.wt, A.kpart, 0, s);   // grad of e[l][0]
+        conv_bwd(A.e[l][0], P, G, 2 * l + 1, dcur, dnext, tmp, h, w, A.wt, A.kpart, A.wtb, 0, s);   // grad of e[l][0]
         TW_LAUNCH(relu_bwd_kernel, blocks_for(ch[l] * lvl_px(H, W, l)), 256, 0, s, A.e[l][0], dnext,
                   (size_t)ch[l] * lvl_px(H, W, l));
         const bf16 *xin = l == 0 ? A.in : A.p[l - 1];
         if (l == 0) {
-            conv_bwd(xin, P, G, 0, dnext, nullptr, tmp, h, w, A.wt, A.kpart, 0, s);
+            conv_bwd(xin, P, G, 0, dnext, nullptr, tmp, h, w, A.wt, A.kpart, A.wtb, 0, s);
         } else {
-            conv_bwd(xin, P, G, 2 * l, dnext, dcur, tmp, h, w, A.wt, A.kpart, 0, s);          // grad of p[l-1]
+            conv_bwd(xin, P, G, 2 * l, dnext, dcur, tmp, h, w, A.wt, A.kpart, A.wtb, 0, s);          // grad of p[l-1]
             // p[l-1] = pool2(e[l-1][1]): spread into a zeroed gradient of e[l-1][1]
             cudaMemsetAsync(dnext, 0, sizeof(bf16) * ch[l - 1] * lvl_px(H, W, l - 1), s);
             TW_LAUNCH(pool2_bwd_kernel, dim3(ceil_div(W >> (l - 1), 256), H >> (l - 1), ch[l - 1]), 256, 0, s, dcur,
@@ -881,6 +924,7 @@ extern "C" int ws_unet_warm_start(const float *params, const uint8_t *occ, int H
     }
     const size_t nc = (size_t)hc * wc;
     TW_LAUNCH(features_kernel, blocks_for(nc), 256, 0, s, oin, hc, wc, gxc, gyc, A.in);
+    prepare_tc_weights(params, A, false, s);
     forward(params, A, hc, wc, s);
     TW_LAUNCH(upsample_to_u_kernel, dim3(ceil_div(W, 256), H), 256, 0, s, A.out, hc, wc, stride, occ, W, gx, gy,
               u_out);
@@ -920,6 +964,7 @@ extern "C" int ws_unet_forward(const float *params, const uint8_t *occ, int H, i
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)H * W;
     TW_LAUNCH(features_kernel, blocks_for(n), 256, 0, s, occ, H, W, gx, gy, A.in);
+    prepare_tc_weights(params, A, false, s);
     forward(params, A, H, W, s);
     if (u_out) TW_LAUNCH(to_u_kernel, blocks_for(n), 256, 0, s, A.out, occ, gx, gy, W, n, u_out);
     if (pred_out) {
@@ -943,6 +988,7 @@ extern "C" int ws_unet_train_step(float *params, float *grads, float *adam_m, fl
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)H * W;
     TW_LAUNCH(features_kernel, blocks_for(n), 256, 0, s, occ, H, W, gx, gy, A.in);
+    prepare_tc_weights(params, A, true, s);
     forward(params, A, H, W, s);
     // free-cell count for the loss normalisation (the mask: occ == 0 and not the goal)
     TW_CUDA(cudaMemsetAsync(A.loss, 0, 2 * sizeof(float), s));
