@@ -1040,7 +1040,7 @@ def main():
     ap.add_argument("--no-dynamic", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learn-fields", type=int, default=1024)
-    ap.add_argument("--learn-steps", type=int, default=8000)
+    ap.add_argument("--learn-steps", type=int, default=16000)
     ap.add_argument("--dynamic-eval", action="store_true",
                     help="also run the success / collision-free evaluation over 1-16 moving obstacles")
     ap.add_argument("--batch", type=int, default=256)
