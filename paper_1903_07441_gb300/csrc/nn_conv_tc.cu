@@ -712,10 +712,10 @@ int conv3x3_tc_error(int *flag) {
 // build the two copies of X shifted by one pixel (taps kx = 0 and 2) from the
 // landed groups and their neighbours (zero across the image's left and right
 // edges), so that every tap's operand starts on a 16-byte boundary; the
-// unshifted tap reads the landed X directly.  M = 128 is the side with 128
-// channels (dY where cout is 128, else X where cin is 128, else dY with its rows
-// beyond cout unused), N the other side's channel count; the three taps'
-// accumulators lie side by side in tensor memory.  Each CTA writes its chunk's
+// unshifted tap reads the landed X directly.  M = 128 rows: X where cin is 128
+// and cout at most 64, else dY (its rows beyond cout unused); N the other side's
+// channel count rounded up to 32, 64 or 128 (columns beyond it unused); the
+// three taps' accumulators lie side by side in tensor memory.  Each CTA writes its chunk's
 // sums to part[z][k][m][n] (m the M row, n the N column), the bias sums (CTAs
 // with ky = 0) to part_b[z][co]; conv_wgrad_tc_sum_kernel adds the chunks in
 // order, so the result does not depend on the order the CTAs finish in.
