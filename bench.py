@@ -746,9 +746,9 @@ def run_dynamic(args, dev, tw):
                      "min_clearance_m": res.min_clearance, "path_length_m": res.path_length(),
                      "turning_angle_hist_deg": {f"{int(a)}-{int(b)}": int(h)
                                                 for a, b, h in zip(edges[:-1], edges[1:], hist)}}
-    out["note"] = ("most frames without a path end in TW_NO_PATH because the potential at the robot is "
-                   "1e-11..1e-13 through 200 obstacles (the FP64 oracle's own descent fails on this frame), "
-                   "below what any field solved to an absolute tolerance orders; obstacles move up to 1 m/s "
+    out["note"] = ("most frames without a path end in TW_NO_PATH: the potential at the robot is 1e-11..1e-13 "
+                   "through 200 obstacles and the FP64 oracle's own descent fails on these frames; relaxing longer "
+                   "(500-6000 fixed sweeps per frame) does not add frames with a path; obstacles move up to 1 m/s "
                    "without avoiding the robot (0.75 m/s)")
     if args.dynamic_eval:
         out["evaluation"] = dynamic_eval(dev, tw)
